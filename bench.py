@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput of the matrix-free TPFA conjugate-gradient solve on GB300.
+
+One step = one full solve of the paper-scale workload through the C ABI:
+transmissibilities + diagonal (tpfa_build_trans), right-hand side
+(tpfa_build_rhs), and cg_solve to the FP64-checked relative residual (inner
+FP32 CG sweeps, FP64 residual, refinement).  Metric: cell-updates/s =
+cells x CG iterations / time (the paper's Gcell/s definition, Table III).
+
+Workload (synthetic, seeded): 1024 x 1024 x 256 cells, ln K ~ N(0, 1.5^2)
+drawn per (i, j, floor(k/8)) (8-cell vertical layer correlation),
+accumulation diagonal d = 1e-3, injector/producer (q = +-1) at opposite
+corners, no Dirichlet cells, CG to relative residual 1e-6.
+
+--impl reference times the CPU FP64 oracle (CSR assembly + textbook CG) on
+a bounded sample of the same workload recipe.
+
+Multi-GPU: the solve does not shard here (replicas only): each rank solves
+its own copy; value = all ranks' cell-updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2408_03452_gb300 import synth  # noqa: E402
+
+METRIC = "TPFA-CG cell-updates/s"
+UNIT = "cell-updates/s"
+# algorithmic DRAM bytes per cell of one fused CG sweep: read r, p, q, x and
+# the 16-byte coefficient record, write r, p, q, x (FP32)
+SWEEP_BYTES_PER_CELL = 48
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=1024)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--maxit", type=int, default=200000)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile-vy", type=int, default=0)
+    ap.add_argument("--tile-zc", type=int, default=-1)
+    return ap.parse_args()
+
+
+def workload_desc(a):
+    return (f"paper-scale TPFA pressure solve {a.nx}x{a.ny}x{a.nz}, lnK~N(0,1.5^2) per "
+            f"(i,j,k//8), d=1e-3, well pair q=+-1 at opposite corners, no Dirichlet, "
+            f"CG to FP64-checked relative residual {a.tol:g}")
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------
+
+SAMPLE = (128, 128, 64)
+
+
+def oracle_step(O, iters):
+    """Oracle on a bounded sample of the same recipe: assemble the CSR of a
+    128x128x64 block, build the right-hand side, run `iters` CG iterations,
+    evaluate the FP64 residual.  Returns cell-updates done."""
+    nx, ny, nz = SAMPLE
+    K = synth.lognormal_field(nx, ny, nz, 1.5, 0, layer=8)
+    idx, val = synth.well_pair(nx, ny, nz)
+    q = synth.dense_sources(nx * ny * nz, idx, val)
+    g = O.Grid(nx, ny, nz)
+    A = O.assemble(g, K, None, 1e-3)
+    b = O.rhs(g, K, None, q, None)
+    x, st, it, _ = O.cg(A, b, tol=0.0, maxit=iters)
+    r = b - A.matvec(x)
+    float(np.linalg.norm(r))
+    return nx * ny * nz * it
+
+
+def oracle_sample_iters(O, target_s=12.0):
+    t = time.perf_counter()
+    oracle_step(O, 5)
+    per = (time.perf_counter() - t) / 5
+    return max(5, int(target_s / per))
+
+
+def cpu_baseline(target_s=12.0):
+    from oracle import oracle as O
+    O.build()
+    iters = oracle_sample_iters(O, target_s)
+    t = time.perf_counter()
+    units = oracle_step(O, iters)
+    dt = time.perf_counter() - t
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} block of the same recipe "
+                      f"(sigma 1.5, 8-layer correlation, d=1e-3, corner wells): CSR assembly, "
+                      f"RHS, {iters} CG iterations, FP64 residual; single-threaded C, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    iters = oracle_sample_iters(O, 10.0)
+    for _ in range(a.warmup):
+        oracle_step(O, iters)
+    times, units = [], 0
+    for _ in range(a.steps):
+        t = time.perf_counter()
+        units += oracle_step(O, iters)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    val = units / tot
+    sample = (f"each step: {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} block of the same recipe, CSR "
+              f"assembly, RHS, {iters} CG iterations, FP64 residual")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(a), "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(p))["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sweep_traffic(nx, ny, nz):
+    """DRAM bytes per cell of one CG sweep from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    src = os.path.join(ROOT, "paper_2408_03452_gb300", "csrc", "kernels_cg.cu")
+    prof = os.path.join(ROOT, "profiles", "cg_sweep_traffic.json")
+    try:
+        rec = json.load(open(prof))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return rec["dram_bytes_per_cell"] * nx * ny * nz
+    except Exception:
+        return None
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2408_03452_gb300 import tpfa
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    nx, ny, nz = a.nx, a.ny, a.nz
+    n = nx * ny * nz
+    w = synth.paper_scale(seed=a.seed, nx=nx, ny=ny, nz=nz)
+    K_host = torch.from_numpy(w["K"]).pin_memory()
+    idx_host = torch.from_numpy(w["src_idx"]).pin_memory()
+    val_host = torch.from_numpy(w["src_val"]).pin_memory()
+    d0 = w["d"]
+
+    K = K_host.to(dev)
+    sidx, sval = idx_host.to(dev), val_host.to(dev)
+    ctx = tpfa.Context(nx, ny, nz, device=dev)
+    if a.tile_vy:
+        ctx.set_option("tile_vy", a.tile_vy)
+    if a.tile_zc >= 0:
+        ctx.set_option("tile_zc", a.tile_zc)
+    coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step(Kd, si, sv):
+        ctx.build_trans(Kd, None, None, d0, coef=coef, coef64=coef64)
+        ctx.build_rhs(Kd, None, None, None, si, sv, b=b)
+        x.zero_()
+        _, info = ctx.cg_solve(coef, coef64, b, x=x, tol=a.tol, maxit=a.maxit)
+        if info["code"] not in (0,):
+            raise RuntimeError(f"cg_solve returned {info}")
+        return info
+
+    for _ in range(a.warmup):
+        step(K, sidx, sval)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    infos = [step(K, sidx, sval) for _ in range(a.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    iters = sum(i["iters"] for i in infos)
+    launches = sum(3 + i["kernel_launches"] for i in infos)
+    inner_ms = sum(i["inner_ms"] for i in infos)
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs, the solve, D2H of the solution
+    e2e = None
+    if not a.no_e2e:
+        x_host = torch.empty(n, dtype=torch.float64).pin_memory()
+        Ke = torch.empty_like(K)
+        sie, sve = torch.empty_like(sidx), torch.empty_like(sval)
+        barrier()
+        torch.cuda.synchronize()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        e2e_iters = 0
+        for _ in range(a.steps):
+            Ke.copy_(K_host, non_blocking=True)
+            sie.copy_(idx_host, non_blocking=True)
+            sve.copy_(val_host, non_blocking=True)
+            info = step(Ke, sie, sve)
+            e2e_iters += info["iters"]
+            x_host.copy_(x, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e = (e2e_iters, e2.elapsed_time(e3))
+
+    if world > 1:
+        t = torch.tensor([ms, iters, e2e[1] if e2e else 0.0, e2e[0] if e2e else 0.0],
+                         dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, iters_all = tmax[0].item(), t[1].item()
+        e2e_ms_max, e2e_iters_all = tmax[2].item(), t[3].item()
+    else:
+        ms_max, iters_all = ms, iters
+        e2e_ms_max, e2e_iters_all = (e2e[1], e2e[0]) if e2e else (0.0, 0.0)
+
+    if rank == 0:
+        value = n * iters_all / (ms_max / 1e3)
+        peak, peak_kind = measured_hbm_peak()
+        sweep_ms = inner_ms / max(iters, 1)
+        algo = SWEEP_BYTES_PER_CELL * n
+        achieved = algo / (sweep_ms / 1e3) / 1e9
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(a), "nx": nx, "ny": ny, "nz": nz,
+                       "tol": a.tol, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (no flush needed)",
+                       "iters_per_solve": iters / a.steps,
+                       "time_to_tol_s": ms / 1e3 / a.steps,
+                       "rel_res_fp64": infos[-1]["rel_res_fp64"],
+                       "refinements": infos[-1]["outer"]},
+            "roofline": {"kernel": "cg sweep (fused CG iteration)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "bytes_per_cell": SWEEP_BYTES_PER_CELL,
+                         "sweep_ms": sweep_ms, "traffic": sweep_traffic(nx, ny, nz)},
+            "gpu_launches": launches,
+        }
+        if e2e:
+            out["e2e"] = {"value": n * e2e_iters_all / (e2e_ms_max / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": int(K.numel() * 8 + sidx.numel() * 16),
+                          "d2h_bytes_per_step": int(n * 8)}
+        out["clocks"] = clk
+        if not a.no_cpu:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * tpfa.h -- C ABI of the GB300 (sm_103a) matrix-free TPFA pressure solver.
+ *
+ * Problem (arXiv 2408.03452, "Matrix-Free Finite Volume Kernels on a
+ * Dataflow Architecture", Section II.A): single-phase incompressible Darcy
+ * flow (Eq. 1a-1b) discretised with two-point flux approximation (Eq. 4) on a
+ * structured nx x ny x nz Cartesian grid, giving the linear system
+ *
+ *     (A p)_K = sum_{L in adj(K)} T_KL (p_K - p_L) + d_K p_K = b_K   (K not in T^D)
+ *     p_K = p^D_K                                                  (K in T^D)
+ *
+ * solved matrix-free (Eq. 6, Alg. 2) by conjugate gradient (Alg. 1).
+ *
+ * Layout of every per-cell array: flat index c = i + nx*(j + ny*k), X
+ * innermost and Z outermost (Section IV).  N = nx*ny*nz.
+ *
+ * Coefficient record ("coef"): 4 values per cell, cell-interleaved,
+ *     coef[4c+0] = Tx  transmissibility of the face between c and c+1 (x)
+ *     coef[4c+1] = Ty  ... between c and c+nx (y)
+ *     coef[4c+2] = Tz  ... between c and c+nx*ny (z)
+ *     coef[4c+3] = D   diagonal: sum of the six face transmissibilities + d_c
+ * A face on the outer boundary has T = 0 (no-flow).  A face touching a
+ * Dirichlet cell has T = 0 (its coupling is moved to the right-hand side),
+ * and a Dirichlet cell has D = 1, so the stored operator is the symmetric
+ * positive definite elimination of Eq. 6's constrained rows.
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "dev" are CUDA device pointers (or managed memory) on
+ *    the current device; the caller allocates and owns them.  Pointers marked
+ *    "host" are host memory.  A context owns only its internal workspace.
+ *  - "stream" is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue work on it and return without waiting, except cg_solve, which
+ *    waits for its stream (it drives the refinement loop and fills *info).
+ *  - Return value: TPFA_OK (0) on success, a negative TPFA_E* code on error,
+ *    TPFA_NOTCONV (+1) when cg_solve stops at maxit.  On error nothing was
+ *    enqueued unless the code is TPFA_ECUDA.
+ *  - A context is not thread-safe: calls on one context must not overlap
+ *    (same host thread or externally serialised, one stream at a time).
+ */
+#ifndef TPFA_H
+#define TPFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPFA_ABI_VERSION 1
+
+enum tpfa_status {
+  TPFA_OK = 0,
+  TPFA_NOTCONV = 1,        /* maxit reached; x holds the last iterate          */
+  TPFA_EINVAL = -1,        /* bad size, NULL or misaligned pointer, bad option  */
+  TPFA_ENOMEM = -2,        /* device allocation of the workspace failed         */
+  TPFA_ECUDA = -3,         /* a CUDA runtime call failed                        */
+  TPFA_EBREAKDOWN = -4,    /* CG breakdown: p'Ap <= 0 (operator not SPD)        */
+  TPFA_ENONFINITE = -5,    /* NaN or Inf met in a reduction                     */
+  TPFA_EINTERNAL = -6,     /* iteration guard tripped (should not happen)       */
+  TPFA_ESTAGNATION = -7    /* refinement stopped reducing the FP64 residual     */
+};
+
+/* Grid: nx, ny, nz >= 1 cells of size dx, dy, dz > 0; viscosity mu > 0;
+ * nx*ny + 2*nx < 2^31 (one z-plane is addressed with 32-bit offsets). */
+typedef struct {
+  int64_t nx, ny, nz;
+  double dx, dy, dz, mu;
+} tpfa_grid;
+
+/* Result of cg_solve (host struct filled by the call). */
+typedef struct {
+  int64_t iters;          /* CG iterations (operator applications) in total       */
+  int32_t outer;          /* FP64 refinement corrections applied                  */
+  int32_t status;         /* same as the return code                              */
+  double rel_res_inner;   /* last inner recursive residual, relative to its rhs   */
+  double rel_res_fp64;    /* ||b - A x||_2 / ||b||_2 at exit, in FP64 with coef64 */
+  double inner_ms;        /* GPU time inside the CG iteration loops (CUDA events) */
+  double total_ms;        /* GPU time of the whole call (CUDA events)             */
+  int64_t kernel_launches; /* kernels this call ran (sweeps counted on the device) */
+} tpfa_cg_info;
+
+typedef struct tpfa_ctx tpfa_ctx;
+
+/* Options for tpfa_set_option. */
+enum tpfa_option {
+  TPFA_OPT_INNER_RTOL = 1,   /* lower bound on the inner FP32 CG relative tolerance (default 1e-6) */
+  TPFA_OPT_MAX_OUTER = 2,    /* maximum FP64 refinement steps (default 20)                        */
+  TPFA_OPT_LOOP = 3,         /* 0 = CUDA-graph while node (default), 1 = host-polled graph chunks */
+  TPFA_OPT_TILE_VY = 4,      /* rows per warp in the stencil sweeps: 4 or 8 (default 4)           */
+  TPFA_OPT_TILE_ZC = 5,      /* planes per warp in the stencil sweeps, 0 = automatic              */
+  TPFA_OPT_CHUNK = 6         /* CG iterations per graph launch when TPFA_OPT_LOOP = 1 (default 32) */
+};
+
+/* Create a context for one grid on the current CUDA device.  Allocates the
+ * small reduction workspace (partials, scalars); the CG vectors are
+ * allocated by the first cg_solve.  *out receives the handle. */
+int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out);
+
+/* Free the context and everything it allocated (synchronises the device). */
+int tpfa_destroy(tpfa_ctx* ctx);
+
+/* Human-readable text for a status code (static storage). */
+const char* tpfa_strerror(int code);
+
+/* TPFA_ABI_VERSION of the loaded library. */
+int tpfa_abi_version(void);
+
+/* Set a solver option (see enum tpfa_option); TPFA_EINVAL if out of range. */
+int tpfa_set_option(tpfa_ctx* ctx, int option, double value);
+
+/*
+ * Transmissibilities and diagonal (Section II.A, Eq. 4 and Eq. 6).
+ *   T_KL = (A_f / mu) / (h/(2 k_K) + h/(2 k_L)),  A_f the face area, h the
+ *   cell size normal to the face; lambda_KL = 1/mu (arithmetic mean of the
+ *   two equal mobilities).  Computed in FP64 and rounded to nearest FP32.
+ *   D_K = T(-x)+T(+x)+T(-y)+T(+y)+T(-z)+T(+z) + d_K summed in that order
+ *   in FP64 over the faces that exist (faces to Dirichlet cells included),
+ *   then rounded; D = 1 on Dirichlet cells.
+ * K         dev, N doubles, permeability > 0.
+ * dirichlet dev, N bytes (nonzero = cell in T^D) or NULL (no Dirichlet cells).
+ * d         dev, N doubles, accumulation diagonal d_K >= 0, or NULL: every
+ *           cell uses d_uniform.
+ * coef      dev, 4N floats, 16-byte aligned: output coefficient records.
+ * coef64    dev, 4N doubles, 16-byte aligned: the same in FP64 (needed by
+ *           cg_solve's FP64 residual), or NULL.
+ */
+int tpfa_build_trans(tpfa_ctx* ctx, const double* K, const uint8_t* dirichlet, const double* d,
+                     double d_uniform, float* coef, double* coef64, void* stream);
+
+/*
+ * Right-hand side (Section II.A, Eq. 3 with sources).
+ *   b_K = p^D_K                                    for K in T^D,
+ *   b_K = q_K + sum_{L in adj(K), L in T^D} T_KL p^D_L   otherwise
+ *   (lifted couplings summed in FP64 in the face order -x,+x,-y,+y,-z,+z).
+ * q         dev, N doubles (dense source term) or NULL.
+ * pD        dev, N doubles, Dirichlet values (read on T^D only), or NULL = 0.
+ * src_idx   dev, n_src int64 cell indices, src_val dev, n_src doubles: point
+ *           sources added to q (duplicates add up); both NULL when n_src = 0.
+ *           Indices outside [0, N) are ignored.
+ * b         dev, N doubles, output.
+ */
+int tpfa_build_rhs(tpfa_ctx* ctx, const double* K, const uint8_t* dirichlet, const double* q,
+                   const double* pD, const int64_t* src_idx, const double* src_val, int64_t n_src,
+                   double* b, void* stream);
+
+/*
+ * Matrix-free operator application (Eq. 6, Alg. 2) in FP32:
+ *   Ap_K = D_K p_K - Tx_K p_{K+x} - Tx_{K-x} p_{K-x} - Ty_K p_{K+y}
+ *          - Ty_{K-y} p_{K-y} - Tz_K p_{K+z} - Tz_{K-z} p_{K-z}
+ * evaluated with fused multiply-adds in that order.
+ * coef dev 4N floats (16-byte aligned); p dev N floats; Ap dev N floats
+ * (must not alias p).  pAp: dev pointer to one double receiving p.Ap
+ * (FP32 products, compensated FP32 partial sums, FP64 across warps and
+ * blocks in a fixed order: bit-reproducible run to run), or NULL.
+ */
+int tpfa_apply(tpfa_ctx* ctx, const float* coef, const float* p, float* Ap, double* pAp,
+               void* stream);
+
+/*
+ * FP64 residual r = b - A x with the FP64 coefficient records (final check
+ * of the solve).  coef64 dev 4N doubles (16-byte aligned); b, x dev N
+ * doubles; r dev N doubles (may alias neither b nor x).  norms: dev pointer
+ * to two doubles receiving ||r||_2^2 and ||b||_2^2 (fixed-order FP64
+ * reductions), or NULL.
+ */
+int tpfa_residual64(tpfa_ctx* ctx, const double* coef64, const double* b, const double* x,
+                    double* r, double* norms, void* stream);
+
+/*
+ * Solve A x = b (Alg. 1) to ||b - A x||_2 <= tol ||b||_2 measured in FP64.
+ * Inner solver: unpreconditioned CG in FP32 on coef, one fused sweep per
+ * iteration (operator, both vector updates and the single reduction), run
+ * inside a CUDA graph whose while-loop condition is set on the device.
+ * Outer loop: FP64 residual with coef64, FP32 correction solve, FP64 update
+ * (iterative refinement) until tol is met.
+ * coef    dev 4N floats; coef64 dev 4N doubles (both from tpfa_build_trans).
+ * b       dev N doubles.
+ * x       dev N doubles: initial guess on entry, solution on exit.
+ * tol     > 0; maxit >= 1 bounds the total number of CG iterations.
+ * info    host, filled on return (may be NULL).
+ * Returns TPFA_OK, TPFA_NOTCONV, or an error.  Waits for the stream.
+ */
+int cg_solve(tpfa_ctx* ctx, const float* coef, const double* coef64, const double* b, double* x,
+             double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPFA_H */

@@ -1,0 +1,572 @@
+// C ABI of libtpfa: argument checking, workspace, CUDA-graph iteration loop
+// and the FP64 iterative-refinement driver of cg_solve.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "tpfa_internal.cuh"
+
+using namespace tpfa;
+
+struct tpfa_ctx {
+  Grid g;
+  tpfa_grid geo;
+  int device;
+  int num_sms;
+  // options
+  double inner_rtol;
+  int max_outer;
+  int loop_mode;
+  int vy;
+  int zc;
+  int chunk;
+  // reduction workspace
+  CgState* st;
+  CgState* host_st;  // pinned
+  double* partials;
+  size_t partials_cap;  // doubles
+  unsigned int* counter;
+  int elem_nblocks;
+  // CG vectors (allocated on first solve)
+  float* vec;
+  double* r64;
+  CgVecs v;
+  // iteration-loop graph
+  cudaGraphExec_t loop_exec;
+  const void* loop_key_coef;
+  int loop_key_vy, loop_key_zc, loop_key_mode, loop_key_chunk;
+  cudaStream_t cap_stream;
+  cudaEvent_t ev[4];
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return TPFA_ECUDA;      \
+  } while (0)
+
+typedef int (*AddrRangeFn)(unsigned long long*, size_t*, unsigned long long);
+
+AddrRangeFn addr_range_fn() {
+  static AddrRangeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<AddrRangeFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// A device (or managed) allocation on the current device that holds
+// [p, p + bytes) and starts on an `align`-byte boundary.
+bool dev_ok(const void* p, size_t bytes, size_t align, int device) {
+  if (p == nullptr) return false;
+  if (((uintptr_t)p) % align != 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice) {
+    if (at.device != device) return false;
+  } else if (at.type != cudaMemoryTypeManaged) {
+    return false;
+  }
+  AddrRangeFn fn = addr_range_fn();
+  if (fn != nullptr) {
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (unsigned long long)(uintptr_t)p) == 0) {
+      if ((unsigned long long)(uintptr_t)p + bytes > base + size) return false;
+    }
+  }
+  return true;
+}
+
+bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device) {
+  return p == nullptr || dev_ok(p, bytes, align, device);
+}
+
+int use_device(const tpfa_ctx* c) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return TPFA_ECUDA;
+  if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess) return TPFA_ECUDA;
+  return TPFA_OK;
+}
+
+Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->zc, c->num_sms); }
+
+int ensure_partials(tpfa_ctx* c, size_t need) {
+  if (need <= c->partials_cap) return TPFA_OK;
+  double* p = nullptr;
+  if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return TPFA_ENOMEM;
+  }
+  if (c->partials) {
+    cudaDeviceSynchronize();
+    cudaFree(c->partials);
+  }
+  c->partials = p;
+  c->partials_cap = need;
+  return TPFA_OK;
+}
+
+int ensure_vectors(tpfa_ctx* c) {
+  if (c->vec != nullptr) return TPFA_OK;
+  const size_t n = (size_t)c->g.n;
+  // 7 float vectors (r, p, q twice, e), each padded to a 256-byte multiple
+  const size_t pad = (n + 63) / 64 * 64;
+  if (cudaMalloc(&c->vec, 7 * pad * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    c->vec = nullptr;
+    return TPFA_ENOMEM;
+  }
+  if (cudaMalloc(&c->r64, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->vec);
+    c->vec = nullptr;
+    c->r64 = nullptr;
+    return TPFA_ENOMEM;
+  }
+  float* b = c->vec;
+  c->v.r[0] = b; c->v.r[1] = b + pad;
+  c->v.p[0] = b + 2 * pad; c->v.p[1] = b + 3 * pad;
+  c->v.q[0] = b + 4 * pad; c->v.q[1] = b + 5 * pad;
+  c->v.e = b + 6 * pad;
+  return TPFA_OK;
+}
+
+void drop_loop(tpfa_ctx* c) {
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  c->loop_exec = nullptr;
+  c->loop_key_coef = nullptr;
+}
+
+// Build (or reuse) the executable graph that runs CG sweeps until the device
+// state says stop.  Mode 0: one while-node whose body holds two sweeps (the
+// vector sets ping-pong); the last block of each sweep sets the loop
+// condition.  Mode 1: `chunk` sweeps back to back, the host polls between
+// launches.
+int ensure_loop(tpfa_ctx* c, const float* coef) {
+  if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_vy == c->vy &&
+      c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
+    return TPFA_OK;
+  drop_loop(c);
+  const Sweep sw = ctx_sweep(c);
+  int rc = ensure_partials(c, (size_t)sw.nblocks * 4);
+  if (rc) return rc;
+  if (sweep_blocks_per_sm(c->vy) < 1) return TPFA_ECUDA;
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = c->cap_stream;
+  const float4* cf = reinterpret_cast<const float4*>(coef);
+  if (c->loop_mode == 0) {
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(graph);
+      return TPFA_ECUDA;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, h, 1, cs);
+      cudaError_t e2 = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, h, 1, cs);
+      e = cudaStreamEndCapture(cs, &body);
+      if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(graph);
+      return TPFA_ECUDA;
+    }
+  } else {
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t el = cudaSuccess;
+    for (int i = 0; i < c->chunk; ++i) {
+      cudaError_t e = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, 0, 0, cs);
+      if (e != cudaSuccess) el = e;
+    }
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess || el != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      return TPFA_ECUDA;
+    }
+  }
+  cudaError_t e = cudaGraphInstantiate(&c->loop_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->loop_exec = nullptr;
+    return TPFA_ECUDA;
+  }
+  c->loop_key_coef = coef;
+  c->loop_key_vy = c->vy;
+  c->loop_key_zc = c->zc;
+  c->loop_key_mode = c->loop_mode;
+  c->loop_key_chunk = c->chunk;
+  return TPFA_OK;
+}
+
+int read_state(tpfa_ctx* c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->host_st, c->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return TPFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tpfa_abi_version(void) { return TPFA_ABI_VERSION; }
+
+const char* tpfa_strerror(int code) {
+  switch (code) {
+    case TPFA_OK: return "success";
+    case TPFA_NOTCONV: return "iteration limit reached before the tolerance";
+    case TPFA_EINVAL: return "invalid argument (size, NULL, misaligned or non-device pointer, option)";
+    case TPFA_ENOMEM: return "device memory allocation failed";
+    case TPFA_ECUDA: return "CUDA runtime error";
+    case TPFA_EBREAKDOWN: return "CG breakdown: p'Ap <= 0, operator not positive definite";
+    case TPFA_ENONFINITE: return "non-finite value in a reduction";
+    case TPFA_EINTERNAL: return "internal iteration guard tripped";
+    case TPFA_ESTAGNATION: return "iterative refinement stagnated";
+    default: return "unknown status";
+  }
+}
+
+int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
+  if (out == nullptr) return TPFA_EINVAL;
+  *out = nullptr;
+  if (grid == nullptr) return TPFA_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return TPFA_EINVAL;
+  if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || !(grid->mu > 0)) return TPFA_EINVAL;
+  if (!isfinite(grid->dx) || !isfinite(grid->dy) || !isfinite(grid->dz) || !isfinite(grid->mu))
+    return TPFA_EINVAL;
+  // cell count must fit comfortably in int64 and in a CUDA grid of warps
+  const double n = (double)grid->nx * (double)grid->ny * (double)grid->nz;
+  if (n > 4.0e12) return TPFA_EINVAL;
+  // the sweep kernels address a z-plane (plus two rows) with 32-bit offsets
+  if ((double)grid->nx * (double)grid->ny + 2.0 * (double)grid->nx > 2147483647.0) return TPFA_EINVAL;
+  tpfa_ctx* c = new (std::nothrow) tpfa_ctx();
+  if (!c) return TPFA_ENOMEM;
+  memset((void*)c, 0, sizeof(*c));
+  c->geo = *grid;
+  c->g.nx = grid->nx; c->g.ny = grid->ny; c->g.nz = grid->nz;
+  c->g.plane = grid->nx * grid->ny;
+  c->g.n = c->g.plane * grid->nz;
+  c->inner_rtol = 1e-6;
+  c->max_outer = 20;
+  c->loop_mode = 0;
+  c->vy = 4;
+  c->zc = 0;
+  c->chunk = 32;
+  int rc = TPFA_ECUDA;
+  if (cudaGetDevice(&c->device) != cudaSuccess) goto fail;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    goto fail;
+  c->elem_nblocks = elem_blocks(c->g, c->num_sms);
+  rc = TPFA_ENOMEM;
+  if (cudaMalloc(&c->st, sizeof(CgState)) != cudaSuccess) goto fail;
+  if (cudaMalloc(&c->counter, 64) != cudaSuccess) goto fail;
+  if (cudaMallocHost(&c->host_st, sizeof(CgState)) != cudaSuccess) goto fail;
+  rc = TPFA_ECUDA;
+  if (cudaMemset(c->st, 0, sizeof(CgState)) != cudaSuccess) goto fail;
+  if (cudaMemset(c->counter, 0, 64) != cudaSuccess) goto fail;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) goto fail;
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) goto fail;
+  {
+    const Sweep sw = ctx_sweep(c);
+    size_t need = (size_t)sw.nblocks * 4;
+    if (need < (size_t)c->elem_nblocks * 2) need = (size_t)c->elem_nblocks * 2;
+    rc = ensure_partials(c, need);
+    if (rc) goto fail;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { rc = TPFA_ECUDA; goto fail; }
+  *out = c;
+  return TPFA_OK;
+fail:
+  cudaGetLastError();
+  tpfa_destroy(c);
+  return rc;
+}
+
+int tpfa_destroy(tpfa_ctx* c) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != c->device) cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  drop_loop(c);
+  for (int i = 0; i < 4; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->vec) cudaFree(c->vec);
+  if (c->r64) cudaFree(c->r64);
+  if (c->partials) cudaFree(c->partials);
+  if (c->counter) cudaFree(c->counter);
+  if (c->st) cudaFree(c->st);
+  if (c->host_st) cudaFreeHost(c->host_st);
+  cudaGetLastError();
+  if (cur >= 0 && cur != c->device) cudaSetDevice(cur);
+  delete c;
+  return TPFA_OK;
+}
+
+int tpfa_set_option(tpfa_ctx* c, int option, double value) {
+  if (c == nullptr || !isfinite(value)) return TPFA_EINVAL;
+  switch (option) {
+    case TPFA_OPT_INNER_RTOL:
+      if (!(value > 0.0 && value < 1.0)) return TPFA_EINVAL;
+      c->inner_rtol = value;
+      return TPFA_OK;
+    case TPFA_OPT_MAX_OUTER:
+      if (value < 1 || value > 1000) return TPFA_EINVAL;
+      c->max_outer = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_LOOP:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      c->loop_mode = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_TILE_VY:
+      if (value != 4 && value != 8) return TPFA_EINVAL;
+      c->vy = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_TILE_ZC:
+      if (value < 0 || value > 1 << 20 || value != floor(value)) return TPFA_EINVAL;
+      c->zc = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_CHUNK:
+      if (value < 1 || value > 4096 || value != floor(value)) return TPFA_EINVAL;
+      c->chunk = (int)value;
+      return TPFA_OK;
+    default:
+      return TPFA_EINVAL;
+  }
+}
+
+int tpfa_build_trans(tpfa_ctx* c, const double* K, const uint8_t* dirichlet, const double* d,
+                     double d_uniform, float* coef, double* coef64, void* stream) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(K, n * 8, 8, c->device) || !opt_dev_ok(dirichlet, n, 1, c->device) ||
+      !opt_dev_ok(d, n * 8, 8, c->device) || !dev_ok(coef, n * 16, 16, c->device) ||
+      !opt_dev_ok(coef64, n * 32, 16, c->device))
+    return TPFA_EINVAL;
+  if (d == nullptr && !(d_uniform >= 0.0 && isfinite(d_uniform))) return TPFA_EINVAL;
+  CK(launch_build_trans(c->g, c->geo, K, dirichlet, d, d_uniform, reinterpret_cast<float4*>(coef),
+                        coef64, (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
+int tpfa_build_rhs(tpfa_ctx* c, const double* K, const uint8_t* dirichlet, const double* q,
+                   const double* pD, const int64_t* src_idx, const double* src_val, int64_t n_src,
+                   double* b, void* stream) {
+  if (c == nullptr || n_src < 0) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(K, n * 8, 8, c->device) || !opt_dev_ok(dirichlet, n, 1, c->device) ||
+      !opt_dev_ok(q, n * 8, 8, c->device) || !opt_dev_ok(pD, n * 8, 8, c->device) ||
+      !dev_ok(b, n * 8, 8, c->device))
+    return TPFA_EINVAL;
+  if (n_src > 0 && (!dev_ok(src_idx, (size_t)n_src * 8, 8, c->device) ||
+                    !dev_ok(src_val, (size_t)n_src * 8, 8, c->device)))
+    return TPFA_EINVAL;
+  CK(launch_build_rhs(c->g, c->geo, K, dirichlet, q, pD, src_idx, src_val, n_src, b,
+                      (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
+int tpfa_apply(tpfa_ctx* c, const float* coef, const float* p, float* Ap, double* pAp,
+               void* stream) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(coef, n * 16, 16, c->device) || !dev_ok(p, n * 4, 4, c->device) ||
+      !dev_ok(Ap, n * 4, 4, c->device) || !opt_dev_ok(pAp, 8, 8, c->device))
+    return TPFA_EINVAL;
+  if ((const void*)p == (const void*)Ap) return TPFA_EINVAL;
+  const Sweep sw = ctx_sweep(c);
+  if (pAp != nullptr) {
+    rc = ensure_partials(c, (size_t)sw.nblocks);
+    if (rc) return rc;
+  }
+  CK(launch_apply(c->g, sw, reinterpret_cast<const float4*>(coef), p, Ap, pAp, c->partials,
+                  c->counter, (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
+int tpfa_residual64(tpfa_ctx* c, const double* coef64, const double* b, const double* x,
+                    double* r, double* norms, void* stream) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(coef64, n * 32, 16, c->device) || !dev_ok(b, n * 8, 8, c->device) ||
+      !dev_ok(x, n * 8, 8, c->device) || !dev_ok(r, n * 8, 8, c->device) ||
+      !opt_dev_ok(norms, 16, 8, c->device))
+    return TPFA_EINVAL;
+  if ((const void*)r == (const void*)b || (const void*)r == (const void*)x) return TPFA_EINVAL;
+  CK(launch_residual64(c->g, coef64, b, x, r, norms, nullptr, c->partials, c->counter,
+                       c->elem_nblocks, (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
+int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double* b, double* x,
+             double tol, int64_t maxit, tpfa_cg_info* info, void* stream) {
+  tpfa_cg_info inf;
+  memset(&inf, 0, sizeof(inf));
+  inf.rel_res_fp64 = NAN;
+  inf.rel_res_inner = NAN;
+  int rc = TPFA_OK;
+  if (info) *info = inf;
+  if (c == nullptr || !(tol > 0.0) || !isfinite(tol) || maxit < 1) return TPFA_EINVAL;
+  rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(coef, n * 16, 16, c->device) || !dev_ok(coef64, n * 32, 16, c->device) ||
+      !dev_ok(b, n * 8, 8, c->device) || !dev_ok(x, n * 8, 8, c->device))
+    return TPFA_EINVAL;
+  if ((const void*)b == (const void*)x) return TPFA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = ensure_vectors(c);
+  if (rc) return rc;
+  rc = ensure_loop(c, coef);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(c->counter, 0, 64, s));
+  CK(cudaEventRecord(c->ev[0], s));
+
+  CgState* hs = c->host_st;
+  double inner_ms = 0.0;
+  int64_t total_iters = 0;
+  int64_t launches = 0;
+  int outer = 0;
+  // r64 = b - A x
+  CK(launch_residual64(c->g, coef64, b, x, c->r64, nullptr, c->st, c->partials, c->counter,
+                       c->elem_nblocks, s));
+  launches += 1;
+  rc = read_state(c, s);
+  if (rc) return rc;
+  const double bb = hs->bb64;
+  double rr = hs->rr64;
+  double rel = bb > 0 ? sqrt(rr / bb) : 0.0;
+  double rel_inner = NAN;
+  int status = TPFA_OK;
+  if (!isfinite(rr) || !isfinite(bb)) {
+    status = TPFA_ENONFINITE;
+  } else if (bb == 0.0) {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    rel = 0.0;
+    launches += 1;
+  } else {
+    double best = rel;
+    int stalls = 0;
+    while (rel > tol) {
+      if (total_iters >= maxit) { status = TPFA_NOTCONV; break; }
+      if (outer >= c->max_outer) { status = TPFA_NOTCONV; break; }
+      double rtol = 0.5 * tol / rel;
+      if (rtol < c->inner_rtol) rtol = c->inner_rtol;
+      if (rtol > 0.5) rtol = 0.5;
+      CK(launch_prepare(c->g, c->r64, c->v, c->st, rtol, (long long)(maxit - total_iters), s));
+      launches += 1;
+      int inner_status = kRunning;
+      // host-side bound on relaunches (the device guard normally ends the
+      // loop first): chunks of sweeps in mode 1, finalize restarts in mode 0
+      const long long max_relaunch = (maxit - total_iters) / (c->loop_mode == 1 ? c->chunk : 1) + 64;
+      long long relaunch = 0;
+      for (;;) {
+        if (++relaunch > max_relaunch) { inner_status = kGuard; break; }
+        CK(cudaEventRecord(c->ev[2], s));
+        CK(cudaGraphLaunch(c->loop_exec, s));
+        CK(cudaEventRecord(c->ev[3], s));
+        if (c->loop_mode == 1) {
+          rc = read_state(c, s);
+          if (rc) return rc;
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+          inner_ms += ms;
+          if (hs->done == kRunning) continue;
+        }
+        CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks, s));
+        launches += 1;
+        rc = read_state(c, s);
+        if (rc) return rc;
+        if (c->loop_mode == 0) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+          inner_ms += ms;
+        }
+        if (hs->done == kRunning) continue;  // finalize armed a restart
+        inner_status = hs->done;
+        break;
+      }
+      total_iters += hs->iter;
+      launches += hs->launches;
+      rel_inner = hs->rho0 > 0 ? sqrt(hs->rho / hs->rho0) : 0.0;
+      if (inner_status == kGuard) { status = TPFA_EINTERNAL; break; }
+      if (inner_status == kNonFinite) { status = TPFA_ENONFINITE; break; }
+      if (inner_status == kBreakdown && hs->iter == 0) { status = TPFA_EBREAKDOWN; break; }
+      // x += e / scale;  r64 = b - A x
+      CK(launch_correct(c->g, c->v.e, x, c->st, s));
+      CK(launch_residual64(c->g, coef64, b, x, c->r64, nullptr, c->st, c->partials, c->counter,
+                           c->elem_nblocks, s));
+      launches += 2;
+      ++outer;
+      rc = read_state(c, s);
+      if (rc) return rc;
+      rr = hs->rr64;
+      rel = sqrt(rr / bb);
+      if (!isfinite(rel)) { status = TPFA_ENONFINITE; break; }
+      if (inner_status == kBreakdown) { status = rel <= tol ? TPFA_OK : TPFA_EBREAKDOWN; break; }
+      if (rel <= tol) break;
+      if (rel > 0.5 * best) {
+        if (++stalls >= 3) { status = TPFA_ESTAGNATION; break; }
+      } else {
+        stalls = 0;
+      }
+      if (rel < best) best = rel;
+    }
+  }
+  CK(cudaEventRecord(c->ev[1], s));
+  CK(cudaEventSynchronize(c->ev[1]));
+  float tms = 0.f;
+  CK(cudaEventElapsedTime(&tms, c->ev[0], c->ev[1]));
+  inf.iters = total_iters;
+  inf.outer = outer;
+  inf.status = status;
+  inf.rel_res_inner = rel_inner;
+  inf.rel_res_fp64 = rel;
+  inf.inner_ms = inner_ms;
+  inf.total_ms = tms;
+  inf.kernel_launches = launches;
+  if (info) *info = inf;
+  return status;
+}
+
+}  // extern "C"

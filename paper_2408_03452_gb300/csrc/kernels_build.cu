@@ -1,0 +1,154 @@
+// Coefficient and right-hand-side construction (once per solve).
+//
+// Transmissibility (arXiv 2408.03452, Section II.A, Eq. 4): the flux across
+// the face between cells K and L is T_KL (p_L - p_K) with T_KL = Y_KL *
+// lambda_KL.  The geometric factor Y is the two-point (half-transmissibility)
+// form A_f / (h/(2 k_K) + h/(2 k_L)), which is the harmonic mean of the two
+// permeabilities for unit cells; lambda_KL = 1/mu, the arithmetic mean of the
+// two (equal) mobilities.  Faces on the outer boundary carry no flow.
+// Dirichlet cells (Eq. 3) keep the identity row; their couplings to interior
+// cells move to the right-hand side.
+#include "tpfa_internal.cuh"
+
+namespace tpfa {
+
+namespace {
+
+struct Geo {
+  double ax, ay, az;  // face area / mu for x, y, z faces
+  double hx, hy, hz;  // cell size along each axis
+};
+
+__device__ __forceinline__ double face_trans(double kK, double kL, double a, double h) {
+  const double half = 0.5 * h;
+  return a / (half / kK + half / kL);
+}
+
+__device__ __forceinline__ bool is_dir(const uint8_t* m, int64_t c) { return m != nullptr && m[c] != 0; }
+
+__global__ void __launch_bounds__(kElemThreads)
+build_trans_kernel(Grid g, Geo geo, const double* __restrict__ K, const uint8_t* __restrict__ mask,
+                   const double* __restrict__ d, double d0, float4* __restrict__ coef,
+                   double2* __restrict__ coef64) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    const int64_t i = c % g.nx, j = (c / g.nx) % g.ny, k = c / g.plane;
+    double t[3] = {0.0, 0.0, 0.0};
+    double diag;
+    if (is_dir(mask, c)) {
+      diag = 1.0;
+    } else {
+      const double kc = K[c];
+      diag = 0.0;
+      // faces in the order -x, +x, -y, +y, -z, +z
+      if (i > 0) diag += face_trans(K[c - 1], kc, geo.ax, geo.hx);
+      if (i + 1 < g.nx) {
+        const double T = face_trans(kc, K[c + 1], geo.ax, geo.hx);
+        diag += T;
+        if (!is_dir(mask, c + 1)) t[0] = T;
+      }
+      if (j > 0) diag += face_trans(K[c - g.nx], kc, geo.ay, geo.hy);
+      if (j + 1 < g.ny) {
+        const double T = face_trans(kc, K[c + g.nx], geo.ay, geo.hy);
+        diag += T;
+        if (!is_dir(mask, c + g.nx)) t[1] = T;
+      }
+      if (k > 0) diag += face_trans(K[c - g.plane], kc, geo.az, geo.hz);
+      if (k + 1 < g.nz) {
+        const double T = face_trans(kc, K[c + g.plane], geo.az, geo.hz);
+        diag += T;
+        if (!is_dir(mask, c + g.plane)) t[2] = T;
+      }
+      diag = diag + (d != nullptr ? d[c] : d0);
+    }
+    coef[c] = make_float4(__double2float_rn(t[0]), __double2float_rn(t[1]),
+                          __double2float_rn(t[2]), __double2float_rn(diag));
+    if (coef64 != nullptr) {
+      coef64[2 * c] = make_double2(t[0], t[1]);
+      coef64[2 * c + 1] = make_double2(t[2], diag);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kElemThreads)
+build_rhs_kernel(Grid g, Geo geo, const double* __restrict__ K, const uint8_t* __restrict__ mask,
+                 const double* __restrict__ q, const double* __restrict__ pD,
+                 double* __restrict__ b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    if (is_dir(mask, c)) {
+      b[c] = pD != nullptr ? pD[c] : 0.0;
+      continue;
+    }
+    double s = q != nullptr ? q[c] : 0.0;
+    if (mask != nullptr) {
+      const int64_t i = c % g.nx, j = (c / g.nx) % g.ny, k = c / g.plane;
+      const double kc = K[c];
+      // lifted couplings to Dirichlet neighbours, faces -x, +x, -y, +y, -z, +z
+      const int64_t nb[6] = {c - 1, c + 1, c - g.nx, c + g.nx, c - g.plane, c + g.plane};
+      const bool ex[6] = {i > 0, i + 1 < g.nx, j > 0, j + 1 < g.ny, k > 0, k + 1 < g.nz};
+      const double ar[3] = {geo.ax, geo.ay, geo.az}, hh[3] = {geo.hx, geo.hy, geo.hz};
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        if (!ex[f] || !is_dir(mask, nb[f])) continue;
+        const double T = (f & 1) ? face_trans(kc, K[nb[f]], ar[f >> 1], hh[f >> 1])
+                                 : face_trans(K[nb[f]], kc, ar[f >> 1], hh[f >> 1]);
+        s += T * (pD != nullptr ? pD[nb[f]] : 0.0);
+      }
+    }
+    b[c] = s;
+  }
+}
+
+// Point sources, added one after another by a single thread so that
+// duplicates accumulate in a fixed order.  Sources on Dirichlet cells and
+// indices outside the grid are ignored.
+__global__ void add_sources_kernel(Grid g, const uint8_t* __restrict__ mask,
+                                   const int64_t* __restrict__ idx, const double* __restrict__ val,
+                                   int64_t n, double* __restrict__ b) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t c = idx[t];
+    if (c < 0 || c >= g.n || is_dir(mask, c)) continue;
+    b[c] += val[t];
+  }
+}
+
+Geo make_geo(const tpfa_grid& geo) {
+  Geo o;
+  o.ax = (geo.dy * geo.dz) / geo.mu;
+  o.ay = (geo.dx * geo.dz) / geo.mu;
+  o.az = (geo.dx * geo.dy) / geo.mu;
+  o.hx = geo.dx; o.hy = geo.dy; o.hz = geo.dz;
+  return o;
+}
+
+int grid_for(const Grid& g) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return elem_blocks(g, sms);
+}
+
+}  // namespace
+
+cudaError_t launch_build_trans(const Grid& g, const tpfa_grid& geo, const double* K,
+                               const uint8_t* mask, const double* d, double d0, float4* coef,
+                               double* coef64, cudaStream_t s) {
+  build_trans_kernel<<<grid_for(g), kElemThreads, 0, s>>>(g, make_geo(geo), K, mask, d, d0, coef,
+                                                          reinterpret_cast<double2*>(coef64));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_rhs(const Grid& g, const tpfa_grid& geo, const double* K,
+                             const uint8_t* mask, const double* q, const double* pD,
+                             const int64_t* src_idx, const double* src_val, int64_t n_src,
+                             double* b, cudaStream_t s) {
+  build_rhs_kernel<<<grid_for(g), kElemThreads, 0, s>>>(g, make_geo(geo), K, mask, q, pD, b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_src <= 0) return e;
+  add_sources_kernel<<<1, 32, 0, s>>>(g, mask, src_idx, src_val, n_src, b);
+  return cudaGetLastError();
+}
+
+}  // namespace tpfa

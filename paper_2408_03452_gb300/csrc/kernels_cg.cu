@@ -1,0 +1,586 @@
+// Stencil sweeps, fused CG iteration, FP64 residual and refinement kernels.
+//
+// The operator is the matrix-free TPFA product of Eq. 6 / Alg. 2 (arXiv
+// 2408.03452, Section II.A) in its symmetric positive form
+//   (A p)_K = D_K p_K - sum_faces T_f p_nbr,
+// read from one 16-byte coefficient record per cell (Tx, Ty, Tz, D).
+//
+// Sweep layout (both the plain operator and the fused CG iteration): each
+// warp owns a column block of 32 x-lanes (lanes 1..30 produce output, lanes
+// 0 and 31 carry the x-halo), VY consecutive y-rows, and marches through zc
+// consecutive z-planes, keeping the z-neighbours in registers.  x-neighbours
+// come from warp shuffles, y-neighbours from the warp's own rows plus one
+// halo row on each side.  Every global access is a fully used 32-byte
+// sector; each input array is read once per sweep from DRAM, halos are
+// L1/L2 hits.  No shared memory staging and no block-level barrier inside
+// the march: warps are independent.
+//
+// Reductions are deterministic: per-thread compensated FP32 sums over a
+// fixed cell set, FP64 warp shuffles in a fixed tree, FP64 block sums in a
+// fixed order, and a last-block finish that adds the block partials in a
+// fixed order (no floating-point atomics).
+#include <math.h>
+
+#include "tpfa_internal.cuh"
+
+namespace tpfa {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Kahan-compensated FP32 accumulator: value = s - c.
+struct Acc {
+  float s, c;
+};
+
+__device__ __forceinline__ void kadd(Acc& a, float v) {
+  const float y = __fsub_rn(v, a.c);
+  const float t = __fadd_rn(a.s, y);
+  a.c = __fsub_rn(__fsub_rn(t, a.s), y);
+  a.s = t;
+}
+
+__device__ __forceinline__ double kval(const Acc& a) { return (double)a.s - (double)a.c; }
+
+// Sum NV doubles over the block (fixed order) and store the block partial.
+template <int NV>
+__device__ __forceinline__ void block_partial(double (&v)[NV], double* partials) {
+  __shared__ double sm[32][NV];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_down_sync(kFull, v[i], o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[w][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int nw = blockDim.x >> 5;
+    double s = 0.0;
+    for (int ww = 0; ww < nw; ++ww) s += sm[ww][threadIdx.x];
+    partials[(size_t)blockIdx.x * NV + threadIdx.x] = s;
+  }
+}
+
+// Returns true in the last block to finish; that block then holds the
+// fixed-order total of all block partials in tot (every thread).
+template <int NV>
+__device__ __forceinline__ bool last_block_total(const double* partials, unsigned int* counter,
+                                                 double (&tot)[NV]) {
+  __shared__ bool s_last;
+  __shared__ double sm[32][NV];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(partials + (size_t)b * NV + i);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += __shfl_down_sync(kFull, acc[i], o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[w][i] = acc[i];
+  }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0;
+    for (int ww = 0; ww < nw; ++ww) s += sm[ww][i];
+    tot[i] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+  return true;
+}
+
+// 7-point product for one cell, fused multiply-adds in a fixed order.
+__device__ __forceinline__ float stencil7(float4 c, float txm, float tym, float tzm, float pc,
+                                          float pxp, float pxm, float pyp, float pym, float pzp,
+                                          float pzm) {
+  float q = c.w * pc;
+  q = fmaf(-c.x, pxp, q);
+  q = fmaf(-txm, pxm, q);
+  q = fmaf(-c.y, pyp, q);
+  q = fmaf(-tym, pym, q);
+  q = fmaf(-c.z, pzp, q);
+  q = fmaf(-tzm, pzm, q);
+  return q;
+}
+
+struct SweepArgs {
+  Grid g;
+  int64_t nwx, nwy, nwarps;
+  int zc;
+  const float4* coef;
+  // plain operator
+  const float* p;
+  float* Ap;
+  double* pAp;
+  // fused CG iteration
+  CgVecs v;
+  CgState* st;
+  double* partials;
+  unsigned int* counter;
+  unsigned long long cond;
+  int use_cond;
+};
+
+// CG finish for iteration k (last block, thread 0).  rho = r_k'r_k,
+// pq = p_k'q_k, rq = r_k'q_k, qq = q_k'q_k with q_k = A p_k.
+//   alpha_k = rho / pq                                  (Alg. 1, line 5)
+//   ||r_{k+1}||^2 = rho - 2 alpha rq + alpha^2 qq        (exact identity)
+//   beta_k = ||r_{k+1}||^2 / rho                         (Alg. 1, line 9)
+// so one reduction per iteration suffices.  The next sweep recomputes the
+// true r_{k+1}'r_{k+1} from the stored vector.
+__device__ void cg_finish(CgState* st, const double (&t)[4], unsigned long long cond,
+                          int use_cond) {
+  const double rho = t[0], pq = t[1], rq = t[2], qq = t[3];
+  const long long k = st->iter;
+  if (k == 0) st->rho0 = rho;
+  st->rho = rho;
+  const double thresh = st->rtol2 * st->rho0;
+  int done = kRunning;
+  if (!isfinite(rho) || !isfinite(pq) || !isfinite(rq) || !isfinite(qq)) {
+    done = kNonFinite;
+    st->alpha_fin = 0.0;
+  } else if (rho <= thresh) {
+    done = kConvTrue;
+    st->alpha_fin = 0.0;
+  } else if (!(pq > 0.0)) {
+    done = kBreakdown;
+    st->alpha_fin = 0.0;
+  } else {
+    const double alpha = rho / pq;
+    double rn = rho - 2.0 * alpha * rq + alpha * alpha * qq;
+    if (rn < 0.0) rn = 0.0;
+    st->rho_est = rn;
+    st->iter = k + 1;
+    if (rn <= thresh) {
+      done = kConvEst;
+      st->alpha_fin = alpha;
+    } else if (k + 1 >= st->maxit) {
+      done = kMaxit;
+      st->alpha_fin = alpha;
+    } else {
+      st->alpha = alpha;
+      st->beta = rn / rho;
+    }
+  }
+  if (st->launches > st->guard_limit) done = kGuard;
+  st->parity ^= 1;
+  st->done = done;
+  if (use_cond) cudaGraphSetConditional(cond, done == kRunning ? 1u : 0u);
+}
+
+template <int VY, bool CG>
+__global__ void __launch_bounds__(kSweepWarps * 32)
+sweep_kernel(const SweepArgs a) {
+  const Grid& g = a.g;
+  float alpha = 0.f, beta = 0.f;
+  const float *rin = nullptr, *qin = nullptr, *pin = a.p;
+  float *rout = nullptr, *qout = nullptr, *pout = nullptr;
+  if (CG) {
+    CgState* st = a.st;
+    if (*(volatile int*)&st->done != kRunning) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->launches += 1;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+      }
+      return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const long long n = st->launches + 1;
+      st->launches = n;
+      if (n > st->guard_limit && a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+    }
+    const int par = st->parity;
+    alpha = (float)st->alpha;
+    beta = (float)st->beta;
+    rin = a.v.r[par]; qin = a.v.q[par]; pin = a.v.p[par];
+    rout = a.v.r[par ^ 1]; qout = a.v.q[par ^ 1]; pout = a.v.p[par ^ 1];
+  }
+
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kSweepWarps + (threadIdx.x >> 5);
+  Acc acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+
+  if (gw < a.nwarps) {  // warp-uniform
+    const int64_t wx = gw % a.nwx;
+    const int64_t t = gw / a.nwx;
+    const int64_t wy = t % a.nwy;
+    const int64_t wz = t / a.nwy;
+    const int64_t gx = wx * kTileX - 1 + lane;
+    const bool inx = gx >= 0 && gx < g.nx;
+    const bool outl = inx && lane >= 1 && lane <= kTileX;
+    const int64_t y0 = wy * VY;
+    const int64_t z0 = wz * (int64_t)a.zc;
+    const int64_t z1 = min(z0 + (int64_t)a.zc, g.nz);
+    // row validity bits for rows -1 .. VY (bit jj+1)
+    unsigned rowok = 0u;
+#pragma unroll
+    for (int jj = -1; jj <= VY; ++jj)
+      if (inx && y0 + jj >= 0 && y0 + jj < g.ny) rowok |= 1u << (jj + 1);
+    // in-plane offset of (gx, y0) (fits 32 bits: nx*ny < 2^31 is checked
+    // at context creation); row jj at + jj*nx, plane z at + z*nx*ny
+    const int nxi = (int)g.nx;
+    const int o0 = (int)(gx + g.nx * y0);
+    auto plane_off = [&](int64_t z) {
+      const int64_t zc = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
+      return g.plane * zc;
+    };
+
+    // Form r_k and p_k on plane z, rows -1 .. VY.  For this warp's own
+    // output cells on planes [z0, z1) also write r_k, p_k and the x update
+    // x_k = x_{k-1} + alpha p_{k-1}, and accumulate r_k'r_k.
+    auto form_plane = [&](int64_t z, float (&P)[VY + 2], float (&R)[VY], float& s0) {
+      const bool zok = z >= 0 && z < g.nz;
+      const bool own = outl && z >= z0 && z < z1;
+      const int64_t zo = plane_off(z);
+      const float* rz = rin + zo;
+      const float* qz = qin + zo;
+      const float* pz = pin + zo;
+#pragma unroll
+      for (int jj = -1; jj <= VY; ++jj) {
+        const bool ok = zok && ((rowok >> (jj + 1)) & 1u);
+        const int o = o0 + jj * nxi;
+        float p_ = 0.f, r_ = 0.f;
+        if (CG) {
+          if (ok) {
+            const float r0 = __ldg(rz + o), q0 = __ldg(qz + o), p0 = __ldg(pz + o);
+            r_ = fmaf(-alpha, q0, r0);   // Alg. 1 line 7 (previous iteration)
+            p_ = fmaf(beta, p0, r_);     // Alg. 1 line 10
+            if (jj >= 0 && jj < VY && own) {
+              float* ez = a.v.e + zo;
+              ez[o] = fmaf(alpha, p0, ez[o]);  // Alg. 1 line 6
+              (rout + zo)[o] = r_;
+              (pout + zo)[o] = p_;
+              s0 = fmaf(r_, r_, s0);
+            }
+          }
+        } else {
+          if (ok) p_ = __ldg(pz + o);
+        }
+        P[jj + 1] = p_;
+        if (jj >= 0 && jj < VY) R[jj] = r_;
+      }
+    };
+
+    float Pm[VY], P0[VY + 2], R0[VY], Tzm[VY];
+    float s0 = 0.f;
+    {  // plane z0 - 1 (rows 0..VY-1 are the z-neighbours below) and its Tz
+      float Pt[VY + 2], Rt[VY];
+      form_plane(z0 - 1, Pt, Rt, s0);
+      const float4* cz = a.coef + plane_off(z0 - 1);
+#pragma unroll
+      for (int jj = 0; jj < VY; ++jj) {
+        Pm[jj] = Pt[jj + 1];
+        const bool ok = z0 >= 1 && ((rowok >> (jj + 1)) & 1u);
+        Tzm[jj] = ok ? __ldg(&cz[o0 + jj * nxi].z) : 0.f;
+      }
+    }
+    form_plane(z0, P0, R0, s0);
+
+#pragma unroll 1
+    for (int64_t z = z0; z < z1; ++z) {
+      float Pp[VY + 2], Rp[VY];
+      form_plane(z + 1, Pp, Rp, s0);
+      const int64_t zo = g.plane * z;
+      const float4* cz = a.coef + zo;
+      const float tym0 = (rowok & 1u) ? __ldg(&cz[o0 - nxi].y) : 0.f;
+      float s1 = 0.f, s2 = 0.f, s3 = 0.f, tyl = tym0;
+#pragma unroll
+      for (int jj = 0; jj < VY; ++jj) {
+        const bool ok = (rowok >> (jj + 1)) & 1u;
+        const int o = o0 + jj * nxi;
+        const float4 cf = ok ? __ldg(cz + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float pc = P0[jj + 1];
+        const float pxm = __shfl_up_sync(kFull, pc, 1);
+        const float pxp = __shfl_down_sync(kFull, pc, 1);
+        const float txm = __shfl_up_sync(kFull, cf.x, 1);
+        const float q = stencil7(cf, txm, tyl, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
+                                 Pp[jj + 1], Pm[jj]);
+        if (outl && ok) {
+          if (CG) {
+            (qout + zo)[o] = q;
+            s1 = fmaf(pc, q, s1);
+            s2 = fmaf(R0[jj], q, s2);
+            s3 = fmaf(q, q, s3);
+          } else {
+            (a.Ap + zo)[o] = q;
+            s1 = fmaf(pc, q, s1);
+          }
+        }
+        tyl = cf.y;
+        Tzm[jj] = cf.z;
+        Pm[jj] = pc;
+      }
+      kadd(acc[1], s1);
+      if (CG) {
+        kadd(acc[0], s0);
+        kadd(acc[2], s2);
+        kadd(acc[3], s3);
+        s0 = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < VY; ++jj) R0[jj] = Rp[jj];
+      }
+#pragma unroll
+      for (int jj = 0; jj < VY + 2; ++jj) P0[jj] = Pp[jj];
+    }
+    if (CG) kadd(acc[0], s0);
+  }
+
+  if (CG) {
+    double v[4] = {kval(acc[0]), kval(acc[1]), kval(acc[2]), kval(acc[3])};
+    block_partial<4>(v, a.partials);
+    double tot[4];
+    if (last_block_total<4>(a.partials, a.counter, tot) && threadIdx.x == 0)
+      cg_finish(a.st, tot, a.cond, a.use_cond);
+  } else if (a.pAp != nullptr) {
+    double v[1] = {kval(acc[1])};
+    block_partial<1>(v, a.partials);
+    double tot[1];
+    if (last_block_total<1>(a.partials, a.counter, tot) && threadIdx.x == 0) *a.pAp = tot[0];
+  }
+}
+
+// FP64 residual r = b - A x (one thread per cell, grid-stride, fixed grid).
+__global__ void __launch_bounds__(kElemThreads)
+residual64_kernel(Grid g, const double2* __restrict__ coef64, const double* __restrict__ b,
+                  const double* __restrict__ x, double* __restrict__ r, double* norms,
+                  CgState* st, double* partials, unsigned int* counter) {
+  double rr = 0.0, bb = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    const int64_t i = c % g.nx, j = (c / g.nx) % g.ny, k = c / g.plane;
+    const double2 c01 = __ldg(coef64 + 2 * c), c23 = __ldg(coef64 + 2 * c + 1);
+    const double xc = __ldg(x + c);
+    double s = c23.y * xc;
+    if (i + 1 < g.nx) s = fma(-c01.x, __ldg(x + c + 1), s);
+    if (i > 0) s = fma(-__ldg(&coef64[2 * (c - 1)].x), __ldg(x + c - 1), s);
+    if (j + 1 < g.ny) s = fma(-c01.y, __ldg(x + c + g.nx), s);
+    if (j > 0) s = fma(-__ldg(&coef64[2 * (c - g.nx)].y), __ldg(x + c - g.nx), s);
+    if (k + 1 < g.nz) s = fma(-c23.x, __ldg(x + c + g.plane), s);
+    if (k > 0) s = fma(-__ldg(&coef64[2 * (c - g.plane) + 1].x), __ldg(x + c - g.plane), s);
+    const double bc = __ldg(b + c);
+    const double rc = bc - s;
+    r[c] = rc;
+    rr = fma(rc, rc, rr);
+    bb = fma(bc, bc, bb);
+  }
+  double v[2] = {rr, bb};
+  block_partial<2>(v, partials);
+  double tot[2];
+  if (last_block_total<2>(partials, counter, tot) && threadIdx.x == 0) {
+    if (norms != nullptr) { norms[0] = tot[0]; norms[1] = tot[1]; }
+    if (st != nullptr) { st->rr64 = tot[0]; st->bb64 = tot[1]; }
+  }
+}
+
+// Start of an inner solve: r32 = scale * r64 with scale = 1/||r64||, zero
+// correction and directions, reset the scalars.
+__global__ void __launch_bounds__(kElemThreads)
+prepare_kernel(Grid g, const double* __restrict__ r64, CgVecs v, CgState* st, double rtol2,
+               long long maxit) {
+  const double rr = st->rr64;
+  const double scale = rr > 0.0 ? 1.0 / sqrt(rr) : 1.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    v.r[0][c] = (float)(scale * r64[c]);
+    v.p[0][c] = 0.f;
+    v.q[0][c] = 0.f;
+    v.e[c] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->alpha = 0.0; st->beta = 0.0; st->rho = 0.0; st->rho0 = 0.0; st->rho_est = 0.0;
+    st->alpha_fin = 0.0;
+    st->rtol2 = rtol2;
+    st->scale = scale;
+    st->iter = 0; st->maxit = maxit; st->launches = 0;
+    st->guard_limit = 2 * maxit + 64;
+    st->parity = 0; st->done = kRunning;
+  }
+}
+
+// End of an inner solve: apply the last step alpha_fin (x += alpha p,
+// r -= alpha q) and recompute r'r from the stored residual.  If the
+// estimate that stopped the loop was too optimistic, arm a restart of the
+// loop with the exact CG continuation (alpha = 0, beta = r+'r+ / r'r).
+__global__ void __launch_bounds__(kElemThreads)
+finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* counter) {
+  const int par = st->parity;
+  const float af = (float)st->alpha_fin;
+  float* r = v.r[par];
+  const float* p = v.p[par];
+  const float* q = v.q[par];
+  Acc acc = {0.f, 0.f};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    v.e[c] = fmaf(af, p[c], v.e[c]);
+    const float rn = fmaf(-af, q[c], r[c]);
+    r[c] = rn;
+    kadd(acc, rn * rn);
+  }
+  double vv[1] = {kval(acc)};
+  block_partial<1>(vv, partials);
+  double tot[1];
+  if (last_block_total<1>(partials, counter, tot) && threadIdx.x == 0) {
+    const double rho1 = tot[0];
+    const int done = st->done;
+    if (done == kConvEst || done == kMaxit) {
+      const double rho_prev = st->rho;
+      st->rho = rho1;
+      st->alpha_fin = 0.0;
+      if (done == kConvEst && rho1 > st->rtol2 * st->rho0 && st->iter < st->maxit &&
+          isfinite(rho1) && rho_prev > 0.0) {
+        st->alpha = 0.0;
+        st->beta = rho1 / rho_prev;
+        st->done = kRunning;
+      }
+    }
+  }
+}
+
+// x64 += e / scale.
+__global__ void __launch_bounds__(kElemThreads)
+correct_kernel(Grid g, const float* __restrict__ e, double* __restrict__ x, const CgState* st) {
+  const double inv = 1.0 / st->scale;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride)
+    x[c] = fma((double)e[c], inv, x[c]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+Sweep plan_sweep(const Grid& g, int vy, int zc_opt, int num_sms) {
+  Sweep s;
+  s.vy = vy;
+  s.nwx = (g.nx + kTileX - 1) / kTileX;
+  s.nwy = (g.ny + vy - 1) / vy;
+  int zc = zc_opt;
+  if (zc <= 0) {
+    // enough warps for ~8 waves of 16 resident warps per SM, but keep
+    // runs of at least 16 planes where the grid allows it (the two halo
+    // planes of each run are re-read).
+    const int64_t target = (int64_t)num_sms * 16 * 8;
+    const int64_t cols = s.nwx * s.nwy;
+    zc = (int)g.nz;
+    while (zc > 16 && cols * ((g.nz + zc - 1) / zc) < target) zc = (zc + 1) / 2;
+    if (cols * ((g.nz + zc - 1) / zc) < target) {
+      while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc = (zc + 1) / 2;
+    }
+  }
+  if (zc > g.nz) zc = (int)g.nz;
+  s.zc = zc;
+  s.nwz = (g.nz + zc - 1) / zc;
+  s.nwarps = s.nwx * s.nwy * s.nwz;
+  s.nblocks = (s.nwarps + kSweepWarps - 1) / kSweepWarps;
+  return s;
+}
+
+int elem_blocks(const Grid& g, int num_sms) {
+  const int64_t need = (g.n + kElemThreads - 1) / kElemThreads;
+  const int64_t cap = (int64_t)num_sms * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+static SweepArgs sweep_args(const Grid& g, const Sweep& sw, const float4* coef) {
+  SweepArgs a{};
+  a.g = g;
+  a.nwx = sw.nwx;
+  a.nwy = sw.nwy;
+  a.nwarps = sw.nwarps;
+  a.zc = sw.zc;
+  a.coef = coef;
+  return a;
+}
+
+cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, const float* p,
+                         float* Ap, double* pAp, double* partials, unsigned int* counter,
+                         cudaStream_t s) {
+  SweepArgs a = sweep_args(g, sw, coef);
+  a.p = p;
+  a.Ap = Ap;
+  a.pAp = pAp;
+  a.partials = partials;
+  a.counter = counter;
+  const dim3 grid((unsigned)sw.nblocks), block(kSweepWarps * 32);
+  if (sw.vy == 4) sweep_kernel<4, false><<<grid, block, 0, s>>>(a);
+  else sweep_kernel<8, false><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
+                            CgState* st, double* partials, unsigned int* counter,
+                            unsigned long long cond, int use_cond, cudaStream_t s) {
+  SweepArgs a = sweep_args(g, sw, coef);
+  a.v = v;
+  a.st = st;
+  a.partials = partials;
+  a.counter = counter;
+  a.cond = cond;
+  a.use_cond = use_cond;
+  const dim3 grid((unsigned)sw.nblocks), block(kSweepWarps * 32);
+  if (sw.vy == 4) sweep_kernel<4, true><<<grid, block, 0, s>>>(a);
+  else sweep_kernel<8, true><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(int vy) {
+  int nb = 0;
+  cudaError_t e = vy == 4
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<4, true>, kSweepWarps * 32, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<8, true>, kSweepWarps * 32, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_residual64(const Grid& g, const double* coef64, const double* b,
+                              const double* x, double* r, double* norms, CgState* st,
+                              double* partials, unsigned int* counter, int nblocks,
+                              cudaStream_t s) {
+  residual64_kernel<<<nblocks, kElemThreads, 0, s>>>(g, reinterpret_cast<const double2*>(coef64),
+                                                      b, x, r, norms, st, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* st, double rtol,
+                           long long maxit, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  prepare_kernel<<<elem_blocks(g, sms), kElemThreads, 0, s>>>(g, r64, v, st, rtol * rtol, maxit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
+                            unsigned int* counter, int nblocks, cudaStream_t s) {
+  finalize_kernel<<<nblocks, kElemThreads, 0, s>>>(g, v, st, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
+                           cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  correct_kernel<<<elem_blocks(g, sms), kElemThreads, 0, s>>>(g, e, x, st);
+  return cudaGetLastError();
+}
+
+}  // namespace tpfa

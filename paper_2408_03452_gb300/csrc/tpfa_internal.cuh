@@ -1,0 +1,104 @@
+// Internal declarations shared by the CUDA translation units of libtpfa.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tpfa.h"
+
+namespace tpfa {
+
+constexpr int kWarp = 32;
+constexpr int kTileX = 30;        // output columns per warp (lanes 1..30; lanes 0, 31 are halo)
+constexpr int kSweepWarps = 4;    // warps per block in the stencil sweeps
+constexpr int kElemThreads = 256; // threads per block in element-wise / per-cell kernels
+
+// Device-resident scalars of one solve.  Written only by the last block of a
+// reduction kernel (or by the prepare kernel), read by every block of the
+// following kernels.
+struct CgState {
+  double alpha;        // alpha_{k-1}: x/r update applied at the start of the next sweep
+  double beta;         // beta_{k-1}: direction update applied at the start of the next sweep
+  double rho;          // r_k' r_k of the newest residual (true value of the stored vector)
+  double rho0;         // r_0' r_0 of the current inner solve
+  double rtol2;        // inner relative tolerance squared
+  double rho_est;      // ||r_k - alpha_k q_k||^2 from the fused dot products
+  double alpha_fin;    // step applied by the finalize kernel
+  double scale;        // r32 = scale * r64 for the current inner solve
+  double rr64, bb64;   // ||b - A x||^2 and ||b||^2 from the last FP64 residual
+  double pap;          // p'Ap of the last tpfa_apply (when requested)
+  long long iter;      // CG iterations completed in the current inner solve
+  long long maxit;     // iteration limit of the current inner solve
+  long long launches;  // sweep launches since prepare (guard against a runaway loop)
+  long long guard_limit;
+  int parity;          // which vector set (0/1) holds r_k, p_k, q_k
+  int done;            // kRunning or one of the Done* codes
+  int pad0, pad1;
+};
+
+enum Done : int {
+  kRunning = 0,
+  kConvEst = 1,      // estimated ||r_{k+1}|| met the tolerance: finalize applies alpha_k
+  kConvTrue = 2,     // ||r_k|| already met the tolerance: nothing left to apply
+  kMaxit = 3,        // iteration limit: finalize applies alpha_k
+  kBreakdown = -4,   // p'Ap <= 0
+  kNonFinite = -5,
+  kGuard = -6,       // runaway-loop guard tripped
+};
+
+struct Grid {
+  int64_t nx, ny, nz;
+  int64_t plane;  // nx * ny
+  int64_t n;      // nx * ny * nz
+};
+
+// Warp tiling of the z-marching stencil sweeps.
+struct Sweep {
+  int vy;           // rows per warp (4 or 8)
+  int zc;           // planes per warp
+  int64_t nwx, nwy, nwz;
+  int64_t nwarps;
+  int64_t nblocks;  // blocks of kSweepWarps warps
+};
+
+Sweep plan_sweep(const Grid& g, int vy, int zc_opt, int num_sms);
+
+// Vector set of the inner CG (two sets, ping-ponged between sweeps).
+struct CgVecs {
+  float* r[2];
+  float* p[2];
+  float* q[2];
+  float* e;  // correction being accumulated (x of the inner solve)
+};
+
+// ---- launchers (kernels_*.cu) ---------------------------------------------
+
+cudaError_t launch_build_trans(const Grid& g, const tpfa_grid& geo, const double* K,
+                               const uint8_t* mask, const double* d, double d0, float4* coef,
+                               double* coef64, cudaStream_t s);
+cudaError_t launch_build_rhs(const Grid& g, const tpfa_grid& geo, const double* K,
+                             const uint8_t* mask, const double* q, const double* pD,
+                             const int64_t* src_idx, const double* src_val, int64_t n_src,
+                             double* b, cudaStream_t s);
+
+cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, const float* p,
+                         float* Ap, double* pAp, double* partials, unsigned int* counter,
+                         cudaStream_t s);
+cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
+                            CgState* st, double* partials, unsigned int* counter,
+                            unsigned long long cond, int use_cond, cudaStream_t s);
+cudaError_t launch_residual64(const Grid& g, const double* coef64, const double* b,
+                              const double* x, double* r, double* norms, CgState* st,
+                              double* partials, unsigned int* counter, int nblocks,
+                              cudaStream_t s);
+cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* st,
+                           double rtol, long long maxit, cudaStream_t s);
+cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
+                            unsigned int* counter, int nblocks, cudaStream_t s);
+cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
+                           cudaStream_t s);
+
+int sweep_blocks_per_sm(int vy);
+int elem_blocks(const Grid& g, int num_sms);
+
+}  // namespace tpfa

@@ -1,0 +1,226 @@
+"""Thin Python binding of ``libtpfa.so`` (the C ABI declared in include/tpfa.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  Tensors must be CUDA tensors on the context's device, C
+contiguous, of the dtype stated per argument; work is enqueued on the
+current torch stream.  There is no CPU fallback: if the library is missing
+or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpfa.so")
+
+OK, NOTCONV = 0, 1
+EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, -3, -4, -5, -6, -7
+
+OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6}
+
+
+class TpfaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (status {code})")
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("mu", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("outer", C.c_int32), ("status", C.c_int32),
+                ("rel_res_inner", C.c_double), ("rel_res_fp64", C.c_double),
+                ("inner_ms", C.c_double), ("total_ms", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = C.c_void_p
+SIGNATURES = {
+    "tpfa_create": (C.c_int, [C.POINTER(_Grid), C.POINTER(C.c_void_p)]),
+    "tpfa_destroy": (C.c_int, [_P]),
+    "tpfa_strerror": (C.c_char_p, [C.c_int]),
+    "tpfa_abi_version": (C.c_int, []),
+    "tpfa_set_option": (C.c_int, [_P, C.c_int, C.c_double]),
+    "tpfa_build_trans": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P, _P]),
+    "tpfa_build_rhs": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
+    "tpfa_apply": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "tpfa_residual64": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
+}
+
+
+def lib():
+    """Load libtpfa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2408_03452_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().tpfa_strerror(int(code)).decode()
+
+
+def abi_version() -> int:
+    return lib().tpfa_abi_version()
+
+
+def _check(code: int, where: str, allow=(OK,)):
+    if code not in allow:
+        raise TpfaError(code, where)
+    return code
+
+
+def _ptr(t: Optional[torch.Tensor], dtype, n: Optional[int], dev: torch.device, name: str):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device != dev:
+        raise ValueError(f"{name} must be on {dev}, got {t.device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(dev):
+    return C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+class Context:
+    """One grid on one CUDA device (wraps tpfa_create / tpfa_destroy)."""
+
+    def __init__(self, nx, ny, nz, dx=1.0, dy=1.0, dz=1.0, mu=1.0, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n = self.nx * self.ny * self.nz
+        self._h = C.c_void_p()
+        g = _Grid(self.nx, self.ny, self.nz, float(dx), float(dy), float(dz), float(mu))
+        with torch.cuda.device(self.device):
+            _check(lib().tpfa_create(C.byref(g), C.byref(self._h)), "tpfa_create")
+
+    def close(self):
+        if self._h:
+            with torch.cuda.device(self.device):
+                lib().tpfa_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, name: str, value: float):
+        _check(lib().tpfa_set_option(self._h, OPTIONS[name], float(value)), f"set_option({name})")
+
+    # -- coefficient and right-hand side construction -----------------------
+    def build_trans(self, K, dirichlet=None, d=None, d_uniform=0.0, coef=None, coef64=True):
+        """Returns (coef float32[N,4], coef64 float64[N,4] or None)."""
+        dev, n = self.device, self.n
+        if coef is None:
+            coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        if coef64 is True:
+            coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        elif coef64 is False:
+            coef64 = None
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_build_trans(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(d, torch.float64, n, dev, "d"), float(d_uniform),
+                _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"), _stream(dev)), "tpfa_build_trans")
+        return coef, coef64
+
+    def build_rhs(self, K, dirichlet=None, q=None, pD=None, src_idx=None, src_val=None, b=None):
+        dev, n = self.device, self.n
+        if b is None:
+            b = torch.empty(n, dtype=torch.float64, device=dev)
+        ns = 0 if src_idx is None else int(src_idx.numel())
+        if (src_val is None) != (src_idx is None) or (src_val is not None and src_val.numel() != ns):
+            raise ValueError("src_idx and src_val must be given together, with equal lengths")
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_build_rhs(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(q, torch.float64, n, dev, "q"), _ptr(pD, torch.float64, n, dev, "pD"),
+                _ptr(src_idx, torch.int64, ns, dev, "src_idx") if ns else None,
+                _ptr(src_val, torch.float64, ns, dev, "src_val") if ns else None, ns,
+                _ptr(b, torch.float64, n, dev, "b"), _stream(dev)), "tpfa_build_rhs")
+        return b
+
+    # -- operator --------------------------------------------------------------
+    def apply(self, coef, p, Ap=None, pAp=None):
+        """Ap = A p in FP32.  pAp: optional float64 tensor of one element that
+        receives p.Ap."""
+        dev, n = self.device, self.n
+        if Ap is None:
+            Ap = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_apply(
+                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(p, torch.float32, n, dev, "p"), _ptr(Ap, torch.float32, n, dev, "Ap"),
+                _ptr(pAp, torch.float64, 1, dev, "pAp"), _stream(dev)), "tpfa_apply")
+        return Ap
+
+    def residual64(self, coef64, b, x, r=None, norms=None):
+        """r = b - A x in FP64.  norms: optional float64[2] receiving
+        (||r||^2, ||b||^2)."""
+        dev, n = self.device, self.n
+        if r is None:
+            r = torch.empty(n, dtype=torch.float64, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_residual64(
+                self._h, _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
+                _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
+                _ptr(r, torch.float64, n, dev, "r"), _ptr(norms, torch.float64, 2, dev, "norms"),
+                _stream(dev)), "tpfa_residual64")
+        return r
+
+    def cg_solve(self, coef, coef64, b, x=None, tol=1e-8, maxit=100000, check=True):
+        """Solve A x = b to FP64 relative residual tol.  Returns (x, info dict)."""
+        dev, n = self.device, self.n
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+        info = _Info()
+        with torch.cuda.device(dev):
+            code = lib().cg_solve(
+                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
+                _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
+                float(tol), int(maxit), C.byref(info), _stream(dev))
+        if check:
+            _check(code, "cg_solve", allow=(OK, NOTCONV))
+        out = {f: getattr(info, f) for f, _ in _Info._fields_}
+        out["code"] = code
+        return x, out
