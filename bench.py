@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=1024)
@@ -57,10 +57,14 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--maxit", type=int, default=200000)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1,
+                    help="solves timed end to end with host buffers (0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-vy", type=int, default=0)
     ap.add_argument("--tile-zc", type=int, default=-1)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--loop", type=int, default=0,
+                    help="0: CUDA-graph while loop; 1: host-polled graph chunks")
     return ap.parse_args()
 
 
@@ -257,8 +261,11 @@ def main():
     ctx = tpfa.Context(nx, ny, nz, device=dev)
     if a.tile_vy:
         ctx.set_option("tile_vy", a.tile_vy)
+    if a.stages:
+        ctx.set_option("stages", a.stages)
     if a.tile_zc >= 0:
         ctx.set_option("tile_zc", a.tile_zc)
+    ctx.set_option("loop", a.loop)
     coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
     coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
     b = torch.empty(n, dtype=torch.float64, device=dev)
@@ -298,7 +305,7 @@ def main():
     # end to end through the public API with host buffers: H2D of the step's
     # inputs, the solve, D2H of the solution
     e2e = None
-    if not a.no_e2e:
+    if a.e2e_steps > 0:
         x_host = torch.empty(n, dtype=torch.float64).pin_memory()
         Ke = torch.empty_like(K)
         sie, sve = torch.empty_like(sidx), torch.empty_like(sval)
@@ -308,7 +315,7 @@ def main():
         e3 = torch.cuda.Event(enable_timing=True)
         e2.record(stream)
         e2e_iters = 0
-        for _ in range(a.steps):
+        for _ in range(a.e2e_steps):
             Ke.copy_(K_host, non_blocking=True)
             sie.copy_(idx_host, non_blocking=True)
             sve.copy_(val_host, non_blocking=True)

@@ -87,9 +87,10 @@ enum tpfa_option {
   TPFA_OPT_INNER_RTOL = 1,   /* lower bound on the inner FP32 CG relative tolerance (default 1e-6) */
   TPFA_OPT_MAX_OUTER = 2,    /* maximum FP64 refinement steps (default 20)                        */
   TPFA_OPT_LOOP = 3,         /* 0 = CUDA-graph while node (default), 1 = host-polled graph chunks */
-  TPFA_OPT_TILE_VY = 4,      /* rows per warp in the stencil sweeps: 4 or 8 (default 4)           */
+  TPFA_OPT_TILE_VY = 4,      /* rows per warp in the stencil sweeps: 4 or 8 (default 4; 8 sets 3 stages) */
   TPFA_OPT_TILE_ZC = 5,      /* planes per warp in the stencil sweeps, 0 = automatic              */
-  TPFA_OPT_CHUNK = 6         /* CG iterations per graph launch when TPFA_OPT_LOOP = 1 (default 32) */
+  TPFA_OPT_CHUNK = 6,        /* CG iterations per graph launch when TPFA_OPT_LOOP = 1 (default 32) */
+  TPFA_OPT_STAGES = 7        /* shared-memory plane stages per warp: 3 or 4 (default 4; 4 needs VY = 4) */
 };
 
 /* Create a context for one grid on the current CUDA device.  Allocates the

@@ -20,6 +20,7 @@ struct tpfa_ctx {
   int max_outer;
   int loop_mode;
   int vy;
+  int stages;
   int zc;
   int chunk;
   // reduction workspace
@@ -36,7 +37,7 @@ struct tpfa_ctx {
   // iteration-loop graph
   cudaGraphExec_t loop_exec;
   const void* loop_key_coef;
-  int loop_key_vy, loop_key_zc, loop_key_mode, loop_key_chunk;
+  int loop_key_vy, loop_key_stages, loop_key_zc, loop_key_mode, loop_key_chunk;
   cudaStream_t cap_stream;
   cudaEvent_t ev[4];
 };
@@ -105,7 +106,7 @@ int use_device(const tpfa_ctx* c) {
   return TPFA_OK;
 }
 
-Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->zc, c->num_sms); }
+Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->stages, c->zc, c->num_sms); }
 
 int ensure_partials(tpfa_ctx* c, size_t need) {
   if (need <= c->partials_cap) return TPFA_OK;
@@ -161,13 +162,14 @@ void drop_loop(tpfa_ctx* c) {
 // launches.
 int ensure_loop(tpfa_ctx* c, const float* coef) {
   if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_vy == c->vy &&
-      c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
+      c->loop_key_stages == c->stages && c->loop_key_zc == c->zc &&
+      c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
     return TPFA_OK;
   drop_loop(c);
   const Sweep sw = ctx_sweep(c);
   int rc = ensure_partials(c, (size_t)sw.nblocks * 4);
   if (rc) return rc;
-  if (sweep_blocks_per_sm(c->vy) < 1) return TPFA_ECUDA;
+  if (sweep_blocks_per_sm(c->vy, c->stages) < 1) return TPFA_ECUDA;
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = c->cap_stream;
   const float4* cf = reinterpret_cast<const float4*>(coef);
@@ -223,6 +225,7 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
   }
   c->loop_key_coef = coef;
   c->loop_key_vy = c->vy;
+  c->loop_key_stages = c->stages;
   c->loop_key_zc = c->zc;
   c->loop_key_mode = c->loop_mode;
   c->loop_key_chunk = c->chunk;
@@ -280,6 +283,7 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->max_outer = 20;
   c->loop_mode = 0;
   c->vy = 4;
+  c->stages = 4;
   c->zc = 0;
   c->chunk = 32;
   int rc = TPFA_ECUDA;
@@ -351,8 +355,14 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
       c->loop_mode = (int)value;
       return TPFA_OK;
     case TPFA_OPT_TILE_VY:
-      if (value != 4 && value != 8) return TPFA_EINVAL;
+      if (!sweep_config_ok((int)value, (int)value == 8 ? 3 : c->stages) || value != floor(value))
+        return TPFA_EINVAL;
       c->vy = (int)value;
+      if (c->vy == 8) c->stages = 3;
+      return TPFA_OK;
+    case TPFA_OPT_STAGES:
+      if (!sweep_config_ok(c->vy, (int)value) || value != floor(value)) return TPFA_EINVAL;
+      c->stages = (int)value;
       return TPFA_OK;
     case TPFA_OPT_TILE_ZC:
       if (value < 0 || value > 1 << 20 || value != floor(value)) return TPFA_EINVAL;

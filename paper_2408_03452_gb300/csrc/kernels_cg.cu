@@ -137,7 +137,6 @@ struct SweepArgs {
   double* partials;
   unsigned int* counter;
   unsigned long long cond;
-  int use_cond;
 };
 
 // CG finish for iteration k (last block, thread 0).  rho = r_k'r_k,
@@ -148,7 +147,7 @@ struct SweepArgs {
 // so one reduction per iteration suffices.  The next sweep recomputes the
 // true r_{k+1}'r_{k+1} from the stored vector.
 __device__ void cg_finish(CgState* st, const double (&t)[4], unsigned long long cond,
-                          int use_cond) {
+                          bool use_cond) {
   const double rho = t[0], pq = t[1], rq = t[2], qq = t[3];
   const long long k = st->iter;
   if (k == 0) st->rho0 = rho;
@@ -187,9 +186,48 @@ __device__ void cg_finish(CgState* st, const double (&t)[4], unsigned long long 
   if (use_cond) cudaGraphSetConditional(cond, done == kRunning ? 1u : 0u);
 }
 
-template <int VY, bool CG>
+// ---- asynchronous global -> shared copies (cp.async, zero-filling) --------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// copy 4 bytes, or write 4 zero bytes when !ok (nothing is read then)
+__device__ __forceinline__ void cp4(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared-memory stage of one warp for one z-plane: the coefficient records
+// of the warp's VY rows, r/q/p (or p alone) of rows -1..VY, x of the VY
+// rows, and Ty of row -1.  Lane-minor, each lane reads only its own column.
+template <int VY>
+struct StageLayout {
+  static constexpr int kCoef = 0;                               // float4 [VY][32]
+  static constexpr int kVec = VY * 32 * 16;                     // float [3][VY+2][32]
+  static constexpr int kE = kVec + 3 * (VY + 2) * 32 * 4;       // float [VY][32]
+  static constexpr int kTy = kE + VY * 32 * 4;                  // float [32]
+  static constexpr int kBytes = kTy + 32 * 4;
+};
+
+template <int VY, int S>
+constexpr int sweep_smem_bytes() { return kSweepWarps * S * StageLayout<VY>::kBytes; }
+
+template <int VY, int S, bool CG, bool COND>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 sweep_kernel(const SweepArgs a) {
+  static_assert(S >= 3, "the plane pipeline needs at least three stages");
+  using LY = StageLayout<VY>;
+  extern __shared__ __align__(16) unsigned char smem[];
   const Grid& g = a.g;
   float alpha = 0.f, beta = 0.f;
   const float *rin = nullptr, *qin = nullptr, *pin = a.p;
@@ -199,14 +237,14 @@ sweep_kernel(const SweepArgs a) {
     if (*(volatile int*)&st->done != kRunning) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->launches += 1;
-        if (a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+        if (COND) cudaGraphSetConditional(a.cond, 0u);
       }
       return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       const long long n = st->launches + 1;
       st->launches = n;
-      if (n > st->guard_limit && a.use_cond) cudaGraphSetConditional(a.cond, 0u);
+      if (COND && n > st->guard_limit) cudaGraphSetConditional(a.cond, 0u);
     }
     const int par = st->parity;
     alpha = (float)st->alpha;
@@ -216,7 +254,9 @@ sweep_kernel(const SweepArgs a) {
   }
 
   const int lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kSweepWarps + (threadIdx.x >> 5);
+  const int wib = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kSweepWarps + wib;
+  unsigned char* wsm = smem + (size_t)wib * S * LY::kBytes;
   Acc acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 
   if (gw < a.nwarps) {  // warp-uniform
@@ -230,50 +270,77 @@ sweep_kernel(const SweepArgs a) {
     const int64_t y0 = wy * VY;
     const int64_t z0 = wz * (int64_t)a.zc;
     const int64_t z1 = min(z0 + (int64_t)a.zc, g.nz);
-    // row validity bits for rows -1 .. VY (bit jj+1)
-    unsigned rowok = 0u;
+    unsigned rowok = 0u;  // bit jj+1: row y0+jj inside the grid (and this lane's column too)
 #pragma unroll
     for (int jj = -1; jj <= VY; ++jj)
       if (inx && y0 + jj >= 0 && y0 + jj < g.ny) rowok |= 1u << (jj + 1);
-    // in-plane offset of (gx, y0) (fits 32 bits: nx*ny < 2^31 is checked
-    // at context creation); row jj at + jj*nx, plane z at + z*nx*ny
+    // in-plane offset of (gx, y0) (fits 32 bits: nx*ny + 2nx < 2^31 is
+    // checked at context creation); row jj at + jj*nx, plane z at + z*nx*ny
     const int nxi = (int)g.nx;
     const int o0 = (int)(gx + g.nx * y0);
-    auto plane_off = [&](int64_t z) {
-      const int64_t zc = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
-      return g.plane * zc;
+    const int64_t L = z1 - z0 + 2;  // planes z0-1 .. z1
+
+    // Issue the asynchronous copies of plane j (absolute z = z0 - 1 + j)
+    // into stage j % S; out-of-grid cells are zero-filled.  Always commits
+    // one group so that group counts stay uniform.
+    auto issue = [&](int64_t j) {
+      if (j < L) {
+        const int64_t z = z0 - 1 + j;
+        const bool zok = z >= 0 && z < g.nz;
+        const int64_t zo = g.plane * (z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z));
+        const bool own = outl && z >= z0 && z < z1;
+        unsigned char* sb = wsm + (size_t)(j % S) * LY::kBytes;
+        float4* scf = reinterpret_cast<float4*>(sb + LY::kCoef);
+        float* sv = reinterpret_cast<float*>(sb + LY::kVec);
+        float* se = reinterpret_cast<float*>(sb + LY::kE);
+        float* sty = reinterpret_cast<float*>(sb + LY::kTy);
+#pragma unroll
+        for (int jj = -1; jj <= VY; ++jj) {
+          const bool ok = zok && ((rowok >> (jj + 1)) & 1u);
+          const int64_t src = zo + (ok ? (int64_t)(o0 + jj * nxi) : 0);
+          if (CG) {
+            cp4(sv + (0 * (VY + 2) + jj + 1) * 32 + lane, rin + src, ok);
+            cp4(sv + (1 * (VY + 2) + jj + 1) * 32 + lane, qin + src, ok);
+            cp4(sv + (2 * (VY + 2) + jj + 1) * 32 + lane, pin + src, ok);
+          } else {
+            cp4(sv + (2 * (VY + 2) + jj + 1) * 32 + lane, pin + src, ok);
+          }
+          if (jj == -1) cp4(sty + lane, reinterpret_cast<const float*>(a.coef + src) + 1, ok);
+          if (jj >= 0 && jj < VY) {
+            cp16(scf + jj * 32 + lane, a.coef + src, ok);
+            if (CG) cp4(se + jj * 32 + lane, a.v.e + src, ok && own);
+          }
+        }
+      }
+      cp_commit();
     };
 
-    // Form r_k and p_k on plane z, rows -1 .. VY.  For this warp's own
-    // output cells on planes [z0, z1) also write r_k, p_k and the x update
+    // Form r_k and p_k on plane j from its stage (rows -1 .. VY).  For this
+    // warp's own output cells also write r_k, p_k and the x update
     // x_k = x_{k-1} + alpha p_{k-1}, and accumulate r_k'r_k.
-    auto form_plane = [&](int64_t z, float (&P)[VY + 2], float (&R)[VY], float& s0) {
-      const bool zok = z >= 0 && z < g.nz;
+    auto form = [&](int64_t j, float (&P)[VY + 2], float (&R)[VY], float& s0) {
+      const int64_t z = z0 - 1 + j;
       const bool own = outl && z >= z0 && z < z1;
-      const int64_t zo = plane_off(z);
-      const float* rz = rin + zo;
-      const float* qz = qin + zo;
-      const float* pz = pin + zo;
+      const unsigned char* sb = wsm + (size_t)(j % S) * LY::kBytes;
+      const float* sv = reinterpret_cast<const float*>(sb + LY::kVec);
+      const float* se = reinterpret_cast<const float*>(sb + LY::kE);
+      const int64_t zo = g.plane * z;
 #pragma unroll
       for (int jj = -1; jj <= VY; ++jj) {
-        const bool ok = zok && ((rowok >> (jj + 1)) & 1u);
-        const int o = o0 + jj * nxi;
-        float p_ = 0.f, r_ = 0.f;
+        const float p0 = sv[(2 * (VY + 2) + jj + 1) * 32 + lane];
+        float p_ = p0, r_ = 0.f;
         if (CG) {
-          if (ok) {
-            const float r0 = __ldg(rz + o), q0 = __ldg(qz + o), p0 = __ldg(pz + o);
-            r_ = fmaf(-alpha, q0, r0);   // Alg. 1 line 7 (previous iteration)
-            p_ = fmaf(beta, p0, r_);     // Alg. 1 line 10
-            if (jj >= 0 && jj < VY && own) {
-              float* ez = a.v.e + zo;
-              ez[o] = fmaf(alpha, p0, ez[o]);  // Alg. 1 line 6
-              (rout + zo)[o] = r_;
-              (pout + zo)[o] = p_;
-              s0 = fmaf(r_, r_, s0);
-            }
+          const float r0 = sv[(0 * (VY + 2) + jj + 1) * 32 + lane];
+          const float q0 = sv[(1 * (VY + 2) + jj + 1) * 32 + lane];
+          r_ = fmaf(-alpha, q0, r0);  // Alg. 1 line 7 (previous iteration)
+          p_ = fmaf(beta, p0, r_);    // Alg. 1 line 10
+          if (jj >= 0 && jj < VY && own && ((rowok >> (jj + 1)) & 1u)) {
+            const int64_t id = zo + o0 + jj * nxi;
+            a.v.e[id] = fmaf(alpha, p0, se[jj * 32 + lane]);  // Alg. 1 line 6
+            rout[id] = r_;
+            pout[id] = p_;
+            s0 = fmaf(r_, r_, s0);
           }
-        } else {
-          if (ok) p_ = __ldg(pz + o);
         }
         P[jj + 1] = p_;
         if (jj >= 0 && jj < VY) R[jj] = r_;
@@ -282,46 +349,53 @@ sweep_kernel(const SweepArgs a) {
 
     float Pm[VY], P0[VY + 2], R0[VY], Tzm[VY];
     float s0 = 0.f;
-    {  // plane z0 - 1 (rows 0..VY-1 are the z-neighbours below) and its Tz
+#pragma unroll
+    for (int i = 0; i < S - 1; ++i) issue(i);
+    cp_wait<S - 2>();
+    {  // plane z0 - 1: direction below the first plane, and its Tz
       float Pt[VY + 2], Rt[VY];
-      form_plane(z0 - 1, Pt, Rt, s0);
-      const float4* cz = a.coef + plane_off(z0 - 1);
+      form(0, Pt, Rt, s0);
+      const float4* scf = reinterpret_cast<const float4*>(wsm + LY::kCoef);
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
         Pm[jj] = Pt[jj + 1];
-        const bool ok = z0 >= 1 && ((rowok >> (jj + 1)) & 1u);
-        Tzm[jj] = ok ? __ldg(&cz[o0 + jj * nxi].z) : 0.f;
+        Tzm[jj] = scf[jj * 32 + lane].z;
       }
     }
-    form_plane(z0, P0, R0, s0);
+    issue(S - 1);
+    cp_wait<S - 2>();
+    form(1, P0, R0, s0);
 
 #pragma unroll 1
     for (int64_t z = z0; z < z1; ++z) {
+      const int64_t jf = z - z0 + 2;  // plane z + 1
+      issue(jf + S - 2);              // reuses the stage of plane z - 1
+      cp_wait<S - 2>();
       float Pp[VY + 2], Rp[VY];
-      form_plane(z + 1, Pp, Rp, s0);
+      form(jf, Pp, Rp, s0);
+      const unsigned char* sb = wsm + (size_t)((jf - 1) % S) * LY::kBytes;  // plane z
+      const float4* scf = reinterpret_cast<const float4*>(sb + LY::kCoef);
+      const float* sty = reinterpret_cast<const float*>(sb + LY::kTy);
       const int64_t zo = g.plane * z;
-      const float4* cz = a.coef + zo;
-      const float tym0 = (rowok & 1u) ? __ldg(&cz[o0 - nxi].y) : 0.f;
-      float s1 = 0.f, s2 = 0.f, s3 = 0.f, tyl = tym0;
+      float s1 = 0.f, s2 = 0.f, s3 = 0.f, tyl = sty[lane];
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
-        const bool ok = (rowok >> (jj + 1)) & 1u;
-        const int o = o0 + jj * nxi;
-        const float4 cf = ok ? __ldg(cz + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 cf = scf[jj * 32 + lane];
         const float pc = P0[jj + 1];
         const float pxm = __shfl_up_sync(kFull, pc, 1);
         const float pxp = __shfl_down_sync(kFull, pc, 1);
         const float txm = __shfl_up_sync(kFull, cf.x, 1);
         const float q = stencil7(cf, txm, tyl, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
                                  Pp[jj + 1], Pm[jj]);
-        if (outl && ok) {
+        if (outl && ((rowok >> (jj + 1)) & 1u)) {
+          const int64_t id = zo + o0 + jj * nxi;
           if (CG) {
-            (qout + zo)[o] = q;
+            qout[id] = q;
             s1 = fmaf(pc, q, s1);
             s2 = fmaf(R0[jj], q, s2);
             s3 = fmaf(q, q, s3);
           } else {
-            (a.Ap + zo)[o] = q;
+            a.Ap[id] = q;
             s1 = fmaf(pc, q, s1);
           }
         }
@@ -342,6 +416,7 @@ sweep_kernel(const SweepArgs a) {
       for (int jj = 0; jj < VY + 2; ++jj) P0[jj] = Pp[jj];
     }
     if (CG) kadd(acc[0], s0);
+    cp_wait<0>();  // drain the (empty) trailing groups before the warp leaves
   }
 
   if (CG) {
@@ -349,7 +424,7 @@ sweep_kernel(const SweepArgs a) {
     block_partial<4>(v, a.partials);
     double tot[4];
     if (last_block_total<4>(a.partials, a.counter, tot) && threadIdx.x == 0)
-      cg_finish(a.st, tot, a.cond, a.use_cond);
+      cg_finish(a.st, tot, a.cond, COND);
   } else if (a.pAp != nullptr) {
     double v[1] = {kval(acc[1])};
     block_partial<1>(v, a.partials);
@@ -358,6 +433,7 @@ sweep_kernel(const SweepArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
 // FP64 residual r = b - A x (one thread per cell, grid-stride, fixed grid).
 __global__ void __launch_bounds__(kElemThreads)
 residual64_kernel(Grid g, const double2* __restrict__ coef64, const double* __restrict__ b,
@@ -468,23 +544,20 @@ correct_kernel(Grid g, const float* __restrict__ e, double* __restrict__ x, cons
 
 // ---------------------------------------------------------------------------
 
-Sweep plan_sweep(const Grid& g, int vy, int zc_opt, int num_sms) {
+Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms) {
   Sweep s;
   s.vy = vy;
+  s.stages = stages;
   s.nwx = (g.nx + kTileX - 1) / kTileX;
   s.nwy = (g.ny + vy - 1) / vy;
   int zc = zc_opt;
   if (zc <= 0) {
-    // enough warps for ~8 waves of 16 resident warps per SM, but keep
-    // runs of at least 16 planes where the grid allows it (the two halo
-    // planes of each run are re-read).
-    const int64_t target = (int64_t)num_sms * 16 * 8;
+    // longest run (at most 128 planes; each run re-reads two halo planes)
+    // that still gives about four waves of eight resident warps per SM
+    const int64_t target = (int64_t)num_sms * 8 * 4;
     const int64_t cols = s.nwx * s.nwy;
-    zc = (int)g.nz;
-    while (zc > 16 && cols * ((g.nz + zc - 1) / zc) < target) zc = (zc + 1) / 2;
-    if (cols * ((g.nz + zc - 1) / zc) < target) {
-      while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc = (zc + 1) / 2;
-    }
+    zc = 128;
+    while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc /= 2;
   }
   if (zc > g.nz) zc = (int)g.nz;
   s.zc = zc;
@@ -492,6 +565,10 @@ Sweep plan_sweep(const Grid& g, int vy, int zc_opt, int num_sms) {
   s.nwarps = s.nwx * s.nwy * s.nwz;
   s.nblocks = (s.nwarps + kSweepWarps - 1) / kSweepWarps;
   return s;
+}
+
+bool sweep_config_ok(int vy, int stages) {
+  return (vy == 4 && (stages == 3 || stages == 4)) || (vy == 8 && stages == 3);
 }
 
 int elem_blocks(const Grid& g, int num_sms) {
@@ -511,6 +588,32 @@ static SweepArgs sweep_args(const Grid& g, const Sweep& sw, const float4* coef) 
   return a;
 }
 
+template <int VY, int S, bool CG, bool COND>
+static cudaError_t launch_t(const SweepArgs& a, const Sweep& sw, cudaStream_t s) {
+  constexpr int smem = sweep_smem_bytes<VY, S>();
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<VY, S, CG, COND>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  sweep_kernel<VY, S, CG, COND><<<(unsigned)sw.nblocks, kSweepWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int VY, int S>
+static cudaError_t launch_vs(const SweepArgs& a, const Sweep& sw, bool cg, bool cond,
+                             cudaStream_t s) {
+  if (!cg) return launch_t<VY, S, false, false>(a, sw, s);
+  if (cond) return launch_t<VY, S, true, true>(a, sw, s);
+  return launch_t<VY, S, true, false>(a, sw, s);
+}
+
+static cudaError_t launch_sweep(const SweepArgs& a, const Sweep& sw, bool cg, bool cond,
+                                cudaStream_t s) {
+  if (sw.vy == 4 && sw.stages == 3) return launch_vs<4, 3>(a, sw, cg, cond, s);
+  if (sw.vy == 4 && sw.stages == 4) return launch_vs<4, 4>(a, sw, cg, cond, s);
+  if (sw.vy == 8 && sw.stages == 3) return launch_vs<8, 3>(a, sw, cg, cond, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, const float* p,
                          float* Ap, double* pAp, double* partials, unsigned int* counter,
                          cudaStream_t s) {
@@ -520,10 +623,7 @@ cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, con
   a.pAp = pAp;
   a.partials = partials;
   a.counter = counter;
-  const dim3 grid((unsigned)sw.nblocks), block(kSweepWarps * 32);
-  if (sw.vy == 4) sweep_kernel<4, false><<<grid, block, 0, s>>>(a);
-  else sweep_kernel<8, false><<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_sweep(a, sw, false, false, s);
 }
 
 cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
@@ -535,19 +635,29 @@ cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, 
   a.partials = partials;
   a.counter = counter;
   a.cond = cond;
-  a.use_cond = use_cond;
-  const dim3 grid((unsigned)sw.nblocks), block(kSweepWarps * 32);
-  if (sw.vy == 4) sweep_kernel<4, true><<<grid, block, 0, s>>>(a);
-  else sweep_kernel<8, true><<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_sweep(a, sw, true, use_cond != 0, s);
 }
 
-int sweep_blocks_per_sm(int vy) {
+template <int VY, int S>
+static int blocks_per_sm_t() {
+  constexpr int smem = sweep_smem_bytes<VY, S>();
+  if (cudaFuncSetAttribute(sweep_kernel<VY, S, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 0;
   int nb = 0;
-  cudaError_t e = vy == 4
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<4, true>, kSweepWarps * 32, 0)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<8, true>, kSweepWarps * 32, 0);
-  return e == cudaSuccess ? nb : 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<VY, S, true, true>,
+                                                    kSweepWarps * 32, smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+int sweep_blocks_per_sm(int vy, int stages) {
+  int nb = 0;
+  if (vy == 4 && stages == 3) nb = blocks_per_sm_t<4, 3>();
+  else if (vy == 4 && stages == 4) nb = blocks_per_sm_t<4, 4>();
+  else if (vy == 8 && stages == 3) nb = blocks_per_sm_t<8, 3>();
+  if (nb == 0) cudaGetLastError();
+  return nb;
 }
 
 cudaError_t launch_residual64(const Grid& g, const double* coef64, const double* b,

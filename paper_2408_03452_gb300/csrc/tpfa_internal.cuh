@@ -55,13 +55,15 @@ struct Grid {
 // Warp tiling of the z-marching stencil sweeps.
 struct Sweep {
   int vy;           // rows per warp (4 or 8)
+  int stages;       // shared-memory plane stages per warp (3 or 4)
   int zc;           // planes per warp
   int64_t nwx, nwy, nwz;
   int64_t nwarps;
   int64_t nblocks;  // blocks of kSweepWarps warps
 };
 
-Sweep plan_sweep(const Grid& g, int vy, int zc_opt, int num_sms);
+Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms);
+bool sweep_config_ok(int vy, int stages);
 
 // Vector set of the inner CG (two sets, ping-ponged between sweeps).
 struct CgVecs {
@@ -98,7 +100,7 @@ cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partia
 cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
                            cudaStream_t s);
 
-int sweep_blocks_per_sm(int vy);
+int sweep_blocks_per_sm(int vy, int stages);
 int elem_blocks(const Grid& g, int num_sms);
 
 }  // namespace tpfa

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libtpfa.so")
 OK, NOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, -3, -4, -5, -6, -7
 
-OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6}
+OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6,
+           "stages": 7}
 
 
 class TpfaError(RuntimeError):

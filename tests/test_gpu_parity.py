@@ -137,7 +137,7 @@ def _abs_apply(A, x):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("tile", [(4, 0), (8, 0), (4, 1), (8, 5)])
+@pytest.mark.parametrize("tile", [(4, 0, 3), (4, 0, 4), (8, 0, 3), (4, 1, 3), (4, 2, 4), (8, 5, 3)])
 def test_apply_matches_oracle(tp, oracle_mod, shape, tile):
     O = oracle_mod
     c = _case(shape, seed=5, sigma=1.5, random_mask=0.05, d=1e-3,
@@ -146,6 +146,7 @@ def test_apply_matches_oracle(tp, oracle_mod, shape, tile):
     p = synth.uniform_field(n, 7).astype(np.float32)
     with _ctx(tp, c) as ctx:
         ctx.set_option("tile_vy", tile[0])
+        ctx.set_option("stages", tile[2])
         ctx.set_option("tile_zc", tile[1])
         coef, _ = _build(tp, ctx, c)
         pt = _dev(p)
@@ -204,6 +205,7 @@ def _solve(tp, c, tol, loop=0, maxit=200000, x0=None, tile=None):
         ctx.set_option("loop", loop)
         if tile:
             ctx.set_option("tile_vy", tile[0])
+            ctx.set_option("stages", tile[2])
             ctx.set_option("tile_zc", tile[1])
         coef, coef64 = _build(tp, ctx, c)
         b = ctx.build_rhs(_dev(c["K"]), _dev(c["mask"]), _dev(c["q"]), _dev(c["pD"]))
@@ -248,7 +250,9 @@ def test_cg_loop_modes_and_tiles_agree_bitwise(tp):
     assert ia["iters"] == ib["iters"] == ic["iters"]
     # a different warp tiling changes only the order of the dot-product
     # partial sums: same solution to the tolerance
-    xd, idd = _solve(tp, c, 1e-8, loop=0, tile=(8, 3))
+    xd, idd = _solve(tp, c, 1e-8, loop=0, tile=(8, 3, 3))
+    xe, ie = _solve(tp, c, 1e-8, loop=1, tile=(4, 2, 4))
+    assert ie["code"] == 0 and ie["rel_res_fp64"] <= 1e-8
     assert idd["code"] == 0 and idd["rel_res_fp64"] <= 1e-8
 
 
@@ -327,6 +331,8 @@ def test_argument_checks(tp):
         assert L.cg_solve(*args, 1e-8, 0, C.byref(info), s) == tp.EINVAL
         with pytest.raises(tp.TpfaError):
             ctx.set_option("tile_vy", 5)
+        with pytest.raises(tp.TpfaError):
+            ctx.set_option("stages", 2)
     # a buffer far too small for the grid is refused, not read past its end
     big = _case((256, 256, 64), seed=0, dirichlet=None)
     with _ctx(tp, big) as ctx:
