@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--loop", type=int, default=0,
                     help="0: CUDA-graph while loop; 1: host-polled graph chunks")
+    ap.add_argument("--probe-iters", type=int, default=0,
+                    help="profiling aid: build the workload, run one solve capped at this many "
+                         "CG iterations (host-polled chunks of 4), print its info, no timing")
     return ap.parse_args()
 
 
@@ -279,6 +282,18 @@ def main():
         if info["code"] not in (0,):
             raise RuntimeError(f"cg_solve returned {info}")
         return info
+
+    if a.probe_iters > 0:
+        ctx.set_option("loop", 1)
+        ctx.set_option("chunk", 4)
+        ctx.build_trans(K, None, None, d0, coef=coef, coef64=coef64)
+        ctx.build_rhs(K, None, None, None, sidx, sval, b=b)
+        x.zero_()
+        _, info = ctx.cg_solve(coef, coef64, b, x=x, tol=a.tol, maxit=a.probe_iters, check=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": info}))
+        ctx.close()
+        return
 
     for _ in range(a.warmup):
         step(K, sidx, sval)
