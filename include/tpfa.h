@@ -185,6 +185,42 @@ int tpfa_residual64(tpfa_ctx* ctx, const double* coef64, const double* b, const 
 int cg_solve(tpfa_ctx* ctx, const float* coef, const double* coef64, const double* b, double* x,
              double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
 
+/*
+ * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a library convenience.
+ *
+ * Who needs it: code that is not allowed to call cudaMalloc / cudaFree, for
+ * example a component inside a host application whose allocator owns all
+ * device memory and passes in only the input and output buffers, or a loop
+ * under a fixed memory budget where allocation (and the device
+ * synchronisation cudaFree implies) is not permitted.  tpfa_create
+ * allocates, so these callers cannot hold a context; this call needs none.
+ *
+ * It computes exactly what tpfa_apply computes (same kernel, same per-cell
+ * arithmetic; pAp may differ from tpfa_apply's in the last bits when the
+ * tiling differs) and allocates nothing.  Its reduction workspace is a
+ * fixed array of 256 + 16384 * 8 = 131,328 bytes in the library's device
+ * image, which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * grid  host pointer to the grid (same rules as tpfa_create).
+ * coef, p, Ap, pAp, stream: as for tpfa_apply.
+ *
+ * Limits and behaviour:
+ *  - the grid must be tiled with at most 16384 blocks of the sweep kernel
+ *    (4 warps of 30 x 4 columns each, z-runs lengthened as needed), i.e.
+ *    ceil(nx/30) * ceil(ny/4) <= 65536; larger grids get TPFA_EINVAL.
+ *  - the first call on a device looks up the workspace's device address
+ *    (cudaGetSymbolAddress, no allocation); make that first call before any
+ *    stream capture on that device.
+ *  - all calls share the one workspace: calls whose kernels overlap on the
+ *    GPU (different streams, or different host threads without ordering)
+ *    race and give wrong pAp values.  The completion counter is cleared on
+ *    the stream before each call that requests pAp.
+ */
+int tpfa_apply_noalloc(const tpfa_grid* grid, const float* coef, const float* p, float* Ap,
+                       double* pAp, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

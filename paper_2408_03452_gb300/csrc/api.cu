@@ -42,17 +42,11 @@ struct tpfa_ctx {
   cudaEvent_t ev[4];
 };
 
-namespace {
-
-#define CK(call)                                   \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return TPFA_ECUDA;      \
-  } while (0)
+namespace tpfa {
 
 typedef int (*AddrRangeFn)(unsigned long long*, size_t*, unsigned long long);
 
-AddrRangeFn addr_range_fn() {
+static AddrRangeFn addr_range_fn() {
   static AddrRangeFn fn = nullptr;
   static bool tried = false;
   if (!tried) {
@@ -98,6 +92,16 @@ bool dev_ok(const void* p, size_t bytes, size_t align, int device) {
 bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device) {
   return p == nullptr || dev_ok(p, bytes, align, device);
 }
+
+}  // namespace tpfa
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return TPFA_ECUDA;      \
+  } while (0)
 
 int use_device(const tpfa_ctx* c) {
   int cur = -1;

@@ -101,6 +101,11 @@ cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgSta
                            cudaStream_t s);
 
 int sweep_blocks_per_sm(int vy, int stages);
+
+// Argument checks shared by the entry points: a device (or managed)
+// allocation on `device` that holds [p, p + bytes) and is `align`-aligned.
+bool dev_ok(const void* p, size_t bytes, size_t align, int device);
+bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device);
 int elem_blocks(const Grid& g, int num_sms);
 
 }  // namespace tpfa

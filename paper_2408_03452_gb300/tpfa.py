@@ -57,6 +57,7 @@ SIGNATURES = {
     "tpfa_apply": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "tpfa_residual64": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
+    "tpfa_apply_noalloc": (C.c_int, [C.POINTER(_Grid), _P, _P, _P, _P, _P]),
 }
 
 
