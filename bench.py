@@ -229,6 +229,26 @@ def sweep_traffic(nx, ny, nz):
         return None
 
 
+def cell_updates_per_s(cells, iterations, ms):
+    """The paper's throughput definition (Table III): cells x iterations / time."""
+    return cells * iterations / (ms / 1e3)
+
+
+def combine_ranks(ms, iters, e2e_ms, e2e_iters, device):
+    """Whole-job figures over the replicas: the slowest rank's time and the
+    sum of every rank's iterations.  One process per GPU; without an
+    initialised process group this is the identity."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, iters, e2e_ms, e2e_iters
+    t = torch.tensor([ms, iters, e2e_ms, e2e_iters], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), t[1].item(), tmax[2].item(), t[3].item()
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -342,20 +362,11 @@ def main():
         barrier()
         e2e = (e2e_iters, e2.elapsed_time(e3))
 
-    if world > 1:
-        t = torch.tensor([ms, iters, e2e[1] if e2e else 0.0, e2e[0] if e2e else 0.0],
-                         dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, iters_all = tmax[0].item(), t[1].item()
-        e2e_ms_max, e2e_iters_all = tmax[2].item(), t[3].item()
-    else:
-        ms_max, iters_all = ms, iters
-        e2e_ms_max, e2e_iters_all = (e2e[1], e2e[0]) if e2e else (0.0, 0.0)
+    ms_max, iters_all, e2e_ms_max, e2e_iters_all = combine_ranks(
+        ms, iters, e2e[1] if e2e else 0.0, e2e[0] if e2e else 0.0, dev)
 
     if rank == 0:
-        value = n * iters_all / (ms_max / 1e3)
+        value = cell_updates_per_s(n, iters_all, ms_max)
         peak, peak_kind = measured_hbm_peak()
         sweep_ms = inner_ms / max(iters, 1)
         algo = SWEEP_BYTES_PER_CELL * n
