@@ -90,7 +90,10 @@ enum tpfa_option {
   TPFA_OPT_TILE_VY = 4,      /* rows per warp in the stencil sweeps: 4 or 8 (default 4; 8 sets 3 stages) */
   TPFA_OPT_TILE_ZC = 5,      /* planes per warp in the stencil sweeps, 0 = automatic              */
   TPFA_OPT_CHUNK = 6,        /* CG iterations per graph launch when TPFA_OPT_LOOP = 1 (default 32) */
-  TPFA_OPT_STAGES = 7        /* shared-memory plane stages per warp: 3 or 4 (default 4; 4 needs VY = 4) */
+  TPFA_OPT_STAGES = 7,       /* shared-memory plane stages per warp: 3 or 4 (default 4; 4 needs VY = 4) */
+  TPFA_OPT_SCHEME = 8,       /* CG sweep: 0 = stores q = A p (48 B/cell, default), 1 = recomputes it (40 B/cell) */
+  TPFA_OPT_STAGES40 = 9,     /* stages of the scheme-1 sweep: 4, 5 or 6 with 2 warps/block, 4 or 5 with 4 (default 5) */
+  TPFA_OPT_WARPS40 = 10      /* warps per block of the scheme-1 sweep: 2 (default) or 4                  */
 };
 
 /* Create a context for one grid on the current CUDA device.  Allocates the

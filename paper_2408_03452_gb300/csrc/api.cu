@@ -20,7 +20,10 @@ struct tpfa_ctx {
   int max_outer;
   int loop_mode;
   int vy;
-  int stages;
+  int stages;      // stages of the stored-q sweep and of tpfa_apply
+  int scheme;      // CG sweep: 0 = stored q (48 B/cell), 1 = recomputed q (40 B/cell)
+  int stages40;    // stages of the recomputed-q sweep
+  int warps40;     // warps per block of the recomputed-q sweep
   int zc;
   int chunk;
   // reduction workspace
@@ -37,7 +40,8 @@ struct tpfa_ctx {
   // iteration-loop graph
   cudaGraphExec_t loop_exec;
   const void* loop_key_coef;
-  int loop_key_vy, loop_key_stages, loop_key_zc, loop_key_mode, loop_key_chunk;
+  int loop_key_vy, loop_key_stages, loop_key_scheme, loop_key_stages40, loop_key_warps40;
+  int loop_key_zc, loop_key_mode, loop_key_chunk;
   cudaStream_t cap_stream;
   cudaEvent_t ev[4];
 };
@@ -112,6 +116,19 @@ int use_device(const tpfa_ctx* c) {
 
 Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->stages, c->zc, c->num_sms); }
 
+// the sweep the CG loop runs
+Sweep ctx_cg_sweep(const tpfa_ctx* c) {
+  return c->scheme == 1 ? plan_sweep40(c->g, c->stages40, c->warps40, c->zc, c->num_sms)
+                        : ctx_sweep(c);
+}
+
+cudaError_t launch_cg(const tpfa_ctx* c, const Sweep& sw, const float4* cf,
+                      unsigned long long cond, int use_cond, cudaStream_t s) {
+  return c->scheme == 1
+      ? launch_cg40_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, cond, use_cond, s)
+      : launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, cond, use_cond, s);
+}
+
 int ensure_partials(tpfa_ctx* c, size_t need) {
   if (need <= c->partials_cap) return TPFA_OK;
   double* p = nullptr;
@@ -166,14 +183,17 @@ void drop_loop(tpfa_ctx* c) {
 // launches.
 int ensure_loop(tpfa_ctx* c, const float* coef) {
   if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_vy == c->vy &&
-      c->loop_key_stages == c->stages && c->loop_key_zc == c->zc &&
-      c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
+      c->loop_key_stages == c->stages && c->loop_key_scheme == c->scheme &&
+      c->loop_key_stages40 == c->stages40 && c->loop_key_warps40 == c->warps40 &&
+      c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
     return TPFA_OK;
   drop_loop(c);
-  const Sweep sw = ctx_sweep(c);
+  const Sweep sw = ctx_cg_sweep(c);
   int rc = ensure_partials(c, (size_t)sw.nblocks * 4);
   if (rc) return rc;
-  if (sweep_blocks_per_sm(c->vy, c->stages) < 1) return TPFA_ECUDA;
+  if ((c->scheme == 1 ? sweep40_blocks_per_sm(c->stages40, c->warps40)
+                      : sweep_blocks_per_sm(c->vy, c->stages)) < 1)
+    return TPFA_ECUDA;
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = c->cap_stream;
   const float4* cf = reinterpret_cast<const float4*>(coef);
@@ -196,8 +216,8 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, h, 1, cs);
-      cudaError_t e2 = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, h, 1, cs);
+      cudaError_t e1 = launch_cg(c, sw, cf, h, 1, cs);
+      cudaError_t e2 = launch_cg(c, sw, cf, h, 1, cs);
       e = cudaStreamEndCapture(cs, &body);
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
@@ -210,7 +230,7 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t el = cudaSuccess;
     for (int i = 0; i < c->chunk; ++i) {
-      cudaError_t e = launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, 0, 0, cs);
+      cudaError_t e = launch_cg(c, sw, cf, 0, 0, cs);
       if (e != cudaSuccess) el = e;
     }
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -230,6 +250,9 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
   c->loop_key_coef = coef;
   c->loop_key_vy = c->vy;
   c->loop_key_stages = c->stages;
+  c->loop_key_scheme = c->scheme;
+  c->loop_key_stages40 = c->stages40;
+  c->loop_key_warps40 = c->warps40;
   c->loop_key_zc = c->zc;
   c->loop_key_mode = c->loop_mode;
   c->loop_key_chunk = c->chunk;
@@ -288,6 +311,9 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->loop_mode = 0;
   c->vy = 4;
   c->stages = 4;
+  c->scheme = 0;
+  c->stages40 = 5;
+  c->warps40 = 2;
   c->zc = 0;
   c->chunk = 32;
   int rc = TPFA_ECUDA;
@@ -308,6 +334,8 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   {
     const Sweep sw = ctx_sweep(c);
     size_t need = (size_t)sw.nblocks * 4;
+    const Sweep sw40 = ctx_cg_sweep(c);
+    if ((size_t)sw40.nblocks * 4 > need) need = (size_t)sw40.nblocks * 4;
     if (need < (size_t)c->elem_nblocks * 2) need = (size_t)c->elem_nblocks * 2;
     rc = ensure_partials(c, need);
     if (rc) goto fail;
@@ -367,6 +395,18 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
     case TPFA_OPT_STAGES:
       if (!sweep_config_ok(c->vy, (int)value) || value != floor(value)) return TPFA_EINVAL;
       c->stages = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_SCHEME:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      c->scheme = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_STAGES40:
+      if (!sweep40_config_ok((int)value, c->warps40) || value != floor(value)) return TPFA_EINVAL;
+      c->stages40 = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_WARPS40:
+      if (!sweep40_config_ok(c->stages40, (int)value) || value != floor(value)) return TPFA_EINVAL;
+      c->warps40 = (int)value;
       return TPFA_OK;
     case TPFA_OPT_TILE_ZC:
       if (value < 0 || value > 1 << 20 || value != floor(value)) return TPFA_EINVAL;
@@ -527,7 +567,10 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
           inner_ms += ms;
           if (hs->done == kRunning) continue;
         }
-        CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks, s));
+        if (c->scheme == 1)
+          CK(launch_finalize40(c->g, c->v, c->st, c->elem_nblocks, s));
+        else
+          CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks, s));
         launches += 1;
         rc = read_state(c, s);
         if (rc) return rc;
@@ -542,7 +585,13 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
       }
       total_iters += hs->iter;
       launches += hs->launches;
-      rel_inner = hs->rho0 > 0 ? sqrt(hs->rho / hs->rho0) : 0.0;
+      {
+        // scheme 1 does not advance the recursive residual in finalize: use
+        // the fused estimate when the loop stopped on it
+        const bool est = c->scheme == 1 && (inner_status == kConvEst || inner_status == kMaxit);
+        const double rr_in = est ? hs->rho_est : hs->rho;
+        rel_inner = hs->rho0 > 0 ? sqrt(rr_in / hs->rho0) : 0.0;
+      }
       if (inner_status == kGuard) { status = TPFA_EINTERNAL; break; }
       if (inner_status == kNonFinite) { status = TPFA_ENONFINITE; break; }
       if (inner_status == kBreakdown && hs->iter == 0) { status = TPFA_EBREAKDOWN; break; }

@@ -55,15 +55,19 @@ struct Grid {
 // Warp tiling of the z-marching stencil sweeps.
 struct Sweep {
   int vy;           // rows per warp (4 or 8)
-  int stages;       // shared-memory plane stages per warp (3 or 4)
+  int stages;       // shared-memory plane stages per warp
+  int warps;        // warps per block
   int zc;           // planes per warp
   int64_t nwx, nwy, nwz;
   int64_t nwarps;
-  int64_t nblocks;  // blocks of kSweepWarps warps
+  int64_t nblocks;  // blocks of `warps` warps
 };
 
 Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms);
 bool sweep_config_ok(int vy, int stages);
+// CG sweep that recomputes q_{k-1} instead of storing q (kernels_cg40.cu)
+Sweep plan_sweep40(const Grid& g, int stages, int warps, int zc_opt, int num_sms);
+bool sweep40_config_ok(int stages, int warps);
 
 // Vector set of the inner CG (two sets, ping-ponged between sweeps).
 struct CgVecs {
@@ -89,6 +93,12 @@ cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, con
 cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
                             CgState* st, double* partials, unsigned int* counter,
                             unsigned long long cond, int use_cond, cudaStream_t s);
+cudaError_t launch_cg40_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
+                              CgState* st, double* partials, unsigned int* counter,
+                              unsigned long long cond, int use_cond, cudaStream_t s);
+cudaError_t launch_finalize40(const Grid& g, CgVecs v, const CgState* st, int nblocks,
+                              cudaStream_t s);
+int sweep40_blocks_per_sm(int stages, int warps);
 cudaError_t launch_residual64(const Grid& g, const double* coef64, const double* b,
                               const double* x, double* r, double* norms, CgState* st,
                               double* partials, unsigned int* counter, int nblocks,

@@ -21,7 +21,7 @@ OK, NOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, -3, -4, -5, -6, -7
 
 OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6,
-           "stages": 7}
+           "stages": 7, "scheme": 8, "stages40": 9, "warps40": 10}
 
 
 class TpfaError(RuntimeError):
