@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--loop", type=int, default=0,
                     help="0: CUDA-graph while loop; 1: host-polled graph chunks")
+    ap.add_argument("--scheme", type=int, default=-1,
+                    help="CG sweep: 0 stores q = Ap (48 B/cell), 1 recomputes it (40 B/cell)")
     ap.add_argument("--probe-iters", type=int, default=0,
                     help="profiling aid: build the workload, run one solve capped at this many "
                          "CG iterations (host-polled chunks of 4), print its info, no timing")
@@ -289,6 +291,8 @@ def main():
     if a.tile_zc >= 0:
         ctx.set_option("tile_zc", a.tile_zc)
     ctx.set_option("loop", a.loop)
+    if a.scheme >= 0:
+        ctx.set_option("scheme", a.scheme)
     coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
     coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
     b = torch.empty(n, dtype=torch.float64, device=dev)

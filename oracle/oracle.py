@@ -62,6 +62,7 @@ def _L():
         _lib.orc_rhs.argtypes = [G, P, P, P, P, C.c_int, P]
         _lib.orc_coefficients.argtypes = [G, P, P, P, C.c_double, P, P, P, P]
         _lib.orc_face_trans.argtypes = [G, P, P, P, P]
+        _lib.orc_extra_diagonal.argtypes = [G, P, P, P, C.c_double, P]
         _lib.orc_apply_rows.argtypes = [G, P, P, P, C.c_double, P, C.c_int64, P, P]
         _lib.orc_net_flux.argtypes = [G, P, P, P]
         _lib.orc_spmv.argtypes = [C.c_int64, P, P, P, P, P]
@@ -154,6 +155,15 @@ def coefficients(g: Grid, K, mask=None, d=None):
     out = [np.empty(g.n) for _ in range(4)]
     _L().orc_coefficients(g._c(), _p(K), _p(mask), _p(da), d0, *[_p(o) for o in out])
     return tuple(out)
+
+
+def extra_diagonal(g: Grid, K, mask=None, d=None):
+    """E with (A x)_K = sum_f T'_f (x_K - x_L) + E_K x_K (see the C source)."""
+    K, mask = _f64(K), _u8(mask)
+    da, d0 = _dargs(d)
+    E = np.empty(g.n)
+    _L().orc_extra_diagonal(g._c(), _p(K), _p(mask), _p(da), d0, _p(E))
+    return E
 
 
 def face_trans(g: Grid, K):

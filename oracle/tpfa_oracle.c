@@ -176,6 +176,26 @@ void orc_coefficients(const orc_grid* g, const double* K, const uint8_t* mask, c
   }
 }
 
+/* The same operator written as face terms plus a diagonal remainder:
+ *   (A x)_K = sum_f T'_f (x_K - x_L) + E_K x_K,
+ * T' the eliminated face transmissibilities of orc_coefficients and
+ * E_K = d_K + sum over faces to Dirichlet neighbours of T_KL (faces in the
+ * order -x, +x, -y, +y, -z, +z), E = 1 on Dirichlet cells. */
+void orc_extra_diagonal(const orc_grid* g, const double* K, const uint8_t* mask, const double* d,
+                        double d0, double* E) {
+  int64_t N = ncells(g);
+  for (int64_t c = 0; c < N; ++c) {
+    if (is_dir(mask, c)) { E[c] = 1.0; continue; }
+    double s = dval(d, d0, c);
+    for (int f = 0; f < 6; ++f) {
+      int64_t n = neighbour(g, c, f);
+      if (n < 0 || !is_dir(mask, n)) continue;
+      s += face_T(g, K, c, f, n);
+    }
+    E[c] = s;
+  }
+}
+
 /* Face transmissibilities of the +x/+y/+z face of every cell, without any
  * Dirichlet elimination (0 on the outer boundary). */
 void orc_face_trans(const orc_grid* g, const double* K, double* Tx, double* Ty, double* Tz) {
