@@ -54,8 +54,17 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--nz", type=int, default=256)
-    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--workload", default="paper", choices=["paper", "channelized"],
+                    help="paper: 1024x1024x256 layered lognormal, wells, CG to 1e-6 (default); "
+                         "channelized: 256^3 sigma-2 background + 1e4 channels, Dirichlet x "
+                         "ends, refined to 1e-10 (the mixed-precision configuration)")
+    ap.add_argument("--inner", default="f32", choices=["f32", "bf16"],
+                    help="coefficient records of the inner CG sweeps")
+    ap.add_argument("--precond", type=int, default=0, help="0: plain CG (Alg. 1); 1: Jacobi")
+    ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--maxit", type=int, default=200000)
+    ap.add_argument("--allow-notconv", action="store_true",
+                    help="record solves that stop at maxit instead of failing")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="solves timed end to end with host buffers (0 = skip)")
@@ -74,9 +83,23 @@ def parse():
 
 
 def workload_desc(a):
+    solver = ("plain CG" if a.precond == 0 else "Jacobi-preconditioned CG") + \
+        (", FP32 records" if a.inner == "f32" else ", BF16 records")
+    if a.workload == "channelized":
+        return (f"channelized TPFA pressure solve {a.nx}x{a.ny}x{a.nz}, lnK~N(0,2^2) background "
+                f"plus 8 sinusoidal channels 1e4x more permeable, Dirichlet p=1/0 on the x end "
+                f"layers, {solver} refined to FP64 relative residual {a.tol:g}")
     return (f"paper-scale TPFA pressure solve {a.nx}x{a.ny}x{a.nz}, lnK~N(0,1.5^2) per "
             f"(i,j,k//8), d=1e-3, well pair q=+-1 at opposite corners, no Dirichlet, "
-            f"CG to FP64-checked relative residual {a.tol:g}")
+            f"{solver} to FP64-checked relative residual {a.tol:g}")
+
+
+def finish_args(a):
+    if a.workload == "channelized" and (a.nx, a.ny, a.nz) == (1024, 1024, 256):
+        a.nx = a.ny = a.nz = 256
+    if a.tol is None:
+        a.tol = 1e-10 if a.workload == "channelized" else 1e-6
+    return a
 
 
 # ----------------------------------------------------------------------------
@@ -84,12 +107,23 @@ def workload_desc(a):
 # ----------------------------------------------------------------------------
 
 SAMPLE = (128, 128, 64)
+SAMPLE_CHANNELS = (64, 64, 64)
 
 
-def oracle_step(O, iters):
+def oracle_step(O, iters, workload="paper"):
     """Oracle on a bounded sample of the same recipe: assemble the CSR of a
-    128x128x64 block, build the right-hand side, run `iters` CG iterations,
-    evaluate the FP64 residual.  Returns cell-updates done."""
+    128x128x64 block (64^3 for the channelized recipe), build the
+    right-hand side, run `iters` CG iterations, evaluate the FP64 residual.
+    Returns cell-updates done."""
+    if workload == "channelized":
+        nx, ny, nz = SAMPLE_CHANNELS
+        w = synth.channelized(seed=0, n=nx)
+        g = O.Grid(nx, ny, nz)
+        A = O.assemble(g, w["K"], w["mask"], 0.0)
+        b = O.rhs(g, w["K"], w["mask"], None, w["pD"])
+        x, st, it, _ = O.cg(A, b, tol=0.0, maxit=iters)
+        float(np.linalg.norm(b - A.matvec(x)))
+        return nx * ny * nz * it
     nx, ny, nz = SAMPLE
     K = synth.lognormal_field(nx, ny, nz, 1.5, 0, layer=8)
     idx, val = synth.well_pair(nx, ny, nz)
@@ -103,25 +137,28 @@ def oracle_step(O, iters):
     return nx * ny * nz * it
 
 
-def oracle_sample_iters(O, target_s=12.0):
+def oracle_sample_iters(O, target_s=12.0, workload="paper"):
     t = time.perf_counter()
-    oracle_step(O, 5)
+    oracle_step(O, 5, workload)
     per = (time.perf_counter() - t) / 5
     return max(5, int(target_s / per))
 
 
-def cpu_baseline(target_s=12.0):
+def sample_desc(workload):
+    s = SAMPLE_CHANNELS if workload == "channelized" else SAMPLE
+    return f"{s[0]}x{s[1]}x{s[2]} block of the same recipe"
+
+
+def cpu_baseline(target_s=12.0, workload="paper"):
     from oracle import oracle as O
     O.build()
-    iters = oracle_sample_iters(O, target_s)
+    iters = oracle_sample_iters(O, target_s, workload)
     t = time.perf_counter()
-    units = oracle_step(O, iters)
+    units = oracle_step(O, iters, workload)
     dt = time.perf_counter() - t
     return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} block of the same recipe "
-                      f"(sigma 1.5, 8-layer correlation, d=1e-3, corner wells): CSR assembly, "
-                      f"RHS, {iters} CG iterations, FP64 residual; single-threaded C, "
-                      f"{dt:.1f} s"}
+            "sample": f"{sample_desc(workload)}: CSR assembly, RHS, {iters} CG iterations, "
+                      f"FP64 residual; single-threaded C, {dt:.1f} s"}
 
 
 def run_reference(a, rank, world):
@@ -129,18 +166,18 @@ def run_reference(a, rank, world):
         return
     from oracle import oracle as O
     O.build()
-    iters = oracle_sample_iters(O, 10.0)
+    iters = oracle_sample_iters(O, 10.0, a.workload)
     for _ in range(a.warmup):
-        oracle_step(O, iters)
+        oracle_step(O, iters, a.workload)
     times, units = [], 0
     for _ in range(a.steps):
         t = time.perf_counter()
-        units += oracle_step(O, iters)
+        units += oracle_step(O, iters, a.workload)
         times.append(time.perf_counter() - t)
     tot = sum(times)
     val = units / tot
-    sample = (f"each step: {SAMPLE[0]}x{SAMPLE[1]}x{SAMPLE[2]} block of the same recipe, CSR "
-              f"assembly, RHS, {iters} CG iterations, FP64 residual")
+    sample = (f"each step: {sample_desc(a.workload)}, CSR assembly, RHS, {iters} CG iterations, "
+              f"FP64 residual")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
@@ -252,7 +289,7 @@ def combine_ranks(ms, iters, e2e_ms, e2e_iters, device):
 
 
 def main():
-    a = parse()
+    a = finish_args(parse())
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -275,14 +312,22 @@ def main():
 
     nx, ny, nz = a.nx, a.ny, a.nz
     n = nx * ny * nz
-    w = synth.paper_scale(seed=a.seed, nx=nx, ny=ny, nz=nz)
-    K_host = torch.from_numpy(w["K"]).pin_memory()
-    idx_host = torch.from_numpy(w["src_idx"]).pin_memory()
-    val_host = torch.from_numpy(w["src_val"]).pin_memory()
+    if a.workload == "channelized":
+        if not (nx == ny == nz):
+            raise SystemExit("the channelized workload is cubic: give nx = ny = nz")
+        w = synth.channelized(seed=a.seed, n=nx)
+    else:
+        w = synth.paper_scale(seed=a.seed, nx=nx, ny=ny, nz=nz)
+    # host inputs (pinned) and their device copies
+    host = {"K": torch.from_numpy(w["K"]).pin_memory(),
+            "si": torch.from_numpy(w["src_idx"]).pin_memory(),
+            "sv": torch.from_numpy(w["src_val"]).pin_memory()}
+    if w["mask"] is not None:
+        host["mask"] = torch.from_numpy(w["mask"]).pin_memory()
+        host["pD"] = torch.from_numpy(w["pD"]).pin_memory()
     d0 = w["d"]
+    inp = {k: v.to(dev) for k, v in host.items()}
 
-    K = K_host.to(dev)
-    sidx, sval = idx_host.to(dev), val_host.to(dev)
     ctx = tpfa.Context(nx, ny, nz, device=dev)
     if a.tile_vy:
         ctx.set_option("tile_vy", a.tile_vy)
@@ -293,34 +338,45 @@ def main():
     ctx.set_option("loop", a.loop)
     if a.scheme >= 0:
         ctx.set_option("scheme", a.scheme)
+    ctx.set_option("precond", a.precond)
     coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
     coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    coef16 = torch.empty((n, 4), dtype=torch.int16, device=dev) if a.inner == "bf16" else None
     b = torch.empty(n, dtype=torch.float64, device=dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
 
-    def step(Kd, si, sv):
-        ctx.build_trans(Kd, None, None, d0, coef=coef, coef64=coef64)
-        ctx.build_rhs(Kd, None, None, None, si, sv, b=b)
+    def build(d):
+        ctx.build_trans(d["K"], d.get("mask"), None, d0, coef=coef, coef64=coef64)
+        if coef16 is not None:
+            ctx.build_trans_bf16(d["K"], d.get("mask"), None, d0, coef16=coef16)
+        ns = d["si"].numel()
+        ctx.build_rhs(d["K"], d.get("mask"), None, d.get("pD"), d["si"] if ns else None,
+                      d["sv"] if ns else None, b=b)
         x.zero_()
-        _, info = ctx.cg_solve(coef, coef64, b, x=x, tol=a.tol, maxit=a.maxit)
-        if info["code"] not in (0,):
+        return coef16 if coef16 is not None else coef
+
+    def step(d):
+        inner = build(d)
+        _, info = ctx.cg_solve(inner, coef64, b, x=x, tol=a.tol, maxit=a.maxit)
+        if info["code"] not in ((0, 1) if a.allow_notconv else (0,)):
             raise RuntimeError(f"cg_solve returned {info}")
         return info
+
+    builds_per_step = 3 + (1 if coef16 is not None else 0)
+    K = inp["K"]
 
     if a.probe_iters > 0:
         ctx.set_option("loop", 1)
         ctx.set_option("chunk", 4)
-        ctx.build_trans(K, None, None, d0, coef=coef, coef64=coef64)
-        ctx.build_rhs(K, None, None, None, sidx, sval, b=b)
-        x.zero_()
-        _, info = ctx.cg_solve(coef, coef64, b, x=x, tol=a.tol, maxit=a.probe_iters, check=False)
+        inner = build(inp)
+        _, info = ctx.cg_solve(inner, coef64, b, x=x, tol=a.tol, maxit=a.probe_iters, check=False)
         torch.cuda.synchronize()
         print(json.dumps({"probe": info}))
         ctx.close()
         return
 
     for _ in range(a.warmup):
-        step(K, sidx, sval)
+        step(inp)
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream(dev)
@@ -331,14 +387,14 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     e0.record(stream)
-    infos = [step(K, sidx, sval) for _ in range(a.steps)]
+    infos = [step(inp) for _ in range(a.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     iters = sum(i["iters"] for i in infos)
-    launches = sum(3 + i["kernel_launches"] for i in infos)
+    launches = sum(builds_per_step + i["kernel_launches"] for i in infos)
     inner_ms = sum(i["inner_ms"] for i in infos)
 
     # end to end through the public API with host buffers: H2D of the step's
@@ -346,8 +402,7 @@ def main():
     e2e = None
     if a.e2e_steps > 0:
         x_host = torch.empty(n, dtype=torch.float64).pin_memory()
-        Ke = torch.empty_like(K)
-        sie, sve = torch.empty_like(sidx), torch.empty_like(sval)
+        dev_in = {k: torch.empty_like(v) for k, v in inp.items()}
         barrier()
         torch.cuda.synchronize()
         e2 = torch.cuda.Event(enable_timing=True)
@@ -355,10 +410,9 @@ def main():
         e2.record(stream)
         e2e_iters = 0
         for _ in range(a.e2e_steps):
-            Ke.copy_(K_host, non_blocking=True)
-            sie.copy_(idx_host, non_blocking=True)
-            sve.copy_(val_host, non_blocking=True)
-            info = step(Ke, sie, sve)
+            for k, v in host.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            info = step(dev_in)
             e2e_iters += info["iters"]
             x_host.copy_(x, non_blocking=True)
         e3.record(stream)
@@ -373,33 +427,40 @@ def main():
         value = cell_updates_per_s(n, iters_all, ms_max)
         peak, peak_kind = measured_hbm_peak()
         sweep_ms = inner_ms / max(iters, 1)
-        algo = SWEEP_BYTES_PER_CELL * n
+        bpc = SWEEP_BYTES_PER_CELL - (8 if coef16 is not None else 0)
+        algo = bpc * n
         achieved = algo / (sweep_ms / 1e3) / 1e9
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if coef16 is None else "bf16-coef/f32", "data": "synthetic",
             "config": {"workload": workload_desc(a), "nx": nx, "ny": ny, "nz": nz,
                        "tol": a.tol, "parallelism": f"replicas{world}",
+                       "inner": a.inner, "precond": ["none", "jacobi"][a.precond],
                        "l2": "inputs larger than L2 (no flush needed)",
                        "iters_per_solve": iters / a.steps,
                        "time_to_tol_s": ms / 1e3 / a.steps,
                        "rel_res_fp64": infos[-1]["rel_res_fp64"],
+                       "converged": all(i["code"] == 0 for i in infos),
                        "refinements": infos[-1]["outer"]},
             "roofline": {"kernel": "cg sweep (fused CG iteration)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "bytes_per_cell": SWEEP_BYTES_PER_CELL,
-                         "sweep_ms": sweep_ms, "traffic": sweep_traffic(nx, ny, nz)},
+                         "bytes_per_cell": bpc, "sweep_ms": sweep_ms,
+                         "traffic": (sweep_traffic(nx, ny, nz)
+                                     if (coef16 is None and a.precond == 0 and a.scheme <= 0)
+                                     else None)},
             "gpu_launches": launches,
         }
         if e2e:
             out["e2e"] = {"value": n * e2e_iters_all / (e2e_ms_max / 1e3), "unit": UNIT,
-                          "h2d_bytes_per_step": int(K.numel() * 8 + sidx.numel() * 16),
-                          "d2h_bytes_per_step": int(n * 8)}
+                          "h2d_bytes_per_step": int(sum(v.numel() * v.element_size()
+                                                        for v in host.values())),
+                          "d2h_bytes_per_step": int(n * 8), "steps": a.e2e_steps}
         out["clocks"] = clk
         if not a.no_cpu:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(workload=a.workload)
         print(json.dumps(out))
     ctx.close()
     if world > 1:

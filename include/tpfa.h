@@ -93,7 +93,11 @@ enum tpfa_option {
   TPFA_OPT_STAGES = 7,       /* shared-memory plane stages per warp: 3 or 4 (default 4; 4 needs VY = 4) */
   TPFA_OPT_SCHEME = 8,       /* CG sweep: 0 = stores q = A p (48 B/cell, default), 1 = recomputes it (40 B/cell) */
   TPFA_OPT_STAGES40 = 9,     /* stages of the scheme-1 sweep: 4, 5 or 6 with 2 warps/block, 4 or 5 with 4 (default 5) */
-  TPFA_OPT_WARPS40 = 10      /* warps per block of the scheme-1 sweep: 2 (default) or 4                  */
+  TPFA_OPT_WARPS40 = 10,     /* warps per block of the scheme-1 sweep: 2 (default) or 4                  */
+  TPFA_OPT_INNER_RTOL_BF16 = 11, /* lower bound on the inner relative tolerance of cg_solve_bf16 (1e-3) */
+  TPFA_OPT_PRECOND = 12      /* inner CG of cg_solve: 0 = unpreconditioned (Alg. 1, default),
+                                1 = Jacobi, M = diag(D) (FP32 records only; cg_solve_bf16 with
+                                it set returns TPFA_EINVAL)                                       */
 };
 
 /* Create a context for one grid on the current CUDA device.  Allocates the
@@ -187,6 +191,41 @@ int tpfa_residual64(tpfa_ctx* ctx, const double* coef64, const double* b, const 
  */
 int cg_solve(tpfa_ctx* ctx, const float* coef, const double* coef64, const double* b, double* x,
              double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
+
+/*
+ * Mixed precision (BF16 coefficients, FP32 inner CG, FP64 refinement).
+ *
+ * BF16 record ("coef16"): 4 bf16 values per cell, cell-interleaved, 8 bytes:
+ *     coef16[4c+0..2] = Tx', Ty', Tz'  eliminated face transmissibilities as in
+ *                                      the FP32 record, rounded to nearest-even
+ *     coef16[4c+3]    = E   d_K + sum of T_KL over faces to Dirichlet
+ *                           neighbours (1 on Dirichlet cells)
+ * The diagonal is not stored: the sweep forms D = T'(-x) + T'(+x) + T'(-y) +
+ * T'(+y) + T'(-z) + T'(+z) + E in FP32 from the six face values it reads
+ * anyway.  The BF16 operator is therefore the TPFA operator of the rounded
+ * face values: symmetric positive definite like the FP64 one, with x'Ax
+ * within a factor 1 +- 2^-9 of it, so iterative refinement against the
+ * FP64 residual contracts the error by about 2^-9 per step.
+ */
+
+/* BF16 records (Eq. 4 as tpfa_build_trans, then rounded).  coef16: dev, 4N
+ * uint16 (bf16 bit patterns), 8-byte aligned.  Other arguments as for
+ * tpfa_build_trans. */
+int tpfa_build_trans_bf16(tpfa_ctx* ctx, const double* K, const uint8_t* dirichlet,
+                          const double* d, double d_uniform, uint16_t* coef16, void* stream);
+
+/* tpfa_apply with BF16 records (Eq. 6 / Alg. 2, FP32 arithmetic on the
+ * exactly widened BF16 values; D formed as stated above). */
+int tpfa_apply_bf16(tpfa_ctx* ctx, const uint16_t* coef16, const float* p, float* Ap,
+                    double* pAp, void* stream);
+
+/* cg_solve with the BF16 operator inside the FP32 CG sweeps: each refinement
+ * step solves A_bf16 e = r (relative tolerance max(tol/2 / current relative
+ * residual, TPFA_OPT_INNER_RTOL_BF16)), then x += e and r = b - A x in FP64
+ * with coef64.  Stops when the FP64 relative residual <= tol.  Arguments
+ * and return codes as cg_solve. */
+int cg_solve_bf16(tpfa_ctx* ctx, const uint16_t* coef16, const double* coef64, const double* b,
+                  double* x, double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
 
 /*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device

@@ -17,11 +17,13 @@ struct tpfa_ctx {
   int num_sms;
   // options
   double inner_rtol;
+  double inner_rtol_bf16;
   int max_outer;
   int loop_mode;
   int vy;
   int stages;      // stages of the stored-q sweep and of tpfa_apply
   int scheme;      // CG sweep: 0 = stored q (48 B/cell), 1 = recomputed q (40 B/cell)
+  int precond;     // 0 = none (Alg. 1), 1 = Jacobi
   int stages40;    // stages of the recomputed-q sweep
   int warps40;     // warps per block of the recomputed-q sweep
   int zc;
@@ -40,6 +42,8 @@ struct tpfa_ctx {
   // iteration-loop graph
   cudaGraphExec_t loop_exec;
   const void* loop_key_coef;
+  bool loop_key_b16;
+  int loop_key_precond;
   int loop_key_vy, loop_key_stages, loop_key_scheme, loop_key_stages40, loop_key_warps40;
   int loop_key_zc, loop_key_mode, loop_key_chunk;
   cudaStream_t cap_stream;
@@ -116,17 +120,28 @@ int use_device(const tpfa_ctx* c) {
 
 Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->stages, c->zc, c->num_sms); }
 
+int cg_scheme(const tpfa_ctx* c, bool b16);
+
 // the sweep the CG loop runs
-Sweep ctx_cg_sweep(const tpfa_ctx* c) {
-  return c->scheme == 1 ? plan_sweep40(c->g, c->stages40, c->warps40, c->zc, c->num_sms)
-                        : ctx_sweep(c);
+Sweep ctx_cg_sweep(const tpfa_ctx* c, bool b16 = false) {
+  return cg_scheme(c, b16) == 1 ? plan_sweep40(c->g, c->stages40, c->warps40, c->zc, c->num_sms)
+                                : ctx_sweep(c);
 }
 
-cudaError_t launch_cg(const tpfa_ctx* c, const Sweep& sw, const float4* cf,
+// scheme 1 has neither a BF16 nor a preconditioned variant: those solves
+// always run the stored-q sweep
+int cg_scheme(const tpfa_ctx* c, bool b16) { return (b16 || c->precond) ? 0 : c->scheme; }
+
+cudaError_t launch_cg(const tpfa_ctx* c, const Sweep& sw, const void* coef, bool b16,
                       unsigned long long cond, int use_cond, cudaStream_t s) {
-  return c->scheme == 1
-      ? launch_cg40_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, cond, use_cond, s)
-      : launch_cg_sweep(c->g, sw, cf, c->v, c->st, c->partials, c->counter, cond, use_cond, s);
+  if (c->precond == 1)
+    return launch_cg_sweep_jacobi(c->g, sw, static_cast<const float4*>(coef), c->v, c->st,
+                                  c->partials, c->counter, cond, use_cond, s);
+  return cg_scheme(c, b16) == 1
+      ? launch_cg40_sweep(c->g, sw, static_cast<const float4*>(coef), c->v, c->st, c->partials,
+                          c->counter, cond, use_cond, s)
+      : launch_cg_sweep(c->g, sw, coef, b16, c->v, c->st, c->partials, c->counter, cond,
+                        use_cond, s);
 }
 
 int ensure_partials(tpfa_ctx* c, size_t need) {
@@ -181,22 +196,25 @@ void drop_loop(tpfa_ctx* c) {
 // vector sets ping-pong); the last block of each sweep sets the loop
 // condition.  Mode 1: `chunk` sweeps back to back, the host polls between
 // launches.
-int ensure_loop(tpfa_ctx* c, const float* coef) {
-  if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_vy == c->vy &&
+int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
+  if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_b16 == b16 &&
+      c->loop_key_precond == c->precond && c->loop_key_vy == c->vy &&
       c->loop_key_stages == c->stages && c->loop_key_scheme == c->scheme &&
       c->loop_key_stages40 == c->stages40 && c->loop_key_warps40 == c->warps40 &&
       c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
     return TPFA_OK;
   drop_loop(c);
-  const Sweep sw = ctx_cg_sweep(c);
+  if ((b16 || c->precond) && c->vy != 4) return TPFA_EINVAL;  // 4-row warp tiles only
+  if (b16 && c->precond) return TPFA_EINVAL;  // Jacobi needs D, which BF16 records do not store
+  const Sweep sw = ctx_cg_sweep(c, b16);
   int rc = ensure_partials(c, (size_t)sw.nblocks * 4);
   if (rc) return rc;
-  if ((c->scheme == 1 ? sweep40_blocks_per_sm(c->stages40, c->warps40)
-                      : sweep_blocks_per_sm(c->vy, c->stages)) < 1)
+  if ((cg_scheme(c, b16) == 1 ? sweep40_blocks_per_sm(c->stages40, c->warps40)
+                              : sweep_blocks_per_sm(c->vy, c->stages)) < 1)
     return TPFA_ECUDA;
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = c->cap_stream;
-  const float4* cf = reinterpret_cast<const float4*>(coef);
+  const void* cf = coef;
   if (c->loop_mode == 0) {
     CK(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle h;
@@ -216,8 +234,8 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = launch_cg(c, sw, cf, h, 1, cs);
-      cudaError_t e2 = launch_cg(c, sw, cf, h, 1, cs);
+      cudaError_t e1 = launch_cg(c, sw, cf, b16, h, 1, cs);
+      cudaError_t e2 = launch_cg(c, sw, cf, b16, h, 1, cs);
       e = cudaStreamEndCapture(cs, &body);
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
@@ -230,7 +248,7 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t el = cudaSuccess;
     for (int i = 0; i < c->chunk; ++i) {
-      cudaError_t e = launch_cg(c, sw, cf, 0, 0, cs);
+      cudaError_t e = launch_cg(c, sw, cf, b16, 0, 0, cs);
       if (e != cudaSuccess) el = e;
     }
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -248,6 +266,8 @@ int ensure_loop(tpfa_ctx* c, const float* coef) {
     return TPFA_ECUDA;
   }
   c->loop_key_coef = coef;
+  c->loop_key_b16 = b16;
+  c->loop_key_precond = c->precond;
   c->loop_key_vy = c->vy;
   c->loop_key_stages = c->stages;
   c->loop_key_scheme = c->scheme;
@@ -307,11 +327,13 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->g.plane = grid->nx * grid->ny;
   c->g.n = c->g.plane * grid->nz;
   c->inner_rtol = 1e-6;
+  c->inner_rtol_bf16 = 1e-3;
   c->max_outer = 20;
   c->loop_mode = 0;
   c->vy = 4;
   c->stages = 4;
   c->scheme = 0;
+  c->precond = 0;
   c->stages40 = 5;
   c->warps40 = 2;
   c->zc = 0;
@@ -378,6 +400,10 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
       if (!(value > 0.0 && value < 1.0)) return TPFA_EINVAL;
       c->inner_rtol = value;
       return TPFA_OK;
+    case TPFA_OPT_INNER_RTOL_BF16:
+      if (!(value > 0.0 && value < 1.0)) return TPFA_EINVAL;
+      c->inner_rtol_bf16 = value;
+      return TPFA_OK;
     case TPFA_OPT_MAX_OUTER:
       if (value < 1 || value > 1000) return TPFA_EINVAL;
       c->max_outer = (int)value;
@@ -395,6 +421,10 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
     case TPFA_OPT_STAGES:
       if (!sweep_config_ok(c->vy, (int)value) || value != floor(value)) return TPFA_EINVAL;
       c->stages = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_PRECOND:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      c->precond = (int)value;
       return TPFA_OK;
     case TPFA_OPT_SCHEME:
       if (value != 0 && value != 1) return TPFA_EINVAL;
@@ -456,23 +486,49 @@ int tpfa_build_rhs(tpfa_ctx* c, const double* K, const uint8_t* dirichlet, const
   return TPFA_OK;
 }
 
-int tpfa_apply(tpfa_ctx* c, const float* coef, const float* p, float* Ap, double* pAp,
-               void* stream) {
+static int apply_impl(tpfa_ctx* c, const void* coef, bool b16, const float* p, float* Ap,
+                      double* pAp, void* stream) {
   if (c == nullptr) return TPFA_EINVAL;
   int rc = use_device(c);
   if (rc) return rc;
   const size_t n = (size_t)c->g.n;
-  if (!dev_ok(coef, n * 16, 16, c->device) || !dev_ok(p, n * 4, 4, c->device) ||
-      !dev_ok(Ap, n * 4, 4, c->device) || !opt_dev_ok(pAp, 8, 8, c->device))
+  if (!dev_ok(coef, n * (b16 ? 8 : 16), b16 ? 8 : 16, c->device) ||
+      !dev_ok(p, n * 4, 4, c->device) || !dev_ok(Ap, n * 4, 4, c->device) ||
+      !opt_dev_ok(pAp, 8, 8, c->device))
     return TPFA_EINVAL;
   if ((const void*)p == (const void*)Ap) return TPFA_EINVAL;
+  if (b16 && c->vy != 4) return TPFA_EINVAL;
   const Sweep sw = ctx_sweep(c);
   if (pAp != nullptr) {
     rc = ensure_partials(c, (size_t)sw.nblocks);
     if (rc) return rc;
   }
-  CK(launch_apply(c->g, sw, reinterpret_cast<const float4*>(coef), p, Ap, pAp, c->partials,
-                  c->counter, (cudaStream_t)stream));
+  CK(launch_apply(c->g, sw, coef, b16, p, Ap, pAp, c->partials, c->counter, (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
+int tpfa_apply(tpfa_ctx* c, const float* coef, const float* p, float* Ap, double* pAp,
+               void* stream) {
+  return apply_impl(c, coef, false, p, Ap, pAp, stream);
+}
+
+int tpfa_apply_bf16(tpfa_ctx* c, const uint16_t* coef16, const float* p, float* Ap, double* pAp,
+                    void* stream) {
+  return apply_impl(c, coef16, true, p, Ap, pAp, stream);
+}
+
+int tpfa_build_trans_bf16(tpfa_ctx* c, const double* K, const uint8_t* dirichlet, const double* d,
+                          double d_uniform, uint16_t* coef16, void* stream) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(K, n * 8, 8, c->device) || !opt_dev_ok(dirichlet, n, 1, c->device) ||
+      !opt_dev_ok(d, n * 8, 8, c->device) || !dev_ok(coef16, n * 8, 8, c->device))
+    return TPFA_EINVAL;
+  if (d == nullptr && !(d_uniform >= 0.0 && isfinite(d_uniform))) return TPFA_EINVAL;
+  CK(launch_build_trans_bf16(c->g, c->geo, K, dirichlet, d, d_uniform,
+                             reinterpret_cast<uint2*>(coef16), (cudaStream_t)stream));
   return TPFA_OK;
 }
 
@@ -492,8 +548,9 @@ int tpfa_residual64(tpfa_ctx* c, const double* coef64, const double* b, const do
   return TPFA_OK;
 }
 
-int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double* b, double* x,
-             double tol, int64_t maxit, tpfa_cg_info* info, void* stream) {
+static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coef64,
+                      const double* b, double* x, double tol, int64_t maxit, tpfa_cg_info* info,
+                      void* stream) {
   tpfa_cg_info inf;
   memset(&inf, 0, sizeof(inf));
   inf.rel_res_fp64 = NAN;
@@ -504,14 +561,15 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
   rc = use_device(c);
   if (rc) return rc;
   const size_t n = (size_t)c->g.n;
-  if (!dev_ok(coef, n * 16, 16, c->device) || !dev_ok(coef64, n * 32, 16, c->device) ||
-      !dev_ok(b, n * 8, 8, c->device) || !dev_ok(x, n * 8, 8, c->device))
+  if (!dev_ok(coef, n * (b16 ? 8 : 16), b16 ? 8 : 16, c->device) ||
+      !dev_ok(coef64, n * 32, 16, c->device) || !dev_ok(b, n * 8, 8, c->device) ||
+      !dev_ok(x, n * 8, 8, c->device))
     return TPFA_EINVAL;
   if ((const void*)b == (const void*)x) return TPFA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   rc = ensure_vectors(c);
   if (rc) return rc;
-  rc = ensure_loop(c, coef);
+  rc = ensure_loop(c, coef, b16);
   if (rc) return rc;
   CK(cudaMemsetAsync(c->counter, 0, 64, s));
   CK(cudaEventRecord(c->ev[0], s));
@@ -545,7 +603,8 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
       if (total_iters >= maxit) { status = TPFA_NOTCONV; break; }
       if (outer >= c->max_outer) { status = TPFA_NOTCONV; break; }
       double rtol = 0.5 * tol / rel;
-      if (rtol < c->inner_rtol) rtol = c->inner_rtol;
+      const double floor_rtol = b16 ? c->inner_rtol_bf16 : c->inner_rtol;
+      if (rtol < floor_rtol) rtol = floor_rtol;
       if (rtol > 0.5) rtol = 0.5;
       CK(launch_prepare(c->g, c->r64, c->v, c->st, rtol, (long long)(maxit - total_iters), s));
       launches += 1;
@@ -567,10 +626,11 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
           inner_ms += ms;
           if (hs->done == kRunning) continue;
         }
-        if (c->scheme == 1)
+        if (cg_scheme(c, b16) == 1)
           CK(launch_finalize40(c->g, c->v, c->st, c->elem_nblocks, s));
         else
-          CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks, s));
+          CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks,
+                             c->precond ? static_cast<const float4*>(coef) : nullptr, s));
         launches += 1;
         rc = read_state(c, s);
         if (rc) return rc;
@@ -588,7 +648,7 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
       {
         // scheme 1 does not advance the recursive residual in finalize: use
         // the fused estimate when the loop stopped on it
-        const bool est = c->scheme == 1 && (inner_status == kConvEst || inner_status == kMaxit);
+        const bool est = cg_scheme(c, b16) == 1 && (inner_status == kConvEst || inner_status == kMaxit);
         const double rr_in = est ? hs->rho_est : hs->rho;
         rel_inner = hs->rho0 > 0 ? sqrt(rr_in / hs->rho0) : 0.0;
       }
@@ -630,6 +690,16 @@ int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double*
   inf.kernel_launches = launches;
   if (info) *info = inf;
   return status;
+}
+
+int cg_solve(tpfa_ctx* c, const float* coef, const double* coef64, const double* b, double* x,
+             double tol, int64_t maxit, tpfa_cg_info* info, void* stream) {
+  return solve_impl(c, coef, false, coef64, b, x, tol, maxit, info, stream);
+}
+
+int cg_solve_bf16(tpfa_ctx* c, const uint16_t* coef16, const double* coef64, const double* b,
+                  double* x, double tol, int64_t maxit, tpfa_cg_info* info, void* stream) {
+  return solve_impl(c, coef16, true, coef64, b, x, tol, maxit, info, stream);
 }
 
 }  // extern "C"

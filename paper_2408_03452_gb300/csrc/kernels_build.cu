@@ -8,6 +8,8 @@
 // two (equal) mobilities.  Faces on the outer boundary carry no flow.
 // Dirichlet cells (Eq. 3) keep the identity row; their couplings to interior
 // cells move to the right-hand side.
+#include <cuda_bf16.h>
+
 #include "tpfa_internal.cuh"
 
 namespace tpfa {
@@ -67,6 +69,50 @@ build_trans_kernel(Grid g, Geo geo, const double* __restrict__ K, const uint8_t*
       coef64[2 * c] = make_double2(t[0], t[1]);
       coef64[2 * c + 1] = make_double2(t[2], diag);
     }
+  }
+}
+
+// Compact BF16 record for the mixed-precision inner solve: (Tx', Ty', Tz', E),
+// each rounded to nearest-even from FP64, with E = d_K + sum of the T_KL to
+// Dirichlet neighbours (faces -x..+z in order; E = 1 and T' = 0 on Dirichlet
+// cells).  The sweep forms D = sum of the six T' + E in FP32, so the BF16
+// operator is the TPFA operator of the rounded face values: symmetric
+// positive definite whenever the FP64 one is, with x'Ax within a factor
+// (1 +- 2^-9) of the FP64 operator's.
+__global__ void __launch_bounds__(kElemThreads)
+build_trans_bf16_kernel(Grid g, Geo geo, const double* __restrict__ K,
+                        const uint8_t* __restrict__ mask, const double* __restrict__ d, double d0,
+                        ushort4* __restrict__ coef16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    const int64_t i = c % g.nx, j = (c / g.nx) % g.ny, k = c / g.plane;
+    double t[3] = {0.0, 0.0, 0.0};
+    double e;
+    if (is_dir(mask, c)) {
+      e = 1.0;
+    } else {
+      const double kc = K[c];
+      e = d != nullptr ? d[c] : d0;
+      if (i > 0 && is_dir(mask, c - 1)) e += face_trans(K[c - 1], kc, geo.ax, geo.hx);
+      if (i + 1 < g.nx) {
+        const double T = face_trans(kc, K[c + 1], geo.ax, geo.hx);
+        if (is_dir(mask, c + 1)) e += T; else t[0] = T;
+      }
+      if (j > 0 && is_dir(mask, c - g.nx)) e += face_trans(K[c - g.nx], kc, geo.ay, geo.hy);
+      if (j + 1 < g.ny) {
+        const double T = face_trans(kc, K[c + g.nx], geo.ay, geo.hy);
+        if (is_dir(mask, c + g.nx)) e += T; else t[1] = T;
+      }
+      if (k > 0 && is_dir(mask, c - g.plane)) e += face_trans(K[c - g.plane], kc, geo.az, geo.hz);
+      if (k + 1 < g.nz) {
+        const double T = face_trans(kc, K[c + g.plane], geo.az, geo.hz);
+        if (is_dir(mask, c + g.plane)) e += T; else t[2] = T;
+      }
+    }
+    coef16[c] = make_ushort4(__bfloat16_as_ushort(__double2bfloat16(t[0])),
+                             __bfloat16_as_ushort(__double2bfloat16(t[1])),
+                             __bfloat16_as_ushort(__double2bfloat16(t[2])),
+                             __bfloat16_as_ushort(__double2bfloat16(e)));
   }
 }
 
@@ -137,6 +183,14 @@ cudaError_t launch_build_trans(const Grid& g, const tpfa_grid& geo, const double
                                double* coef64, cudaStream_t s) {
   build_trans_kernel<<<grid_for(g), kElemThreads, 0, s>>>(g, make_geo(geo), K, mask, d, d0, coef,
                                                           reinterpret_cast<double2*>(coef64));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_trans_bf16(const Grid& g, const tpfa_grid& geo, const double* K,
+                                    const uint8_t* mask, const double* d, double d0,
+                                    uint2* coef16, cudaStream_t s) {
+  build_trans_bf16_kernel<<<grid_for(g), kElemThreads, 0, s>>>(
+      g, make_geo(geo), K, mask, d, d0, reinterpret_cast<ushort4*>(coef16));
   return cudaGetLastError();
 }
 

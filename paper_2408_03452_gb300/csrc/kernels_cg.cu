@@ -31,7 +31,8 @@ struct SweepArgs {
   Grid g;
   int64_t nwx, nwy, nwarps;
   int zc;
-  const float4* coef;
+  const float4* coef;     // FP32 records (Tx, Ty, Tz, D)
+  const uint2* coef16;    // BF16 records (Tx, Ty, Tz, E), D = sum of the six T + E
   // plain operator
   const float* p;
   float* Ap;
@@ -46,24 +47,52 @@ struct SweepArgs {
 
 // Shared-memory stage of one warp for one z-plane: the coefficient records
 // of the warp's VY rows, r/q/p (or p alone) of rows -1..VY, x of the VY
-// rows, and Ty of row -1.  Lane-minor, each lane reads only its own column.
-template <int VY>
+// rows, and the word holding Ty of row -1.  Lane-minor, each lane reads only
+// its own column.  Records are 16 bytes (FP32) or 8 bytes (BF16).
+// With Jacobi preconditioning the stage also holds D of the halo rows -1
+// and VY (the records of the own rows carry theirs).
+template <int VY, bool B16, bool JAC = false>
 struct StageLayout {
-  static constexpr int kCoef = 0;                               // float4 [VY][32]
-  static constexpr int kVec = VY * 32 * 16;                     // float [3][VY+2][32]
+  static constexpr int kRec = B16 ? 8 : 16;
+  static constexpr int kCoef = 0;                               // record [VY][32]
+  static constexpr int kVec = VY * 32 * kRec;                   // float [3][VY+2][32]
   static constexpr int kE = kVec + 3 * (VY + 2) * 32 * 4;       // float [VY][32]
-  static constexpr int kTy = kE + VY * 32 * 4;                  // float [32]
-  static constexpr int kBytes = kTy + 32 * 4;
+  static constexpr int kTy = kE + VY * 32 * 4;                  // 32-bit word [32]
+  static constexpr int kDh = kTy + 32 * 4;                      // float [2][32] (JAC only)
+  static constexpr int kBytes = kDh + (JAC ? 2 * 32 * 4 : 0);
 };
 
-template <int VY, int S>
-constexpr int sweep_smem_bytes() { return kSweepWarps * S * StageLayout<VY>::kBytes; }
+template <int VY, int S, bool B16, bool JAC = false>
+constexpr int sweep_smem_bytes() { return kSweepWarps * S * StageLayout<VY, B16, JAC>::kBytes; }
 
-template <int VY, int S, bool CG, bool COND>
+// A staged record as (Tx, Ty, Tz, w): w = D for FP32 records, w = E (the
+// diagonal beyond the six face terms) for BF16 records.
+template <bool B16>
+__device__ __forceinline__ float4 rec_at(const unsigned char* base, int i) {
+  if (B16) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[i];
+    return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+  }
+  return reinterpret_cast<const float4*>(base)[i];
+}
+// Ty from the staged Ty word of row -1
+template <bool B16>
+__device__ __forceinline__ float ty_word(const unsigned char* base, int lane) {
+  const unsigned w = reinterpret_cast<const unsigned*>(base)[lane];
+  return B16 ? bf16_hi(w) : __uint_as_float(w);
+}
+
+// JAC: Jacobi-preconditioned CG (M = diag(D)), FP32 records only.  The
+// preconditioned residual z = r / D is formed on the fly, p_k = z_k + beta
+// p_{k-1}, and the four dots become r'z, p'q, z'q, q'D^-1 q, which give
+// alpha = r'z / p'q and (r - alpha q)' D^-1 (r - alpha q) by the same
+// identity as the plain iteration.  No extra vector is read or written.
+template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 sweep_kernel(const SweepArgs a) {
   static_assert(S >= 3, "the plane pipeline needs at least three stages");
-  using LY = StageLayout<VY>;
+  static_assert(!JAC || (CG && !B16), "Jacobi preconditioning is for FP32-record CG sweeps");
+  using LY = StageLayout<VY, B16, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid& g = a.g;
   float alpha = 0.f, beta = 0.f;
@@ -127,7 +156,7 @@ sweep_kernel(const SweepArgs a) {
         const int64_t zo = g.plane * (z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z));
         const bool own = outl && z >= z0 && z < z1;
         unsigned char* sb = wsm + (size_t)(j % S) * LY::kBytes;
-        float4* scf = reinterpret_cast<float4*>(sb + LY::kCoef);
+        unsigned char* scf = sb + LY::kCoef;
         float* sv = reinterpret_cast<float*>(sb + LY::kVec);
         float* se = reinterpret_cast<float*>(sb + LY::kE);
         float* sty = reinterpret_cast<float*>(sb + LY::kTy);
@@ -142,9 +171,16 @@ sweep_kernel(const SweepArgs a) {
           } else {
             cp4(sv + (2 * (VY + 2) + jj + 1) * 32 + lane, pin + src, ok);
           }
-          if (jj == -1) cp4(sty + lane, reinterpret_cast<const float*>(a.coef + src) + 1, ok);
+          if (jj == -1) {
+            if (B16) cp4(sty + lane, a.coef16 + src, ok);  // word 0 = Tx | Ty << 16
+            else cp4(sty + lane, reinterpret_cast<const float*>(a.coef + src) + 1, ok);
+          }
+          if (JAC && (jj == -1 || jj == VY))
+            cp4(reinterpret_cast<float*>(sb + LY::kDh) + (jj == -1 ? 0 : 32) + lane,
+                reinterpret_cast<const float*>(a.coef + src) + 3, ok);
           if (jj >= 0 && jj < VY) {
-            cp16(scf + jj * 32 + lane, a.coef + src, ok);
+            if (B16) cp8(reinterpret_cast<uint2*>(scf) + jj * 32 + lane, a.coef16 + src, ok);
+            else cp16(reinterpret_cast<float4*>(scf) + jj * 32 + lane, a.coef + src, ok);
             if (CG) cp4(se + jj * 32 + lane, a.v.e + src, ok && own);
           }
         }
@@ -170,14 +206,22 @@ sweep_kernel(const SweepArgs a) {
           const float r0 = sv[(0 * (VY + 2) + jj + 1) * 32 + lane];
           const float q0 = sv[(1 * (VY + 2) + jj + 1) * 32 + lane];
           r_ = fmaf(-alpha, q0, r0);  // Alg. 1 line 7 (previous iteration)
-          p_ = fmaf(beta, p0, r_);    // Alg. 1 line 10
+          float z_ = r_;
+          if (JAC) {
+            const float D = (jj == -1 || jj == VY)
+                ? reinterpret_cast<const float*>(sb + LY::kDh)[(jj == -1 ? 0 : 32) + lane]
+                : rec_at<false>(sb + LY::kCoef, jj * 32 + lane).w;
+            z_ = r_ * jac_inv(D);  // z = M^-1 r
+          }
+          p_ = fmaf(beta, p0, z_);    // Alg. 1 line 10
           if (jj >= 0 && jj < VY && own && ((rowok >> (jj + 1)) & 1u)) {
             const int64_t id = zo + o0 + jj * nxi;
             a.v.e[id] = fmaf(alpha, p0, se[jj * 32 + lane]);  // Alg. 1 line 6
             rout[id] = r_;
             pout[id] = p_;
-            s0 = fmaf(r_, r_, s0);
+            s0 = fmaf(r_, z_, s0);
           }
+          r_ = z_;  // the direction dots below use z (= r without preconditioning)
         }
         P[jj + 1] = p_;
         if (jj >= 0 && jj < VY) R[jj] = r_;
@@ -192,11 +236,10 @@ sweep_kernel(const SweepArgs a) {
     {  // plane z0 - 1: direction below the first plane, and its Tz
       float Pt[VY + 2], Rt[VY];
       form(0, Pt, Rt, s0);
-      const float4* scf = reinterpret_cast<const float4*>(wsm + LY::kCoef);
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
         Pm[jj] = Pt[jj + 1];
-        Tzm[jj] = scf[jj * 32 + lane].z;
+        Tzm[jj] = rec_at<B16>(wsm + LY::kCoef, jj * 32 + lane).z;
       }
     }
     issue(S - 1);
@@ -211,17 +254,17 @@ sweep_kernel(const SweepArgs a) {
       float Pp[VY + 2], Rp[VY];
       form(jf, Pp, Rp, s0);
       const unsigned char* sb = wsm + (size_t)((jf - 1) % S) * LY::kBytes;  // plane z
-      const float4* scf = reinterpret_cast<const float4*>(sb + LY::kCoef);
-      const float* sty = reinterpret_cast<const float*>(sb + LY::kTy);
       const int64_t zo = g.plane * z;
-      float s1 = 0.f, s2 = 0.f, s3 = 0.f, tyl = sty[lane];
+      float s1 = 0.f, s2 = 0.f, s3 = 0.f, tyl = ty_word<B16>(sb + LY::kTy, lane);
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
-        const float4 cf = scf[jj * 32 + lane];
+        float4 cf = rec_at<B16>(sb + LY::kCoef, jj * 32 + lane);
         const float pc = P0[jj + 1];
         const float pxm = __shfl_up_sync(kFull, pc, 1);
         const float pxp = __shfl_down_sync(kFull, pc, 1);
         const float txm = __shfl_up_sync(kFull, cf.x, 1);
+        // BF16 records: D = T(-x) + T(+x) + T(-y) + T(+y) + T(-z) + T(+z) + E
+        if (B16) cf.w = (((((txm + cf.x) + tyl) + cf.y) + Tzm[jj]) + cf.z) + cf.w;
         const float q = stencil7(cf, txm, tyl, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
                                  Pp[jj + 1], Pm[jj]);
         if (outl && ((rowok >> (jj + 1)) & 1u)) {
@@ -230,7 +273,8 @@ sweep_kernel(const SweepArgs a) {
             qout[id] = q;
             s1 = fmaf(pc, q, s1);
             s2 = fmaf(R0[jj], q, s2);
-            s3 = fmaf(q, q, s3);
+            if (JAC) s3 = fmaf(q, q * jac_inv(cf.w), s3);
+            else s3 = fmaf(q, q, s3);
           } else {
             a.Ap[id] = q;
             s1 = fmaf(pc, q, s1);
@@ -334,7 +378,8 @@ prepare_kernel(Grid g, const double* __restrict__ r64, CgVecs v, CgState* st, do
 // estimate that stopped the loop was too optimistic, arm a restart of the
 // loop with the exact CG continuation (alpha = 0, beta = r+'r+ / r'r).
 __global__ void __launch_bounds__(kElemThreads)
-finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* counter) {
+finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* counter,
+                const float4* jac) {
   const int par = st->parity;
   const float af = (float)st->alpha_fin;
   float* r = v.r[par];
@@ -346,7 +391,11 @@ finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* c
     v.e[c] = fmaf(af, p[c], v.e[c]);
     const float rn = fmaf(-af, q[c], r[c]);
     r[c] = rn;
-    kadd(acc, rn * rn);
+    if (jac != nullptr) {  // preconditioned norm r' D^-1 r
+      kadd(acc, rn * (rn * jac_inv(jac[c].w)));
+    } else {
+      kadd(acc, rn * rn);
+    }
   }
   double vv[1] = {kval(acc)};
   block_partial<1>(vv, partials);
@@ -426,36 +475,48 @@ static SweepArgs sweep_args(const Grid& g, const Sweep& sw, const float4* coef) 
   return a;
 }
 
-template <int VY, int S, bool CG, bool COND>
+template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false>
 static cudaError_t launch_t(const SweepArgs& a, const Sweep& sw, cudaStream_t s) {
-  constexpr int smem = sweep_smem_bytes<VY, S>();
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<VY, S, CG, COND>,
+  constexpr int smem = sweep_smem_bytes<VY, S, B16, JAC>();
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<VY, S, CG, COND, B16, JAC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  sweep_kernel<VY, S, CG, COND><<<(unsigned)sw.nblocks, kSweepWarps * 32, smem, s>>>(a);
+  sweep_kernel<VY, S, CG, COND, B16, JAC><<<(unsigned)sw.nblocks, kSweepWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int VY, int S>
+template <int VY, int S, bool B16>
 static cudaError_t launch_vs(const SweepArgs& a, const Sweep& sw, bool cg, bool cond,
                              cudaStream_t s) {
-  if (!cg) return launch_t<VY, S, false, false>(a, sw, s);
-  if (cond) return launch_t<VY, S, true, true>(a, sw, s);
-  return launch_t<VY, S, true, false>(a, sw, s);
+  if (!cg) return launch_t<VY, S, false, false, B16>(a, sw, s);
+  if (cond) return launch_t<VY, S, true, true, B16>(a, sw, s);
+  return launch_t<VY, S, true, false, B16>(a, sw, s);
 }
 
 static cudaError_t launch_sweep(const SweepArgs& a, const Sweep& sw, bool cg, bool cond,
                                 cudaStream_t s) {
-  if (sw.vy == 4 && sw.stages == 3) return launch_vs<4, 3>(a, sw, cg, cond, s);
-  if (sw.vy == 4 && sw.stages == 4) return launch_vs<4, 4>(a, sw, cg, cond, s);
-  if (sw.vy == 8 && sw.stages == 3) return launch_vs<8, 3>(a, sw, cg, cond, s);
+  const bool b16 = a.coef16 != nullptr;
+  if (b16) {
+    if (sw.vy == 4 && sw.stages == 3) return launch_vs<4, 3, true>(a, sw, cg, cond, s);
+    if (sw.vy == 4 && sw.stages == 4) return launch_vs<4, 4, true>(a, sw, cg, cond, s);
+    return cudaErrorInvalidValue;
+  }
+  if (sw.vy == 4 && sw.stages == 3) return launch_vs<4, 3, false>(a, sw, cg, cond, s);
+  if (sw.vy == 4 && sw.stages == 4) return launch_vs<4, 4, false>(a, sw, cg, cond, s);
+  if (sw.vy == 8 && sw.stages == 3) return launch_vs<8, 3, false>(a, sw, cg, cond, s);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, const float* p,
-                         float* Ap, double* pAp, double* partials, unsigned int* counter,
-                         cudaStream_t s) {
-  SweepArgs a = sweep_args(g, sw, coef);
+static SweepArgs sweep_args_rec(const Grid& g, const Sweep& sw, const void* coef, bool b16) {
+  SweepArgs a = sweep_args(g, sw, b16 ? nullptr : static_cast<const float4*>(coef));
+  a.coef16 = b16 ? static_cast<const uint2*>(coef) : nullptr;
+  return a;
+}
+
+cudaError_t launch_apply(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                         const float* p, float* Ap, double* pAp, double* partials,
+                         unsigned int* counter, cudaStream_t s) {
+  SweepArgs a = sweep_args_rec(g, sw, coef, b16);
   a.p = p;
   a.Ap = Ap;
   a.pAp = pAp;
@@ -464,10 +525,29 @@ cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, con
   return launch_sweep(a, sw, false, false, s);
 }
 
-cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
-                            CgState* st, double* partials, unsigned int* counter,
-                            unsigned long long cond, int use_cond, cudaStream_t s) {
+cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
+                                   CgState* st, double* partials, unsigned int* counter,
+                                   unsigned long long cond, int use_cond, cudaStream_t s) {
   SweepArgs a = sweep_args(g, sw, coef);
+  a.v = v;
+  a.st = st;
+  a.partials = partials;
+  a.counter = counter;
+  a.cond = cond;
+  const bool c = use_cond != 0;
+  if (sw.vy == 4 && sw.stages == 3)
+    return c ? launch_t<4, 3, true, true, false, true>(a, sw, s)
+             : launch_t<4, 3, true, false, false, true>(a, sw, s);
+  if (sw.vy == 4 && sw.stages == 4)
+    return c ? launch_t<4, 4, true, true, false, true>(a, sw, s)
+             : launch_t<4, 4, true, false, false, true>(a, sw, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                            CgVecs v, CgState* st, double* partials, unsigned int* counter,
+                            unsigned long long cond, int use_cond, cudaStream_t s) {
+  SweepArgs a = sweep_args_rec(g, sw, coef, b16);
   a.v = v;
   a.st = st;
   a.partials = partials;
@@ -478,12 +558,12 @@ cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, 
 
 template <int VY, int S>
 static int blocks_per_sm_t() {
-  constexpr int smem = sweep_smem_bytes<VY, S>();
-  if (cudaFuncSetAttribute(sweep_kernel<VY, S, true, true>,
+  constexpr int smem = sweep_smem_bytes<VY, S, false>();
+  if (cudaFuncSetAttribute(sweep_kernel<VY, S, true, true, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<VY, S, true, true>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<VY, S, true, true, false>,
                                                     kSweepWarps * 32, smem) != cudaSuccess)
     return 0;
   return nb;
@@ -517,8 +597,9 @@ cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* 
 }
 
 cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
-                            unsigned int* counter, int nblocks, cudaStream_t s) {
-  finalize_kernel<<<nblocks, kElemThreads, 0, s>>>(g, v, st, partials, counter);
+                            unsigned int* counter, int nblocks, const float4* jac,
+                            cudaStream_t s) {
+  finalize_kernel<<<nblocks, kElemThreads, 0, s>>>(g, v, st, partials, counter, jac);
   return cudaGetLastError();
 }
 

@@ -89,8 +89,7 @@ extern "C" int tpfa_apply_noalloc(const tpfa_grid* grid, const float* coef, cons
     cudaGetLastError();
     return TPFA_ECUDA;
   }
-  if (launch_apply(g, sw, reinterpret_cast<const float4*>(coef), p, Ap, pAp, partials, counter,
-                   s) != cudaSuccess) {
+  if (launch_apply(g, sw, coef, false, p, Ap, pAp, partials, counter, s) != cudaSuccess) {
     cudaGetLastError();
     return TPFA_ECUDA;
   }

@@ -168,6 +168,20 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, bool ok) {
                "r"(ok ? 16 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(ok ? 8 : 0)
+               : "memory");
+}
+// Jacobi preconditioner M^-1 = diag(jac_inv(D)): one approximate reciprocal
+// per cell.  Any fixed positive diagonal is a valid SPD preconditioner; what
+// matters is that every kernel uses this same function of D, so z = M^-1 r
+// and the M^-1-weighted dot products refer to one and the same M.
+__device__ __forceinline__ float jac_inv(float D) { return D != 0.f ? __fdividef(1.0f, D) : 0.f; }
+
+// BF16 halves of a 32-bit word as FP32 (exact)
+__device__ __forceinline__ float bf16_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {

@@ -87,12 +87,20 @@ cudaError_t launch_build_rhs(const Grid& g, const tpfa_grid& geo, const double* 
                              const int64_t* src_idx, const double* src_val, int64_t n_src,
                              double* b, cudaStream_t s);
 
-cudaError_t launch_apply(const Grid& g, const Sweep& sw, const float4* coef, const float* p,
-                         float* Ap, double* pAp, double* partials, unsigned int* counter,
-                         cudaStream_t s);
-cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
-                            CgState* st, double* partials, unsigned int* counter,
+// coef: FP32 records (float4) or, with b16, BF16 records (4 x bf16 = uint2)
+cudaError_t launch_apply(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                         const float* p, float* Ap, double* pAp, double* partials,
+                         unsigned int* counter, cudaStream_t s);
+cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                            CgVecs v, CgState* st, double* partials, unsigned int* counter,
                             unsigned long long cond, int use_cond, cudaStream_t s);
+// Jacobi-preconditioned CG sweep (stored q, FP32 records, VY = 4)
+cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
+                                   CgState* st, double* partials, unsigned int* counter,
+                                   unsigned long long cond, int use_cond, cudaStream_t s);
+cudaError_t launch_build_trans_bf16(const Grid& g, const tpfa_grid& geo, const double* K,
+                                    const uint8_t* mask, const double* d, double d0,
+                                    uint2* coef16, cudaStream_t s);
 cudaError_t launch_cg40_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
                               CgState* st, double* partials, unsigned int* counter,
                               unsigned long long cond, int use_cond, cudaStream_t s);
@@ -106,7 +114,8 @@ cudaError_t launch_residual64(const Grid& g, const double* coef64, const double*
 cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* st,
                            double rtol, long long maxit, cudaStream_t s);
 cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
-                            unsigned int* counter, int nblocks, cudaStream_t s);
+                            unsigned int* counter, int nblocks, const float4* jac,
+                            cudaStream_t s);
 cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
                            cudaStream_t s);
 

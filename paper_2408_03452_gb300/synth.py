@@ -117,6 +117,14 @@ def channelized_field(nx, ny, nz, sigma, seed, n_channels=8, width=4, thickness=
     seed.
     """
     K = lognormal_field(nx, ny, nz, sigma, seed).reshape(nz, ny, nx)
+    return np.where(channel_mask(nx, ny, nz, seed, n_channels, width, thickness, amplitude,
+                                 wavelength), K * contrast, K).reshape(-1)
+
+
+def channel_mask(nx, ny, nz, seed, n_channels=8, width=4, thickness=8, amplitude=16.0,
+                 wavelength=128.0):
+    """Cells inside any of the sinusoidal channels (bool, shape (nz, ny, nx))."""
+    inside_any = np.zeros((nz, ny, nx), dtype=bool)
     u = uniform(seed, STREAM_CHANNEL, np.arange(3 * n_channels, dtype=np.uint64)).reshape(n_channels, 3)
     x = np.arange(nx, dtype=np.float64)
     jj = np.arange(ny)[:, None]
@@ -126,8 +134,8 @@ def channelized_field(nx, ny, nz, sigma, seed, n_channels=8, width=4, thickness=
         phi = 2.0 * np.pi * u[c, 2]
         centre = yc + amplitude * np.sin(2.0 * np.pi * x / wavelength + phi)  # per x
         inside = np.abs(jj - centre[None, :]) < 0.5 * width                  # (ny, nx)
-        K[z0:z0 + thickness][:, inside] *= contrast
-    return K.reshape(-1)
+        inside_any[z0:z0 + thickness] |= inside[None, :, :]
+    return inside_any
 
 
 # ----------------------------------------------------------------------------
@@ -196,6 +204,16 @@ def small_dirichlet(seed=0, n=32, sigma=1.0):
     K = lognormal_field(nx, ny, nz, sigma, seed)
     mask, pD = dirichlet_faces(nx, ny, nz, "x", 1.0, 0.0)
     return dict(nx=nx, ny=ny, nz=nz, K=K, mask=mask, pD=pD, d=0.0,
+                src_idx=np.zeros(0, np.int64), src_val=np.zeros(0))
+
+
+def channelized(seed=0, n=256, sigma=2.0, contrast=1e4):
+    """Mixed-precision workload: n^3 lognormal background (sigma) with eight
+    sinusoidal channels 4 cells wide, 8 layers thick, `contrast` times more
+    permeable; p = 1 / 0 on the x end layers."""
+    K = channelized_field(n, n, n, sigma, seed, contrast=contrast)
+    mask, pD = dirichlet_faces(n, n, n, "x", 1.0, 0.0)
+    return dict(nx=n, ny=n, nz=n, K=K, mask=mask, pD=pD, d=0.0,
                 src_idx=np.zeros(0, np.int64), src_val=np.zeros(0))
 
 

@@ -21,7 +21,8 @@ OK, NOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, -3, -4, -5, -6, -7
 
 OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6,
-           "stages": 7, "scheme": 8, "stages40": 9, "warps40": 10}
+           "stages": 7, "scheme": 8, "stages40": 9, "warps40": 10, "inner_rtol_bf16": 11,
+           "precond": 12}
 
 
 class TpfaError(RuntimeError):
@@ -58,6 +59,9 @@ SIGNATURES = {
     "tpfa_residual64": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
     "tpfa_apply_noalloc": (C.c_int, [C.POINTER(_Grid), _P, _P, _P, _P, _P]),
+    "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
+    "tpfa_apply_bf16": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "cg_solve_bf16": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
 }
 
 
@@ -164,6 +168,20 @@ class Context:
                 _ptr(coef64, torch.float64, 4 * n, dev, "coef64"), _stream(dev)), "tpfa_build_trans")
         return coef, coef64
 
+    def build_trans_bf16(self, K, dirichlet=None, d=None, d_uniform=0.0, coef16=None):
+        """BF16 records (Tx', Ty', Tz', E) as int16 bit patterns, shape [N, 4]."""
+        dev, n = self.device, self.n
+        if coef16 is None:
+            coef16 = torch.empty((n, 4), dtype=torch.int16, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_build_trans_bf16(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(d, torch.float64, n, dev, "d"), float(d_uniform),
+                _ptr(coef16, torch.int16, 4 * n, dev, "coef16"), _stream(dev)),
+                "tpfa_build_trans_bf16")
+        return coef16
+
     def build_rhs(self, K, dirichlet=None, q=None, pD=None, src_idx=None, src_val=None, b=None):
         dev, n = self.device, self.n
         if b is None:
@@ -195,6 +213,17 @@ class Context:
                 _ptr(pAp, torch.float64, 1, dev, "pAp"), _stream(dev)), "tpfa_apply")
         return Ap
 
+    def apply_bf16(self, coef16, p, Ap=None, pAp=None):
+        dev, n = self.device, self.n
+        if Ap is None:
+            Ap = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_apply_bf16(
+                self._h, _ptr(coef16, torch.int16, 4 * n, dev, "coef16"),
+                _ptr(p, torch.float32, n, dev, "p"), _ptr(Ap, torch.float32, n, dev, "Ap"),
+                _ptr(pAp, torch.float64, 1, dev, "pAp"), _stream(dev)), "tpfa_apply_bf16")
+        return Ap
+
     def residual64(self, coef64, b, x, r=None, norms=None):
         """r = b - A x in FP64.  norms: optional float64[2] receiving
         (||r||^2, ||b||^2)."""
@@ -210,14 +239,18 @@ class Context:
         return r
 
     def cg_solve(self, coef, coef64, b, x=None, tol=1e-8, maxit=100000, check=True):
-        """Solve A x = b to FP64 relative residual tol.  Returns (x, info dict)."""
+        """Solve A x = b to FP64 relative residual tol.  Returns (x, info dict).
+        coef: FP32 records (float32 [N,4]) or BF16 records (int16 [N,4], the
+        mixed-precision solve cg_solve_bf16)."""
         dev, n = self.device, self.n
         if x is None:
             x = torch.zeros(n, dtype=torch.float64, device=dev)
         info = _Info()
+        b16 = coef.dtype == torch.int16
+        fn = lib().cg_solve_bf16 if b16 else lib().cg_solve
         with torch.cuda.device(dev):
-            code = lib().cg_solve(
-                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+            code = fn(
+                self._h, _ptr(coef, torch.int16 if b16 else torch.float32, 4 * n, dev, "coef"),
                 _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
                 _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
                 float(tol), int(maxit), C.byref(info), _stream(dev))

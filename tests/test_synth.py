@@ -51,3 +51,15 @@ def test_boundary_and_wells():
     assert m[:, :, 0].all() and m[:, :, -1].all() and not m[:, :, 1:-1].any()
     idx, val = synth.well_pair(4, 3, 2)
     assert idx.tolist() == [0, 23] and val.tolist() == [1.0, -1.0]
+
+
+def test_channels_multiply_once():
+    nx, ny, nz = 40, 30, 20
+    m = synth.channel_mask(nx, ny, nz, 1, n_channels=6, width=4, thickness=6, amplitude=5.0,
+                           wavelength=20.0)
+    base = synth.lognormal_field(nx, ny, nz, 1.0, 1).reshape(nz, ny, nx)
+    K = synth.channelized_field(nx, ny, nz, 1.0, 1, n_channels=6, width=4, thickness=6,
+                                amplitude=5.0, wavelength=20.0, contrast=1e3).reshape(nz, ny, nx)
+    assert m.any() and not m.all()
+    np.testing.assert_allclose(K[m], 1e3 * base[m])
+    np.testing.assert_array_equal(K[~m], base[~m])
