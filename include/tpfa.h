@@ -228,6 +228,45 @@ int cg_solve_bf16(tpfa_ctx* ctx, const uint16_t* coef16, const double* coef64, c
                   double* x, double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
 
 /*
+ * Batched ensembles: n_inst independent problems (each its own grid, K,
+ * boundary set and tolerance target) solved together.  Every per-cell array
+ * of a batch is the concatenation of the instances' arrays: instance i
+ * occupies cells offsets[i] .. offsets[i+1]-1 (tpfa_batch_offsets), X
+ * innermost inside the instance.  The CG iterations of all instances run as
+ * one sweep launch per iteration inside one CUDA-graph while loop; each
+ * instance has its own scalars and convergence flag, and the blocks of a
+ * converged instance return immediately.
+ */
+typedef struct tpfa_batch tpfa_batch;
+
+/* grids: host array of n_inst grids (rules of tpfa_create each).  zc: host
+ * array of n_inst z-run lengths for the sweep tiling (0 = automatic), or NULL
+ * (all automatic); an autotuner may supply them. */
+int tpfa_batch_create(const tpfa_grid* grids, int n_inst, const int* zc, tpfa_batch** out);
+int tpfa_batch_destroy(tpfa_batch* batch);
+/* offsets: host, n_inst + 1 entries (cell offsets, last = total cells). */
+int tpfa_batch_offsets(const tpfa_batch* batch, int64_t* offsets);
+/* zc: host, n_inst entries: the z-run length each instance uses. */
+int tpfa_batch_zc(const tpfa_batch* batch, int* zc);
+/* TPFA_OPT_INNER_RTOL, TPFA_OPT_MAX_OUTER, TPFA_OPT_PRECOND. */
+int tpfa_batch_set_option(tpfa_batch* batch, int option, double value);
+/* As tpfa_build_trans / tpfa_build_rhs over the concatenated arrays. */
+int tpfa_batch_build_trans(tpfa_batch* batch, const double* K, const uint8_t* dirichlet,
+                           const double* d, double d_uniform, float* coef, double* coef64,
+                           void* stream);
+int tpfa_batch_build_rhs(tpfa_batch* batch, const double* K, const uint8_t* dirichlet,
+                         const double* q, const double* pD, double* b, void* stream);
+/* Solve every instance to ||b_i - A_i x_i|| <= tol ||b_i|| (FP64), refined
+ * as cg_solve.  infos: host, n_inst entries (per-instance results; the
+ * timing fields are the whole call's), or NULL.  total: host summary
+ * (iterations summed over instances, largest relative residual), or NULL.
+ * Returns TPFA_OK if every instance converged, else the most severe status
+ * (errors before TPFA_NOTCONV).  Waits for the stream. */
+int cg_solve_batch(tpfa_batch* batch, const float* coef, const double* coef64, const double* b,
+                   double* x, double tol, int64_t maxit, tpfa_cg_info* infos,
+                   tpfa_cg_info* total, void* stream);
+
+/*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a library convenience.
  *

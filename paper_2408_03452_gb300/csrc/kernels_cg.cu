@@ -28,6 +28,8 @@ namespace tpfa {
 namespace {
 
 struct SweepArgs {
+  const BatchInst* inst;  // batched sweeps: instance table (ninst entries)
+  int ninst;
   Grid g;
   int64_t nwx, nwy, nwarps;
   int zc;
@@ -87,27 +89,49 @@ __device__ __forceinline__ float ty_word(const unsigned char* base, int lane) {
 // p_{k-1}, and the four dots become r'z, p'q, z'q, q'D^-1 q, which give
 // alpha = r'z / p'q and (r - alpha q)' D^-1 (r - alpha q) by the same
 // identity as the plain iteration.  No extra vector is read or written.
-template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false>
+// BATCH: one launch sweeps every instance of a batch; each block finds its
+// instance in the table (blocks of one instance are contiguous) and uses that
+// instance's grid, tiling, cell offset, CG state, completion counter and
+// partial sums.  A finished instance's blocks return at once.
+template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false, bool BATCH = false>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 sweep_kernel(const SweepArgs a) {
   static_assert(S >= 3, "the plane pipeline needs at least three stages");
   static_assert(!JAC || (CG && !B16), "Jacobi preconditioning is for FP32-record CG sweeps");
+  static_assert(!BATCH || (CG && !B16 && !COND), "batched sweeps are FP32-record CG sweeps");
   using LY = StageLayout<VY, B16, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const Grid& g = a.g;
+  Grid g = a.g;
+  int64_t nwx = a.nwx, nwy = a.nwy, nwarps = a.nwarps, zcr = a.zc, off = 0;
+  int64_t lb = blockIdx.x, pstart = 0, pcount = gridDim.x;
+  CgState* st = a.st;
+  unsigned int* counter = a.counter;
+  if (BATCH) {
+    int lo = 0, hi = a.ninst - 1;  // last instance whose first block <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.inst[mid].bstart <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const BatchInst& I = a.inst[lo];
+    g = I.g; nwx = I.nwx; nwy = I.nwy; nwarps = I.nwarps; zcr = I.zc; off = I.off;
+    lb = blockIdx.x - I.bstart; pstart = I.bstart; pcount = I.nblocks;
+    st = a.st + lo;
+    counter = a.counter + lo;
+  }
+  const float4* coefp = a.coef != nullptr ? a.coef + off : nullptr;
+  float* ep = CG ? a.v.e + off : nullptr;
   float alpha = 0.f, beta = 0.f;
   const float *rin = nullptr, *qin = nullptr, *pin = a.p;
   float *rout = nullptr, *qout = nullptr, *pout = nullptr;
   if (CG) {
-    CgState* st = a.st;
     if (*(volatile int*)&st->done != kRunning) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (lb == 0 && threadIdx.x == 0) {
         st->launches += 1;
         if (COND) cudaGraphSetConditional(a.cond, 0u);
       }
       return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (lb == 0 && threadIdx.x == 0) {
       const long long n = st->launches + 1;
       st->launches = n;
       if (COND && n > st->guard_limit) cudaGraphSetConditional(a.cond, 0u);
@@ -115,27 +139,27 @@ sweep_kernel(const SweepArgs a) {
     const int par = st->parity;
     alpha = (float)st->alpha;
     beta = (float)st->beta;
-    rin = a.v.r[par]; qin = a.v.q[par]; pin = a.v.p[par];
-    rout = a.v.r[par ^ 1]; qout = a.v.q[par ^ 1]; pout = a.v.p[par ^ 1];
+    rin = a.v.r[par] + off; qin = a.v.q[par] + off; pin = a.v.p[par] + off;
+    rout = a.v.r[par ^ 1] + off; qout = a.v.q[par ^ 1] + off; pout = a.v.p[par ^ 1] + off;
   }
 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * kSweepWarps + wib;
+  const int64_t gw = lb * kSweepWarps + wib;
   unsigned char* wsm = smem + (size_t)wib * S * LY::kBytes;
   Acc acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 
-  if (gw < a.nwarps) {  // warp-uniform
-    const int64_t wx = gw % a.nwx;
-    const int64_t t = gw / a.nwx;
-    const int64_t wy = t % a.nwy;
-    const int64_t wz = t / a.nwy;
+  if (gw < nwarps) {  // warp-uniform
+    const int64_t wx = gw % nwx;
+    const int64_t t = gw / nwx;
+    const int64_t wy = t % nwy;
+    const int64_t wz = t / nwy;
     const int64_t gx = wx * kTileX - 1 + lane;
     const bool inx = gx >= 0 && gx < g.nx;
     const bool outl = inx && lane >= 1 && lane <= kTileX;
     const int64_t y0 = wy * VY;
-    const int64_t z0 = wz * (int64_t)a.zc;
-    const int64_t z1 = min(z0 + (int64_t)a.zc, g.nz);
+    const int64_t z0 = wz * zcr;
+    const int64_t z1 = min(z0 + zcr, g.nz);
     unsigned rowok = 0u;  // bit jj+1: row y0+jj inside the grid (and this lane's column too)
 #pragma unroll
     for (int jj = -1; jj <= VY; ++jj)
@@ -173,15 +197,15 @@ sweep_kernel(const SweepArgs a) {
           }
           if (jj == -1) {
             if (B16) cp4(sty + lane, a.coef16 + src, ok);  // word 0 = Tx | Ty << 16
-            else cp4(sty + lane, reinterpret_cast<const float*>(a.coef + src) + 1, ok);
+            else cp4(sty + lane, reinterpret_cast<const float*>(coefp + src) + 1, ok);
           }
           if (JAC && (jj == -1 || jj == VY))
             cp4(reinterpret_cast<float*>(sb + LY::kDh) + (jj == -1 ? 0 : 32) + lane,
-                reinterpret_cast<const float*>(a.coef + src) + 3, ok);
+                reinterpret_cast<const float*>(coefp + src) + 3, ok);
           if (jj >= 0 && jj < VY) {
             if (B16) cp8(reinterpret_cast<uint2*>(scf) + jj * 32 + lane, a.coef16 + src, ok);
-            else cp16(reinterpret_cast<float4*>(scf) + jj * 32 + lane, a.coef + src, ok);
-            if (CG) cp4(se + jj * 32 + lane, a.v.e + src, ok && own);
+            else cp16(reinterpret_cast<float4*>(scf) + jj * 32 + lane, coefp + src, ok);
+            if (CG) cp4(se + jj * 32 + lane, ep + src, ok && own);
           }
         }
       }
@@ -216,7 +240,7 @@ sweep_kernel(const SweepArgs a) {
           p_ = fmaf(beta, p0, z_);    // Alg. 1 line 10
           if (jj >= 0 && jj < VY && own && ((rowok >> (jj + 1)) & 1u)) {
             const int64_t id = zo + o0 + jj * nxi;
-            a.v.e[id] = fmaf(alpha, p0, se[jj * 32 + lane]);  // Alg. 1 line 6
+            ep[id] = fmaf(alpha, p0, se[jj * 32 + lane]);  // Alg. 1 line 6
             rout[id] = r_;
             pout[id] = p_;
             s0 = fmaf(r_, z_, s0);
@@ -304,8 +328,8 @@ sweep_kernel(const SweepArgs a) {
     double v[4] = {kval(acc[0]), kval(acc[1]), kval(acc[2]), kval(acc[3])};
     block_partial<4>(v, a.partials);
     double tot[4];
-    if (last_block_total<4>(a.partials, a.counter, tot) && threadIdx.x == 0)
-      cg_finish(a.st, tot, a.cond, COND);
+    if (last_block_range<4>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0)
+      cg_finish(st, tot, a.cond, COND);
   } else if (a.pAp != nullptr) {
     double v[1] = {kval(acc[1])};
     block_partial<1>(v, a.partials);
@@ -475,13 +499,14 @@ static SweepArgs sweep_args(const Grid& g, const Sweep& sw, const float4* coef) 
   return a;
 }
 
-template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false>
+template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false, bool BATCH = false>
 static cudaError_t launch_t(const SweepArgs& a, const Sweep& sw, cudaStream_t s) {
   constexpr int smem = sweep_smem_bytes<VY, S, B16, JAC>();
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<VY, S, CG, COND, B16, JAC>,
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel<VY, S, CG, COND, B16, JAC, BATCH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  sweep_kernel<VY, S, CG, COND, B16, JAC><<<(unsigned)sw.nblocks, kSweepWarps * 32, smem, s>>>(a);
+  sweep_kernel<VY, S, CG, COND, B16, JAC, BATCH>
+      <<<(unsigned)sw.nblocks, kSweepWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -542,6 +567,47 @@ cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4*
     return c ? launch_t<4, 4, true, true, false, true>(a, sw, s)
              : launch_t<4, 4, true, false, false, true>(a, sw, s);
   return cudaErrorInvalidValue;
+}
+
+// Condition of the batched while loop: continue while any instance runs
+// (one block; a single thread sets the condition).
+__global__ void batch_cond_kernel(const CgState* st, int ninst, unsigned long long cond,
+                                  long long* sweeps, long long limit) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  int r = 0;
+  for (int i = threadIdx.x; i < ninst; i += blockDim.x) r += st[i].done == kRunning ? 1 : 0;
+  if (r) atomicAdd(&running, r);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long n = *sweeps + 1;
+    *sweeps = n;
+    cudaGraphSetConditional(cond, (running > 0 && n <= limit) ? 1u : 0u);
+  }
+}
+
+cudaError_t launch_cg_sweep_batch(const BatchInst* inst, int ninst, int64_t nblocks,
+                                  const float4* coef, CgVecs v, CgState* st, double* partials,
+                                  unsigned int* counters, bool jac, cudaStream_t s) {
+  SweepArgs a{};
+  a.inst = inst;
+  a.ninst = ninst;
+  a.coef = coef;
+  a.v = v;
+  a.st = st;
+  a.partials = partials;
+  a.counter = counters;
+  Sweep sw{};
+  sw.nblocks = nblocks;
+  if (jac) return launch_t<4, 4, true, false, false, true, true>(a, sw, s);
+  return launch_t<4, 4, true, false, false, false, true>(a, sw, s);
+}
+
+cudaError_t launch_batch_cond(const CgState* st, int ninst, unsigned long long cond,
+                              long long* sweeps, long long limit, cudaStream_t s) {
+  batch_cond_kernel<<<1, 128, 0, s>>>(st, ninst, cond, sweeps, limit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const void* coef, bool b16,

@@ -49,16 +49,18 @@ __device__ __forceinline__ void block_partial(double (&v)[NV], double* partials)
   }
 }
 
-// Returns true in the last block to finish; that block then holds the
-// fixed-order total of all block partials in tot (every thread).
+// Returns true in the last of `count` blocks (blocks first .. first+count-1
+// of the grid, which share `counter`) to finish; that block then holds the
+// fixed-order total of their partials in tot (every thread).
 template <int NV>
-__device__ __forceinline__ bool last_block_total(const double* partials, unsigned int* counter,
+__device__ __forceinline__ bool last_block_range(const double* partials, unsigned int* counter,
+                                                 int64_t first, int64_t count,
                                                  double (&tot)[NV]) {
   __shared__ bool s_last;
   __shared__ double sm[32][NV];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)(count - 1));
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
@@ -66,9 +68,9 @@ __device__ __forceinline__ bool last_block_total(const double* partials, unsigne
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
 #pragma unroll 8
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+  for (int64_t b = threadIdx.x; b < count; b += blockDim.x) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(partials + (size_t)b * NV + i);
+    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(partials + (size_t)(first + b) * NV + i);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -90,6 +92,13 @@ __device__ __forceinline__ bool last_block_total(const double* partials, unsigne
   }
   if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
   return true;
+}
+
+// The same over the whole grid.
+template <int NV>
+__device__ __forceinline__ bool last_block_total(const double* partials, unsigned int* counter,
+                                                 double (&tot)[NV]) {
+  return last_block_range<NV>(partials, counter, 0, gridDim.x, tot);
 }
 
 // 7-point product for one cell, fused multiply-adds in a fixed order.

@@ -69,6 +69,17 @@ bool sweep_config_ok(int vy, int stages);
 Sweep plan_sweep40(const Grid& g, int stages, int warps, int zc_opt, int num_sms);
 bool sweep40_config_ok(int stages, int warps);
 
+// One instance of a batched solve: its grid, its sweep tiling, where its
+// cells start in the concatenated arrays and which sweep blocks it owns.
+struct BatchInst {
+  Grid g;
+  int64_t nwx, nwy, nwarps;
+  int64_t zc;
+  int64_t off;      // first cell in the concatenated arrays
+  int64_t bstart;   // first sweep block
+  int64_t nblocks;  // sweep blocks of this instance
+};
+
 // Vector set of the inner CG (two sets, ping-ponged between sweeps).
 struct CgVecs {
   float* r[2];
@@ -120,6 +131,14 @@ cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgSta
                            cudaStream_t s);
 
 int sweep_blocks_per_sm(int vy, int stages);
+
+// Batched CG sweep over every instance (VY = 4, 4 stages, FP32 records) and
+// the one-block kernel that sets the while-loop condition after it.
+cudaError_t launch_cg_sweep_batch(const BatchInst* inst, int ninst, int64_t nblocks,
+                                  const float4* coef, CgVecs v, CgState* st, double* partials,
+                                  unsigned int* counters, bool jac, cudaStream_t s);
+cudaError_t launch_batch_cond(const CgState* st, int ninst, unsigned long long cond,
+                              long long* sweeps, long long limit, cudaStream_t s);
 
 // Argument checks shared by the entry points: a device (or managed)
 // allocation on `device` that holds [p, p + bytes) and is `align`-aligned.

@@ -217,6 +217,28 @@ def channelized(seed=0, n=256, sigma=2.0, contrast=1e4):
                 src_idx=np.zeros(0, np.int64), src_val=np.zeros(0))
 
 
+ENSEMBLE_SIZES = ((48, 48, 24), (64, 64, 32), (96, 96, 48), (128, 128, 64))
+
+
+def ensemble(seed=0, n_inst=96, sizes=ENSEMBLE_SIZES, sigma_range=(0.5, 2.5)):
+    """Batched workload: n_inst realizations, each with a size drawn uniformly
+    from `sizes`, ln K ~ N(0, sigma^2) with sigma ~ U(sigma_range), Dirichlet
+    end layers on an axis drawn from {x, y, z} with p_hi ~ U(0.5, 2), p_lo = 0.
+    Returns a list of per-instance dicts (the K seeds differ per instance)."""
+    u = uniform(seed, STREAM_INSTANCE, np.arange(4 * n_inst, dtype=np.uint64)).reshape(n_inst, 4)
+    out = []
+    for i in range(n_inst):
+        nx, ny, nz = sizes[min(int(u[i, 0] * len(sizes)), len(sizes) - 1)]
+        sigma = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * u[i, 1]
+        axis = "xyz"[min(int(u[i, 2] * 3), 2)]
+        p_hi = 0.5 + 1.5 * u[i, 3]
+        K = lognormal_field(nx, ny, nz, sigma, seed * 1000003 + i + 1)
+        mask, pD = dirichlet_faces(nx, ny, nz, axis, p_hi, 0.0)
+        out.append(dict(nx=nx, ny=ny, nz=nz, K=K, mask=mask, pD=pD, d=0.0, sigma=sigma,
+                        axis=axis, p_hi=p_hi))
+    return out
+
+
 def paper_scale(seed=0, nx=1024, ny=1024, nz=256, sigma=1.5, layer=8, d=1e-3):
     """Layered lognormal field, accumulation diagonal d, corner well pair, no Dirichlet."""
     K = lognormal_field(nx, ny, nz, sigma, seed, layer=layer)

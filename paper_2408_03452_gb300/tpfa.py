@@ -62,6 +62,15 @@ SIGNATURES = {
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "tpfa_apply_bf16": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "cg_solve_bf16": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
+    "tpfa_batch_create": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_void_p)]),
+    "tpfa_batch_destroy": (C.c_int, [_P]),
+    "tpfa_batch_offsets": (C.c_int, [_P, _P]),
+    "tpfa_batch_zc": (C.c_int, [_P, _P]),
+    "tpfa_batch_set_option": (C.c_int, [_P, C.c_int, C.c_double]),
+    "tpfa_batch_build_trans": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P, _P]),
+    "tpfa_batch_build_rhs": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cg_solve_batch": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, _P,
+                                 C.POINTER(_Info), _P]),
 }
 
 
@@ -259,3 +268,100 @@ class Context:
         out = {f: getattr(info, f) for f, _ in _Info._fields_}
         out["code"] = code
         return x, out
+
+
+class BatchContext:
+    """Many grids solved together (wraps tpfa_batch_*).  Per-cell tensors are
+    the concatenation of the instances' arrays; `offsets` gives the split."""
+
+    def __init__(self, grids, zc=None, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.ninst = len(grids)
+        arr = (_Grid * self.ninst)()
+        for i, g in enumerate(grids):
+            g = tuple(g) + (1.0, 1.0, 1.0, 1.0)[len(g) - 3:] if len(g) < 7 else tuple(g)
+            arr[i] = _Grid(int(g[0]), int(g[1]), int(g[2]), float(g[3]), float(g[4]),
+                           float(g[5]), float(g[6]))
+        zarr = None
+        if zc is not None:
+            zarr = (C.c_int * self.ninst)(*[int(z) for z in zc])
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().tpfa_batch_create(C.cast(arr, C.c_void_p), self.ninst,
+                                           C.cast(zarr, C.c_void_p) if zarr is not None else None,
+                                           C.byref(self._h)), "tpfa_batch_create")
+        off = (C.c_int64 * (self.ninst + 1))()
+        _check(lib().tpfa_batch_offsets(self._h, C.cast(off, C.c_void_p)), "tpfa_batch_offsets")
+        self.offsets = [int(v) for v in off]
+        self.n = self.offsets[-1]
+        z = (C.c_int * self.ninst)()
+        _check(lib().tpfa_batch_zc(self._h, C.cast(z, C.c_void_p)), "tpfa_batch_zc")
+        self.zc = [int(v) for v in z]
+
+    def close(self):
+        if self._h:
+            with torch.cuda.device(self.device):
+                lib().tpfa_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, name, value):
+        _check(lib().tpfa_batch_set_option(self._h, OPTIONS[name], float(value)),
+               f"batch set_option({name})")
+
+    def build_trans(self, K, dirichlet=None, d=None, d_uniform=0.0):
+        dev, n = self.device, self.n
+        coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_batch_build_trans(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(d, torch.float64, n, dev, "d"), float(d_uniform),
+                _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"), _stream(dev)),
+                "tpfa_batch_build_trans")
+        return coef, coef64
+
+    def build_rhs(self, K, dirichlet=None, q=None, pD=None):
+        dev, n = self.device, self.n
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_batch_build_rhs(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(q, torch.float64, n, dev, "q"), _ptr(pD, torch.float64, n, dev, "pD"),
+                _ptr(b, torch.float64, n, dev, "b"), _stream(dev)), "tpfa_batch_build_rhs")
+        return b
+
+    def cg_solve(self, coef, coef64, b, x=None, tol=1e-8, maxit=100000, check=True):
+        """Returns (x, per-instance info list, total info)."""
+        dev, n = self.device, self.n
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+        infos = (_Info * self.ninst)()
+        tot = _Info()
+        with torch.cuda.device(dev):
+            code = lib().cg_solve_batch(
+                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
+                _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
+                float(tol), int(maxit), C.cast(infos, C.c_void_p), C.byref(tot), _stream(dev))
+        if check:
+            _check(code, "cg_solve_batch", allow=(OK, NOTCONV))
+        per = [{f: getattr(infos[i], f) for f, _ in _Info._fields_} for i in range(self.ninst)]
+        total = {f: getattr(tot, f) for f, _ in _Info._fields_}
+        total["code"] = code
+        return x, per, total

@@ -63,3 +63,12 @@ def test_channels_multiply_once():
     assert m.any() and not m.all()
     np.testing.assert_allclose(K[m], 1e3 * base[m])
     np.testing.assert_array_equal(K[~m], base[~m])
+
+
+def test_ensemble_generator_recipe():
+    ens = synth.ensemble(seed=1, n_inst=24)
+    assert len(ens) == 24
+    assert {(w["nx"], w["ny"], w["nz"]) for w in ens} <= set(synth.ENSEMBLE_SIZES)
+    assert all(0.5 <= w["sigma"] <= 2.5 and 0.5 <= w["p_hi"] <= 2.0 for w in ens)
+    assert len({w["axis"] for w in ens}) > 1
+    assert len({(w["nx"], w["ny"], w["nz"]) for w in ens}) > 1
