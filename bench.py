@@ -54,7 +54,11 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--nz", type=int, default=256)
-    ap.add_argument("--workload", default="paper", choices=["paper", "channelized"],
+    ap.add_argument("--n-inst", type=int, default=96, help="ensemble size (--workload ensemble)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--compare-single", action="store_true",
+                    help="ensemble: also time the instances solved one after another")
+    ap.add_argument("--workload", default="paper", choices=["paper", "channelized", "ensemble"],
                     help="paper: 1024x1024x256 layered lognormal, wells, CG to 1e-6 (default); "
                          "channelized: 256^3 sigma-2 background + 1e4 channels, Dirichlet x "
                          "ends, refined to 1e-10 (the mixed-precision configuration)")
@@ -85,6 +89,12 @@ def parse():
 def workload_desc(a):
     solver = ("plain CG" if a.precond == 0 else "Jacobi-preconditioned CG") + \
         (", FP32 records" if a.inner == "f32" else ", BF16 records")
+    if a.workload == "ensemble":
+        return (f"batched ensemble of {a.n_inst} TPFA problems, sizes uniform over "
+                f"{{48x48x24, 64x64x32, 96x96x48, 128x128x64}}, lnK~N(0,s^2) with s~U(0.5,2.5) "
+                f"per instance, Dirichlet end layers on a random axis (p_hi~U(0.5,2), p_lo=0), "
+                f"{solver}, each refined to FP64 relative residual {a.tol:g}, one batched sweep "
+                f"launch per iteration")
     if a.workload == "channelized":
         return (f"channelized TPFA pressure solve {a.nx}x{a.ny}x{a.nz}, lnK~N(0,2^2) background "
                 f"plus 8 sinusoidal channels 1e4x more permeable, Dirichlet p=1/0 on the x end "
@@ -98,7 +108,7 @@ def finish_args(a):
     if a.workload == "channelized" and (a.nx, a.ny, a.nz) == (1024, 1024, 256):
         a.nx = a.ny = a.nz = 256
     if a.tol is None:
-        a.tol = 1e-10 if a.workload == "channelized" else 1e-6
+        a.tol = {"channelized": 1e-10, "ensemble": 1e-8}.get(a.workload, 1e-6)
     return a
 
 
@@ -268,6 +278,135 @@ def sweep_traffic(nx, ny, nz):
         return None
 
 
+def run_ensemble(a, dev, rank, world, local, barrier):
+    """Batched-ensemble step: build + batched CG solve of every instance."""
+    import torch
+    from paper_2408_03452_gb300 import autotune, tpfa
+
+    ens = synth.ensemble(seed=a.seed, n_inst=a.n_inst)
+    grids = [(w["nx"], w["ny"], w["nz"]) for w in ens]
+    cells = [w["nx"] * w["ny"] * w["nz"] for w in ens]
+    host = {k: torch.from_numpy(np.concatenate([w[k] for w in ens])).pin_memory()
+            for k in ("K", "mask", "pD")}
+    inp = {k: v.to(dev) for k, v in host.items()}
+    with tpfa.BatchContext(grids) as bc0:
+        coef, coef64 = bc0.build_trans(inp["K"], inp["mask"], None, 0.0)
+        b = bc0.build_rhs(inp["K"], inp["mask"], None, inp["pD"])
+        zc_auto = bc0.zc
+    zc = zc_auto if a.no_autotune else autotune.tune(grids, coef, coef64, b, tol=a.tol,
+                                                      maxit=a.maxit, precond=a.precond)
+    bc = tpfa.BatchContext(grids, zc=zc, device=dev)
+    bc.set_option("precond", a.precond)
+    x = torch.empty(bc.n, dtype=torch.float64, device=dev)
+
+    def step(d):
+        c, c64 = bc.build_trans(d["K"], d["mask"], None, 0.0)
+        rhs = bc.build_rhs(d["K"], d["mask"], None, d["pD"])
+        x.zero_()
+        _, per, tot = bc.cg_solve(c, c64, rhs, x=x, tol=a.tol, maxit=a.maxit)
+        if tot["code"] not in ((0, 1) if a.allow_notconv else (0,)):
+            raise RuntimeError(f"cg_solve_batch returned {tot}")
+        return per, tot
+
+    for _ in range(a.warmup):
+        step(inp)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    res = [step(inp) for _ in range(a.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    units = sum(sum(c * p["iters"] for c, p in zip(cells, per)) for per, _ in res)
+    inner_ms = sum(t["inner_ms"] for _, t in res)
+    launches = sum(2 * len(ens) + t["kernel_launches"] for _, t in res)  # builds + solve
+
+    e2e = None
+    if a.e2e_steps > 0:
+        x_host = torch.empty(bc.n, dtype=torch.float64).pin_memory()
+        dev_in = {k: torch.empty_like(v) for k, v in inp.items()}
+        barrier()
+        torch.cuda.synchronize()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        e2e_units = 0
+        for _ in range(a.e2e_steps):
+            for k, v in host.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            per, _ = step(dev_in)
+            e2e_units += sum(c * p["iters"] for c, p in zip(cells, per))
+            x_host.copy_(x, non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e = (e2e_units, e2.elapsed_time(e3))
+
+    single_ms = None
+    if a.compare_single:
+        torch.cuda.synchronize()
+        e4 = torch.cuda.Event(enable_timing=True)
+        e5 = torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for i, w in enumerate(ens):
+            with tpfa.Context(*grids[i], device=dev) as ctx:
+                ctx.set_option("precond", a.precond)
+                o0, o1 = bc.offsets[i], bc.offsets[i + 1]
+                c, c64 = ctx.build_trans(inp["K"][o0:o1], inp["mask"][o0:o1], None, 0.0)
+                rhs = ctx.build_rhs(inp["K"][o0:o1], inp["mask"][o0:o1], None, inp["pD"][o0:o1])
+                ctx.cg_solve(c, c64, rhs, tol=a.tol, maxit=a.maxit)
+        e5.record(stream)
+        torch.cuda.synchronize()
+        single_ms = e4.elapsed_time(e5)
+
+    ms_max, units_all, e2e_ms_max, e2e_units_all = combine_ranks(
+        ms, units, e2e[1] if e2e else 0.0, e2e[0] if e2e else 0.0, dev)
+    if rank == 0:
+        per, tot = res[-1]
+        peak, peak_kind = measured_hbm_peak()
+        achieved = SWEEP_BYTES_PER_CELL * units / a.steps / (inner_ms / a.steps / 1e3) / 1e9
+        out = {
+            "metric": METRIC, "value": units_all / (ms_max / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(a), "instances": len(ens),
+                       "cells": int(sum(cells)), "tol": a.tol,
+                       "parallelism": f"replicas{world}",
+                       "precond": ["none", "jacobi"][a.precond],
+                       "zc_per_size": {f"{g[0]}x{g[1]}x{g[2]}": z for g, z in zip(grids, zc)},
+                       "autotuned": not a.no_autotune,
+                       "iters_min_max": [min(p["iters"] for p in per), max(p["iters"] for p in per)],
+                       "time_to_tol_s": ms / 1e3 / a.steps,
+                       "rel_res_fp64_max": tot["rel_res_fp64"],
+                       "single_solves_s": None if single_ms is None else single_ms / 1e3,
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "roofline": {"kernel": "batched cg sweep", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind, "bytes_per_cell": SWEEP_BYTES_PER_CELL,
+                         "traffic": None},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if e2e:
+            out["e2e"] = {"value": e2e_units_all / (e2e_ms_max / 1e3), "unit": UNIT,
+                          "h2d_bytes_per_step": int(sum(v.numel() * v.element_size()
+                                                        for v in host.values())),
+                          "d2h_bytes_per_step": int(bc.n * 8), "steps": a.e2e_steps}
+        if not a.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(workload="paper")
+        print(json.dumps(out))
+    bc.close()
+
+
 def cell_updates_per_s(cells, iterations, ms):
     """The paper's throughput definition (Table III): cells x iterations / time."""
     return cells * iterations / (ms / 1e3)
@@ -309,6 +448,12 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if a.workload == "ensemble":
+        run_ensemble(a, dev, rank, world, local, barrier)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     nx, ny, nz = a.nx, a.ny, a.nz
     n = nx * ny * nz

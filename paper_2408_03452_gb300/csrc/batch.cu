@@ -428,10 +428,17 @@ int cg_solve_batch(tpfa_batch* b, const float* coef, const double* coef64, const
         if (active[i] && hs[i].done == kRunning) ++again;
       if (again == 0 || relaunch > 64) break;
     }
+    {
+      // every batched sweep launch (and the condition kernel after it) is
+      // counted once in each instance's state: the most any instance saw
+      long long sweeps = 0;
+      for (int i = 0; i < N; ++i)
+        if (active[i] && hs[i].launches > sweeps) sweeps = hs[i].launches;
+      launches += 2 * sweeps;
+    }
     for (int i = 0; i < N; ++i) {
       if (!active[i]) continue;
       iters[i] += hs[i].iter;
-      launches += hs[i].launches;
       rel_inner[i] = hs[i].rho0 > 0 ? sqrt(hs[i].rho / hs[i].rho0) : 0.0;
       const int d = hs[i].done;
       if (d == kGuard || d == kRunning) { status[i] = TPFA_EINTERNAL; active[i] = 0; }
