@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--compare-single", action="store_true",
                     help="ensemble: also time the instances solved one after another")
-    ap.add_argument("--workload", default="paper", choices=["paper", "channelized", "ensemble"],
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "channelized", "ensemble", "table3"],
                     help="paper: 1024x1024x256 layered lognormal, wells, CG to 1e-6 (default); "
                          "channelized: 256^3 sigma-2 background + 1e4 channels, Dirichlet x "
                          "ends, refined to 1e-10 (the mixed-precision configuration)")
@@ -278,6 +279,69 @@ def sweep_traffic(nx, ny, nz):
         return None
 
 
+# Table III of the paper (Section V.C): grid, CG iterations, CS-2 and A100
+# times of the whole CG solve (Alg. 1), in seconds.  Context, not targets.
+TABLE3 = [((200, 200, 922), 226, 0.0251, 2.8021), ((400, 400, 922), 225, 0.0337, 5.6343),
+          ((600, 600, 922), 225, 0.0423, 11.8380), ((750, 600, 922), 225, 0.0456, 16.3473),
+          ((750, 800, 922), 225, 0.0500, 20.9367), ((750, 950, 922), 225, 0.0532, 22.9128),
+          ((750, 994, 922), 225, 0.0542, 23.1879)]
+
+
+def run_table3(a, dev, rank):
+    """Weak-scaling sweep over the paper's Table III grids (nz = 922): the
+    paper-scale recipe (layered lognormal, d = 1e-3, corner wells) on each
+    grid, 225 CG iterations as in the table, timed with CUDA events
+    (coefficient build, right-hand side, the iterations and the FP64 check)."""
+    import torch
+    from paper_2408_03452_gb300 import tpfa
+    rows = []
+    for (nx, ny, nz), it_paper, cs2_s, a100_s in TABLE3:
+        n = nx * ny * nz
+        w = synth.paper_scale(seed=a.seed, nx=nx, ny=ny, nz=nz)
+        K = torch.from_numpy(w["K"]).to(dev)
+        si, sv = torch.from_numpy(w["src_idx"]).to(dev), torch.from_numpy(w["src_val"]).to(dev)
+        del w
+        with tpfa.Context(nx, ny, nz, device=dev) as ctx:
+            ctx.set_option("precond", a.precond)
+            coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
+            coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
+            b = torch.empty(n, dtype=torch.float64, device=dev)
+            x = torch.empty(n, dtype=torch.float64, device=dev)
+            times = []
+            for rep in range(1 + max(a.steps, 1)):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.build_trans(K, None, None, 1e-3, coef=coef, coef64=coef64)
+                ctx.build_rhs(K, None, None, None, si, sv, b=b)
+                x.zero_()
+                _, info = ctx.cg_solve(coef, coef64, b, x=x, tol=1e-30, maxit=225, check=False)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep > 0:  # the first run is a warm-up
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            t = sum(times) / len(times)
+            rows.append({"grid": [nx, ny, nz], "cells": n, "iters": info["iters"],
+                         "time_s": t, "gcell_s": n * info["iters"] / t / 1e9,
+                         "sweep_ms": info["inner_ms"] / max(info["iters"], 1),
+                         "paper_cs2_s": cs2_s, "paper_a100_s": a100_s,
+                         "paper_iters": it_paper})
+        del K, coef, coef64, b, x
+        torch.cuda.empty_cache()
+    if rank == 0:
+        last = rows[-1]
+        print(json.dumps({
+            "metric": METRIC, "value": last["cells"] * last["iters"] / last["time_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": 1,
+            "ms_per_step": 1e3 * last["time_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Table III weak-scaling grids (nz = 922) with the paper-scale "
+                                   "recipe, 225 CG iterations each, "
+                                   + ("plain CG" if a.precond == 0 else "Jacobi PCG")},
+            "sweep": rows}))
+
+
 def run_ensemble(a, dev, rank, world, local, barrier):
     """Batched-ensemble step: build + batched CG solve of every instance."""
     import torch
@@ -449,6 +513,9 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if a.workload == "table3":
+        run_table3(a, dev, rank)
+        return
     if a.workload == "ensemble":
         run_ensemble(a, dev, rank, world, local, barrier)
         if world > 1:

@@ -153,6 +153,19 @@ int tpfa_build_rhs(tpfa_ctx* ctx, const double* K, const uint8_t* dirichlet, con
                    double* b, void* stream);
 
 /*
+ * Right-hand side of one backward-Euler time step of the slightly
+ * compressible problem (Section II.A: implicit time discretisation; the
+ * accumulation diagonal d = c V / dt is the one given to tpfa_build_trans):
+ *   b = (tpfa_build_rhs) + d_K p_prev_K   on interior cells,
+ * so that solving A p = b gives p^{n+1} from p^n = p_prev.  d / d_uniform:
+ * as for tpfa_build_trans.  p_prev: dev, N doubles (must not alias b).
+ */
+int tpfa_build_rhs_transient(tpfa_ctx* ctx, const double* K, const uint8_t* dirichlet,
+                             const double* q, const double* pD, const int64_t* src_idx,
+                             const double* src_val, int64_t n_src, const double* d,
+                             double d_uniform, const double* p_prev, double* b, void* stream);
+
+/*
  * Matrix-free operator application (Eq. 6, Alg. 2) in FP32:
  *   Ap_K = D_K p_K - Tx_K p_{K+x} - Tx_{K-x} p_{K-x} - Ty_K p_{K+y}
  *          - Ty_{K-y} p_{K-y} - Tz_K p_{K+z} - Tz_{K-z} p_{K-z}

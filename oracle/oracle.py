@@ -60,6 +60,7 @@ def _L():
         _lib.orc_assemble.argtypes = [G, P, P, P, C.c_double, C.c_int, P, P, P]
         _lib.orc_assemble.restype = C.c_int64
         _lib.orc_rhs.argtypes = [G, P, P, P, P, C.c_int, P]
+        _lib.orc_rhs_transient.argtypes = [G, P, P, P, P, P, C.c_double, P, P]
         _lib.orc_coefficients.argtypes = [G, P, P, P, C.c_double, P, P, P, P]
         _lib.orc_face_trans.argtypes = [G, P, P, P, P]
         _lib.orc_extra_diagonal.argtypes = [G, P, P, P, C.c_double, P]
@@ -146,6 +147,29 @@ def rhs(g: Grid, K, mask=None, q=None, pD=None, literal=False):
     _L().orc_rhs(g._c(), _p(_f64(K)), _p(_u8(mask)), _p(_f64(q)), _p(_f64(pD)),
                  int(bool(literal)), _p(b))
     return b
+
+
+def rhs_transient(g: Grid, K, mask, q, pD, d, p_prev):
+    """Right-hand side of one backward-Euler step: rhs + d * p_prev on interior cells."""
+    da, d0 = _dargs(d)
+    b = np.empty(g.n)
+    _L().orc_rhs_transient(g._c(), _p(_f64(K)), _p(_u8(mask)), _p(_f64(q)), _p(_f64(pD)),
+                           _p(da), d0, _p(_f64(p_prev)), _p(b))
+    return b
+
+
+def transient(g: Grid, K, mask, d, q, pD, p0, steps, tol=1e-12):
+    """Backward-Euler steps: A p^{n+1} = q + d p^n (+ Dirichlet lifts), each
+    solved by CG from p^n.  Returns the list [p^1, ..., p^steps]."""
+    A = assemble(g, K, mask, d)
+    out, p = [], _f64(p0).copy()
+    for _ in range(steps):
+        b = rhs_transient(g, K, mask, q, pD, d, p)
+        p, st, _, _ = cg(A, b, x0=p, tol=tol)
+        if st < 0:
+            raise RuntimeError(f"oracle CG failed with status {st}")
+        out.append(p.copy())
+    return out
 
 
 def coefficients(g: Grid, K, mask=None, d=None):

@@ -156,6 +156,19 @@ void orc_rhs(const orc_grid* g, const double* K, const uint8_t* mask, const doub
   }
 }
 
+/* Right-hand side of one backward-Euler step of the slightly compressible
+ * problem (Section II.A, implicit time discretisation): the accumulation
+ * d_K (p_K^{n+1} - p_K^n) joins the flux balance, so the known part
+ * d_K p_K^n adds to the interior rows of orc_rhs. */
+void orc_rhs_transient(const orc_grid* g, const double* K, const uint8_t* mask, const double* q,
+                       const double* pD, const double* d, double d0, const double* p_prev,
+                       double* b) {
+  orc_rhs(g, K, mask, q, pD, 0, b);
+  int64_t N = ncells(g);
+  for (int64_t c = 0; c < N; ++c)
+    if (!is_dir(mask, c)) b[c] += dval(d, d0, c) * p_prev[c];
+}
+
 /* The eliminated operator as a coefficient set: for each cell the +x, +y, +z
  * face transmissibility (0 on the outer boundary and on faces that touch a
  * Dirichlet cell) and the diagonal (1 on Dirichlet cells). */

@@ -507,6 +507,23 @@ static int apply_impl(tpfa_ctx* c, const void* coef, bool b16, const float* p, f
   return TPFA_OK;
 }
 
+int tpfa_build_rhs_transient(tpfa_ctx* c, const double* K, const uint8_t* dirichlet,
+                             const double* q, const double* pD, const int64_t* src_idx,
+                             const double* src_val, int64_t n_src, const double* d,
+                             double d_uniform, const double* p_prev, double* b, void* stream) {
+  if (c == nullptr) return TPFA_EINVAL;
+  int rc = use_device(c);
+  if (rc) return rc;
+  const size_t n = (size_t)c->g.n;
+  if (!dev_ok(p_prev, n * 8, 8, c->device) || !opt_dev_ok(d, n * 8, 8, c->device)) return TPFA_EINVAL;
+  if (d == nullptr && !(d_uniform >= 0.0 && isfinite(d_uniform))) return TPFA_EINVAL;
+  if ((const void*)p_prev == (const void*)b) return TPFA_EINVAL;
+  rc = tpfa_build_rhs(c, K, dirichlet, q, pD, src_idx, src_val, n_src, b, stream);
+  if (rc) return rc;
+  CK(launch_accumulation(c->g, dirichlet, d, d_uniform, p_prev, b, (cudaStream_t)stream));
+  return TPFA_OK;
+}
+
 int tpfa_apply(tpfa_ctx* c, const float* coef, const float* p, float* Ap, double* pAp,
                void* stream) {
   return apply_impl(c, coef, false, p, Ap, pAp, stream);

@@ -160,6 +160,16 @@ __global__ void add_sources_kernel(Grid g, const uint8_t* __restrict__ mask,
   }
 }
 
+// Known part of the accumulation term of one backward-Euler step:
+// b_K += d_K p_K^n on interior cells.
+__global__ void __launch_bounds__(kElemThreads)
+accumulation_kernel(Grid g, const uint8_t* __restrict__ mask, const double* __restrict__ d,
+                    double d0, const double* __restrict__ p_prev, double* __restrict__ b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride)
+    if (!is_dir(mask, c)) b[c] += (d != nullptr ? d[c] : d0) * p_prev[c];
+}
+
 Geo make_geo(const tpfa_grid& geo) {
   Geo o;
   o.ax = (geo.dy * geo.dz) / geo.mu;
@@ -183,6 +193,12 @@ cudaError_t launch_build_trans(const Grid& g, const tpfa_grid& geo, const double
                                double* coef64, cudaStream_t s) {
   build_trans_kernel<<<grid_for(g), kElemThreads, 0, s>>>(g, make_geo(geo), K, mask, d, d0, coef,
                                                           reinterpret_cast<double2*>(coef64));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulation(const Grid& g, const uint8_t* mask, const double* d, double d0,
+                                const double* p_prev, double* b, cudaStream_t s) {
+  accumulation_kernel<<<grid_for(g), kElemThreads, 0, s>>>(g, mask, d, d0, p_prev, b);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,8 @@ cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const void* coef, bo
 cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
                                    CgState* st, double* partials, unsigned int* counter,
                                    unsigned long long cond, int use_cond, cudaStream_t s);
+cudaError_t launch_accumulation(const Grid& g, const uint8_t* mask, const double* d, double d0,
+                                const double* p_prev, double* b, cudaStream_t s);
 cudaError_t launch_build_trans_bf16(const Grid& g, const tpfa_grid& geo, const double* K,
                                     const uint8_t* mask, const double* d, double d0,
                                     uint2* coef16, cudaStream_t s);

@@ -56,6 +56,8 @@ SIGNATURES = {
     "tpfa_build_trans": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P, _P]),
     "tpfa_build_rhs": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     "tpfa_apply": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "tpfa_build_rhs_transient": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_double,
+                                           _P, _P, _P]),
     "tpfa_residual64": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
     "tpfa_apply_noalloc": (C.c_int, [C.POINTER(_Grid), _P, _P, _P, _P, _P]),
@@ -206,6 +208,25 @@ class Context:
                 _ptr(src_idx, torch.int64, ns, dev, "src_idx") if ns else None,
                 _ptr(src_val, torch.float64, ns, dev, "src_val") if ns else None, ns,
                 _ptr(b, torch.float64, n, dev, "b"), _stream(dev)), "tpfa_build_rhs")
+        return b
+
+    def build_rhs_transient(self, K, p_prev, dirichlet=None, q=None, pD=None, src_idx=None,
+                            src_val=None, d=None, d_uniform=0.0, b=None):
+        """Right-hand side of one backward-Euler step from p_prev (float64 [N])."""
+        dev, n = self.device, self.n
+        if b is None:
+            b = torch.empty(n, dtype=torch.float64, device=dev)
+        ns = 0 if src_idx is None else int(src_idx.numel())
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_build_rhs_transient(
+                self._h, _ptr(K, torch.float64, n, dev, "K"),
+                _ptr(dirichlet, torch.uint8, n, dev, "dirichlet"),
+                _ptr(q, torch.float64, n, dev, "q"), _ptr(pD, torch.float64, n, dev, "pD"),
+                _ptr(src_idx, torch.int64, ns, dev, "src_idx") if ns else None,
+                _ptr(src_val, torch.float64, ns, dev, "src_val") if ns else None, ns,
+                _ptr(d, torch.float64, n, dev, "d"), float(d_uniform),
+                _ptr(p_prev, torch.float64, n, dev, "p_prev"),
+                _ptr(b, torch.float64, n, dev, "b"), _stream(dev)), "tpfa_build_rhs_transient")
         return b
 
     # -- operator --------------------------------------------------------------

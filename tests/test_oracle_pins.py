@@ -292,3 +292,48 @@ def test_face_form_with_extra_diagonal_reproduces_csr(oracle_mod):
     # D = sum of the six T' + E to rounding; E = 1 and T' = 0 around Dirichlet cells
     m = mask.astype(bool)
     assert np.all(E[m] == 1.0)
+
+
+def test_transient_single_cell_closed_form(oracle_mod):
+    """One cell, no faces: d (p^{n+1} - p^n) = q, so p^n = p^0 + n q / d."""
+    O = oracle_mod
+    g = _grid(O, 1, 1, 1)
+    ps = O.transient(g, np.array([3.0]), None, 0.25, np.array([0.5]), None, np.array([1.0]), 4)
+    np.testing.assert_allclose([p[0] for p in ps], [1.0 + 2.0 * k for k in range(1, 5)], rtol=1e-14)
+
+
+def test_transient_mass_balance(oracle_mod):
+    """No Dirichlet cells: summing the rows of each step gives
+    sum d (p^{n+1} - p^n) = sum q, so sum d p^n = sum d p^0 + n sum q."""
+    O = oracle_mod
+    nx, ny, nz = 7, 6, 5
+    g = _grid(O, nx, ny, nz, dx=0.8, dy=1.1, dz=1.3, mu=1.2)
+    K = synth.lognormal_field(nx, ny, nz, 1.0, 21)
+    n = g.n
+    d = 0.05 + 0.1 * synth.uniform(21, 3, np.arange(n))
+    q = np.zeros(n)
+    q[3], q[n - 5] = 0.7, -0.2
+    p0 = synth.uniform_field(n, 22)
+    ps = O.transient(g, K, None, d, q, None, p0, 5, tol=1e-14)
+    for k, p in enumerate(ps, start=1):
+        assert np.dot(d, p) == pytest.approx(np.dot(d, p0) + k * q.sum(), rel=1e-11)
+
+
+def test_transient_step_matches_dense_implicit_euler(oracle_mod):
+    """Small grid with Dirichlet cells: each oracle step equals the dense
+    implicit-Euler update (A_eliminated) p^{n+1} = b_lift + q + D_acc p^n
+    solved with LAPACK."""
+    O = oracle_mod
+    nx, ny, nz = 5, 4, 3
+    g = _grid(O, nx, ny, nz)
+    K = synth.lognormal_field(nx, ny, nz, 1.0, 23)
+    mask, pD = synth.dirichlet_faces(nx, ny, nz, "x", 2.0, 0.5)
+    d = 0.3
+    p0 = np.where(mask == 1, pD, 0.0)
+    ps = O.transient(g, K, mask, d, None, pD, p0, 3, tol=1e-14)
+    A = O.assemble(g, K, mask, d).dense()
+    b0 = O.rhs(g, K, mask, None, pD)
+    p = p0.copy()
+    for k in range(3):
+        p = np.linalg.solve(A, b0 + np.where(mask == 1, 0.0, d * p))
+        np.testing.assert_allclose(ps[k], p, rtol=0, atol=1e-11)
