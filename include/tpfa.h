@@ -280,6 +280,18 @@ int cg_solve_batch(tpfa_batch* batch, const float* coef, const double* coef64, c
                    tpfa_cg_info* total, void* stream);
 
 /*
+ * Tensor-core GEMM tile (tcgen05, BF16 inputs, FP32 accumulation in tensor
+ * memory): C[M x N] = A[M x K] * B[K x N], with A row-major (K contiguous),
+ * B passed as its transpose Bt[N x K] (K contiguous), C row-major FP32; all
+ * dev, 16-byte aligned.  1 <= M, K a multiple of 16 up to 256, N in
+ * {16, 32, 64, 128}.  The building block of the learned preconditioner's
+ * implicit-GEMM convolutions, exposed so that it can be checked on its own.
+ * Waits for the stream; TPFA_EINTERNAL if the tensor core did not complete.
+ */
+int tpfa_tc_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, int M, int N, int K,
+                      void* stream);
+
+/*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a library convenience.
  *

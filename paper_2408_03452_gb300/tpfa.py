@@ -61,6 +61,7 @@ SIGNATURES = {
     "tpfa_residual64": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
     "tpfa_apply_noalloc": (C.c_int, [C.POINTER(_Grid), _P, _P, _P, _P, _P]),
+    "tpfa_tc_gemm_bf16": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, _P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "tpfa_apply_bf16": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "cg_solve_bf16": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
@@ -98,6 +99,20 @@ def strerror(code: int) -> str:
 
 def abi_version() -> int:
     return lib().tpfa_abi_version()
+
+
+def tc_gemm_bf16(A, Bt, C=None):
+    """C = A @ Bt.T on the tensor cores (A [M,K], Bt [N,K] bfloat16; C float32)."""
+    M, K = A.shape
+    N = Bt.shape[0]
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    dev = A.device
+    _check(lib().tpfa_tc_gemm_bf16(_ptr(A, torch.bfloat16, M * K, dev, "A"),
+                                   _ptr(Bt, torch.bfloat16, N * K, dev, "Bt"),
+                                   _ptr(C, torch.float32, M * N, dev, "C"), M, N, K,
+                                   _stream(dev)), "tpfa_tc_gemm_bf16")
+    return C
 
 
 def _check(code: int, where: str, allow=(OK,)):
