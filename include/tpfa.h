@@ -292,6 +292,44 @@ int tpfa_tc_gemm_bf16(const uint16_t* A, const uint16_t* Bt, float* C, int M, in
                       void* stream);
 
 /*
+ * Learned preconditioner: 3x3x3 convolutions (the layers of a 3D U-Net,
+ * Ronneberger et al. 2015) on the tensor cores.  Not part of the paper's
+ * method, which runs CG unpreconditioned; the preconditioner only changes how
+ * fast the same system converges.
+ *
+ * Volumes use the haloed channels-last BF16 layout: ns samples of
+ * nz x ny x nx cells, each padded with a one-cell zero halo, channels
+ * innermost; element (s, z, y, x, c) sits at
+ *   ((((s*(nz+2) + z+1)*(ny+2) + y+1)*(nx+2) + x+1)*C + c,
+ * V = (nx+2)(ny+2)(nz+2) ns voxels.  The caller zeroes a volume once; these
+ * calls never write its halo, which is what makes the convolution zero-padded
+ * and keeps samples apart.  Weights w[27][cout][ci] with tap
+ * t = 9(dz+1) + 3(dy+1) + (dx+1):
+ *   y[v][co] = bias[co] + sum_t sum_ci x[v + off_t][ci] w[t][co][ci].
+ * Supported (cin, cout): (16,16) (16,32) (32,16) (32,64) (64,32).
+ * All pointers dev, 16-byte aligned; V*(nx+2)-sized indices must fit in int.
+ * Asynchronous on the stream: a tensor-core wait that gives up is reported by
+ * the next tpfa_net_status.
+ */
+#define TPFA_CONV_RELU 1 /* y = max(y, 0) */
+#define TPFA_CONV_MASK 2 /* y = 0 where mask[v][co] <= 0 (ReLU derivative) */
+/* y [V][cout] = flags-epilogue(conv(x [V][cin]; w) + bias); bias may be NULL;
+ * mask [V][cout] read only with TPFA_CONV_MASK.  x and y must not overlap.
+ * The input gradient of a layer is this call with the taps flipped and each
+ * tap's matrix transposed (w'[t][ci][co] = w[26-t][co][ci]). */
+int tpfa_conv3d_bf16(const uint16_t* x, const uint16_t* w, const float* bias,
+                     const uint16_t* mask, uint16_t* y, int nx, int ny, int nz, int ns, int cin,
+                     int cout, int flags, void* stream);
+/* Weight gradient: dw[t][co][ci] (+)= sum_v dy[v][co] x[v + off_t][ci] over all
+ * voxels, FP32 (accumulate != 0 adds to dw).  Allocates a stream-ordered
+ * workspace. */
+int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int nx, int ny,
+                           int nz, int ns, int cin, int cout, int accumulate, void* stream);
+/* Waits for the stream; TPFA_EINTERNAL (and clears the flag) if any
+ * tensor-core wait of the convolution kernels gave up since the last call. */
+int tpfa_net_status(void* stream);
+
+/*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a library convenience.
  *

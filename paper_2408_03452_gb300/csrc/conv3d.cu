@@ -1,0 +1,508 @@
+// 3x3x3 convolutions of BF16 channels-last volumes on the tcgen05 tensor
+// cores (implicit GEMM, FP32 accumulation in tensor memory).
+//
+// Forward (and input gradient).  An output tile is 128 consecutive voxel
+// indices of the haloed layout (halo voxels inside the range are computed
+// and discarded).  For one z-offset dz the three rows dy = -1, 0, 1 of 130
+// voxels (the tile plus one voxel either side) are copied to shared memory
+// as "row groups" in the K-major core-matrix layout [CIN/8][130][8 channels],
+// i.e. 16 bytes per voxel and channel block.  With M-direction stride 128
+// bytes per 8 voxels, tap (dy, dx) of the GEMM operand A[m][ci] =
+// x[s0 + m + off][ci] is the row group of dy started dx voxels later -- a
+// descriptor offset of 16 dx bytes, no data movement.  Each (dz, dy, dx, 16
+// channel) step is one tcgen05.mma with M = 128, N = COUT, K = 16 against
+// the weights of that tap, which sit in shared memory for the whole
+// persistent CTA.  The dz row-group triples are double-buffered: the copy
+// of the next one runs while the tensor core works on the current one.
+// Epilogue: bias, ReLU or a ReLU-derivative mask, BF16 rounding, halo skip.
+// The input gradient of a convolution is the same operation with the taps
+// flipped and the weight matrices transposed.
+//
+// Weight gradient.  dw[t][co][ci] = sum_v dy[v][co] x[v + off_t][ci] is a
+// GEMM with rows (t, ci) -- 128/CIN taps per 128-row tile -- columns co and
+// the voxels as the reduction.  Chunks of 64 voxels of x (shifted per tap)
+// and of dy are transposed 8x8 at a time with movmatrix into K-major tiles;
+// CTAs split the voxel range, write FP32 partial tiles, and a second kernel
+// adds the partials in a fixed order.
+#include <cuda_bf16.h>
+
+#include "net_internal.cuh"
+#include "tc_common.cuh"
+#include "tpfa_internal.cuh"
+
+namespace tpfa {
+namespace net {
+
+// Set (never cleared by a kernel) when a bounded tensor-core wait gave up.
+__device__ int g_tc_timeout;
+
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before giving up
+constexpr int kRG = 130;                   // voxels per staged row group
+
+__device__ __forceinline__ void cp16z(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(tc::smem_addr(dst)),
+               "l"(src), "r"(ok ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit_group() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t movmatrix_trans(uint32_t a) {
+  uint32_t d;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+  return d;
+}
+
+__device__ __forceinline__ bool bf16_positive(uint32_t h) {
+  return (h & 0x8000u) == 0 && (h & 0x7fffu) != 0;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int CIN, int COUT>
+struct FwdCfg {
+  static constexpr int kWTap = COUT * CIN * 2;  // bytes of one tap's weight matrix
+  static constexpr int kWBytes = 27 * kWTap;
+  static constexpr int kRGBytes = kRG * CIN * 2;
+  static constexpr int kStage = 3 * kRGBytes;
+  static constexpr int kSmem = kWBytes + 2 * kStage;
+  static constexpr uint32_t kCols = COUT < 32 ? 32 : COUT;
+  static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "shape");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
+                const float* __restrict__ bias, const uint16_t* __restrict__ mask,
+                uint16_t* __restrict__ y, Vol g, int flags, int ntiles) {
+  using Cfg = FwdCfg<CIN, COUT>;
+  constexpr int kc = CIN / 8;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tbase;
+  unsigned char* sW = sm;
+  unsigned char* sS = sm + Cfg::kWBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < 27 * COUT * kc; i += 128) {
+    const int c = i % kc, r = (i / kc) % COUT, t = i / (kc * COUT);
+    const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
+    *reinterpret_cast<uint4*>(sW + t * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t acc = tbase;
+
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int njobs = 3 * my_tiles;  // job = (tile, dz)
+
+  auto load_job = [&](int j, int buf) {
+    const int tile = blockIdx.x + (j / 3) * gridDim.x;
+    const int dz = j % 3 - 1;
+    const int base = g.g0 + tile * 128 + dz * g.pp - g.wp - 1;
+    unsigned char* st = sS + buf * Cfg::kStage;
+    for (int i = tid; i < 3 * kRG * kc; i += 128) {
+      const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+      const int row = base + gi * g.wp + v;
+      const bool ok = row >= 0 && row < g.vp;
+      cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
+            x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+    }
+    cp_commit_group();
+  };
+
+  bool abort = false;
+  if (njobs > 0) load_job(0, 0);
+  for (int j = 0; j < njobs; ++j) {
+    const int buf = j & 1;
+    cp_wait_all();
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const int dzi = j % 3;
+      const uint32_t st = tc::smem_addr(sS + buf * Cfg::kStage);
+      const uint32_t wb = tc::smem_addr(sW);
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+#pragma unroll 1
+      for (int gi = 0; gi < 3; ++gi) {
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int t = dzi * 9 + gi * 3 + dx;
+#pragma unroll
+          for (int ks = 0; ks < CIN / 16; ++ks) {
+            const uint64_t ad = tc::smem_desc(st + gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16,
+                                              kRG * 16, 128);
+            const uint64_t bd = tc::smem_desc(wb + t * Cfg::kWTap + ks * 256, 128, kc * 128);
+            tc::mma_bf16(acc, ad, bd, idesc, (dzi | gi | dx | ks) != 0);
+          }
+        }
+      }
+      tc::mma_commit(&bars[buf]);
+    }
+    if (j + 1 < njobs) {
+      // the other buffer is free once the MMAs of job j-1 have completed
+      bool ok = true;
+      if (j >= 1) ok = tc::mbar_wait(&bars[buf ^ 1], ((j - 1) >> 1) & 1, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      load_job(j + 1, buf ^ 1);
+    }
+    if (j % 3 == 2) {
+      const bool ok = tc::mbar_wait(&bars[buf], (j >> 1) & 1, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      tc::fence_after();
+      const int tile = blockIdx.x + (j / 3) * gridDim.x;
+      const int idx = g.g0 + tile * 128 + warp * 32 + lane;
+      const bool in = vol_interior(g, idx);
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 8) {
+        float v[8];
+        tc::tmem_ld8(acc + ((uint32_t)(warp * 32) << 16) + c0, v);
+        if (in) {
+          uint4 mk = make_uint4(0, 0, 0, 0);
+          if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + (size_t)idx * COUT + c0);
+          const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+          uint32_t o[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            float a = v[2 * h], b = v[2 * h + 1];
+            if (bias) {
+              a += bias[c0 + 2 * h];
+              b += bias[c0 + 2 * h + 1];
+            }
+            if (flags & kConvRelu) {
+              a = fmaxf(a, 0.f);
+              b = fmaxf(b, 0.f);
+            }
+            if (flags & kConvMask) {
+              if (!bf16_positive(mw[h] & 0xffffu)) a = 0.f;
+              if (!bf16_positive(mw[h] >> 16)) b = 0.f;
+            }
+            o[h] = pack_bf16(a, b);
+          }
+          *reinterpret_cast<uint4*>(y + (size_t)idx * COUT + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+      }
+      tc::fence_before();
+    }
+  }
+  cp_wait_all();
+  if (abort && tid == 0) atomicOr(&g_tc_timeout, 1);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(acc, Cfg::kCols);
+}
+
+template <int CIN, int COUT>
+struct WgCfg {
+  static constexpr int kTaps = 128 / CIN;                    // taps per 128-row tile
+  static constexpr int kMTiles = (27 + kTaps - 1) / kTaps;
+  static constexpr int kKV = 64;                             // voxels per reduction chunk
+  static constexpr int kABytes = 128 * kKV * 2;
+  static constexpr int kBBytes = COUT * kKV * 2;
+  static constexpr int kStage = kABytes + kBBytes;
+  static constexpr int kSmem = 2 * kStage;
+  static constexpr uint32_t kCols = COUT < 32 ? 32 : COUT;
+  static_assert(128 % CIN == 0, "CIN must divide 128");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv_wgrad_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ dy,
+                  float* __restrict__ ws, Vol g, int nchunks) {
+  using Cfg = WgCfg<CIN, COUT>;
+  constexpr int kKV = Cfg::kKV;
+  constexpr int kAB = Cfg::kTaps * (CIN / 8) * (kKV / 8);  // 8x8 blocks of A per chunk
+  constexpr int kBB = (COUT / 8) * (kKV / 8);              // 8x8 blocks of B per chunk
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
+  const int my = (nchunks - split + nsplit - 1) / nsplit;
+
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t acc = tbase;
+  bool abort = false;
+
+  for (int i = 0; i < my; ++i) {
+    const int buf = i & 1;
+    if (i >= 2) {
+      const bool ok = tc::mbar_wait(&bars[buf], ((i - 2) >> 1) & 1, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+    }
+    const int v0 = g.g0 + (split + i * nsplit) * kKV;
+    unsigned char* sA = sm + buf * Cfg::kStage;
+    unsigned char* sB = sA + Cfg::kABytes;
+    for (int b = warp; b < kAB + kBB; b += 4) {
+      uint32_t val = 0;
+      if (b < kAB) {
+        const int vb = b % 8, cb = (b / 8) % (CIN / 8), tl = b / (8 * (CIN / 8));
+        const int t = mt * Cfg::kTaps + tl;
+        if (t < 27) {
+          const int off = (t / 9 - 1) * g.pp + ((t / 3) % 3 - 1) * g.wp + (t % 3 - 1);
+          const int v = v0 + vb * 8 + (lane >> 2) + off;
+          if (v >= 0 && v < g.vp)
+            val = *reinterpret_cast<const uint32_t*>(x + (size_t)v * CIN + cb * 8 + 2 * (lane & 3));
+        }
+        val = movmatrix_trans(val);
+        *reinterpret_cast<uint32_t*>(
+            sA + tc::kmajor_off(tl * CIN + cb * 8 + (lane >> 2), vb * 8 + 2 * (lane & 3), kKV)) = val;
+      } else {
+        const int bb = b - kAB, vb = bb % 8, cb = bb / 8;
+        const int v = v0 + vb * 8 + (lane >> 2);
+        if (v < g.g1)
+          val = *reinterpret_cast<const uint32_t*>(dy + (size_t)v * COUT + cb * 8 + 2 * (lane & 3));
+        val = movmatrix_trans(val);
+        *reinterpret_cast<uint32_t*>(
+            sB + tc::kmajor_off(cb * 8 + (lane >> 2), vb * 8 + 2 * (lane & 3), kKV)) = val;
+      }
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+      const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB);
+#pragma unroll
+      for (int ks = 0; ks < kKV / 16; ++ks)
+        tc::mma_bf16(acc, tc::smem_desc(a0 + ks * 256, 128, (kKV / 8) * 128),
+                     tc::smem_desc(b0 + ks * 256, 128, (kKV / 8) * 128), idesc, (i | ks) != 0);
+      tc::mma_commit(&bars[buf]);
+    }
+  }
+  if (!abort && my > 0) {
+    const bool ok = tc::mbar_wait(&bars[(my - 1) & 1], ((my - 1) >> 1) & 1, kWaitLimit);
+    if (__syncthreads_or(!ok)) abort = true;
+  }
+  tc::fence_after();
+  float* out = ws + ((size_t)(split * gridDim.x + mt) * 128 + warp * 32 + lane) * COUT;
+  if (!abort && my > 0) {
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 8) {
+      float v[8];
+      tc::tmem_ld8(acc + ((uint32_t)(warp * 32) << 16) + c0, v);
+      *reinterpret_cast<float4*>(out + c0) = make_float4(v[0], v[1], v[2], v[3]);
+      *reinterpret_cast<float4*>(out + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    }
+  } else {
+    for (int c = 0; c < COUT; ++c) out[c] = 0.f;
+    if (abort && tid == 0) atomicOr(&g_tc_timeout, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(acc, Cfg::kCols);
+}
+
+template <int CIN, int COUT>
+__global__ void wgrad_reduce_kernel(const float* __restrict__ ws, float* __restrict__ dw,
+                                    int nsplit, int accumulate) {
+  using Cfg = WgCfg<CIN, COUT>;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 27 * COUT * CIN) return;
+  const int ci = i % CIN, co = (i / CIN) % COUT, t = i / (CIN * COUT);
+  const int mt = t / Cfg::kTaps, row = (t % Cfg::kTaps) * CIN + ci;
+  double s = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp)
+    s += ws[((size_t)(sp * Cfg::kMTiles + mt) * 128 + row) * COUT + co];
+  dw[i] = accumulate ? (float)(dw[i] + s) : (float)s;
+}
+
+template <int CIN, int COUT>
+int fwd_grid(int ntiles) {
+  static int per_sm = -1, nsm = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         FwdCfg<CIN, COUT>::kSmem);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, conv_fwd_kernel<CIN, COUT>, 128,
+                                                  FwdCfg<CIN, COUT>::kSmem);
+    per_sm = b < 1 ? 1 : b;
+  }
+  const int cap = per_sm * nsm;
+  return ntiles < cap ? ntiles : cap;
+}
+
+template <int CIN, int COUT>
+cudaError_t fwd_launch(const uint16_t* x, const uint16_t* w, const float* bias,
+                       const uint16_t* mask, uint16_t* y, const Vol& g, int flags,
+                       cudaStream_t s) {
+  const int ntiles = (g.g1 - g.g0 + 127) / 128;
+  if (ntiles <= 0) return cudaSuccess;
+  const int grid = fwd_grid<CIN, COUT>(ntiles);
+  conv_fwd_kernel<CIN, COUT><<<grid, 128, FwdCfg<CIN, COUT>::kSmem, s>>>(x, w, bias, mask, y, g,
+                                                                        flags, ntiles);
+  return cudaGetLastError();
+}
+
+int wgrad_splits(int mtiles, int nchunks) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int ns = (2 * nsm + mtiles - 1) / mtiles;
+  if (ns > nchunks) ns = nchunks;
+  return ns < 1 ? 1 : ns;
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad_launch(const uint16_t* x, const uint16_t* dy, float* dw, float* ws,
+                         const Vol& g, int accumulate, cudaStream_t s) {
+  using Cfg = WgCfg<CIN, COUT>;
+  const int nchunks = (g.g1 - g.g0 + Cfg::kKV - 1) / Cfg::kKV;
+  const int nsplit = wgrad_splits(Cfg::kMTiles, nchunks);
+  if (nchunks > 0) {
+    cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Cfg::kSmem);
+    conv_wgrad_kernel<CIN, COUT>
+        <<<dim3(Cfg::kMTiles, nsplit), 128, Cfg::kSmem, s>>>(x, dy, ws, g, nchunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int n = 27 * COUT * CIN;
+  wgrad_reduce_kernel<CIN, COUT><<<(n + 255) / 256, 256, 0, s>>>(ws, dw, nchunks > 0 ? nsplit : 0,
+                                                                  accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool vol_ok(int nx, int ny, int nz, int ns) {
+  if (nx < 1 || ny < 1 || nz < 1 || ns < 1) return false;
+  const double v = (double)(nx + 2) * (ny + 2) * (nz + 2) * ns;
+  return v + 4.0 * (nx + 2) * (ny + 2) < 2147483647.0 / 2;
+}
+
+bool conv_shape_ok(int cin, int cout) {
+  return (cin == 16 && (cout == 16 || cout == 32)) || (cin == 32 && (cout == 16 || cout == 64)) ||
+         (cin == 64 && cout == 32);
+}
+
+#define TPFA_CONV_SHAPES(X) X(16, 16) X(16, 32) X(32, 16) X(32, 64) X(64, 32)
+
+cudaError_t conv_fwd(const uint16_t* x, const uint16_t* w, const float* bias, const uint16_t* mask,
+                     uint16_t* y, const Vol& g, int cin, int cout, int flags, cudaStream_t s) {
+#define X(CI, CO) \
+  if (cin == CI && cout == CO) return fwd_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
+  TPFA_CONV_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+size_t conv_wgrad_ws_bytes(const Vol& g, int cin, int cout) {
+  const int mtiles = (27 + 128 / cin - 1) / (128 / cin);
+  const int nchunks = (g.g1 - g.g0 + 63) / 64;
+  const int ns = wgrad_splits(mtiles, nchunks < 1 ? 1 : nchunks);
+  return (size_t)ns * mtiles * 128 * cout * sizeof(float);
+}
+
+cudaError_t conv_wgrad(const uint16_t* x, const uint16_t* dy, float* dw, float* ws, const Vol& g,
+                       int cin, int cout, int accumulate, cudaStream_t s) {
+#define X(CI, CO) \
+  if (cin == CI && cout == CO) return wgrad_launch<CI, CO>(x, dy, dw, ws, g, accumulate, s);
+  TPFA_CONV_SHAPES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace net
+}  // namespace tpfa
+
+using tpfa::net::Vol;
+
+static int conv_args_ok(const void* x, const void* y, int nx, int ny, int nz, int ns, int cin,
+                        int cout, int* dev) {
+  if (!tpfa::net::vol_ok(nx, ny, nz, ns) || !tpfa::net::conv_shape_ok(cin, cout))
+    return TPFA_EINVAL;
+  if (cudaGetDevice(dev) != cudaSuccess) return TPFA_ECUDA;
+  const Vol g = tpfa::net::make_vol(nx, ny, nz, ns);
+  if (!tpfa::dev_ok(x, (size_t)g.vp * cin * 2, 16, *dev) ||
+      !tpfa::dev_ok(y, (size_t)g.vp * cout * 2, 16, *dev))
+    return TPFA_EINVAL;
+  return TPFA_OK;
+}
+
+extern "C" int tpfa_conv3d_bf16(const uint16_t* x, const uint16_t* w, const float* bias,
+                                const uint16_t* mask, uint16_t* y, int nx, int ny, int nz,
+                                int ns, int cin, int cout, int flags, void* stream) {
+  int dev = -1;
+  int rc = conv_args_ok(x, y, nx, ny, nz, ns, cin, cout, &dev);
+  if (rc != TPFA_OK) return rc;
+  if (flags & ~3) return TPFA_EINVAL;
+  const Vol g = tpfa::net::make_vol(nx, ny, nz, ns);
+  if (!tpfa::dev_ok(w, (size_t)27 * cin * cout * 2, 16, dev) ||
+      !tpfa::opt_dev_ok(bias, (size_t)cout * 4, 4, dev))
+    return TPFA_EINVAL;
+  if ((flags & tpfa::net::kConvMask) && !tpfa::dev_ok(mask, (size_t)g.vp * cout * 2, 16, dev))
+    return TPFA_EINVAL;
+  if (x == y) return TPFA_EINVAL;
+  return tpfa::net::conv_fwd(x, w, bias, mask, y, g, cin, cout, flags, (cudaStream_t)stream) ==
+                 cudaSuccess
+             ? TPFA_OK
+             : TPFA_ECUDA;
+}
+
+extern "C" int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int nx,
+                                      int ny, int nz, int ns, int cin, int cout, int accumulate,
+                                      void* stream) {
+  int dev = -1;
+  int rc = conv_args_ok(x, dy, nx, ny, nz, ns, cin, cout, &dev);
+  if (rc != TPFA_OK) return rc;
+  if (!tpfa::dev_ok(dw, (size_t)27 * cin * cout * 4, 4, dev)) return TPFA_EINVAL;
+  const Vol g = tpfa::net::make_vol(nx, ny, nz, ns);
+  cudaStream_t s = (cudaStream_t)stream;
+  float* ws = nullptr;
+  if (cudaMallocAsync((void**)&ws, tpfa::net::conv_wgrad_ws_bytes(g, cin, cout), s) != cudaSuccess)
+    return TPFA_ENOMEM;
+  cudaError_t e = tpfa::net::conv_wgrad(x, dy, dw, ws, g, cin, cout, accumulate, s);
+  cudaFreeAsync(ws, s);
+  return e == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
+// Waits for the stream, then reports (and clears) a tensor-core wait that
+// gave up in any kernel of this library since the last call.
+extern "C" int tpfa_net_status(void* stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TPFA_ECUDA;
+  int h = 0;
+  if (cudaMemcpyFromSymbol(&h, tpfa::net::g_tc_timeout, sizeof(int)) != cudaSuccess)
+    return TPFA_ECUDA;
+  if (h) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(tpfa::net::g_tc_timeout, &zero, sizeof(int));
+    return TPFA_EINTERNAL;
+  }
+  return TPFA_OK;
+}

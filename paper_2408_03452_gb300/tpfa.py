@@ -62,6 +62,9 @@ SIGNATURES = {
     "cg_solve": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
     "tpfa_apply_noalloc": (C.c_int, [C.POINTER(_Grid), _P, _P, _P, _P, _P]),
     "tpfa_tc_gemm_bf16": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, _P]),
+    "tpfa_conv3d_bf16": (C.c_int, [_P, _P, _P, _P, _P] + [C.c_int] * 7 + [_P]),
+    "tpfa_conv3d_wgrad_bf16": (C.c_int, [_P, _P, _P] + [C.c_int] * 7 + [_P]),
+    "tpfa_net_status": (C.c_int, [_P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "tpfa_apply_bf16": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "cg_solve_bf16": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
@@ -113,6 +116,49 @@ def tc_gemm_bf16(A, Bt, C=None):
                                    _ptr(C, torch.float32, M * N, dev, "C"), M, N, K,
                                    _stream(dev)), "tpfa_tc_gemm_bf16")
     return C
+
+
+CONV_RELU, CONV_MASK = 1, 2
+
+
+def halo_voxels(nx: int, ny: int, nz: int, ns: int = 1) -> int:
+    """Voxels of the haloed channels-last layout of ns samples of nz x ny x nx."""
+    return (nx + 2) * (ny + 2) * (nz + 2) * ns
+
+
+def conv3d_bf16(x, w, y, shape, cin, cout, bias=None, mask=None, flags=0):
+    """y = epilogue(conv3x3x3(x; w) + bias) on haloed BF16 volumes (tensor cores).
+
+    shape = (nx, ny, nz, ns); x [V, cin], y [V, cout] and mask [V, cout] are
+    bfloat16 with V = halo_voxels(*shape); w [27, cout, cin] bfloat16; bias
+    [cout] float32.  flags: CONV_RELU, CONV_MASK (zero where mask <= 0)."""
+    dev = x.device
+    V = halo_voxels(*shape)
+    _check(lib().tpfa_conv3d_bf16(_ptr(x, torch.bfloat16, V * cin, dev, "x"),
+                                  _ptr(w, torch.bfloat16, 27 * cin * cout, dev, "w"),
+                                  _ptr(bias, torch.float32, cout, dev, "bias"),
+                                  _ptr(mask, torch.bfloat16, V * cout, dev, "mask"),
+                                  _ptr(y, torch.bfloat16, V * cout, dev, "y"), *shape, cin, cout,
+                                  flags, _stream(dev)), "tpfa_conv3d_bf16")
+    return y
+
+
+def conv3d_wgrad_bf16(x, dy, dw, shape, cin, cout, accumulate=False):
+    """dw[t, co, ci] (+)= sum_v dy[v, co] x[v + off_t, ci] (tensor cores); dw float32."""
+    dev = x.device
+    V = halo_voxels(*shape)
+    _check(lib().tpfa_conv3d_wgrad_bf16(_ptr(x, torch.bfloat16, V * cin, dev, "x"),
+                                        _ptr(dy, torch.bfloat16, V * cout, dev, "dy"),
+                                        _ptr(dw, torch.float32, 27 * cin * cout, dev, "dw"),
+                                        *shape, cin, cout, int(accumulate), _stream(dev)),
+           "tpfa_conv3d_wgrad_bf16")
+    return dw
+
+
+def net_status(device=None):
+    """Synchronise and report a tensor-core wait that gave up (raises)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    _check(lib().tpfa_net_status(_stream(dev)), "tpfa_net_status")
 
 
 def _check(code: int, where: str, allow=(OK,)):
