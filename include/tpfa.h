@@ -330,6 +330,67 @@ int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int
 int tpfa_net_status(void* stream);
 
 /*
+ * The 3-level U-Net preconditioner M(r) = rms(r) * net(r / rms(r), ln K):
+ *   e0 = relu(conv(in; W0 2->16))          level 0 (full resolution)
+ *   e1 = relu(conv(pool(e0); W1 16->32))   level 1 (half, 2x2x2 average pool)
+ *   e2 = relu(conv(pool(e1); W2 32->64))   level 2 (quarter)
+ *   d2 = relu(conv(e2; W3 64->32))         level 2
+ *   s1 = up(d2) + e1                       level 1 (nearest upsampling)
+ *   d1 = relu(conv(s1; W4 32->16))         level 1
+ *   s0 = up(d1) + e0                       level 0
+ *   d0 = relu(conv(s0; W5 16->16))         level 0
+ *   z  = conv(d0; W6 16->1)                level 0
+ * rms(r) = sqrt(mean of r^2) per sample.  Parameters: one FP32 vector of
+ * tpfa_unet_param_count() values, layer by layer W_i[27][cout][cin] then
+ * b_i[cout].  Vectors r, ln K, z, gz: FP32, ns samples of nx*ny*nz cells
+ * each in the solver's x-fastest order, sample after sample.
+ */
+typedef struct tpfa_unet tpfa_unet;
+int64_t tpfa_unet_param_count(void);
+/* nx, ny, nz multiples of 4 (two poolings); ns samples per call; train != 0
+ * also allocates what tpfa_unet_backward needs.  Uses the current device. */
+int tpfa_unet_create(int nx, int ny, int nz, int ns, int train, tpfa_unet** out);
+int tpfa_unet_destroy(tpfa_unet* net);
+/* dims4 (host) = {nx, ny, nz, ns} */
+int tpfa_unet_shape(const tpfa_unet* net, int* dims4);
+/* Converts the FP32 parameters (dev) to the BF16 copies the kernels use
+ * (forward layout, and tap-flipped transposed layout for the input gradients). */
+int tpfa_unet_set_params(tpfa_unet* net, const float* params, void* stream);
+/* z = M(r) for every sample (dev pointers).  Keeps the activations for a
+ * following tpfa_unet_backward.  Asynchronous. */
+int tpfa_unet_forward(tpfa_unet* net, const float* r, const float* lnk, float* z, void* stream);
+/* grad (dev, param_count FP32, overwritten) = d(sum gz . z)/d(params) at the
+ * last forward pass; gz dev.  Requires train.  Asynchronous. */
+int tpfa_unet_backward(tpfa_unet* net, const float* gz, float* grad, void* stream);
+/* One Adam step (Kingma and Ba 2015, Algorithm 1), t >= 1 the step number:
+ * m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ * p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).  All dev FP32, n values. */
+int tpfa_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int t,
+                   double lr, double b1, double b2, double eps, void* stream);
+/* Gradient of the A-norm training loss L = d' A d / (e' A e), d = mr - e, for
+ * one sample on the context's grid: g = 2 A d / eae and dad = d' A d.  coef:
+ * the sample's FP32 coefficient records; eae (dev double) = e' A e; d, q dev
+ * workspace of N floats; all dev.  Asynchronous. */
+int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, const float* e,
+                         const double* eae, float* d, float* q, float* g, double* dad,
+                         void* stream);
+/* Flexible CG (Notay 2000, one retained direction) preconditioned by net
+ * (NULL: the identity, i.e. plain CG), refined in FP64 as cg_solve: outer
+ * r = b - A64 x, inner FP32 FCG on A e = r / ||r|| to
+ * max(TPFA_OPT_INNER_RTOL, 0.3 tol / ||r||/||b||), x += e ||r||.  The inner
+ * iteration falls back to plain CG from its current iterate when p'Ap <= 0,
+ * a value is not finite, or r'r falls by less than 1% over 50 iterations
+ * (*fell_back = 1, may be NULL).  net must have been created for this grid
+ * with ns = 1; lnk dev N floats (ignored without net).  coef, coef64, b, x as
+ * cg_solve.  Waits for the stream.  Returns TPFA_OK, TPFA_NOTCONV (maxit
+ * inner iterations or TPFA_OPT_MAX_OUTER refinements), TPFA_EBREAKDOWN,
+ * TPFA_ENONFINITE, TPFA_EINTERNAL (a tensor-core wait gave up) or an
+ * argument / CUDA error. */
+int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* coef64,
+              const float* lnk, const double* b, double* x, double tol, int64_t maxit,
+              tpfa_cg_info* info, int* fell_back, void* stream);
+
+/*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a library convenience.
  *

@@ -155,46 +155,54 @@ def init_params(seed: int, scale: float = 1.0) -> dict:
     return p
 
 
-def unet_forward(p: dict, inp: np.ndarray):
-    """inp (ns, nz, ny, nx, 2) -> (z (ns, nz, ny, nx), cache)."""
-    c = {"in": inp}
-    c["e0"] = relu(conv3d(inp, p["W0"], p["b0"]))
-    c["p0"] = avgpool2(c["e0"])
-    c["e1"] = relu(conv3d(c["p0"], p["W1"], p["b1"]))
-    c["p1"] = avgpool2(c["e1"])
-    c["e2"] = relu(conv3d(c["p1"], p["W2"], p["b2"]))
-    c["d2"] = relu(conv3d(c["e2"], p["W3"], p["b3"]))
-    c["s1"] = upsample2(c["d2"]) + c["e1"]
-    c["d1"] = relu(conv3d(c["s1"], p["W4"], p["b4"]))
-    c["s0"] = upsample2(c["d1"]) + c["e0"]
-    c["d0"] = relu(conv3d(c["s0"], p["W5"], p["b5"]))
-    z = conv3d(c["d0"], p["W6"], p["b6"])[..., 0]
+def unet_forward(p: dict, inp: np.ndarray, store=None):
+    """inp (ns, nz, ny, nx, 2) -> (z (ns, nz, ny, nx), cache).
+
+    store, if given, is applied to every tensor the network keeps (the input,
+    each activation, each pooled, summed or output tensor), e.g. a rounding
+    to the storage precision of an implementation; by default every value
+    stays exact (FP64)."""
+    st = store or (lambda a: a)
+    c = {"in": st(inp)}
+    c["e0"] = st(relu(conv3d(c["in"], p["W0"], p["b0"])))
+    c["p0"] = st(avgpool2(c["e0"]))
+    c["e1"] = st(relu(conv3d(c["p0"], p["W1"], p["b1"])))
+    c["p1"] = st(avgpool2(c["e1"]))
+    c["e2"] = st(relu(conv3d(c["p1"], p["W2"], p["b2"])))
+    c["d2"] = st(relu(conv3d(c["e2"], p["W3"], p["b3"])))
+    c["s1"] = st(upsample2(c["d2"]) + c["e1"])
+    c["d1"] = st(relu(conv3d(c["s1"], p["W4"], p["b4"])))
+    c["s0"] = st(upsample2(c["d1"]) + c["e0"])
+    c["d0"] = st(relu(conv3d(c["s0"], p["W5"], p["b5"])))
+    z = st(conv3d(c["d0"], p["W6"], p["b6"]))[..., 0]
     return z, c
 
 
-def unet_backward(p: dict, c: dict, dz: np.ndarray) -> dict:
+def unet_backward(p: dict, c: dict, dz: np.ndarray, store=None) -> dict:
     """Reverse-mode derivative of unet_forward: dz (ns, nz, ny, nx) -> grads
-    of every weight and bias (same keys as the parameters)."""
+    of every weight and bias (same keys as the parameters).  store, if given,
+    is applied to every activation gradient that is kept (see unet_forward)."""
+    st = store or (lambda a: a)
     g = {}
 
     def layer_back(name, bname, xin, dpre):
         g[name] = conv3d_wgrad(xin, dpre)
         g[bname] = dpre.sum(axis=(0, 1, 2, 3))
-        return conv3d_adjoint(dpre, p[name])
+        return st(conv3d_adjoint(dpre, p[name]))
 
-    dpre6 = dz[..., None]
+    dpre6 = st(dz)[..., None]
     dd0 = layer_back("W6", "b6", c["d0"], dpre6)
     ds0 = layer_back("W5", "b5", c["s0"], dd0 * (c["d0"] > 0))
-    dd1 = upsample2_adjoint(ds0)
+    dd1 = st(upsample2_adjoint(ds0))
     de0 = ds0.copy()
     ds1 = layer_back("W4", "b4", c["s1"], dd1 * (c["d1"] > 0))
-    dd2 = upsample2_adjoint(ds1)
+    dd2 = st(upsample2_adjoint(ds1))
     de1 = ds1.copy()
     de2 = layer_back("W3", "b3", c["e2"], dd2 * (c["d2"] > 0))
     dp1 = layer_back("W2", "b2", c["p1"], de2 * (c["e2"] > 0))
-    de1 += avgpool2_adjoint(dp1)
+    de1 = st(de1 + avgpool2_adjoint(dp1))
     dp0 = layer_back("W1", "b1", c["p0"], de1 * (c["e1"] > 0))
-    de0 += avgpool2_adjoint(dp0)
+    de0 = st(de0 + avgpool2_adjoint(dp0))
     layer_back("W0", "b0", c["in"], de0 * (c["e0"] > 0))
     return g
 

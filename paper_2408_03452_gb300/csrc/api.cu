@@ -287,6 +287,22 @@ int read_state(tpfa_ctx* c, cudaStream_t s) {
 
 }  // namespace
 
+namespace tpfa {
+int64_t ctx_cells(const tpfa_ctx* c) { return c ? c->g.n : 0; }
+void ctx_dims(const tpfa_ctx* c, int64_t* d3) {
+  d3[0] = c->g.nx;
+  d3[1] = c->g.ny;
+  d3[2] = c->g.nz;
+}
+double ctx_option(const tpfa_ctx* c, int option) {
+  switch (option) {
+    case TPFA_OPT_INNER_RTOL: return c->inner_rtol;
+    case TPFA_OPT_MAX_OUTER: return c->max_outer;
+    default: return 0.0;
+  }
+}
+}  // namespace tpfa
+
 extern "C" {
 
 int tpfa_abi_version(void) { return TPFA_ABI_VERSION; }

@@ -144,6 +144,10 @@ cudaError_t launch_batch_cond(const CgState* st, int ninst, unsigned long long c
 
 // Argument checks shared by the entry points: a device (or managed)
 // allocation on `device` that holds [p, p + bytes) and is `align`-aligned.
+// context accessors for the solvers outside api.cu
+int64_t ctx_cells(const tpfa_ctx* c);
+void ctx_dims(const tpfa_ctx* c, int64_t* d3);
+double ctx_option(const tpfa_ctx* c, int option);
 bool dev_ok(const void* p, size_t bytes, size_t align, int device);
 bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device);
 int elem_blocks(const Grid& g, int num_sms);

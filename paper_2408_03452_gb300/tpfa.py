@@ -65,6 +65,18 @@ SIGNATURES = {
     "tpfa_conv3d_bf16": (C.c_int, [_P, _P, _P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_conv3d_wgrad_bf16": (C.c_int, [_P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_net_status": (C.c_int, [_P]),
+    "tpfa_unet_param_count": (C.c_int64, []),
+    "tpfa_unet_create": (C.c_int, [C.c_int] * 5 + [C.POINTER(C.c_void_p)]),
+    "tpfa_unet_destroy": (C.c_int, [_P]),
+    "tpfa_unet_shape": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "tpfa_unet_set_params": (C.c_int, [_P, _P, _P]),
+    "tpfa_unet_forward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "tpfa_unet_backward": (C.c_int, [_P, _P, _P, _P]),
+    "tpfa_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, _P]),
+    "tpfa_anorm_loss_grad": (C.c_int, [_P] * 10),
+    "fcg_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64,
+                            C.POINTER(_Info), C.POINTER(C.c_int), _P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "tpfa_apply_bf16": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "cg_solve_bf16": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, C.POINTER(_Info), _P]),
@@ -350,6 +362,114 @@ class Context:
         out = {f: getattr(info, f) for f, _ in _Info._fields_}
         out["code"] = code
         return x, out
+
+
+    def fcg_solve(self, coef, coef64, b, net=None, lnk=None, x=None, tol=1e-8, maxit=100000,
+                  check=True):
+        """Flexible CG preconditioned by a UNet (None: plain CG), FP64-refined.
+        Returns (x, info dict with 'fell_back')."""
+        dev, n = self.device, self.n
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+        info = _Info()
+        fb = C.c_int(0)
+        with torch.cuda.device(dev):
+            code = lib().fcg_solve(
+                self._h, net._h if net is not None else None,
+                _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
+                _ptr(lnk, torch.float32, n, dev, "lnk") if net is not None else None,
+                _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
+                float(tol), int(maxit), C.byref(info), C.byref(fb), _stream(dev))
+        if check:
+            _check(code, "fcg_solve", allow=(OK, NOTCONV))
+        out = {f: getattr(info, f) for f, _ in _Info._fields_}
+        out["code"] = code
+        out["fell_back"] = bool(fb.value)
+        return x, out
+
+    def anorm_loss_grad(self, coef, mr, e, eae, d, q, g, dad):
+        """g = 2 A (mr - e) / eae and dad = (mr - e)' A (mr - e) (all dev tensors;
+        eae and dad float64 [1])."""
+        dev, n = self.device, self.n
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_anorm_loss_grad(
+                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(mr, torch.float32, n, dev, "mr"), _ptr(e, torch.float32, n, dev, "e"),
+                _ptr(eae, torch.float64, 1, dev, "eae"), _ptr(d, torch.float32, n, dev, "d"),
+                _ptr(q, torch.float32, n, dev, "q"), _ptr(g, torch.float32, n, dev, "g"),
+                _ptr(dad, torch.float64, 1, dev, "dad"), _stream(dev)), "tpfa_anorm_loss_grad")
+        return g
+
+
+def unet_param_count() -> int:
+    return int(lib().tpfa_unet_param_count())
+
+
+class UNet:
+    """The U-Net preconditioner for ns samples of nx x ny x nz (wraps tpfa_unet_*).
+    Parameters: one float32 tensor of unet_param_count() values."""
+
+    def __init__(self, nx, ny, nz, ns=1, train=False, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        self.shape = (nx, ny, nz, ns)
+        self.n = nx * ny * nz * ns
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().tpfa_unet_create(nx, ny, nz, ns, int(bool(train)), C.byref(self._h)),
+                   "tpfa_unet_create")
+
+    def close(self):
+        if self._h:
+            with torch.cuda.device(self.device):
+                lib().tpfa_unet_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        dev = self.device
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_unet_set_params(
+                self._h, _ptr(params, torch.float32, unet_param_count(), dev, "params"),
+                _stream(dev)), "tpfa_unet_set_params")
+
+    def forward(self, r, lnk, z=None):
+        dev, n = self.device, self.n
+        if z is None:
+            z = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_unet_forward(self._h, _ptr(r, torch.float32, n, dev, "r"),
+                                           _ptr(lnk, torch.float32, n, dev, "lnk"),
+                                           _ptr(z, torch.float32, n, dev, "z"), _stream(dev)),
+                   "tpfa_unet_forward")
+        return z
+
+    def backward(self, gz, grad=None):
+        dev, n = self.device, self.n
+        if grad is None:
+            grad = torch.empty(unet_param_count(), dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_unet_backward(self._h, _ptr(gz, torch.float32, n, dev, "gz"),
+                                            _ptr(grad, torch.float32, grad.numel(), dev, "grad"),
+                                            _stream(dev)), "tpfa_unet_backward")
+        return grad
+
+
+def adam_step(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    dev, n = params.device, params.numel()
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_adam_step(_ptr(params, torch.float32, n, dev, "params"),
+                                    _ptr(grad, torch.float32, n, dev, "grad"),
+                                    _ptr(m, torch.float32, n, dev, "m"),
+                                    _ptr(v, torch.float32, n, dev, "v"), n, int(t), float(lr),
+                                    float(b1), float(b2), float(eps), _stream(dev)),
+               "tpfa_adam_step")
 
 
 class BatchContext:

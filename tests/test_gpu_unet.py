@@ -1,0 +1,233 @@
+"""The U-Net preconditioner, its gradients, Adam, the A-norm loss and flexible
+CG through the C ABI, against the FP64 oracle (oracle/unet_oracle.py).
+
+Tolerances.  The network stores every activation and activation gradient in
+BF16 (unit roundoff 2^-8) and uses BF16 weights.  Two comparisons:
+  * against the exact FP64 oracle on the same BF16-rounded weights: about
+    ten roundings of relative size <= 2^-8 lie on the longest forward path,
+    so the output agrees in relative 2-norm to 3e-2;
+  * against the oracle with its storage hook rounding each kept tensor to
+    BF16 at the same points as the kernels: what remains is FP32
+    accumulation order and the rare BF16 rounding (or ReLU) decision it
+    flips.  The output agrees to 1e-2; a parameter gradient sums over every
+    voxel through up to twenty such stages, where a flipped ReLU mask moves
+    one term by O(1), and agrees to 3e-2 (measured up to 1.9e-2).
+A wrong tap, layer, skip or mask produces O(1) relative errors.  Adam and the loss run in FP32 against
+FP64: relative 1e-5.  Solves are judged by the oracle's FP64 residual.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import unet_oracle as U
+from paper_2408_03452_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_03452_gb300 import build, tpfa
+    build.build()
+    return tpfa
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def params_case(seed):
+    """Oracle parameter dict with BF16-representable weights, non-zero biases,
+    and the flat FP32 vector in the library's layout."""
+    p = U.init_params(seed)
+    rng = np.random.default_rng(seed)
+    flat = []
+    for i, (name, cin, cout) in enumerate(U.LAYERS):
+        p[name] = bf16_round(p[name])
+        p["b%d" % i] = (0.05 * rng.standard_normal(cout)).astype(np.float32).astype(np.float64)
+        flat += [p[name].ravel(), p["b%d" % i]]
+    return p, np.concatenate(flat).astype(np.float32)
+
+
+def flat_grads(g):
+    return np.concatenate([np.concatenate([g[name].ravel(), g["b%d" % i]])
+                           for i, (name, _, _) in enumerate(U.LAYERS)])
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def field_case(shape, ns, seed):
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    r = np.stack([synth.uniform_field(n, seed + s) for s in range(ns)])
+    lnk = np.stack([np.log(synth.lognormal_field(nx, ny, nz, 1.0, seed + 10 + s))
+                    for s in range(ns)])
+    return r, lnk
+
+
+def to_vol(a, shape, ns):
+    nx, ny, nz = shape
+    return a.reshape(ns, nz, ny, nx)
+
+
+@pytest.mark.parametrize("shape,ns", [((8, 8, 8), 2), ((16, 12, 8), 1), ((12, 8, 20), 3)])
+def test_unet_forward_backward_match_oracle(tp, shape, ns):
+    p, flat = params_case(3)
+    r, lnk = field_case(shape, ns, 100)
+    dev = torch.device("cuda")
+    net = tp.UNet(*shape, ns=ns, train=True)
+    net.set_params(torch.from_numpy(flat).to(dev))
+    R = torch.from_numpy(r.ravel().astype(np.float32)).to(dev)
+    LK = torch.from_numpy(lnk.ravel().astype(np.float32)).to(dev)
+    z = net.forward(R, LK)
+    gz = np.stack([synth.uniform_field(r.shape[1], 500 + s) for s in range(ns)])
+    grad = net.backward(torch.from_numpy(gz.ravel().astype(np.float32)).to(dev))
+    tp.net_status()
+    # oracle on the same FP32 inputs
+    r32 = r.astype(np.float32).astype(np.float64)
+    lnk32 = lnk.astype(np.float32).astype(np.float64)
+    inp, rms = U.net_input(to_vol(r32, shape, ns), to_vol(lnk32, shape, ns))
+    zo, cache = U.unet_forward(p, inp)
+    mr = zo * rms[:, None, None, None]
+    assert rel(z.cpu().double().numpy(), mr.ravel()) < 3e-2
+    zb, cache = U.unet_forward(p, inp, store=bf16_round)
+    assert rel(z.cpu().double().numpy(), (zb * rms[:, None, None, None]).ravel()) < 1e-2
+    go = U.unet_backward(p, cache, to_vol(gz, shape, ns) * rms[:, None, None, None],
+                         store=bf16_round)
+    gg = grad.cpu().double().numpy()
+    ref = flat_grads(go)
+    off = 0
+    for i, (name, cin, cout) in enumerate(U.LAYERS):
+        nw = 27 * cin * cout
+        assert rel(gg[off:off + nw], ref[off:off + nw]) < 3e-2, name
+        assert rel(gg[off + nw:off + nw + cout], ref[off + nw:off + nw + cout]) < 3e-2, "b%d" % i
+        off += nw + cout
+    assert off == tp.unet_param_count() == gg.size
+
+
+def test_unet_homogeneous_and_samples_independent(tp):
+    """M(c r) = c M(r) up to BF16 rounding of r/rms (exact for c a power of
+    two), and each sample of a batch equals the same sample run alone."""
+    shape, ns = (8, 8, 12), 3
+    _, flat = params_case(5)
+    r, lnk = field_case(shape, ns, 7)
+    dev = torch.device("cuda")
+    P = torch.from_numpy(flat).to(dev)
+    net = tp.UNet(*shape, ns=ns)
+    net.set_params(P)
+    R = torch.from_numpy(r.ravel().astype(np.float32)).to(dev)
+    LK = torch.from_numpy(lnk.ravel().astype(np.float32)).to(dev)
+    z1 = net.forward(R, LK).clone()
+    z2 = net.forward(4.0 * R, LK)
+    assert torch.equal(z2, 4.0 * z1)
+    one = tp.UNet(*shape, ns=1)
+    one.set_params(P)
+    n = r.shape[1]
+    for s in range(ns):
+        zs = one.forward(R[s * n:(s + 1) * n].contiguous(), LK[s * n:(s + 1) * n].contiguous())
+        assert torch.equal(zs, z1[s * n:(s + 1) * n])
+
+
+def test_adam_matches_oracle(tp):
+    n = 10007
+    rng = np.random.default_rng(1)
+    w, g = rng.standard_normal(n), rng.standard_normal(n)
+    m, v = 0.1 * rng.standard_normal(n), rng.uniform(0, 1, n)
+    dev = torch.device("cuda")
+    W, G, M, V = (torch.from_numpy(a.astype(np.float32)).to(dev) for a in (w, g, m, v))
+    tp.adam_step(W, G, M, V, 7, 1e-3)
+    w32, g32, m32, v32 = (a.astype(np.float32).astype(np.float64) for a in (w, g, m, v))
+    wr, mr, vr = U.adam_step(w32, g32, m32, v32, 7, 1e-3)
+    np.testing.assert_allclose(M.cpu().double().numpy(), mr, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(V.cpu().double().numpy(), vr, rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(W.cpu().double().numpy(), wr, rtol=1e-5, atol=1e-6)
+
+
+def _problem(shape, seed=2, sigma=1.0):
+    nx, ny, nz = shape
+    K = synth.lognormal_field(nx, ny, nz, sigma, seed)
+    mask, pD = synth.dirichlet_faces(nx, ny, nz, "x", 1.0, 0.0)
+    return K, mask, pD
+
+
+def _gpu_problem(tp, shape, K, mask, pD):
+    dev = torch.device("cuda")
+    ctx = tp.Context(*shape)
+    Kd = torch.from_numpy(K).to(dev)
+    md = torch.from_numpy(mask).to(dev)
+    coef, coef64 = ctx.build_trans(Kd, md)
+    b = ctx.build_rhs(Kd, md, pD=torch.from_numpy(pD).to(dev))
+    return ctx, coef, coef64, b
+
+
+def test_anorm_loss_grad_matches_oracle(tp, oracle_mod):
+    O = oracle_mod
+    shape = (12, 10, 8)
+    K, mask, pD = _problem(shape)
+    ctx, coef, coef64, _ = _gpu_problem(tp, shape, K, mask, pD)
+    A = O.assemble(O.Grid(*shape), K, mask)
+    n = A.n
+    e = synth.uniform_field(n, 3).astype(np.float32)
+    mr = (e + 0.3 * synth.uniform_field(n, 4)).astype(np.float32)
+    dev = torch.device("cuda")
+    E, MR = torch.from_numpy(e).to(dev), torch.from_numpy(mr).to(dev)
+    eae = torch.zeros(1, dtype=torch.float64, device=dev)
+    ctx.apply(coef, E, pAp=eae)
+    d, q, g = (torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3))
+    dad = torch.zeros(1, dtype=torch.float64, device=dev)
+    ctx.anorm_loss_grad(coef, MR, E, eae, d, q, g, dad)
+    L_ref, g_ref = U.anorm_loss(mr.astype(np.float64), e.astype(np.float64), A.matvec)
+    L = float(dad.item() / eae.item())
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert rel(g.cpu().double().numpy(), g_ref) < 1e-5
+
+
+def _oracle_rel_residual(O, shape, K, mask, pD, x):
+    return O.rel_residual(O.Grid(*shape), K, mask, 0.0, None, pD, x)
+
+
+def test_fcg_identity_is_plain_cg(tp, oracle_mod):
+    """Without a network FCG is plain CG: it reaches the FP64 tolerance with
+    close to the iteration count of the library's own refined CG solve."""
+    O = oracle_mod
+    shape = (24, 20, 16)
+    K, mask, pD = _problem(shape)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    x, info = ctx.fcg_solve(coef, coef64, b, tol=1e-10, maxit=20000)
+    assert info["code"] == tp.OK and not info["fell_back"]
+    assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-10 * 1.01
+    _, info_cg = ctx.cg_solve(coef, coef64, b, tol=1e-10, maxit=20000)
+    assert abs(info["iters"] - info_cg["iters"]) <= 0.1 * info_cg["iters"] + 5, (info, info_cg)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 24, 40)])
+def test_fcg_with_unet_converges(tp, oracle_mod, shape):
+    """With an untrained network (random weights) FCG still reaches the FP64
+    tolerance (falling back to plain CG if the network is useless)."""
+    O = oracle_mod
+    K, mask, pD = _problem(shape, seed=4, sigma=1.5)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    _, flat = params_case(9)
+    dev = torch.device("cuda")
+    net = tp.UNet(*shape)
+    net.set_params(torch.from_numpy(flat).to(dev))
+    lnk = torch.from_numpy(np.log(K).astype(np.float32)).to(dev)
+    x, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, tol=1e-8, maxit=20000)
+    assert info["code"] == tp.OK
+    assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-8 * 1.01
+
+
+def test_fcg_rejects_mismatched_network(tp):
+    shape = (16, 16, 16)
+    K, mask, pD = _problem(shape)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    net = tp.UNet(16, 16, 8)
+    _, flat = params_case(1)
+    net.set_params(torch.from_numpy(flat).cuda())
+    lnk = torch.zeros(16 ** 3, dtype=torch.float32, device="cuda")
+    _, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, check=False)
+    assert info["code"] == tp.EINVAL
