@@ -14,7 +14,8 @@ solver.  Each function states the published definition it writes out:
 * the U-Net of Ronneberger, Fischer and Brox (2015), here with three
   resolution levels (16, 32, 64 channels), 2x2x2 average pooling, nearest
   upsampling and additive skip connections;
-* the A-norm error loss  (M r - e)^T A (M r - e) / (e^T A e)  with A e = r;
+* the A-norm error loss  (M r - e)^T A (M r - e) / (e^T A e)  with A e = r,
+  and the same loss minimised over a scalar multiple of M r;
 * Adam (Kingma and Ba, 2015, Algorithm 1);
 * flexible CG (Notay 2000, truncated to one previous direction), which for a
   fixed SPD preconditioner generates the PCG iterates.
@@ -232,6 +233,22 @@ def anorm_loss(mr: np.ndarray, e: np.ndarray, apply_a):
     ad = apply_a(d)
     eae = float(e @ apply_a(e))
     return float(d @ ad) / eae, 2.0 * ad / eae
+
+
+def anorm_loss_scaled(mr: np.ndarray, r: np.ndarray, e: np.ndarray, apply_a):
+    """The A-norm loss of the best multiple of Mr:  min_c L(c Mr) with
+    L(v) = (v - e)^T A (v - e) / (e^T A e) and A e = r.  The minimiser is
+    c* = Mr^T r / Mr^T A Mr, giving
+        L* = 1 - (Mr^T r)^2 / ((Mr^T A Mr)(e^T A e)),
+    which is invariant to the scale of Mr (as CG is to the scale of its
+    preconditioner).  Returns (L*, dL*/dMr) with
+        dL*/dMr = (2 a / (b g)) ((a / b) A Mr - r),  a = Mr^T r, b = Mr^T A Mr,
+    g = e^T A e."""
+    amr = apply_a(mr)
+    a = float(mr @ r)
+    b = float(mr @ amr)
+    g = float(e @ apply_a(e))
+    return 1.0 - a * a / (b * g), (2.0 * a / (b * g)) * ((a / b) * amr - r)
 
 
 def adam_step(w, g, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):

@@ -200,6 +200,30 @@ def test_anorm_loss(oracle_mod):
     assert abs(fd - grad @ d) < 1e-7 * max(1.0, abs(fd))
 
 
+def test_anorm_loss_scaled(oracle_mod):
+    """Equals the plain A-norm loss at the scale found by a library 1-D
+    minimiser; invariant to the scale of Mr; zero when Mr is a multiple of
+    e; gradient by central differences."""
+    import scipy.optimize
+    O, A, b = _tpfa_problem(oracle_mod)
+    e = O.cholesky_solve(A.dense(), b)
+    rng = np.random.default_rng(4)
+    mr = e + 0.3 * np.abs(e).max() * rng.standard_normal(e.shape)
+    L, grad = U.anorm_loss_scaled(mr, b, e, A.matvec)
+    res = scipy.optimize.minimize_scalar(lambda c: U.anorm_loss(c * mr, e, A.matvec)[0],
+                                         bracket=(0.1, 10.0), tol=1e-12)
+    assert abs(L - res.fun) < 1e-9
+    L2, _ = U.anorm_loss_scaled(-3.0 * mr, b, e, A.matvec)
+    assert abs(L2 - L) < 1e-12
+    L0, g0 = U.anorm_loss_scaled(2.5 * e, b, e, A.matvec)
+    assert abs(L0) < 1e-12 and np.abs(g0).max() < 1e-9 * np.abs(b).max() / np.abs(e).max()
+    d = rng.standard_normal(e.shape)
+    h = 1e-6 * np.abs(mr).max()
+    fd = (U.anorm_loss_scaled(mr + h * d, b, e, A.matvec)[0] -
+          U.anorm_loss_scaled(mr - h * d, b, e, A.matvec)[0]) / (2 * h)
+    assert abs(fd - grad @ d) < 1e-6 * max(abs(fd), 1e-12)
+
+
 def test_adam_closed_forms():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     w0 = np.array([1.0, 1.0, 1.0, 1.0])
