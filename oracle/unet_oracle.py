@@ -15,7 +15,8 @@ solver.  Each function states the published definition it writes out:
   resolution levels (16, 32, 64 channels), 2x2x2 average pooling, nearest
   upsampling and additive skip connections;
 * the A-norm error loss  (M r - e)^T A (M r - e) / (e^T A e)  with A e = r,
-  and the same loss minimised over a scalar multiple of M r;
+  the same loss minimised over a scalar multiple of M r, and the loss of the
+  network output inside the Jacobi blend D^-1 r + c u;
 * Adam (Kingma and Ba, 2015, Algorithm 1);
 * flexible CG (Notay 2000, truncated to one previous direction), which for a
   fixed SPD preconditioner generates the PCG iterates.
@@ -249,6 +250,34 @@ def anorm_loss_scaled(mr: np.ndarray, r: np.ndarray, e: np.ndarray, apply_a):
     b = float(mr @ amr)
     g = float(e @ apply_a(e))
     return 1.0 - a * a / (b * g), (2.0 * a / (b * g)) * ((a / b) * amr - r)
+
+
+def jacobi_blend(u: np.ndarray, r: np.ndarray, dinv: np.ndarray, apply_a):
+    """The preconditioner z = D^-1 r + c u with the A-norm-optimal weight:
+    c* minimises ||D^-1 r + c u - e||_A over c, where A e = r, which gives
+        c* = (u^T r - (A u)^T D^-1 r) / (u^T A u)
+    (c* = 0 when u^T A u is not positive).  Returns (z, c*)."""
+    au = apply_a(u)
+    den = float(u @ au)
+    c = (float(u @ r) - float(au @ (dinv * r))) / den if den > 0 else 0.0
+    return dinv * r + c * u, c
+
+
+def anorm_loss_blend(u: np.ndarray, r: np.ndarray, e: np.ndarray, dinv: np.ndarray, apply_a):
+    """Training loss of the network output u inside jacobi_blend: the A-norm
+    error of the blended preconditioner relative to ||e||_A,
+        L = min_c ||D^-1 r + c u - e||_A^2 / ||e||_A^2
+          = (w^T A w - (u^T s)^2 / (u^T A u)) / (e^T A e),
+    with w = e - D^-1 r (the error left by one Jacobi step) and
+    s = A w = r - A D^-1 r.  Returns (L, dL/du)."""
+    w = e - dinv * r
+    sv = r - apply_a(dinv * r)
+    au = apply_a(u)
+    a = float(u @ sv)
+    b = float(u @ au)
+    g = float(e @ apply_a(e))
+    L = (float(w @ apply_a(w)) - a * a / b) / g
+    return L, (2.0 * a / (b * g)) * ((a / b) * au - sv)
 
 
 def adam_step(w, g, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):

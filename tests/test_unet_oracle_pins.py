@@ -224,6 +224,40 @@ def test_anorm_loss_scaled(oracle_mod):
     assert abs(fd - grad @ d) < 1e-6 * max(abs(fd), 1e-12)
 
 
+def test_jacobi_blend_and_its_loss(oracle_mod):
+    """The blend weight minimises the A-norm error (library 1-D minimiser);
+    u = w (the exact Jacobi error) makes the blend exact; u = 0 gives Jacobi;
+    the loss equals the minimised error and its gradient matches central
+    differences."""
+    import scipy.optimize
+    O, A, b = _tpfa_problem(oracle_mod)
+    Ad = A.dense()
+    e = O.cholesky_solve(Ad, b)
+    dinv = 1.0 / np.diag(Ad)
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal(e.shape)
+
+    def err(z):
+        d = z - e
+        return float(d @ A.matvec(d))
+
+    z, c = U.jacobi_blend(u, b, dinv, A.matvec)
+    res = scipy.optimize.minimize_scalar(lambda cc: err(dinv * b + cc * u), bracket=(-1, 1), tol=1e-14)
+    assert abs(c - res.x) < 1e-6 * max(1.0, abs(res.x)) and abs(err(z) - res.fun) < 1e-9 * err(e * 0)
+    w = e - dinv * b
+    zw, cw = U.jacobi_blend(3.0 * w, b, dinv, A.matvec)
+    np.testing.assert_allclose(zw, e, rtol=0, atol=1e-10 * np.abs(e).max())
+    z0, c0 = U.jacobi_blend(np.zeros_like(u), b, dinv, A.matvec)
+    assert c0 == 0.0 and np.array_equal(z0, dinv * b)
+    L, grad = U.anorm_loss_blend(u, b, e, dinv, A.matvec)
+    assert abs(L - err(z) / err(0 * e)) < 1e-10
+    d = rng.standard_normal(e.shape)
+    h = 1e-6
+    fd = (U.anorm_loss_blend(u + h * d, b, e, dinv, A.matvec)[0] -
+          U.anorm_loss_blend(u - h * d, b, e, dinv, A.matvec)[0]) / (2 * h)
+    assert abs(fd - grad @ d) < 1e-6 * max(abs(fd), 1e-12)
+
+
 def test_adam_closed_forms():
     g = np.array([0.3, -2.0, 1e-3, 0.0])
     w0 = np.array([1.0, 1.0, 1.0, 1.0])
