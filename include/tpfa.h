@@ -367,25 +367,39 @@ int tpfa_unet_backward(tpfa_unet* net, const float* gz, float* grad, void* strea
  * p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).  All dev FP32, n values. */
 int tpfa_adam_step(float* params, const float* grad, float* m, float* v, int64_t n, int t,
                    double lr, double b1, double b2, double eps, void* stream);
-/* Gradient of the A-norm training loss L = d' A d / (e' A e), d = mr - e, for
- * one sample on the context's grid: g = 2 A d / eae and dad = d' A d.  coef:
- * the sample's FP32 coefficient records; eae (dev double) = e' A e; d, q dev
- * workspace of N floats; all dev.  Asynchronous. */
-int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, const float* e,
-                         const double* eae, float* d, float* q, float* g, double* dad,
-                         void* stream);
-/* Flexible CG (Notay 2000, one retained direction) preconditioned by net
- * (NULL: the identity, i.e. plain CG), refined in FP64 as cg_solve: outer
- * r = b - A64 x, inner FP32 FCG on A e = r / ||r|| to
- * max(TPFA_OPT_INNER_RTOL, 0.3 tol / ||r||/||b||), x += e ||r||.  The inner
- * iteration falls back to plain CG from its current iterate when p'Ap <= 0,
- * a value is not finite, or r'r falls by less than 1% over 50 iterations
- * (*fell_back = 1, may be NULL).  net must have been created for this grid
- * with ns = 1; lnk dev N floats (ignored without net).  coef, coef64, b, x as
- * cg_solve.  Waits for the stream.  Returns TPFA_OK, TPFA_NOTCONV (maxit
- * inner iterations or TPFA_OPT_MAX_OUTER refinements), TPFA_EBREAKDOWN,
- * TPFA_ENONFINITE, TPFA_EINTERNAL (a tensor-core wait gave up) or an
- * argument / CUDA error. */
+/* Gradient of the training loss for one sample on the context's grid: the
+ * A-norm error of the best multiple of mr,
+ *   L = min_c (c mr - e)' A (c mr - e) / (e' A e)
+ *     = 1 - a^2 / (b eae),  a = mr' r,  b = mr' A mr,  A e = r,
+ * (CG is invariant to the scale of its preconditioner's output).  Writes
+ * q = A mr, stats (dev, two doubles) = (a, b) and
+ * g = dL/dmr = (2 a / (b eae)) ((a / b) q - r).  coef: the sample's FP32
+ * coefficient records; mr, r, q, g dev N floats, pairwise distinct; eae dev
+ * double = e' A e.  Asynchronous (stream-ordered workspace). */
+int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, const float* r,
+                         const double* eae, float* q, float* g, double* stats, void* stream);
+/* Flexible CG (Notay 2000, one retained direction) refined in FP64 as
+ * cg_solve: outer r = b - A64 x, inner FP32 FCG on A e = r / ||r|| to
+ * max(TPFA_OPT_INNER_RTOL, 0.3 tol / (||r||/||b||)), x += e ||r||.
+ * Preconditioner: net == NULL gives the identity (plain CG); otherwise the
+ * Jacobi blend z = D^-1 r + c u with u = net(r) and the A-norm-optimal
+ * weight c = (u'r - (Au)'D^-1 r) / (u'Au), one extra operator application per
+ * iteration.  The inner iteration falls back to plain CG from its current
+ * iterate when p'Ap <= 0, a value is not finite, or r'r falls by less than 1%
+ * over 50 iterations (*fell_back = 1; may be NULL).  net must have been
+ * created for this grid with ns = 1; lnk dev N floats (ignored without net).
+ * coef, coef64, b, x as cg_solve.  Waits for the stream.  Returns TPFA_OK,
+ * TPFA_NOTCONV (maxit inner iterations or TPFA_OPT_MAX_OUTER refinements),
+ * TPFA_EBREAKDOWN, TPFA_ENONFINITE, TPFA_EINTERNAL (a tensor-core wait gave
+ * up) or an argument / CUDA error. */
+/* Training target of the network inside the Jacobi blend, for one sample:
+ * s = r - A D^-1 r (= A w, w = e - D^-1 r the error left by one Jacobi step)
+ * and, when e and wAw are both given, wAw = w' A w.  Pass s as the r argument
+ * of tpfa_anorm_loss_grad; the blended loss is (wAw - a^2 / b) / (e' A e).
+ * r, e, s dev N floats (s distinct from r and e); wAw dev double.
+ * Asynchronous (stream-ordered workspace). */
+int tpfa_jacobi_split(tpfa_ctx* ctx, const float* coef, const float* r, const float* e, float* s,
+                      double* wAw, void* stream);
 int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* coef64,
               const float* lnk, const double* b, double* x, double tol, int64_t maxit,
               tpfa_cg_info* info, int* fell_back, void* stream);

@@ -50,6 +50,10 @@ __device__ __forceinline__ void cp_commit_group() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_groups() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ uint32_t movmatrix_trans(uint32_t a) {
   uint32_t d;
@@ -66,13 +70,21 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// stages of the row-group ring: as deep as shared memory allows several CTAs
+// per SM for the small layers; the 64-channel layers hold 110 KB of weights
+template <int CIN, int COUT>
+constexpr int fwd_stages() {
+  return (CIN == 16) ? 4 : (CIN == 32 && COUT == 16) ? 3 : 2;
+}
+
 template <int CIN, int COUT>
 struct FwdCfg {
+  static constexpr int kS = fwd_stages<CIN, COUT>();
   static constexpr int kWTap = COUT * CIN * 2;  // bytes of one tap's weight matrix
   static constexpr int kWBytes = 27 * kWTap;
   static constexpr int kRGBytes = kRG * CIN * 2;
   static constexpr int kStage = 3 * kRGBytes;
-  static constexpr int kSmem = kWBytes + 2 * kStage;
+  static constexpr int kSmem = kWBytes + kS * kStage;
   static constexpr uint32_t kCols = COUT < 32 ? 32 : COUT;
   static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 256, "shape");
   static_assert(kSmem <= 227 * 1024, "shared memory");
@@ -85,8 +97,9 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
                 uint16_t* __restrict__ y, Vol g, int flags, int ntiles) {
   using Cfg = FwdCfg<CIN, COUT>;
   constexpr int kc = CIN / 8;
+  constexpr int S = Cfg::kS;
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[S];
   __shared__ uint32_t tbase;
   unsigned char* sW = sm;
   unsigned char* sS = sm + Cfg::kWBytes;
@@ -97,10 +110,8 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
     const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
     *reinterpret_cast<uint4*>(sW + t * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
   }
-  if (tid == 0) {
-    tc::mbar_init(&bars[0], 1);
-    tc::mbar_init(&bars[1], 1);
-  }
+  if (tid == 0)
+    for (int b = 0; b < S; ++b) tc::mbar_init(&bars[b], 1);
   if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
   tc::fence_proxy_async();
   tc::fence_before();
@@ -111,26 +122,30 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int njobs = 3 * my_tiles;  // job = (tile, dz)
 
-  auto load_job = [&](int j, int buf) {
-    const int tile = blockIdx.x + (j / 3) * gridDim.x;
-    const int dz = j % 3 - 1;
-    const int base = g.g0 + tile * 128 + dz * g.pp - g.wp - 1;
-    unsigned char* st = sS + buf * Cfg::kStage;
-    for (int i = tid; i < 3 * kRG * kc; i += 128) {
-      const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
-      const int row = base + gi * g.wp + v;
-      const bool ok = row >= 0 && row < g.vp;
-      cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
-            x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+  // copies of job j into buffer j % S; every call commits one group (empty
+  // past the last job) so that wait_group counts stay uniform
+  auto load_job = [&](int j) {
+    if (j < njobs) {
+      const int tile = blockIdx.x + (j / 3) * gridDim.x;
+      const int dz = j % 3 - 1;
+      const int base = g.g0 + tile * 128 + dz * g.pp - g.wp - 1;
+      unsigned char* st = sS + (j % S) * Cfg::kStage;
+      for (int i = tid; i < 3 * kRG * kc; i += 128) {
+        const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+        const int row = base + gi * g.wp + v;
+        const bool ok = row >= 0 && row < g.vp;
+        cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
+              x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+      }
     }
     cp_commit_group();
   };
 
   bool abort = false;
-  if (njobs > 0) load_job(0, 0);
+  for (int j = 0; j < S - 1; ++j) load_job(j);
   for (int j = 0; j < njobs; ++j) {
-    const int buf = j & 1;
-    cp_wait_all();
+    const int buf = j % S;
+    cp_wait_groups<S - 2>();  // job j's group is complete
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
@@ -155,19 +170,18 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
       }
       tc::mma_commit(&bars[buf]);
     }
-    if (j + 1 < njobs) {
-      // the other buffer is free once the MMAs of job j-1 have completed
-      bool ok = true;
-      if (j >= 1) ok = tc::mbar_wait(&bars[buf ^ 1], ((j - 1) >> 1) & 1, kWaitLimit);
-      if (__syncthreads_or(!ok)) {
-        abort = true;
-        break;
-      }
-      load_job(j + 1, buf ^ 1);
+    // job j+S-1 reuses the buffer of job j-1: wait for that job's MMAs
+    bool ok = true;
+    if (j >= 1 && j + S - 1 < njobs)
+      ok = tc::mbar_wait(&bars[(j - 1) % S], ((j - 1) / S) & 1, kWaitLimit);
+    if (__syncthreads_or(!ok)) {
+      abort = true;
+      break;
     }
+    load_job(j + S - 1);
     if (j % 3 == 2) {
-      const bool ok = tc::mbar_wait(&bars[buf], (j >> 1) & 1, kWaitLimit);
-      if (__syncthreads_or(!ok)) {
+      const bool done = tc::mbar_wait(&bars[buf], (j / S) & 1, kWaitLimit);
+      if (__syncthreads_or(!done)) {
         abort = true;
         break;
       }
@@ -339,20 +353,29 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ ws, float* __restr
   dw[i] = accumulate ? (float)(dw[i] + s) : (float)s;
 }
 
+// CTAs per SM from the shared-memory and tensor-memory budgets (the occupancy
+// calculator does not see TMEM), with the carveout set to all shared memory
+int ctas_per_sm(const void* fn, int smem, uint32_t tmem_cols, int* nsm) {
+  int dev = 0, per_sm_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  int b = per_sm_smem / (smem + 1024);  // 1 KB reserved per CTA
+  const int bt = (int)(512 / tmem_cols);
+  if (b > bt) b = bt;
+  if (b > 8) b = 8;
+  return b < 1 ? 1 : b;
+}
+
 template <int CIN, int COUT>
 int fwd_grid(int ntiles) {
   static int per_sm = -1, nsm = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         FwdCfg<CIN, COUT>::kSmem);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, conv_fwd_kernel<CIN, COUT>, 128,
-                                                  FwdCfg<CIN, COUT>::kSmem);
-    per_sm = b < 1 ? 1 : b;
-  }
+  if (per_sm < 0)
+    per_sm = ctas_per_sm((const void*)conv_fwd_kernel<CIN, COUT>, FwdCfg<CIN, COUT>::kSmem,
+                         FwdCfg<CIN, COUT>::kCols, &nsm);
   const int cap = per_sm * nsm;
   return ntiles < cap ? ntiles : cap;
 }

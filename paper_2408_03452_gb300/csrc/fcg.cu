@@ -1,5 +1,10 @@
 // Flexible conjugate gradients (Notay 2000, one retained direction) with the
-// learned U-Net preconditioner, and the A-norm training loss.
+// learned U-Net preconditioner, and the gradient of the training loss.
+//
+// Preconditioner with a network: z = D^-1 r + c u, u = net(r), with the
+// A-norm-optimal weight c = (u'r - (Au)'D^-1 r) / (u'Au) (one extra operator
+// application), so that each application is at least as good as one Jacobi
+// step in the A-norm.
 //
 // Outer loop (FP64): r = b - A x with the FP64 coefficient records; stop when
 // ||r|| <= tol ||b||; otherwise solve A e = r / ||r|| in FP32 by FCG and add
@@ -113,26 +118,79 @@ __global__ void copy_kernel(const float* __restrict__ a, float* __restrict__ b, 
     b[i] = a[i];
 }
 
-__global__ void sub_kernel(const float* __restrict__ a, const float* __restrict__ b,
-                           float* __restrict__ d, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    d[i] = a[i] - b[i];
+// partials of u'r and (Au)'(r / D)
+__global__ void blend_dots_kernel(const float* __restrict__ u, const float* __restrict__ r,
+                                  const float* __restrict__ au, const float4* __restrict__ coef,
+                                  int64_t n, double* part) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const float ri = r[i];
+    s0 += (double)u[i] * ri;
+    s1 += (double)au[i] * (ri / coef[i].w);
+  }
+  block_sum3(s0, s1, 0.0, part);
 }
 
-// g = (2 / eae) q
-__global__ void loss_grad_kernel(const float* __restrict__ q, const double* __restrict__ eae,
-                                 float* __restrict__ g, int64_t n) {
-  const float f = (float)(2.0 / *eae);
+// z = r / D + c u (in place over u)
+__global__ void blend_kernel(float* __restrict__ uz, const float* __restrict__ r,
+                             const float4* __restrict__ coef, float c, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    g[i] = f * q[i];
+    uz[i] = fmaf(c, uz[i], r[i] / coef[i].w);
+}
+
+// y = x / D
+__global__ void jacobi_kernel(const float* __restrict__ x, const float4* __restrict__ coef,
+                              float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    y[i] = x[i] / coef[i].w;
+}
+
+// y = a - b (y may alias b)
+__global__ void sub_kernel(const float* a, const float* b, float* y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    y[i] = a[i] - b[i];
+}
+
+// partial a'b per block (fixed order); finish: out = sum of partials in block order
+__global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                   int64_t n, double* part) {
+  __shared__ double sh[kT];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    s += (double)a[i] * b[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void dot_finish_kernel(const double* part, int nb, double* out) {
+  double s = 0.0;
+  for (int i = 0; i < nb; ++i) s += part[i];
+  *out = s;
+}
+
+// g = (2 a / (b c)) ((a / b) q - r) with a = stats[0], b = stats[1], c = *eae
+__global__ void loss_grad_kernel(const float* __restrict__ q, const float* __restrict__ r,
+                                 const double* __restrict__ stats, const double* __restrict__ eae,
+                                 float* __restrict__ g, int64_t n) {
+  const double a = stats[0], b = stats[1], c = *eae;
+  const float f = (float)(2.0 * a / (b * c));
+  const float ab = (float)(a / b);
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    g[i] = f * fmaf(ab, q[i], -r[i]);
 }
 
 struct Work {
   cudaStream_t s = nullptr;
   int nb = 0;
   int64_t n = 0;
-  float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *e = nullptr;
+  float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *e = nullptr, *au = nullptr;
   double* r64 = nullptr;
+  double* uau = nullptr;     // dev, 1
   double* part = nullptr;    // dev, 3 * nb
   double* hpart = nullptr;   // pinned host
   double* norms = nullptr;   // dev, 2
@@ -144,6 +202,7 @@ struct Work {
     return cudaMalloc(&r, n * 4) == cudaSuccess && cudaMalloc(&z, n * 4) == cudaSuccess &&
            cudaMalloc(&p, n * 4) == cudaSuccess && cudaMalloc(&q, n * 4) == cudaSuccess &&
            cudaMalloc(&e, n * 4) == cudaSuccess && cudaMalloc(&r64, n * 8) == cudaSuccess &&
+           cudaMalloc(&au, n * 4) == cudaSuccess && cudaMalloc(&uau, 8) == cudaSuccess &&
            cudaMalloc(&part, sizeof(double) * 3 * nb) == cudaSuccess &&
            cudaMalloc(&norms, 16) == cudaSuccess && cudaMalloc(&pq, 8) == cudaSuccess &&
            cudaMallocHost(&hpart, sizeof(double) * 3 * nb) == cudaSuccess &&
@@ -156,6 +215,8 @@ struct Work {
     cudaFree(p);
     cudaFree(q);
     cudaFree(e);
+    cudaFree(au);
+    cudaFree(uau);
     cudaFree(r64);
     cudaFree(part);
     cudaFree(norms);
@@ -203,9 +264,22 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
   std::vector<double> hist(1, rr);
   while (res->iters < maxit && rr > target * target * rr0) {
     if (precond_on) {
-      const int rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
+      // z = D^-1 r + c u, u = net(r), c the A-norm-optimal weight
+      int rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
       if (rc) return rc;
       w.launches += 15;
+      rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
+      if (rc) return rc;
+      blend_dots_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, w.au, reinterpret_cast<const float4*>(coef),
+                                               w.n, w.part);
+      w.launches += 2;
+      double uau = 0.0;
+      if (!w.fetch(d3) || !w.fetch_scalar(w.uau, &uau)) return TPFA_ECUDA;
+      double cw = uau > 0.0 && std::isfinite(uau) ? (d3[0] - d3[1]) / uau : 0.0;
+      if (!std::isfinite(cw)) cw = 0.0;
+      blend_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, reinterpret_cast<const float4*>(coef), (float)cw,
+                                          w.n);
+      ++w.launches;
     } else {
       copy_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.z, w.n);
       ++w.launches;
@@ -352,27 +426,68 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
   return rc ? rc : res.status;
 }
 
-// g = 2 A (mr - e) / eae and dad = (mr - e)' A (mr - e): gradient of the
-// A-norm loss (mr - e)' A (mr - e) / (e' A e) for one sample.  d and q are
-// caller workspace.
+// Gradient of the A-norm loss of the best multiple of mr (see the header):
+// q = A mr, stats = (mr' r, mr' A mr), g = (2a/(b eae)) ((a/b) q - r).
 extern "C" int tpfa_anorm_loss_grad(tpfa_ctx* c, const float* coef, const float* mr,
-                                    const float* e, const double* eae, float* d, float* q,
-                                    float* g, double* dad, void* stream) {
+                                    const float* r, const double* eae, float* q, float* g,
+                                    double* stats, void* stream) {
   const int64_t n = c ? tpfa::ctx_cells(c) : 0;
   if (n <= 0) return TPFA_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
-  if (!tpfa::dev_ok(mr, n * 4, 4, dev) || !tpfa::dev_ok(e, n * 4, 4, dev) ||
-      !tpfa::dev_ok(eae, 8, 8, dev) || !tpfa::dev_ok(d, n * 4, 4, dev) ||
-      !tpfa::dev_ok(q, n * 4, 4, dev) || !tpfa::dev_ok(g, n * 4, 4, dev) ||
-      !tpfa::dev_ok(dad, 8, 8, dev))
+  if (!tpfa::dev_ok(mr, n * 4, 4, dev) || !tpfa::dev_ok(r, n * 4, 4, dev) ||
+      !tpfa::dev_ok(eae, 8, 8, dev) || !tpfa::dev_ok(q, n * 4, 4, dev) ||
+      !tpfa::dev_ok(g, n * 4, 4, dev) || !tpfa::dev_ok(stats, 16, 8, dev))
     return TPFA_EINVAL;
+  if (mr == q || mr == g || r == q || r == g || q == g) return TPFA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  constexpr int nb = 512;
+  double* part = nullptr;
+  if (cudaMallocAsync((void**)&part, nb * sizeof(double), s) != cudaSuccess) return TPFA_ENOMEM;
+  int rc = tpfa_apply(c, coef, mr, q, stats + 1, stream);
+  if (rc == TPFA_OK) {
+    dot_partial_kernel<<<nb, kT, 0, s>>>(mr, r, n, part);
+    dot_finish_kernel<<<1, 1, 0, s>>>(part, nb, stats);
+    loss_grad_kernel<<<nb, kT, 0, s>>>(q, r, stats, eae, g, n);
+    if (cudaGetLastError() != cudaSuccess) rc = TPFA_ECUDA;
+  }
+  cudaFreeAsync(part, s);
+  return rc;
+}
+
+// s = r - A D^-1 r and, when e and wAw are given, wAw = w' A w with
+// w = e - D^-1 r: the training target of the network inside the Jacobi blend.
+extern "C" int tpfa_jacobi_split(tpfa_ctx* c, const float* coef, const float* r, const float* e,
+                                 float* s, double* wAw, void* stream) {
+  const int64_t n = c ? tpfa::ctx_cells(c) : 0;
+  if (n <= 0) return TPFA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
+  if (!tpfa::dev_ok(coef, n * 16, 16, dev) || !tpfa::dev_ok(r, n * 4, 4, dev) ||
+      !tpfa::dev_ok(s, n * 4, 4, dev) || !tpfa::opt_dev_ok(e, n * 4, 4, dev) ||
+      !tpfa::opt_dev_ok(wAw, 8, 8, dev) || (e == nullptr) != (wAw == nullptr))
+    return TPFA_EINVAL;
+  if (r == s || e == s) return TPFA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  float *t1 = nullptr, *t2 = nullptr;
+  if (cudaMallocAsync((void**)&t1, n * 4, st) != cudaSuccess) return TPFA_ENOMEM;
+  if (cudaMallocAsync((void**)&t2, n * 4, st) != cudaSuccess) {
+    cudaFreeAsync(t1, st);
+    return TPFA_ENOMEM;
+  }
   const int nb = (int)((n + kT - 1) / kT < 4096 ? (n + kT - 1) / kT : 4096);
-  sub_kernel<<<nb, kT, 0, s>>>(mr, e, d, n);
-  if (cudaGetLastError() != cudaSuccess) return TPFA_ECUDA;
-  int rc = tpfa_apply(c, coef, d, q, dad, stream);
-  if (rc) return rc;
-  loss_grad_kernel<<<nb, kT, 0, s>>>(q, eae, g, n);
-  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+  const float4* c4 = reinterpret_cast<const float4*>(coef);
+  jacobi_kernel<<<nb, kT, 0, st>>>(r, c4, t1, n);
+  int rc = tpfa_apply(c, coef, t1, t2, nullptr, stream);
+  if (rc == TPFA_OK) {
+    sub_kernel<<<nb, kT, 0, st>>>(r, t2, s, n);
+    if (e != nullptr) {
+      sub_kernel<<<nb, kT, 0, st>>>(e, t1, t1, n);
+      rc = tpfa_apply(c, coef, t1, t2, wAw, stream);
+    }
+  }
+  if (rc == TPFA_OK && cudaGetLastError() != cudaSuccess) rc = TPFA_ECUDA;
+  cudaFreeAsync(t1, st);
+  cudaFreeAsync(t2, st);
+  return rc;
 }

@@ -1,0 +1,282 @@
+"""Learned preconditioner: training pairs from plain CG, training of the
+U-Net with the A-norm loss and Adam, and evaluation inside flexible CG.
+
+Every numerical step runs in the library's kernels through the C ABI
+(tpfa.py); torch only holds the buffers and gathers samples into batches.
+
+Training data.  For each lognormal realization (ln K ~ N(0, sigma^2) i.i.d.
+per cell, Dirichlet p = 1 / 0 on the x = 0 / x = n-1 layers) plain CG is run
+once to tol (x*) and then stopped after k iterations for a geometric range
+of k; each stop gives the pair (r_k, e_k) = (b - A x_k, x* - x_k), which
+satisfies A e_k = r_k -- the residuals plain CG itself generates (k = 0 gives
+(b, x*)).
+
+The network output u enters the preconditioner as the Jacobi blend
+z = D^-1 r + c u with the A-norm-optimal weight c (flexible CG in the
+library).  Loss: the A-norm error of that blend relative to ||e||_A,
+  min_c ||D^-1 r + c u - e||_A^2 / ||e||_A^2 = (w'Aw - (u's)^2 / (u'Au)) / (e'Ae),
+w = e - D^-1 r, s = A w = r - A D^-1 r, per sample, summed over the batch
+(Adam is invariant to a constant factor).  Minimising over the weight makes
+the loss blind to the scale of u, as CG is to the scale of its
+preconditioner; without it an untrained network is driven to u = 0, because
+e = A^-1 r is orders of magnitude larger than r.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import synth, tpfa
+
+LAYERS = [(2, 16), (16, 32), (32, 64), (64, 32), (32, 16), (16, 16), (16, 1)]
+STREAM_INIT = 40
+
+
+def init_params(seed: int) -> torch.Tensor:
+    """He-style initial weights N(0, 2/(27 cin)) from the counter-based
+    generator, zero biases, in the library's flat layout."""
+    flat = []
+    for i, (cin, cout) in enumerate(LAYERS):
+        nw = 27 * cout * cin
+        w = synth.normal(seed, STREAM_INIT + i, np.arange(nw)) * np.sqrt(2.0 / (27 * cin))
+        flat += [w, np.zeros(cout)]
+    p = np.concatenate(flat).astype(np.float32)
+    if p.size != tpfa.unet_param_count():
+        raise RuntimeError("parameter layout does not match the library")
+    return torch.from_numpy(p)
+
+
+def realization(seed: int, n: int, sigma: float):
+    K = synth.lognormal_field(n, n, n, sigma, seed)
+    mask, pD = synth.dirichlet_faces(n, n, n, "x", 1.0, 0.0)
+    return K, mask, pD
+
+
+class Problem:
+    """One realization on the GPU: coefficients, right-hand side, ln K."""
+
+    def __init__(self, ctx: tpfa.Context, seed: int, n: int, sigma: float):
+        dev = ctx.device
+        K, mask, pD = realization(seed, n, sigma)
+        Kd = torch.from_numpy(K).to(dev)
+        md = torch.from_numpy(mask).to(dev)
+        self.coef, self.coef64 = ctx.build_trans(Kd, md)
+        self.b = ctx.build_rhs(Kd, md, pD=torch.from_numpy(pD).to(dev))
+        self.lnk = torch.from_numpy(np.log(K).astype(np.float32)).to(dev)
+
+
+class Dataset:
+    def __init__(self, n: int):
+        self.n = n
+        self.R, self.E, self.S, self.eae, self.wAw, self.real = [], [], [], [], [], []
+        self.problems: list[Problem] = []
+
+    def finish(self):
+        self.R = torch.stack(self.R)
+        self.E = torch.stack(self.E)
+        self.S = torch.stack(self.S)
+        self.eae = torch.cat(self.eae)
+        self.wAw = torch.cat(self.wAw)
+        self.real = np.asarray(self.real)
+        self.lnk = torch.stack([p.lnk for p in self.problems])
+
+
+def make_dataset(n_real=50, snaps=40, n=64, sigma=1.5, seed=1000, tol=1e-10, log=None):
+    """n_real realizations x snaps pairs (r_k, e_k) from plain CG."""
+    ctx = tpfa.Context(n, n, n)
+    ctx.set_option("precond", 0)
+    ds = Dataset(n)
+    ds.ctx = ctx
+    t0 = time.perf_counter()
+    for q in range(n_real):
+        pr = Problem(ctx, seed + q, n, sigma)
+        ds.problems.append(pr)
+        xs, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=100000)
+        if info["code"] != tpfa.OK:
+            raise RuntimeError(f"training solve did not converge: {info}")
+        caps = np.unique(np.geomspace(1, 0.9 * info["iters"], snaps - 1).astype(int))
+        ks = [0] + [int(k) for k in caps]
+        while len(ks) < snaps:  # small iteration counts: repeat late snapshots
+            ks.append(int(caps[-1]))
+        for k in ks[:snaps]:
+            if k == 0:
+                r64, e64 = pr.b, xs
+            else:
+                xk, _ = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=1e-14, maxit=k, check=False)
+                r64 = ctx.residual64(pr.coef64, pr.b, xk)
+                e64 = xs - xk
+            r, e = r64.float(), e64.float()
+            eae = torch.zeros(1, dtype=torch.float64, device=ctx.device)
+            ctx.apply(pr.coef, e, pAp=eae)
+            wAw = torch.zeros(1, dtype=torch.float64, device=ctx.device)
+            s = ctx.jacobi_split(pr.coef, r, e=e, wAw=wAw)
+            ds.R.append(r)
+            ds.E.append(e)
+            ds.S.append(s)
+            ds.eae.append(eae)
+            ds.wAw.append(wAw)
+            ds.real.append(q)
+        if log:
+            log(f"realization {q}: {info['iters']} CG iterations, {len(ks[:snaps])} pairs, "
+                f"{time.perf_counter() - t0:.1f} s")
+    ds.finish()
+    return ds
+
+
+def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, log=None):
+    """Adam on the A-norm loss.  Returns (params, history dict)."""
+    dev = ds.R.device
+    n = ds.n
+    N = n ** 3
+    ctx = ds.ctx
+    nreal = len(ds.problems)
+    n_val = max(1, int(round(holdout * nreal)))
+    val_real = set(range(nreal - n_val, nreal))
+    idx_train = np.array([i for i in range(len(ds.real)) if ds.real[i] not in val_real])
+    idx_val = np.array([i for i in range(len(ds.real)) if ds.real[i] in val_real])
+    net = tpfa.UNet(n, n, n, ns=batch, train=True, device=dev)
+    P = init_params(seed).to(dev)
+    M = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    G = torch.empty(batch * N, dtype=torch.float32, device=dev)
+    q = torch.empty(N, dtype=torch.float32, device=dev)
+    stats = torch.zeros((batch, 2), dtype=torch.float64, device=dev)
+    hist = {"epoch_loss": [], "val_loss": [], "seconds": [],
+            "jacobi_loss": float((ds.wAw / ds.eae).mean().item())}
+    t = 0
+    t0 = time.perf_counter()
+
+    def batch_loss(idx, backward):
+        nonlocal t
+        Rb = ds.R[idx].reshape(-1)
+        Sb = ds.S[idx].reshape(-1)
+        Lb = ds.lnk[ds.real[idx]].reshape(-1)
+        Z = net.forward(Rb, Lb)
+        for j, s in enumerate(idx):
+            ctx.anorm_loss_grad(ds.problems[ds.real[s]].coef, Z[j * N:(j + 1) * N],
+                                Sb[j * N:(j + 1) * N], ds.eae[s:s + 1], q, G[j * N:(j + 1) * N],
+                                stats[j])
+        if backward:
+            grad = net.backward(G)
+            t += 1
+            tpfa.adam_step(P, grad, M, V, t, lr)
+        st = stats[:len(idx)]
+        return ((ds.wAw[idx] - st[:, 0] ** 2 / st[:, 1]) / ds.eae[idx]).sum().item()
+
+    for ep in range(epochs):
+        perm = np.random.default_rng(seed + 7919 * (ep + 1)).permutation(idx_train)
+        tot, cnt = 0.0, 0
+        for st in range(0, len(perm) - batch + 1, batch):
+            net.set_params(P)
+            tot += batch_loss(perm[st:st + batch], True)
+            cnt += batch
+        net.set_params(P)
+        vt, vc = 0.0, 0
+        for st in range(0, len(idx_val) - batch + 1, batch):
+            vt += batch_loss(idx_val[st:st + batch], False)
+            vc += batch
+        tpfa.net_status(dev)
+        hist["epoch_loss"].append(tot / max(cnt, 1))
+        hist["val_loss"].append(vt / max(vc, 1))
+        hist["seconds"].append(time.perf_counter() - t0)
+        if log:
+            log(f"epoch {ep}: train {hist['epoch_loss'][-1]:.4g} val {hist['val_loss'][-1]:.4g} "
+                f"({hist['seconds'][-1]:.1f} s, {t} steps)")
+    hist["steps"] = t
+    return P, hist
+
+
+def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, log=None):
+    """Plain CG, Jacobi PCG and U-Net FCG on one held-out realization."""
+    ctx = tpfa.Context(n, n, n)
+    pr = Problem(ctx, seed, n, sigma)
+    out = {"grid": [n, n, n], "sigma": sigma, "seed": seed, "tol": tol}
+
+    def rec(name, info):
+        out[name] = {"iters": int(info["iters"]), "seconds": info["total_ms"] / 1e3,
+                     "rel_res_fp64": info["rel_res_fp64"], "code": int(info["code"])}
+        if "fell_back" in info:
+            out[name]["fell_back"] = bool(info["fell_back"])
+        if log:
+            log(f"{name}: {out[name]}")
+
+    ctx.set_option("precond", 0)
+    _, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=maxit)
+    rec("plain_cg", info)
+    ctx.set_option("precond", 1)
+    _, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=maxit)
+    rec("jacobi_pcg", info)
+    ctx.set_option("precond", 0)
+    net = tpfa.UNet(n, n, n, device=ctx.device)
+    net.set_params(P.to(ctx.device))
+    _, info = ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, tol=tol, maxit=maxit)
+    rec("unet_fcg", info)
+    # time of one preconditioner application
+    r = torch.randn(n ** 3, dtype=torch.float32, device=ctx.device)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        net.forward(r, pr.lnk, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.forward(r, pr.lnk, z)
+    e1.record()
+    torch.cuda.synchronize()
+    out["unet_apply_ms"] = e0.elapsed_time(e1) / 10
+    return out
+
+
+def apply_bench(n: int, reps: int = 10, seed: int = 0) -> dict:
+    """Time M(r) on an n^3 grid (initial weights; the cost does not depend on them)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    net = tpfa.UNet(n, n, n, device=dev)
+    net.set_params(init_params(seed).to(dev))
+    r = torch.from_numpy(synth.uniform_field(n ** 3, seed).astype(np.float32)).to(dev)
+    lnk = torch.from_numpy(np.log(realization(seed, n, 1.5)[0]).astype(np.float32)).to(dev)
+    z = torch.empty_like(r)
+    for _ in range(2):
+        net.forward(r, lnk, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.forward(r, lnk, z)
+    e1.record()
+    tpfa.net_status(dev)
+    return {"grid": n, "reps": reps, "apply_ms": e0.elapsed_time(e1) / reps}
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="train and evaluate the U-Net preconditioner")
+    ap.add_argument("--n-real", type=int, default=50)
+    ap.add_argument("--snaps", type=int, default=40)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-n", type=int, default=256)
+    ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--apply-bench", type=int, default=0,
+                    help="only time preconditioner applications on an N^3 grid")
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args(argv)
+    log = lambda m: print(m, flush=True)  # noqa: E731
+    if a.apply_bench:
+        print(json.dumps(apply_bench(a.apply_bench, a.reps)))
+        return
+    ds = make_dataset(a.n_real, a.snaps, a.n, log=log)
+    P, hist = train(ds, a.epochs, a.batch, a.lr, log=log)
+    if a.save:
+        np.save(a.save, P.cpu().numpy())
+    res = evaluate(P, n=a.eval_n, log=log)
+    res["train"] = hist
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -74,7 +74,8 @@ SIGNATURES = {
     "tpfa_unet_backward": (C.c_int, [_P, _P, _P, _P]),
     "tpfa_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, C.c_double, C.c_double,
                                  C.c_double, C.c_double, _P]),
-    "tpfa_anorm_loss_grad": (C.c_int, [_P] * 10),
+    "tpfa_anorm_loss_grad": (C.c_int, [_P] * 9),
+    "tpfa_jacobi_split": (C.c_int, [_P] * 7),
     "fcg_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64,
                             C.POINTER(_Info), C.POINTER(C.c_int), _P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
@@ -388,18 +389,33 @@ class Context:
         out["fell_back"] = bool(fb.value)
         return x, out
 
-    def anorm_loss_grad(self, coef, mr, e, eae, d, q, g, dad):
-        """g = 2 A (mr - e) / eae and dad = (mr - e)' A (mr - e) (all dev tensors;
-        eae and dad float64 [1])."""
+    def anorm_loss_grad(self, coef, mr, r, eae, q, g, stats):
+        """Gradient of the scale-optimal A-norm loss (see tpfa_anorm_loss_grad):
+        q = A mr, stats float64[2] = (mr'r, mr'A mr), g = dL/dmr.  The loss is
+        1 - stats[0]^2 / (stats[1] eae)."""
         dev, n = self.device, self.n
         with torch.cuda.device(dev):
             _check(lib().tpfa_anorm_loss_grad(
                 self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
-                _ptr(mr, torch.float32, n, dev, "mr"), _ptr(e, torch.float32, n, dev, "e"),
-                _ptr(eae, torch.float64, 1, dev, "eae"), _ptr(d, torch.float32, n, dev, "d"),
-                _ptr(q, torch.float32, n, dev, "q"), _ptr(g, torch.float32, n, dev, "g"),
-                _ptr(dad, torch.float64, 1, dev, "dad"), _stream(dev)), "tpfa_anorm_loss_grad")
+                _ptr(mr, torch.float32, n, dev, "mr"), _ptr(r, torch.float32, n, dev, "r"),
+                _ptr(eae, torch.float64, 1, dev, "eae"), _ptr(q, torch.float32, n, dev, "q"),
+                _ptr(g, torch.float32, n, dev, "g"), _ptr(stats, torch.float64, 2, dev, "stats"),
+                _stream(dev)), "tpfa_anorm_loss_grad")
         return g
+
+
+    def jacobi_split(self, coef, r, s=None, e=None, wAw=None):
+        """s = r - A D^-1 r; with e and wAw (float64 [1]): wAw = w'Aw, w = e - D^-1 r."""
+        dev, n = self.device, self.n
+        if s is None:
+            s = torch.empty(n, dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            _check(lib().tpfa_jacobi_split(
+                self._h, _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(r, torch.float32, n, dev, "r"), _ptr(e, torch.float32, n, dev, "e"),
+                _ptr(s, torch.float32, n, dev, "s"), _ptr(wAw, torch.float64, 1, dev, "wAw"),
+                _stream(dev)), "tpfa_jacobi_split")
+        return s
 
 
 def unet_param_count() -> int:
