@@ -43,6 +43,13 @@ UNIT = "cell-updates/s"
 # the 16-byte coefficient record, write r, p, q, x (FP32)
 SWEEP_BYTES_PER_CELL = 48
 FALLBACK_HBM_GBS = 6800.0
+LEARNED_METRIC = "U-Net FCG cell-iterations/s"
+LEARNED_UNIT = "cell-iterations/s"
+# useful FLOPs per cell of one U-Net application (true layer shapes: 2->16,
+# 16->16 and 16->1 at full resolution, 16->32 and 32->16 at 1/8, 32->64 and
+# 64->32 at 1/64 of the cells; 2*27*cin*cout per layer and cell)
+UNET_FLOP_PER_CELL = 2 * 27 * (2 * 16 + 16 * 16 + 16 * 1 + (16 * 32 + 32 * 16) / 8
+                               + (32 * 64 + 64 * 32) / 64)
 
 
 def parse():
@@ -59,10 +66,13 @@ def parse():
     ap.add_argument("--compare-single", action="store_true",
                     help="ensemble: also time the instances solved one after another")
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "channelized", "ensemble", "table3"],
+                    choices=["paper", "channelized", "ensemble", "table3", "learned"],
                     help="paper: 1024x1024x256 layered lognormal, wells, CG to 1e-6 (default); "
                          "channelized: 256^3 sigma-2 background + 1e4 channels, Dirichlet x "
                          "ends, refined to 1e-10 (the mixed-precision configuration)")
+    ap.add_argument("--epochs", type=int, default=12, help="learned: training epochs")
+    ap.add_argument("--n-real", type=int, default=50, help="learned: training realizations")
+    ap.add_argument("--snaps", type=int, default=40, help="learned: pairs per realization")
     ap.add_argument("--inner", default="f32", choices=["f32", "bf16"],
                     help="coefficient records of the inner CG sweeps")
     ap.add_argument("--precond", type=int, default=0, help="0: plain CG (Alg. 1); 1: Jacobi")
@@ -106,10 +116,10 @@ def workload_desc(a):
 
 
 def finish_args(a):
-    if a.workload == "channelized" and (a.nx, a.ny, a.nz) == (1024, 1024, 256):
+    if a.workload in ("channelized", "learned") and (a.nx, a.ny, a.nz) == (1024, 1024, 256):
         a.nx = a.ny = a.nz = 256
     if a.tol is None:
-        a.tol = {"channelized": 1e-10, "ensemble": 1e-8}.get(a.workload, 1e-6)
+        a.tol = {"channelized": 1e-10, "ensemble": 1e-8, "learned": 1e-8}.get(a.workload, 1e-6)
     return a
 
 
@@ -126,6 +136,8 @@ def oracle_step(O, iters, workload="paper"):
     128x128x64 block (64^3 for the channelized recipe), build the
     right-hand side, run `iters` CG iterations, evaluate the FP64 residual.
     Returns cell-updates done."""
+    if workload == "learned":
+        return oracle_fcg_step(iters)
     if workload == "channelized":
         nx, ny, nz = SAMPLE_CHANNELS
         w = synth.channelized(seed=0, n=nx)
@@ -148,6 +160,49 @@ def oracle_step(O, iters, workload="paper"):
     return nx * ny * nz * it
 
 
+SAMPLE_LEARNED = 32
+
+
+def oracle_fcg_step(iters, params=None):
+    """Oracle flexible CG with the Jacobi-blended U-Net on a 32^3 lognormal
+    (sigma 1.5) realization with Dirichlet x ends: CSR assembly, RHS, `iters`
+    FCG iterations.  params: flat parameter vector (default: He
+    initialisation of the oracle).  Returns cell-iterations done."""
+    from oracle import oracle as O
+    from oracle import unet_oracle as U
+    n = SAMPLE_LEARNED
+    K = synth.lognormal_field(n, n, n, 1.5, 5)
+    mask, pD = synth.dirichlet_faces(n, n, n, "x", 1.0, 0.0)
+    g = O.Grid(n, n, n)
+    A = O.assemble(g, K, mask)
+    b = O.rhs(g, K, mask, None, pD)
+    if params is None:
+        p = U.init_params(0)
+    else:
+        p, off = {}, 0
+        for i, (name, cin, cout) in enumerate(U.LAYERS):
+            nw = 27 * cin * cout
+            p[name] = params[off:off + nw].reshape(27, cout, cin).astype(np.float64)
+            p["b%d" % i] = params[off + nw:off + nw + cout].astype(np.float64)
+            off += nw + cout
+    lnk = np.log(K).reshape(1, n, n, n)
+    dinv = 1.0 / np.asarray(A.dense().diagonal()) if n ** 3 <= 4096 else None
+    if dinv is None:
+        diag = np.zeros(n ** 3)
+        for i in range(n ** 3):
+            lo, hi = A.rowptr[i], A.rowptr[i + 1]
+            j = np.nonzero(A.cols[lo:hi] == i)[0]
+            diag[i] = A.vals[lo + j[0]]
+        dinv = 1.0 / diag
+
+    def precond(r):
+        u = U.precondition(p, r.reshape(1, n, n, n), lnk).reshape(-1)
+        return U.jacobi_blend(u, r, dinv, A.matvec)[0]
+
+    _, it, _ = U.fcg(A.matvec, b, precond, 0.0, iters)
+    return n ** 3 * it
+
+
 def oracle_sample_iters(O, target_s=12.0, workload="paper"):
     t = time.perf_counter()
     oracle_step(O, 5, workload)
@@ -156,8 +211,22 @@ def oracle_sample_iters(O, target_s=12.0, workload="paper"):
 
 
 def sample_desc(workload):
+    if workload == "learned":
+        n = SAMPLE_LEARNED
+        return f"{n}x{n}x{n} lognormal (sigma 1.5) realization, U-Net FCG with the Jacobi blend"
     s = SAMPLE_CHANNELS if workload == "channelized" else SAMPLE
     return f"{s[0]}x{s[1]}x{s[2]} block of the same recipe"
+
+
+def metric_unit(workload):
+    if workload == "learned":
+        return LEARNED_METRIC, LEARNED_UNIT
+    return METRIC, UNIT
+
+
+def oracle_cores(workload):
+    # the learned-preconditioner oracle runs numpy matrix products (BLAS threads)
+    return os.cpu_count() if workload == "learned" else 1
 
 
 def cpu_baseline(target_s=12.0, workload="paper"):
@@ -167,9 +236,12 @@ def cpu_baseline(target_s=12.0, workload="paper"):
     t = time.perf_counter()
     units = oracle_step(O, iters, workload)
     dt = time.perf_counter() - t
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample_desc(workload)}: CSR assembly, RHS, {iters} CG iterations, "
-                      f"FP64 residual; single-threaded C, {dt:.1f} s"}
+    what = "FCG" if workload == "learned" else "CG"
+    how = "numpy" if workload == "learned" else "single-threaded C"
+    return {"value": units / dt, "unit": metric_unit(workload)[1], "cores": oracle_cores(workload),
+            "kind": "oracle",
+            "sample": f"{sample_desc(workload)}: CSR assembly, RHS, {iters} {what} iterations, "
+                      f"FP64; {how}, {dt:.1f} s"}
 
 
 def run_reference(a, rank, world):
@@ -187,16 +259,19 @@ def run_reference(a, rank, world):
         times.append(time.perf_counter() - t)
     tot = sum(times)
     val = units / tot
-    sample = (f"each step: {sample_desc(a.workload)}, CSR assembly, RHS, {iters} CG iterations, "
-              f"FP64 residual")
+    metric, unit = metric_unit(a.workload)
+    what = "FCG" if a.workload == "learned" else "CG"
+    sample = (f"each step: {sample_desc(a.workload)}, CSR assembly, RHS, {iters} {what} "
+              f"iterations, FP64")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+        "impl": "reference", "metric": metric, "value": val, "unit": unit, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": workload_desc(a), "sample": sample},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": val, "unit": unit, "cores": oracle_cores(a.workload),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
@@ -340,6 +415,138 @@ def run_table3(a, dev, rank):
                                    "recipe, 225 CG iterations each, "
                                    + ("plain CG" if a.precond == 0 else "Jacobi PCG")},
             "sweep": rows}))
+
+
+def measured_tensor_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def time_conv(tpfa, dev, n, cin, cout, reps=10):
+    """CUDA-event time of one tensor-core convolution launch on an n^3
+    haloed BF16 volume (random data, ReLU epilogue)."""
+    import torch
+    V = tpfa.halo_voxels(n, n, n)
+    x = torch.zeros((n + 2, n + 2, n + 2, cin), dtype=torch.bfloat16, device=dev)
+    x[1:-1, 1:-1, 1:-1] = torch.rand((n, n, n, cin), device=dev, dtype=torch.float32).to(torch.bfloat16)
+    y = torch.zeros((V, cout), dtype=torch.bfloat16, device=dev)
+    w = (torch.rand((27, cout, cin), device=dev) - 0.5).to(torch.bfloat16)
+    b = torch.zeros(cout, dtype=torch.float32, device=dev)
+    xs = x.reshape(V, cin)
+    for _ in range(3):
+        tpfa.conv3d_bf16(xs, w, y, (n, n, n, 1), cin, cout, bias=b, flags=tpfa.CONV_RELU)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        tpfa.conv3d_bf16(xs, w, y, (n, n, n, 1), cin, cout, bias=b, flags=tpfa.CONV_RELU)
+    e1.record(stream)
+    tpfa.net_status(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def run_learned(a, dev, rank, local, barrier):
+    """Learned-preconditioner workload.  Setup (untimed): 50 lognormal
+    (sigma 1.5) 64^3 realizations x 40 pairs (r_k, e_k) from plain-CG iterates,
+    Adam on the blended A-norm loss.  Step: a held-out n^3 realization solved
+    to FP64 relative residual tol by flexible CG with the Jacobi-blended
+    U-Net.  Plain CG and Jacobi PCG on the same system are timed beside it."""
+    import torch
+    from paper_2408_03452_gb300 import learned, tpfa
+    n = a.nx
+    t0 = time.perf_counter()
+    ds = learned.make_dataset(a.n_real, a.snaps, 64)
+    P, hist = learned.train(ds, epochs=a.epochs, batch=16, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    n_pairs = len(ds.real)
+    del ds
+    torch.cuda.empty_cache()
+    ctx = tpfa.Context(n, n, n, device=dev)
+    pr = learned.Problem(ctx, 777001 + a.seed, n, 1.5)
+    net = tpfa.UNet(n, n, n, device=dev)
+    net.set_params(P)
+    x = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
+
+    def fcg():
+        x.zero_()
+        _, info = ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, x=x, tol=a.tol,
+                                maxit=a.maxit)
+        if info["code"] != tpfa.OK:
+            raise RuntimeError(f"fcg_solve returned {info}")
+        return info
+
+    def cg(precond):
+        ctx.set_option("precond", precond)
+        x.zero_()
+        _, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, x=x, tol=a.tol, maxit=a.maxit)
+        ctx.set_option("precond", 0)
+        return info
+
+    for _ in range(a.warmup):
+        fcg()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    infos = [fcg() for _ in range(a.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    iters = infos[-1]["iters"]
+    cg(0)
+    plain = cg(0)
+    cg(1)
+    jac = cg(1)
+    apply = learned.apply_bench(n, 10)
+    conv_ms = time_conv(tpfa, dev, n, 16, 16)
+    if rank == 0:
+        cells = n ** 3
+        tpeak, tkind = measured_tensor_peak()
+        flop = 2 * 27 * 16 * 16 * cells
+        achieved = flop / (conv_ms / 1e3) / 1e12
+        out = {
+            "metric": LEARNED_METRIC, "value": cells * iters / (ms / 1e3), "unit": LEARNED_UNIT,
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-net/f32-fcg/f64-refine", "data": "synthetic",
+            "config": {
+                "workload": (f"learned preconditioner: U-Net trained at 64^3 on {n_pairs} plain-CG "
+                             f"pairs, applied in flexible CG (Jacobi blend) on a held-out {n}^3 "
+                             f"lognormal sigma-1.5 realization with Dirichlet x ends, FP64 "
+                             f"relative residual {a.tol:g}"),
+                "time_to_tol_s": {"unet_fcg": ms / 1e3, "plain_cg": plain["total_ms"] / 1e3,
+                                  "jacobi_pcg": jac["total_ms"] / 1e3},
+                "iters": {"unet_fcg": iters, "plain_cg": plain["iters"],
+                          "jacobi_pcg": jac["iters"]},
+                "rel_res_fp64": {"unet_fcg": infos[-1]["rel_res_fp64"],
+                                 "plain_cg": plain["rel_res_fp64"],
+                                 "jacobi_pcg": jac["rel_res_fp64"]},
+                "fell_back": infos[-1]["fell_back"],
+                "unet_apply_ms": apply["apply_ms"],
+                "unet_flop_per_cell": UNET_FLOP_PER_CELL,
+                "training": {"pairs": n_pairs, "epochs": a.epochs, "steps": hist["steps"],
+                             "seconds": train_s, "final_train_loss": hist["epoch_loss"][-1],
+                             "final_val_loss": hist["val_loss"][-1],
+                             "jacobi_loss": hist["jacobi_loss"]},
+                "l2": "inputs larger than L2 (no flush needed)"},
+            "roofline": {"kernel": "tensor-core 3x3x3 convolution 16->16 (full resolution)",
+                         "bound": "tensor", "achieved": achieved, "peak": tpeak,
+                         "unit": "TFLOP/s", "frac": achieved / tpeak, "peak_source": tkind,
+                         "flop_per_launch": flop, "launch_ms": conv_ms, "traffic": None},
+            "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+            "clocks": clk,
+        }
+        if not a.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(workload="learned")
+        print(json.dumps(out))
 
 
 def run_ensemble(a, dev, rank, world, local, barrier):
@@ -518,6 +725,11 @@ def main():
         return
     if a.workload == "ensemble":
         run_ensemble(a, dev, rank, world, local, barrier)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if a.workload == "learned":
+        run_learned(a, dev, rank, local, barrier)
         if world > 1:
             dist.destroy_process_group()
         return

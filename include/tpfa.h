@@ -95,9 +95,13 @@ enum tpfa_option {
   TPFA_OPT_STAGES40 = 9,     /* stages of the scheme-1 sweep: 4, 5 or 6 with 2 warps/block, 4 or 5 with 4 (default 5) */
   TPFA_OPT_WARPS40 = 10,     /* warps per block of the scheme-1 sweep: 2 (default) or 4                  */
   TPFA_OPT_INNER_RTOL_BF16 = 11, /* lower bound on the inner relative tolerance of cg_solve_bf16 (1e-3) */
-  TPFA_OPT_PRECOND = 12      /* inner CG of cg_solve: 0 = unpreconditioned (Alg. 1, default),
+  TPFA_OPT_PRECOND = 12,     /* inner CG of cg_solve: 0 = unpreconditioned (Alg. 1, default),
                                 1 = Jacobi, M = diag(D) (FP32 records only; cg_solve_bf16 with
                                 it set returns TPFA_EINVAL)                                       */
+  TPFA_OPT_FCG_M = 13,       /* fcg_solve: previous directions each new one is A-orthogonalised
+                                against, 1..16 (default 16)                                       */
+  TPFA_OPT_FCG_FALLBACK = 14 /* fcg_solve with a network, after breakdown or stagnation: 1 = drop
+                                the network, keep Jacobi (default); 0 = unpreconditioned CG       */
 };
 
 /* Create a context for one grid on the current CUDA device.  Allocates the
@@ -378,20 +382,23 @@ int tpfa_adam_step(float* params, const float* grad, float* m, float* v, int64_t
  * double = e' A e.  Asynchronous (stream-ordered workspace). */
 int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, const float* r,
                          const double* eae, float* q, float* g, double* stats, void* stream);
-/* Flexible CG (Notay 2000, one retained direction) refined in FP64 as
- * cg_solve: outer r = b - A64 x, inner FP32 FCG on A e = r / ||r|| to
- * max(TPFA_OPT_INNER_RTOL, 0.3 tol / (||r||/||b||)), x += e ||r||.
+/* Flexible CG (Notay 2000) with m = TPFA_OPT_FCG_M retained directions,
+ * refined in FP64 as cg_solve: outer r = b - A64 x, inner FP32 FCG on
+ * A e = r / ||r|| to max(TPFA_OPT_INNER_RTOL, 0.3 tol / (||r||/||b||)),
+ * x += e ||r||.  Inner step: z = M(r); p = z - sum_j (z'q_j / p_j'q_j) p_j over
+ * the last m directions; q = A p; alpha = p'r / p'q; e += alpha p; r -= alpha q.
  * Preconditioner: net == NULL gives the identity (plain CG); otherwise the
  * Jacobi blend z = D^-1 r + c u with u = net(r) and the A-norm-optimal
  * weight c = (u'r - (Au)'D^-1 r) / (u'Au), one extra operator application per
- * iteration.  The inner iteration falls back to plain CG from its current
- * iterate when p'Ap <= 0, a value is not finite, or r'r falls by less than 1%
- * over 50 iterations (*fell_back = 1; may be NULL).  net must have been
- * created for this grid with ns = 1; lnk dev N floats (ignored without net).
- * coef, coef64, b, x as cg_solve.  Waits for the stream.  Returns TPFA_OK,
- * TPFA_NOTCONV (maxit inner iterations or TPFA_OPT_MAX_OUTER refinements),
- * TPFA_EBREAKDOWN, TPFA_ENONFINITE, TPFA_EINTERNAL (a tensor-core wait gave
- * up) or an argument / CUDA error. */
+ * iteration.  With a network, when p'Ap <= 0, a value is not finite, or the
+ * smallest r'r of the last 100 iterations is not 1% below the smallest before
+ * them, the inner iteration drops the network (TPFA_OPT_FCG_FALLBACK) and
+ * restarts its directions from the current iterate (*fell_back = 1; may be
+ * NULL).  net must have been created for this grid with ns = 1; lnk dev N
+ * floats (ignored without net).  coef, coef64, b, x as cg_solve.  Waits for
+ * the stream.  Returns TPFA_OK, TPFA_NOTCONV (maxit inner iterations or
+ * TPFA_OPT_MAX_OUTER refinements), TPFA_EBREAKDOWN, TPFA_ENONFINITE,
+ * TPFA_EINTERNAL (a tensor-core wait gave up) or an argument / CUDA error. */
 /* Training target of the network inside the Jacobi blend, for one sample:
  * s = r - A D^-1 r (= A w, w = e - D^-1 r the error left by one Jacobi step)
  * and, when e and wAw are both given, wAw = w' A w.  Pass s as the r argument

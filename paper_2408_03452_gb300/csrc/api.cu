@@ -24,6 +24,8 @@ struct tpfa_ctx {
   int stages;      // stages of the stored-q sweep and of tpfa_apply
   int scheme;      // CG sweep: 0 = stored q (48 B/cell), 1 = recomputed q (40 B/cell)
   int precond;     // 0 = none (Alg. 1), 1 = Jacobi
+  int fcg_m;       // directions retained by fcg_solve
+  int fcg_fallback;  // fcg_solve fallback: 1 = Jacobi, 0 = unpreconditioned
   int stages40;    // stages of the recomputed-q sweep
   int warps40;     // warps per block of the recomputed-q sweep
   int zc;
@@ -298,6 +300,8 @@ double ctx_option(const tpfa_ctx* c, int option) {
   switch (option) {
     case TPFA_OPT_INNER_RTOL: return c->inner_rtol;
     case TPFA_OPT_MAX_OUTER: return c->max_outer;
+    case TPFA_OPT_FCG_M: return c->fcg_m;
+    case TPFA_OPT_FCG_FALLBACK: return c->fcg_fallback;
     default: return 0.0;
   }
 }
@@ -345,6 +349,8 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->inner_rtol = 1e-6;
   c->inner_rtol_bf16 = 1e-3;
   c->max_outer = 20;
+  c->fcg_m = 16;
+  c->fcg_fallback = 1;
   c->loop_mode = 0;
   c->vy = 4;
   c->stages = 4;
@@ -441,6 +447,14 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
     case TPFA_OPT_PRECOND:
       if (value != 0 && value != 1) return TPFA_EINVAL;
       c->precond = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_FCG_M:
+      if (!(value >= 1 && value <= 16) || value != floor(value)) return TPFA_EINVAL;
+      c->fcg_m = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_FCG_FALLBACK:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      c->fcg_fallback = (int)value;
       return TPFA_OK;
     case TPFA_OPT_SCHEME:
       if (value != 0 && value != 1) return TPFA_EINVAL;

@@ -1,4 +1,4 @@
-// Flexible conjugate gradients (Notay 2000, one retained direction) with the
+// Flexible conjugate gradients (Notay 2000, m retained directions) with the
 // learned U-Net preconditioner, and the gradient of the training loss.
 //
 // Preconditioner with a network: z = D^-1 r + c u, u = net(r), with the
@@ -9,17 +9,19 @@
 // Outer loop (FP64): r = b - A x with the FP64 coefficient records; stop when
 // ||r|| <= tol ||b||; otherwise solve A e = r / ||r|| in FP32 by FCG and add
 // e ||r|| to x.  Inner FCG:
-//   z_k = M(r_k);  p_0 = z_0,  p_k = z_k - (z_k' q_{k-1} / p_{k-1}' q_{k-1}) p_{k-1};
+//   z_k = M(r_k);  p_k = z_k - sum_{j=1..m} (z_k' q_{k-j} / p_{k-j}' q_{k-j}) p_{k-j};
 //   q_k = A p_k;  alpha_k = p_k' r_k / p_k' q_k;  e += alpha_k p_k;  r -= alpha_k q_k.
-// For a fixed SPD preconditioner this generates the PCG iterates; for the
-// network, which is neither linear nor symmetric, the explicit
-// A-orthogonalisation against the previous direction keeps the method
-// convergent.  If p'q <= 0, a value is not finite, or the residual stops
-// decreasing, the solve falls back to the identity preconditioner (plain CG)
-// from the current iterate.
+// For a fixed SPD preconditioner this generates the PCG iterates (the extra
+// coefficients vanish in exact arithmetic); for the network, which is neither
+// linear nor symmetric, the explicit A-orthogonalisation against the last m
+// directions keeps much of the Krylov optimality that a single retained
+// direction loses.  If p'q <= 0, a value is not finite, or the residual stops
+// decreasing, the solve drops the network (Jacobi or the identity) from the
+// current iterate.
 //
 // Dot products: FP64 per-thread sums, per-block partials in a fixed order,
 // added on the host in block order (bit-reproducible).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -118,6 +120,87 @@ __global__ void copy_kernel(const float* __restrict__ a, float* __restrict__ b, 
     b[i] = a[i];
 }
 
+// Block sums of M per-thread FP64 values (warp shuffles, then the warps in
+// order): part[blockIdx.x * M + j].
+template <int M>
+__device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) {
+  __shared__ double sh[M][kT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[j][wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += sh[threadIdx.x][w];
+    part[(size_t)blockIdx.x * M + threadIdx.x] = t;
+  }
+}
+
+constexpr int kMaxDirs = 16;
+struct Dirs {
+  const float* v[kMaxDirs];
+  float beta[kMaxDirs];
+};
+
+// partials of z'v_j, j < M
+template <int M>
+__global__ void mdot_kernel(const float* __restrict__ z, Dirs d, int64_t n, double* part) {
+  double s[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) s[j] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const float zi = z[i];
+#pragma unroll
+    for (int j = 0; j < M; ++j) s[j] += (double)zi * d.v[j][i];
+  }
+  block_sum_m<M>(s, part);
+}
+
+// p = z + sum_j beta_j v_j (p may be one of the v_j); partial p'r
+template <int M>
+__global__ void mdir_kernel(const float* __restrict__ z, Dirs d, float* p,
+                            const float* __restrict__ r, int64_t n, double* part) {
+  double pr[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    float v = z[i];
+#pragma unroll
+    for (int j = 0; j < M; ++j) v = fmaf(d.beta[j], d.v[j][i], v);
+    p[i] = v;
+    pr[0] += (double)v * r[i];
+  }
+  block_sum_m<1>(pr, part);
+}
+
+#define TPFA_FCG_M(X) \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+void launch_mdot(int m, int nb, cudaStream_t s, const float* z, const Dirs& d, int64_t n,
+                 double* part) {
+  switch (m) {
+#define X(M) \
+  case M: mdot_kernel<M><<<nb, kT, 0, s>>>(z, d, n, part); break;
+    TPFA_FCG_M(X)
+#undef X
+    default: break;
+  }
+}
+
+void launch_mdir(int m, int nb, cudaStream_t s, const float* z, const Dirs& d, float* p,
+                 const float* r, int64_t n, double* part) {
+  switch (m) {
+#define X(M) \
+  case M: mdir_kernel<M><<<nb, kT, 0, s>>>(z, d, p, r, n, part); break;
+    TPFA_FCG_M(X)
+#undef X
+    default: break;
+  }
+}
+
 // partials of u'r and (Au)'(r / D)
 __global__ void blend_dots_kernel(const float* __restrict__ u, const float* __restrict__ r,
                                   const float* __restrict__ au, const float4* __restrict__ coef,
@@ -188,10 +271,12 @@ struct Work {
   cudaStream_t s = nullptr;
   int nb = 0;
   int64_t n = 0;
-  float *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *e = nullptr, *au = nullptr;
+  int m = 1;                 // retained directions
+  float *r = nullptr, *z = nullptr, *e = nullptr, *au = nullptr;
+  float *P = nullptr, *Q = nullptr;  // m directions and their images A p
   double* r64 = nullptr;
   double* uau = nullptr;     // dev, 1
-  double* part = nullptr;    // dev, 3 * nb
+  double* part = nullptr;    // dev, kMaxDirs * nb
   double* hpart = nullptr;   // pinned host
   double* norms = nullptr;   // dev, 2
   double* hnorms = nullptr;  // pinned
@@ -200,20 +285,21 @@ struct Work {
 
   bool alloc() {
     return cudaMalloc(&r, n * 4) == cudaSuccess && cudaMalloc(&z, n * 4) == cudaSuccess &&
-           cudaMalloc(&p, n * 4) == cudaSuccess && cudaMalloc(&q, n * 4) == cudaSuccess &&
+           cudaMalloc(&P, (size_t)m * n * 4) == cudaSuccess &&
+           cudaMalloc(&Q, (size_t)m * n * 4) == cudaSuccess &&
            cudaMalloc(&e, n * 4) == cudaSuccess && cudaMalloc(&r64, n * 8) == cudaSuccess &&
            cudaMalloc(&au, n * 4) == cudaSuccess && cudaMalloc(&uau, 8) == cudaSuccess &&
-           cudaMalloc(&part, sizeof(double) * 3 * nb) == cudaSuccess &&
+           cudaMalloc(&part, sizeof(double) * kMaxDirs * nb) == cudaSuccess &&
            cudaMalloc(&norms, 16) == cudaSuccess && cudaMalloc(&pq, 8) == cudaSuccess &&
-           cudaMallocHost(&hpart, sizeof(double) * 3 * nb) == cudaSuccess &&
+           cudaMallocHost(&hpart, sizeof(double) * kMaxDirs * nb) == cudaSuccess &&
            cudaMallocHost(&hnorms, 16) == cudaSuccess;
   }
   ~Work() {
     if (s) cudaStreamSynchronize(s);
     cudaFree(r);
     cudaFree(z);
-    cudaFree(p);
-    cudaFree(q);
+    cudaFree(P);
+    cudaFree(Q);
     cudaFree(e);
     cudaFree(au);
     cudaFree(uau);
@@ -236,6 +322,18 @@ struct Work {
       for (int k = 0; k < 3; ++k) out3[k] += hpart[3 * b + k];
     return true;
   }
+  // sums of k per-block partials laid out [block][k], in block order
+  bool fetch_k(int k, double* out) {
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hpart, part, sizeof(double) * k * nb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return false;
+    for (int j = 0; j < k; ++j) out[j] = 0.0;
+    for (int b = 0; b < nb; ++b)
+      for (int j = 0; j < k; ++j) out[j] += hpart[(size_t)b * k + j];
+    return true;
+  }
   bool fetch_scalar(const double* dev, double* out) {
     if (cudaMemcpyAsync(hnorms, dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -253,75 +351,120 @@ struct Result {
   int status = TPFA_NOTCONV;
 };
 
+enum PrecMode { kIdentity = 0, kJacobi = 1, kBlend = 2 };
+
+// z = M(r) for the current mode
+int precondition(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
+                 PrecMode mode) {
+  const float4* c4 = reinterpret_cast<const float4*>(coef);
+  if (mode == kIdentity) {
+    copy_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.z, w.n);
+    ++w.launches;
+    return TPFA_OK;
+  }
+  if (mode == kJacobi) {
+    jacobi_kernel<<<w.nb, kT, 0, w.s>>>(w.r, c4, w.z, w.n);
+    ++w.launches;
+    return TPFA_OK;
+  }
+  // z = D^-1 r + c u, u = net(r), c the A-norm-optimal weight
+  int rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
+  if (rc) return rc;
+  w.launches += 15;
+  rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
+  if (rc) return rc;
+  blend_dots_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, w.au, c4, w.n, w.part);
+  w.launches += 2;
+  double d3[3], uau = 0.0;
+  if (!w.fetch(d3) || !w.fetch_scalar(w.uau, &uau)) return TPFA_ECUDA;
+  double cw = uau > 0.0 && std::isfinite(uau) ? (d3[0] - d3[1]) / uau : 0.0;
+  if (!std::isfinite(cw)) cw = 0.0;
+  blend_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, c4, (float)cw, w.n);
+  ++w.launches;
+  return TPFA_OK;
+}
+
+constexpr int kStallWindow = 100;
+
 // Inner FCG on A e = r (r, e already set, r'r = rr0); returns a TPFA_* error or
-// TPFA_OK, with res->status = TPFA_EBREAKDOWN if plain CG itself broke down.
+// TPFA_OK, with res->status = TPFA_EBREAKDOWN if the method without network
+// broke down.
 int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
-              double rr0, double target, int64_t maxit, Result* res) {
-  double d3[3];
-  double rr = rr0, pq_prev = 0.0;
-  bool first = true;
-  bool precond_on = net != nullptr && !res->fallback;
+              double rr0, double target, int64_t maxit, PrecMode fallback_mode, Result* res) {
+  const int m = w.m;
+  double dots[kMaxDirs], pqv[kMaxDirs];
+  double rr = rr0;
+  int stored = 0, head = 0;
+  PrecMode mode = net == nullptr ? kIdentity : (res->fallback ? fallback_mode : kBlend);
   std::vector<double> hist(1, rr);
   while (res->iters < maxit && rr > target * target * rr0) {
-    if (precond_on) {
-      // z = D^-1 r + c u, u = net(r), c the A-norm-optimal weight
-      int rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
-      if (rc) return rc;
-      w.launches += 15;
-      rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
-      if (rc) return rc;
-      blend_dots_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, w.au, reinterpret_cast<const float4*>(coef),
-                                               w.n, w.part);
-      w.launches += 2;
-      double uau = 0.0;
-      if (!w.fetch(d3) || !w.fetch_scalar(w.uau, &uau)) return TPFA_ECUDA;
-      double cw = uau > 0.0 && std::isfinite(uau) ? (d3[0] - d3[1]) / uau : 0.0;
-      if (!std::isfinite(cw)) cw = 0.0;
-      blend_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, reinterpret_cast<const float4*>(coef), (float)cw,
-                                          w.n);
+    int rc = precondition(c, net, coef, lnk, w, mode);
+    if (rc) return rc;
+    // A-orthogonalise against the retained directions, newest first
+    Dirs d;
+    for (int j = 0; j < stored; ++j) d.v[j] = w.Q + (size_t)((head - 1 - j + m) % m) * w.n;
+    if (stored > 0) {
+      launch_mdot(stored, w.nb, w.s, w.z, d, w.n, w.part);
       ++w.launches;
-    } else {
-      copy_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.z, w.n);
-      ++w.launches;
+      if (!w.fetch_k(stored, dots)) return TPFA_ECUDA;
     }
-    float beta = 0.f;
-    if (!first) {
-      dot_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.q, w.n, w.part);
-      ++w.launches;
-      if (!w.fetch(d3)) return TPFA_ECUDA;
-      beta = (float)(-d3[0] / pq_prev);
+    bool finite = true;
+    for (int j = 0; j < stored; ++j) {
+      const int slot = (head - 1 - j + m) % m;
+      const double beta = -dots[j] / pqv[slot];
+      finite = finite && std::isfinite(beta);
+      d.v[j] = w.P + (size_t)slot * w.n;
+      d.beta[j] = (float)beta;
     }
-    dir_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.p, w.r, beta, first ? 1 : 0, w.n, w.part);
+    float* p = w.P + (size_t)head * w.n;
+    float* q = w.Q + (size_t)head * w.n;
+    if (stored > 0)
+      launch_mdir(stored, w.nb, w.s, w.z, d, p, w.r, w.n, w.part);
+    else
+      dir_kernel<<<w.nb, kT, 0, w.s>>>(w.z, p, w.r, 0.f, 1, w.n, w.part);
     ++w.launches;
-    if (!w.fetch(d3)) return TPFA_ECUDA;
+    double d3[3];
+    if (stored > 0) {
+      if (!w.fetch_k(1, d3)) return TPFA_ECUDA;
+    } else if (!w.fetch(d3)) {
+      return TPFA_ECUDA;
+    }
     const double pr = d3[0];
-    int rc = tpfa_apply(c, coef, w.p, w.q, w.pq, w.s);
+    rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
     if (rc) return rc;
     ++w.launches;
     double pq = 0.0;
     if (!w.fetch_scalar(w.pq, &pq)) return TPFA_ECUDA;
-    const bool bad = !(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr) ||
-                     !std::isfinite((double)beta);
-    // stagnation: less than 1% reduction of r'r over the last 50 iterations
-    const bool stalled = precond_on && hist.size() > 50 && rr > 0.99 * hist[hist.size() - 51];
+    const bool bad = !(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr) || !finite;
+    // stagnation: the smallest r'r of the last kStallWindow iterations is not
+    // 1% below the smallest before them
+    bool stalled = false;
+    if (mode == kBlend && (int)hist.size() > 2 * kStallWindow) {
+      const size_t cut = hist.size() - kStallWindow;
+      const double before = *std::min_element(hist.begin(), hist.begin() + cut);
+      const double recent = *std::min_element(hist.begin() + cut, hist.end());
+      stalled = recent > 0.99 * before;
+    }
     if (bad || stalled) {
-      if (!precond_on) {
+      if (mode != kBlend) {
         res->status = TPFA_EBREAKDOWN;
         return TPFA_OK;
       }
-      precond_on = false;  // plain CG from the current iterate
+      mode = fallback_mode;
       res->fallback = true;
-      first = true;
+      stored = 0;
+      hist.assign(1, rr);
       continue;
     }
     const float alpha = (float)(pr / pq);
-    update_kernel<<<w.nb, kT, 0, w.s>>>(w.e, w.r, w.p, w.q, alpha, w.n, w.part);
+    update_kernel<<<w.nb, kT, 0, w.s>>>(w.e, w.r, p, q, alpha, w.n, w.part);
     ++w.launches;
     if (!w.fetch(d3)) return TPFA_ECUDA;
     rr = d3[0];
     hist.push_back(rr);
-    pq_prev = pq;
-    first = false;
+    pqv[head] = pq;
+    head = (head + 1) % m;
+    if (stored < m) ++stored;
     ++res->iters;
   }
   return TPFA_OK;
@@ -329,7 +472,7 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
 
 int fcg_outer(tpfa_ctx* c, tpfa_unet* net, const float* coef, const double* coef64,
               const float* lnk, const double* b, double* x, double tol, int64_t maxit,
-              double inner_rtol, int max_outer, Work& w, Result* res) {
+              double inner_rtol, int max_outer, PrecMode fallback_mode, Work& w, Result* res) {
   for (res->outer = 0; res->outer <= max_outer; ++res->outer) {
     int rc = tpfa_residual64(c, coef64, b, x, w.r64, w.norms, w.s);
     if (rc) return rc;
@@ -355,7 +498,7 @@ int fcg_outer(tpfa_ctx* c, tpfa_unet* net, const float* coef, const double* coef
     start_kernel<<<w.nb, kT, 0, w.s>>>(w.r64, scale, w.r, w.e, w.n, w.part);
     ++w.launches;
     if (!w.fetch(d3)) return TPFA_ECUDA;
-    rc = fcg_inner(c, net, coef, lnk, w, d3[0], target, maxit, res);
+    rc = fcg_inner(c, net, coef, lnk, w, d3[0], target, maxit, fallback_mode, res);
     if (rc) return rc;
     correct_kernel<<<w.nb, kT, 0, w.s>>>(x, w.e, 1.0 / scale, w.n);
     ++w.launches;
@@ -392,6 +535,8 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
   }
   const double inner_rtol = tpfa::ctx_option(c, TPFA_OPT_INNER_RTOL);
   const int max_outer = (int)tpfa::ctx_option(c, TPFA_OPT_MAX_OUTER);
+  const PrecMode fallback_mode =
+      tpfa::ctx_option(c, TPFA_OPT_FCG_FALLBACK) != 0.0 ? kJacobi : kIdentity;
   Result res;
   int rc;
   int64_t launches = 0;
@@ -399,6 +544,7 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     Work w;
     w.s = (cudaStream_t)stream;
     w.n = n;
+    w.m = (int)tpfa::ctx_option(c, TPFA_OPT_FCG_M);
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     w.nb = 4 * nsm;
@@ -406,7 +552,8 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
       cudaGetLastError();
       rc = TPFA_ENOMEM;
     } else {
-      rc = fcg_outer(c, net, coef, coef64, lnk, b, x, tol, maxit, inner_rtol, max_outer, w, &res);
+      rc = fcg_outer(c, net, coef, coef64, lnk, b, x, tol, maxit, inner_rtol, max_outer,
+                     fallback_mode, w, &res);
       if (rc == TPFA_OK && net != nullptr && tpfa_net_status(stream) != TPFA_OK) rc = TPFA_EINTERNAL;
     }
     launches = w.launches;

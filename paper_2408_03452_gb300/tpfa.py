@@ -22,7 +22,7 @@ EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, 
 
 OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6,
            "stages": 7, "scheme": 8, "stages40": 9, "warps40": 10, "inner_rtol_bf16": 11,
-           "precond": 12}
+           "precond": 12, "fcg_m": 13, "fcg_fallback": 14}
 
 
 class TpfaError(RuntimeError):
