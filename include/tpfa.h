@@ -329,6 +329,12 @@ int tpfa_conv3d_bf16(const uint16_t* x, const uint16_t* w, const float* bias,
  * workspace. */
 int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int nx, int ny,
                            int nz, int ns, int cin, int cout, int accumulate, void* stream);
+/* Forward-convolution kernel for the calls that follow (process-wide):
+ * 0 = 128-voxel tiles, each copying the nine row groups it reads;
+ * 1 = z-marching (default): each CTA follows a 128-voxel plane segment
+ *     through consecutive planes with a ring of row-group triples, loading
+ *     each triple once; (cin, cout) = (64, 32) always uses kernel 0. */
+int tpfa_conv3d_select(int kernel);
 /* Waits for the stream; TPFA_EINTERNAL (and clears the flag) if any
  * tensor-core wait of the convolution kernels gave up since the last call. */
 int tpfa_net_status(void* stream);

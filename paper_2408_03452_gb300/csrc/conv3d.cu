@@ -228,6 +228,202 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
   if (warp == 0) tc::tmem_dealloc(acc, Cfg::kCols);
 }
 
+// ---- z-marching forward kernel ---------------------------------------------
+// A work unit is one 128-voxel segment of a padded plane (offset bi * 128)
+// followed through zc consecutive interior planes of one sample.  Output k of
+// the unit needs the row-group triples of planes k-1, k, k+1; triple j of the
+// unit goes to ring slot j % ST and is loaded once, ST - 3 outputs ahead of its
+// first use, instead of three times.  Two TMEM accumulators alternate between
+// outputs so that the epilogue of output k-1 runs while the tensor core works
+// on output k.
+template <int CIN, int COUT>
+constexpr int zm_stages() {
+  return (CIN == 32 && COUT == 64) ? 4 : 5;
+}
+
+template <int CIN, int COUT>
+struct ZmCfg {
+  static constexpr int kST = zm_stages<CIN, COUT>();
+  static constexpr int kWTap = COUT * CIN * 2;
+  static constexpr int kWBytes = 27 * kWTap;
+  static constexpr int kRGBytes = kRG * CIN * 2;
+  static constexpr int kTriple = 3 * kRGBytes;
+  static constexpr int kSmem = kWBytes + kST * kTriple;
+  static constexpr uint32_t kCols = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+struct ZmGrid {
+  int nb;   // 128-voxel segments per padded plane
+  int zc;   // interior planes per unit
+  int nzc;  // units per sample along z
+  int units;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
+                   const float* __restrict__ bias, const uint16_t* __restrict__ mask,
+                   uint16_t* __restrict__ y, Vol g, int flags, ZmGrid zg) {
+  using Cfg = ZmCfg<CIN, COUT>;
+  constexpr int ST = Cfg::kST;
+  constexpr int kc = CIN / 8;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tbase;
+  unsigned char* sW = sm;
+  unsigned char* sR = sm + Cfg::kWBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < 27 * COUT * kc; i += 128) {
+    const int c = i % kc, r = (i / kc) % COUT, t = i / (kc * COUT);
+    const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
+    *reinterpret_cast<uint4*>(sW + t * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t acc0 = tbase;
+
+  bool abort = false;
+  int o = 0;  // outputs issued by this CTA (accumulator and barrier phase)
+  for (int u = blockIdx.x; u < zg.units && !abort; u += gridDim.x) {
+    const int bi = u % zg.nb, cz = u / zg.nb;
+    const int sidx = cz / zg.nzc;
+    const int z0 = (cz % zg.nzc) * zg.zc;
+    const int nout = min(zg.zc, g.nz - z0);
+    const int kp0 = sidx * g.dp + 1 + z0;     // padded plane of output 0
+    const int seg = bi * 128;                 // offset of the segment in its plane
+    const int ntrip = nout + 2;               // triples: planes kp0-1 .. kp0+nout
+    // triple j (plane kp0 - 1 + j) into slot j % ST; always one commit group
+    auto load_triple = [&](int j) {
+      if (j < ntrip) {
+        const int base = seg + (kp0 - 1 + j) * g.pp - g.wp - 1;
+        unsigned char* st = sR + (j % ST) * Cfg::kTriple;
+        for (int i = tid; i < 3 * kRG * kc; i += 128) {
+          const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+          const int row = base + gi * g.wp + v;
+          const bool ok = row >= 0 && row < g.vp;
+          cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
+                x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+        }
+      }
+      cp_commit_group();
+    };
+    for (int j = 0; j < ST; ++j) load_triple(j);
+
+    auto epilogue = [&](int k, int ok_) {
+      // output k of this unit, accumulator ok_ & 1
+      const int kp = kp0 + k;
+      const int off = seg + warp * 32 + lane;  // offset inside the plane
+      const int idx = kp * g.pp + off;
+      const bool in = off < g.pp && vol_interior(g, idx);
+      const uint32_t acc = acc0 + (uint32_t)((ok_ & 1) * COUT);
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 8) {
+        float v[8];
+        tc::tmem_ld8(acc + ((uint32_t)(warp * 32) << 16) + c0, v);
+        if (in) {
+          uint4 mk = make_uint4(0, 0, 0, 0);
+          if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + (size_t)idx * COUT + c0);
+          const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+          uint32_t ov[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            float a = v[2 * h], b = v[2 * h + 1];
+            if (bias) {
+              a += bias[c0 + 2 * h];
+              b += bias[c0 + 2 * h + 1];
+            }
+            if (flags & kConvRelu) {
+              a = fmaxf(a, 0.f);
+              b = fmaxf(b, 0.f);
+            }
+            if (flags & kConvMask) {
+              if (!bf16_positive(mw[h] & 0xffffu)) a = 0.f;
+              if (!bf16_positive(mw[h] >> 16)) b = 0.f;
+            }
+            ov[h] = pack_bf16(a, b);
+          }
+          *reinterpret_cast<uint4*>(y + (size_t)idx * COUT + c0) =
+              make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        }
+      }
+    };
+
+    for (int k = 0; k < nout; ++k, ++o) {
+      cp_wait_groups<ST - 4>();  // triples k .. k+2 are complete
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+        const uint32_t rb = tc::smem_addr(sR);
+        const uint32_t wb = tc::smem_addr(sW);
+        const uint32_t acc = acc0 + (uint32_t)((o & 1) * COUT);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+#pragma unroll 1
+        for (int dz = 0; dz < 3; ++dz) {
+          const uint32_t st = rb + ((k + dz) % ST) * Cfg::kTriple;
+#pragma unroll 1
+          for (int gi = 0; gi < 3; ++gi) {
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              const int t = dz * 9 + gi * 3 + dx;
+#pragma unroll
+              for (int ks = 0; ks < CIN / 16; ++ks) {
+                const uint64_t ad = tc::smem_desc(
+                    st + gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16, kRG * 16, 128);
+                const uint64_t bd = tc::smem_desc(wb + t * Cfg::kWTap + ks * 256, 128, kc * 128);
+                tc::mma_bf16(acc, ad, bd, idesc, (dz | gi | dx | ks) != 0);
+              }
+            }
+          }
+        }
+        tc::mma_commit(&bars[o & 1]);
+      }
+      if (k >= 1) {
+        // output k-1 done: its triple k-1 is free and its accumulator is final
+        const bool ok = tc::mbar_wait(&bars[(o - 1) & 1], ((o - 1) >> 1) & 1, kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+          abort = true;
+          break;
+        }
+        load_triple(k - 1 + ST);
+        tc::fence_after();
+        epilogue(k - 1, o - 1);
+        tc::fence_before();
+      } else {
+        cp_commit_group();
+      }
+    }
+    if (abort) break;
+    // last output of the unit
+    {
+      const bool ok = tc::mbar_wait(&bars[(o - 1) & 1], ((o - 1) >> 1) & 1, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      tc::fence_after();
+      epilogue(nout - 1, o - 1);
+      tc::fence_before();
+    }
+    cp_wait_all();
+    __syncthreads();  // ring slots are rewritten by the next unit
+  }
+  cp_wait_all();
+  if (abort && tid == 0) atomicOr(&g_tc_timeout, 1);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(acc0, Cfg::kCols);
+}
+
 template <int CIN, int COUT>
 struct WgCfg {
   static constexpr int kTaps = 128 / CIN;                    // taps per 128-row tile
@@ -392,6 +588,29 @@ cudaError_t fwd_launch(const uint16_t* x, const uint16_t* w, const float* bias,
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
+cudaError_t zm_launch(const uint16_t* x, const uint16_t* w, const float* bias,
+                      const uint16_t* mask, uint16_t* y, const Vol& g, int flags,
+                      cudaStream_t s) {
+  static int per_sm = -1, nsm = 0;
+  if (per_sm < 0)
+    per_sm = ctas_per_sm((const void*)conv_fwd_zm_kernel<CIN, COUT>, ZmCfg<CIN, COUT>::kSmem,
+                         ZmCfg<CIN, COUT>::kCols, &nsm);
+  const int ctas = per_sm * nsm;
+  ZmGrid zg;
+  zg.nb = (g.pp + 127) / 128;
+  zg.zc = g.nz;
+  // shorter z runs until there are at least two units per resident CTA
+  while (zg.zc > 4 && (long long)zg.nb * g.ns * ((g.nz + zg.zc - 1) / zg.zc) < 2LL * ctas)
+    zg.zc = (zg.zc + 1) / 2;
+  zg.nzc = (g.nz + zg.zc - 1) / zg.zc;
+  zg.units = zg.nb * g.ns * zg.nzc;
+  const int grid = zg.units < ctas ? zg.units : ctas;
+  conv_fwd_zm_kernel<CIN, COUT><<<grid, 128, ZmCfg<CIN, COUT>::kSmem, s>>>(x, w, bias, mask, y,
+                                                                           g, flags, zg);
+  return cudaGetLastError();
+}
+
 int wgrad_splits(int mtiles, int nchunks) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -436,8 +655,18 @@ bool conv_shape_ok(int cin, int cout) {
 
 #define TPFA_CONV_SHAPES(X) X(16, 16) X(16, 32) X(32, 16) X(32, 64) X(64, 32)
 
+// 0: tile kernel, 1: z-marching kernel (where its ring fits), else automatic
+static int g_conv_kernel = -1;
+
 cudaError_t conv_fwd(const uint16_t* x, const uint16_t* w, const float* bias, const uint16_t* mask,
                      uint16_t* y, const Vol& g, int cin, int cout, int flags, cudaStream_t s) {
+  const bool zm = g_conv_kernel != 0 && !(cin == 64 && cout == 32);
+  if (zm) {
+#define X(CI, CO) \
+  if (cin == CI && cout == CO) return zm_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
+    X(16, 16) X(16, 32) X(32, 16) X(32, 64)
+#undef X
+  }
 #define X(CI, CO) \
   if (cin == CI && cout == CO) return fwd_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
   TPFA_CONV_SHAPES(X)
@@ -513,6 +742,14 @@ extern "C" int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, flo
   cudaError_t e = tpfa::net::conv_wgrad(x, dy, dw, ws, g, cin, cout, accumulate, s);
   cudaFreeAsync(ws, s);
   return e == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
+// Selects the forward convolution kernel: 0 = 128-voxel tiles with all nine
+// row groups per tile, 1 = z-marching ring where it fits (default).
+extern "C" int tpfa_conv3d_select(int kernel) {
+  if (kernel != 0 && kernel != 1) return TPFA_EINVAL;
+  tpfa::net::g_conv_kernel = kernel;
+  return TPFA_OK;
 }
 
 // Waits for the stream, then reports (and clears) a tensor-core wait that

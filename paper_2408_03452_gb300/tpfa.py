@@ -65,6 +65,7 @@ SIGNATURES = {
     "tpfa_conv3d_bf16": (C.c_int, [_P, _P, _P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_conv3d_wgrad_bf16": (C.c_int, [_P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_net_status": (C.c_int, [_P]),
+    "tpfa_conv3d_select": (C.c_int, [C.c_int]),
     "tpfa_unet_param_count": (C.c_int64, []),
     "tpfa_unet_create": (C.c_int, [C.c_int] * 5 + [C.POINTER(C.c_void_p)]),
     "tpfa_unet_destroy": (C.c_int, [_P]),
@@ -166,6 +167,11 @@ def conv3d_wgrad_bf16(x, dy, dw, shape, cin, cout, accumulate=False):
                                         *shape, cin, cout, int(accumulate), _stream(dev)),
            "tpfa_conv3d_wgrad_bf16")
     return dw
+
+
+def conv3d_select(kernel: int):
+    """0: tile kernel; 1: z-marching kernel (default)."""
+    _check(lib().tpfa_conv3d_select(int(kernel)), "tpfa_conv3d_select")
 
 
 def net_status(device=None):

@@ -27,6 +27,14 @@ def tp():
     return tpfa
 
 
+@pytest.fixture(params=[1, 0], ids=["zmarch", "tiles"])
+def kernel(tp, request):
+    """Both forward kernels: the z-marching ring (default) and the tile kernel."""
+    tp.conv3d_select(request.param)
+    yield request.param
+    tp.conv3d_select(1)
+
+
 def bf16(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16)
 
@@ -57,8 +65,8 @@ def check_bf16_out(got, ref, absbound):
 
 
 @pytest.mark.parametrize("cin,cout", SHAPES)
-@pytest.mark.parametrize("vol", VOLS)
-def test_conv_forward(tp, cin, cout, vol):
+@pytest.mark.parametrize("vol", VOLS + [(20, 13, 70, 2)])
+def test_conv_forward(tp, kernel, cin, cout, vol):
     nx, ny, nz, ns = vol
     xt, x = rand_bf16(11, (ns, nz, ny, nx, cin))
     wt, w = rand_bf16(12, (27, cout, cin), 1.0 / np.sqrt(27 * cin))
@@ -80,7 +88,7 @@ def test_conv_forward(tp, cin, cout, vol):
 
 
 @pytest.mark.parametrize("cin,cout", SHAPES)
-def test_conv_input_gradient_with_mask(tp, cin, cout):
+def test_conv_input_gradient_with_mask(tp, kernel, cin, cout):
     """dx = mask * conv^T(dy, w), computed by the forward kernel with the taps
     flipped and each tap's matrix transposed."""
     nx, ny, nz, ns = 20, 9, 6, 2
