@@ -268,9 +268,12 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
   using Cfg = ZmCfg<CIN, COUT>;
   constexpr int ST = Cfg::kST;
   constexpr int kc = CIN / 8;
+  constexpr int kChunks = 3 * kRG * kc;            // 16-byte copies per triple
+  constexpr int kPer = (kChunks + 127) / 128;      // per thread
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ uint32_t tbase;
+  __shared__ float sbias[COUT];
   unsigned char* sW = sm;
   unsigned char* sR = sm + Cfg::kWBytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -280,16 +283,33 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
     const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
     *reinterpret_cast<uint4*>(sW + t * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
   }
+  if (tid < COUT) sbias[tid] = bias ? bias[tid] : 0.f;
   if (tid == 0) {
     tc::mbar_init(&bars[0], 1);
     tc::mbar_init(&bars[1], 1);
   }
   if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
+  // this thread's copies of a triple: row offset from the triple's first row,
+  // and byte offset inside the ring slot
+  int roff[kPer], coff[kPer];
+  uint32_t soff[kPer];
+#pragma unroll
+  for (int m = 0; m < kPer; ++m) {
+    const int i = tid + 128 * m;
+    const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+    roff[m] = gi * g.wp + v;
+    coff[m] = c * 8;
+    soff[m] = (uint32_t)(gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16);
+  }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t acc0 = tbase;
+  // descriptors of ring slot 0 (A) and of the weights (B); a byte offset d
+  // inside shared memory adds d >> 4 to the start-address field
+  const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sR), kRG * 16, 128);
+  const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sW), 128, kc * 128);
 
   bool abort = false;
   int o = 0;  // outputs issued by this CTA (accumulator and barrier phase)
@@ -298,20 +318,25 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
     const int sidx = cz / zg.nzc;
     const int z0 = (cz % zg.nzc) * zg.zc;
     const int nout = min(zg.zc, g.nz - z0);
-    const int kp0 = sidx * g.dp + 1 + z0;     // padded plane of output 0
-    const int seg = bi * 128;                 // offset of the segment in its plane
-    const int ntrip = nout + 2;               // triples: planes kp0-1 .. kp0+nout
-    // triple j (plane kp0 - 1 + j) into slot j % ST; always one commit group
+    const int kp0 = sidx * g.dp + 1 + z0;  // padded plane of output 0
+    const int seg = bi * 128;              // offset of the segment in its plane
+    const int ntrip = nout + 2;            // triples: planes kp0-1 .. kp0+nout
+    // this thread's output voxel in the plane: interior in x and y (every
+    // plane of a unit is interior in z)
+    const int poff = seg + warp * 32 + lane;
+    const int px = poff % g.wp, py = poff / g.wp;
+    const bool in_xy = poff < g.pp && px >= 1 && px <= g.nx && py >= 1 && py <= g.ny;
     auto load_triple = [&](int j) {
       if (j < ntrip) {
         const int base = seg + (kp0 - 1 + j) * g.pp - g.wp - 1;
         unsigned char* st = sR + (j % ST) * Cfg::kTriple;
-        for (int i = tid; i < 3 * kRG * kc; i += 128) {
-          const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
-          const int row = base + gi * g.wp + v;
-          const bool ok = row >= 0 && row < g.vp;
-          cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
-                x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+          if (kChunks % 128 == 0 || tid + 128 * m < kChunks) {
+            const int row = base + roff[m];
+            const bool ok = row >= 0 && row < g.vp;
+            cp16z(st + soff[m], x + (size_t)(ok ? row : 0) * CIN + coff[m], ok);
+          }
         }
       }
       cp_commit_group();
@@ -319,28 +344,20 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
     for (int j = 0; j < ST; ++j) load_triple(j);
 
     auto epilogue = [&](int k, int ok_) {
-      // output k of this unit, accumulator ok_ & 1
-      const int kp = kp0 + k;
-      const int off = seg + warp * 32 + lane;  // offset inside the plane
-      const int idx = kp * g.pp + off;
-      const bool in = off < g.pp && vol_interior(g, idx);
+      const size_t idx = (size_t)(kp0 + k) * g.pp + poff;
       const uint32_t acc = acc0 + (uint32_t)((ok_ & 1) * COUT);
 #pragma unroll
       for (int c0 = 0; c0 < COUT; c0 += 8) {
         float v[8];
         tc::tmem_ld8(acc + ((uint32_t)(warp * 32) << 16) + c0, v);
-        if (in) {
+        if (in_xy) {
           uint4 mk = make_uint4(0, 0, 0, 0);
-          if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + (size_t)idx * COUT + c0);
+          if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + idx * COUT + c0);
           const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
           uint32_t ov[4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            float a = v[2 * h], b = v[2 * h + 1];
-            if (bias) {
-              a += bias[c0 + 2 * h];
-              b += bias[c0 + 2 * h + 1];
-            }
+            float a = v[2 * h] + sbias[c0 + 2 * h], b = v[2 * h + 1] + sbias[c0 + 2 * h + 1];
             if (flags & kConvRelu) {
               a = fmaxf(a, 0.f);
               b = fmaxf(b, 0.f);
@@ -351,8 +368,7 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
             }
             ov[h] = pack_bf16(a, b);
           }
-          *reinterpret_cast<uint4*>(y + (size_t)idx * COUT + c0) =
-              make_uint4(ov[0], ov[1], ov[2], ov[3]);
+          *reinterpret_cast<uint4*>(y + idx * COUT + c0) = make_uint4(ov[0], ov[1], ov[2], ov[3]);
         }
       }
     };
@@ -363,28 +379,26 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
       __syncthreads();
       if (tid == 0) {
         tc::fence_after();
-        const uint32_t rb = tc::smem_addr(sR);
-        const uint32_t wb = tc::smem_addr(sW);
         const uint32_t acc = acc0 + (uint32_t)((o & 1) * COUT);
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
-#pragma unroll 1
-        for (int dz = 0; dz < 3; ++dz) {
-          const uint32_t st = rb + ((k + dz) % ST) * Cfg::kTriple;
-#pragma unroll 1
-          for (int gi = 0; gi < 3; ++gi) {
+        uint64_t slot[3];
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const int t = dz * 9 + gi * 3 + dx;
+        for (int dz = 0; dz < 3; ++dz)
+          slot[dz] = adesc0 + (uint64_t)(((k + dz) % ST) * (Cfg::kTriple >> 4));
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+          for (int gi = 0; gi < 3; ++gi)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
               for (int ks = 0; ks < CIN / 16; ++ks) {
-                const uint64_t ad = tc::smem_desc(
-                    st + gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16, kRG * 16, 128);
-                const uint64_t bd = tc::smem_desc(wb + t * Cfg::kWTap + ks * 256, 128, kc * 128);
+                const int t = dz * 9 + gi * 3 + dx;
+                const uint64_t ad =
+                    slot[dz] + (uint64_t)((gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)((t * Cfg::kWTap + ks * 256) >> 4);
                 tc::mma_bf16(acc, ad, bd, idesc, (dz | gi | dx | ks) != 0);
               }
-            }
-          }
-        }
         tc::mma_commit(&bars[o & 1]);
       }
       if (k >= 1) {

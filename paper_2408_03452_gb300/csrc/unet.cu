@@ -93,7 +93,7 @@ __host__ __device__ __forceinline__ int cells(const Vol& g) { return g.nx * g.ny
 int blocks_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
 // ---- per-sample root mean square (fixed-order reduction) ------------------
-constexpr int kRmsBlocks = 128;  // blocks per sample
+constexpr int kRmsBlocks = 1024;  // blocks per sample
 
 __global__ void sumsq_partial_kernel(const float* __restrict__ r, int n, double* partials) {
   __shared__ double sh[kThreads];
