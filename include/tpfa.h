@@ -333,7 +333,8 @@ int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int
  * 0 = 128-voxel tiles, each copying the nine row groups it reads;
  * 1 = z-marching (default): each CTA follows a 128-voxel plane segment
  *     through consecutive planes with a ring of row-group triples, loading
- *     each triple once; (cin, cout) = (64, 32) always uses kernel 0. */
+ *     each triple once, with two TMEM accumulators; (cin, cout) = (64, 32)
+ *     always uses kernel 0. */
 int tpfa_conv3d_select(int kernel);
 /* Waits for the stream; TPFA_EINTERNAL (and clears the flag) if any
  * tensor-core wait of the convolution kernels gave up since the last call. */

@@ -238,7 +238,7 @@ conv_fwd_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
 // on output k.
 template <int CIN, int COUT>
 constexpr int zm_stages() {
-  return (CIN == 32 && COUT == 64) ? 4 : 5;
+  return (CIN == 32 && COUT == 64) ? 4 : (CIN == 16) ? 7 : 5;
 }
 
 template <int CIN, int COUT>
@@ -346,10 +346,11 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
     auto epilogue = [&](int k, int ok_) {
       const size_t idx = (size_t)(kp0 + k) * g.pp + poff;
       const uint32_t acc = acc0 + (uint32_t)((ok_ & 1) * COUT);
+      float va[COUT];
+      tc::tmem_ld_cols<COUT>(acc + ((uint32_t)(warp * 32) << 16), va);
 #pragma unroll
       for (int c0 = 0; c0 < COUT; c0 += 8) {
-        float v[8];
-        tc::tmem_ld8(acc + ((uint32_t)(warp * 32) << 16) + c0, v);
+        const float* v = va + c0;
         if (in_xy) {
           uint4 mk = make_uint4(0, 0, 0, 0);
           if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + idx * COUT + c0);
@@ -669,13 +670,13 @@ bool conv_shape_ok(int cin, int cout) {
 
 #define TPFA_CONV_SHAPES(X) X(16, 16) X(16, 32) X(32, 16) X(32, 64) X(64, 32)
 
-// 0: tile kernel, 1: z-marching kernel (where its ring fits), else automatic
-static int g_conv_kernel = -1;
+// 0: tile kernel, 1: z-marching kernel (default; where its ring fits)
+static int g_conv_kernel = 1;
 
 cudaError_t conv_fwd(const uint16_t* x, const uint16_t* w, const float* bias, const uint16_t* mask,
                      uint16_t* y, const Vol& g, int cin, int cout, int flags, cudaStream_t s) {
-  const bool zm = g_conv_kernel != 0 && !(cin == 64 && cout == 32);
-  if (zm) {
+  const bool ring = !(cin == 64 && cout == 32);
+  if (ring && g_conv_kernel == 1) {
 #define X(CI, CO) \
   if (cin == CI && cout == CO) return zm_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
     X(16, 16) X(16, 32) X(32, 16) X(32, 64)
