@@ -73,3 +73,30 @@ def test_null_context_is_rejected_without_a_gpu(tp):
     assert tp.lib().tpfa_set_option(None, 1, 1e-6) == tp.EINVAL
     assert tp.lib().tpfa_create(None, None) == tp.EINVAL
     assert tp.lib().tpfa_destroy(None) == tp.EINVAL
+
+
+def test_unet_parameter_layout_without_a_gpu(tp):
+    """The library's parameter count equals the layer table of the Python
+    side (W_i[27][cout][cin] then b_i[cout] per layer), and the counter-based
+    initialisation fills exactly that many values; the network's argument
+    checks reject a null handle before any CUDA call."""
+    from paper_2408_03452_gb300 import learned
+    n = sum(27 * ci * co + co for ci, co in learned.LAYERS)
+    assert tp.unet_param_count() == n == 146625
+    p = learned.init_params(3)
+    assert p.numel() == n and p.dtype.is_floating_point
+    off = 0
+    for ci, co in learned.LAYERS:  # He scale per layer, zero biases
+        w = p[off:off + 27 * ci * co].double()
+        assert abs(float(w.std()) / (2.0 / (27 * ci)) ** 0.5 - 1.0) < 0.25
+        assert float(p[off + 27 * ci * co:off + 27 * ci * co + co].abs().sum()) == 0.0
+        off += 27 * ci * co + co
+    L = tp.lib()
+    assert L.tpfa_unet_destroy(None) == tp.EINVAL
+    assert L.tpfa_unet_set_params(None, None, None) == tp.EINVAL
+    assert L.tpfa_unet_forward(None, None, None, None, None) == tp.EINVAL
+    assert L.tpfa_unet_backward(None, None, None, None) == tp.EINVAL
+    assert L.tpfa_conv3d_select(7) == tp.EINVAL
+    assert L.tpfa_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == tp.EINVAL
+    assert L.fcg_solve(None, None, None, None, None, None, None, 1e-8, 10, None, None,
+                       None) == tp.EINVAL

@@ -82,3 +82,15 @@ def test_combine_ranks_world2_gloo():
 
 def test_combine_ranks_single_process_is_identity():
     assert bench.combine_ranks(5.0, 7, 9.0, 3, torch.device("cpu")) == (5.0, 7, 9.0, 3)
+
+
+def test_learned_workload_oracle_leg():
+    """The CPU leg of the learned-preconditioner workload runs the oracle's
+    flexible CG with the Jacobi-blended U-Net on the 32^3 sample and counts
+    cell-iterations; the line's metric and unit are the workload's own."""
+    assert bench.metric_unit("learned") == (bench.LEARNED_METRIC, bench.LEARNED_UNIT)
+    assert bench.metric_unit("paper") == (bench.METRIC, bench.UNIT)
+    assert bench.oracle_fcg_step(2) == 2 * bench.SAMPLE_LEARNED ** 3
+    # useful FLOPs of one application per cell: 2*27*cin*cout summed over the
+    # layers at their resolution (1, 1/8, 1/64 of the cells)
+    assert bench.UNET_FLOP_PER_CELL == 26784.0
