@@ -113,13 +113,22 @@ __global__ void sumsq_partial_kernel(const float* __restrict__ r, int n, double*
   if (threadIdx.x == 0) partials[s * gridDim.x + blockIdx.x] = sh[0];
 }
 
-__global__ void rms_finish_kernel(const double* partials, int nb, int n, float* rms, int ns) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ns) return;
+// one block per sample: strided sums, then a tree, in a fixed order
+__global__ void rms_finish_kernel(const double* partials, int nb, int n, float* rms) {
+  __shared__ double sh[kThreads];
+  const int s = blockIdx.x;
   double t = 0.0;
-  for (int b = 0; b < nb; ++b) t += partials[s * nb + b];
-  const double v = sqrt(t / n);
-  rms[s] = v > 0.0 ? (float)v : 1.0f;  // a zero residual maps to a zero input
+  for (int b = threadIdx.x; b < nb; b += kThreads) t += partials[s * nb + b];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = sqrt(sh[0] / n);
+    rms[s] = v > 0.0 ? (float)v : 1.0f;  // a zero residual maps to a zero input
+  }
 }
 
 // ---- element-wise kernels ----------------------------------------------------
@@ -551,8 +560,7 @@ int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z, 
   cudaStream_t s = (cudaStream_t)stream;
   const int per = g0.nx * g0.ny * g0.nz;
   sumsq_partial_kernel<<<dim3(kRmsBlocks, g0.ns), kThreads, 0, s>>>(r, per, u->partials);
-  rms_finish_kernel<<<(g0.ns + 127) / 128, 128, 0, s>>>(u->partials, kRmsBlocks, per, u->rms,
-                                                           g0.ns);
+  rms_finish_kernel<<<g0.ns, kThreads, 0, s>>>(u->partials, kRmsBlocks, per, u->rms);
   prep_input_kernel<<<blocks_for(n0), kThreads, 0, s>>>(r, lnk, u->rms, u->in16, g0);
   if (elem_launch_ok()) return TPFA_ECUDA;
   using tpfa::net::kConvRelu;
