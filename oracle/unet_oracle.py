@@ -224,6 +224,23 @@ def precondition(p: dict, r: np.ndarray, lnk: np.ndarray) -> np.ndarray:
     return z * rms[:, None, None, None]
 
 
+def restrict2(v: np.ndarray) -> np.ndarray:
+    """Scalar field (ns, nz, ny, nx) -> the mean of each 2x2x2 block of cells."""
+    return avgpool2(v[..., None])[..., 0]
+
+
+def prolong2(v: np.ndarray) -> np.ndarray:
+    """Scalar field on the 2x coarser grid -> each fine cell takes its parent's value."""
+    return upsample2(v[..., None])[..., 0]
+
+
+def precondition_coarse(p: dict, r: np.ndarray, lnk: np.ndarray) -> np.ndarray:
+    """The network applied on the 2x coarser grid: P net(R r, R ln K), with R
+    the 2x2x2 mean and P the nearest prolongation (homogeneous of degree one
+    in r, like precondition)."""
+    return prolong2(precondition(p, restrict2(r), restrict2(lnk)))
+
+
 # ----------------------------------------------------------------------------
 # Loss, optimiser, solver
 # ----------------------------------------------------------------------------

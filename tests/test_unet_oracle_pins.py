@@ -174,6 +174,35 @@ def test_precondition_homogeneous():
     np.testing.assert_allclose(m2, 3.5 * m1, rtol=1e-12, atol=1e-14)
 
 
+def test_restrict_prolong_pins():
+    """R is the block mean (loops), P copies the parent, R P = identity, and
+    P is 8 times the adjoint of R."""
+    rng = np.random.default_rng(12)
+    v = rng.standard_normal((2, 4, 6, 8))
+    rv = U.restrict2(v)
+    for s_, k, j, i in [(0, 0, 0, 0), (1, 1, 2, 3), (0, 1, 1, 2)]:
+        ref = np.mean([v[s_, 2 * k + a, 2 * j + b, 2 * i + c] for a in (0, 1) for b in (0, 1)
+                       for c in (0, 1)])
+        assert abs(rv[s_, k, j, i] - ref) < 1e-14
+    w = rng.standard_normal(rv.shape)
+    pw = U.prolong2(w)
+    assert pw[1, 3, 5, 7] == w[1, 1, 2, 3]
+    np.testing.assert_allclose(U.restrict2(pw), w, rtol=0, atol=1e-15)
+    assert abs(np.sum(pw * v) - 8.0 * np.sum(w * rv)) < 1e-10
+
+
+def test_precondition_coarse_homogeneous_and_smooth():
+    p, _, _ = _tiny_net()
+    rng = np.random.default_rng(13)
+    r = rng.standard_normal((1, 8, 8, 16))
+    lnk = rng.standard_normal((1, 8, 8, 16))
+    m1 = U.precondition_coarse(p, r, lnk)
+    np.testing.assert_allclose(U.precondition_coarse(p, 2.5 * r, lnk), 2.5 * m1, rtol=1e-12,
+                               atol=1e-14)
+    # constant on every 2x2x2 block
+    assert np.all(m1[:, 0::2, 0::2, 0::2] == m1[:, 1::2, 1::2, 1::2])
+
+
 def _tpfa_problem(oracle_mod, nx=6, ny=5, nz=4, seed=3):
     O = oracle_mod
     g = O.Grid(nx, ny, nz)
