@@ -99,9 +99,10 @@ enum tpfa_option {
                                 1 = Jacobi, M = diag(D) (FP32 records only; cg_solve_bf16 with
                                 it set returns TPFA_EINVAL)                                       */
   TPFA_OPT_FCG_M = 13,       /* fcg_solve: previous directions each new one is A-orthogonalised
-                                against, 1..16 (default 16)                                       */
-  TPFA_OPT_FCG_FALLBACK = 14 /* fcg_solve with a network, after breakdown or stagnation: 1 = drop
-                                the network, keep Jacobi (default); 0 = unpreconditioned CG       */
+                                against, 1..16 (default 4)                                        */
+  TPFA_OPT_FCG_FALLBACK = 14 /* fcg_solve with a network, after breakdown or stagnation:
+                                0 = unpreconditioned CG (default); 1 = drop the network, keep
+                                Jacobi                                                            */
 };
 
 /* Create a context for one grid on the current CUDA device.  Allocates the
@@ -395,15 +396,17 @@ int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, cons
  * x += e ||r||.  Inner step: z = M(r); p = z - sum_j (z'q_j / p_j'q_j) p_j over
  * the last m directions; q = A p; alpha = p'r / p'q; e += alpha p; r -= alpha q.
  * Preconditioner: net == NULL gives the identity (plain CG); otherwise the
- * Jacobi blend z = D^-1 r + c u with u = net(r) and the A-norm-optimal
- * weight c = (u'r - (Au)'D^-1 r) / (u'Au), one extra operator application per
- * iteration.  With a network, when p'Ap <= 0, a value is not finite, or the
- * smallest r'r of the last 100 iterations is not 1% below the smallest before
- * them, the inner iteration drops the network (TPFA_OPT_FCG_FALLBACK) and
- * restarts its directions from the current iterate (*fell_back = 1; may be
- * NULL).  net must have been created for this grid with ns = 1; lnk dev N
- * floats (ignored without net).  coef, coef64, b, x as cg_solve.  Waits for
- * the stream.  Returns TPFA_OK, TPFA_NOTCONV (maxit inner iterations or
+ * Jacobi blend z = D^-1 r + c u with the A-norm-optimal weight
+ * c = (u'r - (Au)'D^-1 r) / (u'Au) (one extra operator application), where
+ * u = net(r, ln K) if net was created for this grid, or u = P net(R r, R ln K)
+ * if it was created for the 2x coarser grid (R: mean of each 2x2x2 block,
+ * P: nearest prolongation; grid extents even).  When p'Ap <= 0, a value is
+ * not finite, or the smallest r'r of the last 100 iterations is not 1% below
+ * the smallest before them, the inner iteration drops the network
+ * (TPFA_OPT_FCG_FALLBACK: plain CG by default) and restarts its directions
+ * from the current iterate (*fell_back = 1; may be NULL).  net: ns = 1; lnk
+ * dev N floats (ignored without net).  coef, coef64, b, x as cg_solve.  Waits
+ * for the stream.  Returns TPFA_OK, TPFA_NOTCONV (maxit inner iterations or
  * TPFA_OPT_MAX_OUTER refinements), TPFA_EBREAKDOWN, TPFA_ENONFINITE,
  * TPFA_EINTERNAL (a tensor-core wait gave up) or an argument / CUDA error. */
 /* Training target of the network inside the Jacobi blend, for one sample:
@@ -414,6 +417,15 @@ int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, cons
  * Asynchronous (stream-ordered workspace). */
 int tpfa_jacobi_split(tpfa_ctx* ctx, const float* coef, const float* r, const float* e, float* s,
                       double* wAw, void* stream);
+/* Restriction to the 2x coarser grid: coarse = scale * (sum of the 8
+ * children) (scale 1/8: block mean; scale 1: adjoint of tpfa_prolong2).
+ * fine: ns samples of nx x ny x nz (all even) FP32 in the solver's order, dev,
+ * 8-byte aligned; coarse: ns (nx/2)(ny/2)(nz/2) FP32, dev.  Asynchronous. */
+int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, int nz, int ns, float scale,
+                   void* stream);
+/* Nearest prolongation: fine[c] = coarse[parent(c)] (shapes as tpfa_restrict2).
+ * Asynchronous. */
+int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, int nz, int ns, void* stream);
 int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* coef64,
               const float* lnk, const double* b, double* x, double tol, int64_t maxit,
               tpfa_cg_info* info, int* fell_back, void* stream);

@@ -25,7 +25,7 @@ struct tpfa_ctx {
   int scheme;      // CG sweep: 0 = stored q (48 B/cell), 1 = recomputed q (40 B/cell)
   int precond;     // 0 = none (Alg. 1), 1 = Jacobi
   int fcg_m;       // directions retained by fcg_solve
-  int fcg_fallback;  // fcg_solve fallback: 1 = Jacobi, 0 = unpreconditioned
+  int fcg_fallback;  // fcg_solve fallback: 0 = unpreconditioned (default), 1 = Jacobi
   int stages40;    // stages of the recomputed-q sweep
   int warps40;     // warps per block of the recomputed-q sweep
   int zc;
@@ -349,8 +349,8 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->inner_rtol = 1e-6;
   c->inner_rtol_bf16 = 1e-3;
   c->max_outer = 20;
-  c->fcg_m = 16;
-  c->fcg_fallback = 1;
+  c->fcg_m = 4;
+  c->fcg_fallback = 0;
   c->loop_mode = 0;
   c->vy = 4;
   c->stages = 4;

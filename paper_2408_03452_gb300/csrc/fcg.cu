@@ -234,6 +234,49 @@ __global__ void sub_kernel(const float* a, const float* b, float* y, int64_t n) 
     y[i] = a[i] - b[i];
 }
 
+// coarse[C] = scale * sum of the 8 children of C (fine grid nx x ny x nz, all
+// even, ns samples in the solver's x-fastest order)
+__global__ void restrict2_kernel(const float* __restrict__ fine, float* __restrict__ coarse, int nx,
+                                 int ny, int nz, int ns, float scale) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const int64_t nc = (int64_t)cx * cy * cz * ns;
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < nc; c += (int64_t)gridDim.x * kT) {
+    const int i = (int)(c % cx);
+    int64_t t = c / cx;
+    const int j = (int)(t % cy);
+    t /= cy;
+    const int k = (int)(t % cz);
+    const int64_t s = t / cz;
+    const float* f = fine + s * ((int64_t)nx * ny * nz);
+    float acc = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float2 v = *reinterpret_cast<const float2*>(
+            f + ((int64_t)(2 * k + dz) * ny + 2 * j + dy) * nx + 2 * i);
+        acc += v.x + v.y;
+      }
+    coarse[c] = scale * acc;
+  }
+}
+
+// fine[c] = coarse[parent(c)]
+__global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restrict__ fine, int nx,
+                                int ny, int nz, int ns) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const int64_t n = (int64_t)nx * ny * nz * ns;
+  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
+    const int i = (int)(c % nx);
+    int64_t t = c / nx;
+    const int j = (int)(t % ny);
+    t /= ny;
+    const int k = (int)(t % nz);
+    const int64_t s = t / nz;
+    fine[c] = coarse[((s * cz + k / 2) * cy + j / 2) * cx + i / 2];
+  }
+}
+
 // partial a'b per block (fixed order); finish: out = sum of partials in block order
 __global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b,
                                    int64_t n, double* part) {
@@ -281,6 +324,10 @@ struct Work {
   double* norms = nullptr;   // dev, 2
   double* hnorms = nullptr;  // pinned
   double* pq = nullptr;      // dev, 1
+  // network on the 2x coarser grid: restricted residual, its image, ln K
+  bool coarse = false;
+  int dims[3] = {0, 0, 0};
+  float *rc = nullptr, *uc = nullptr, *lnkc = nullptr;
   int64_t launches = 0;
 
   bool alloc() {
@@ -309,6 +356,9 @@ struct Work {
     cudaFree(pq);
     cudaFreeHost(hpart);
     cudaFreeHost(hnorms);
+    cudaFree(rc);
+    cudaFree(uc);
+    cudaFree(lnkc);
   }
   // sums of the three per-block partials, in block order
   bool fetch(double* out3) {
@@ -332,6 +382,22 @@ struct Work {
     for (int j = 0; j < k; ++j) out[j] = 0.0;
     for (int b = 0; b < nb; ++b)
       for (int j = 0; j < k; ++j) out[j] += hpart[(size_t)b * k + j];
+    return true;
+  }
+  // k per-block partials ([block][k], or the 3-slot layout when k3) and one
+  // device scalar, with a single synchronisation
+  bool fetch_with_scalar(int k, bool k3, double* out, const double* dev, double* sc) {
+    const int per = k3 ? 3 : k;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(hpart, part, sizeof(double) * per * nb, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hnorms, dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return false;
+    for (int j = 0; j < k; ++j) out[j] = 0.0;
+    for (int b = 0; b < nb; ++b)
+      for (int j = 0; j < k; ++j) out[j] += hpart[(size_t)b * per + j];
+    *sc = hnorms[0];
     return true;
   }
   bool fetch_scalar(const double* dev, double* out) {
@@ -367,16 +433,26 @@ int precondition(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* ln
     ++w.launches;
     return TPFA_OK;
   }
-  // z = D^-1 r + c u, u = net(r), c the A-norm-optimal weight
-  int rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
-  if (rc) return rc;
-  w.launches += 15;
+  // z = D^-1 r + c u, u = net(r) (or P net(R r) on the coarser grid), c the
+  // A-norm-optimal weight
+  int rc;
+  if (w.coarse) {
+    restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.rc, w.dims[0], w.dims[1], w.dims[2], 1, 0.125f);
+    rc = tpfa_unet_forward(net, w.rc, w.lnkc, w.uc, w.s);
+    if (rc) return rc;
+    prolong2_kernel<<<w.nb, kT, 0, w.s>>>(w.uc, w.z, w.dims[0], w.dims[1], w.dims[2], 1);
+    w.launches += 17;
+  } else {
+    rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
+    if (rc) return rc;
+    w.launches += 15;
+  }
   rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
   if (rc) return rc;
   blend_dots_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, w.au, c4, w.n, w.part);
   w.launches += 2;
   double d3[3], uau = 0.0;
-  if (!w.fetch(d3) || !w.fetch_scalar(w.uau, &uau)) return TPFA_ECUDA;
+  if (!w.fetch_with_scalar(2, true, d3, w.uau, &uau)) return TPFA_ECUDA;
   double cw = uau > 0.0 && std::isfinite(uau) ? (d3[0] - d3[1]) / uau : 0.0;
   if (!std::isfinite(cw)) cw = 0.0;
   blend_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, c4, (float)cw, w.n);
@@ -424,17 +500,12 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
       dir_kernel<<<w.nb, kT, 0, w.s>>>(w.z, p, w.r, 0.f, 1, w.n, w.part);
     ++w.launches;
     double d3[3];
-    if (stored > 0) {
-      if (!w.fetch_k(1, d3)) return TPFA_ECUDA;
-    } else if (!w.fetch(d3)) {
-      return TPFA_ECUDA;
-    }
-    const double pr = d3[0];
     rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
     if (rc) return rc;
     ++w.launches;
     double pq = 0.0;
-    if (!w.fetch_scalar(w.pq, &pq)) return TPFA_ECUDA;
+    if (!w.fetch_with_scalar(1, stored == 0, d3, w.pq, &pq)) return TPFA_ECUDA;
+    const double pr = d3[0];
     const bool bad = !(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr) || !finite;
     // stagnation: the smallest r'r of the last kStallWindow iterations is not
     // 1% below the smallest before them
@@ -526,12 +597,16 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
       !tpfa::dev_ok(b, n * 8, 8, dev) || !tpfa::dev_ok(x, n * 8, 8, dev) ||
       (net != nullptr && !tpfa::dev_ok(lnk, n * 4, 4, dev)))
     return TPFA_EINVAL;
+  int64_t d3[3];
+  tpfa::ctx_dims(c, d3);
+  bool coarse = false;
   if (net != nullptr) {
     int d4[4];
-    int64_t d3[3];
     tpfa_unet_shape(net, d4);
-    tpfa::ctx_dims(c, d3);
-    if (d4[0] != d3[0] || d4[1] != d3[1] || d4[2] != d3[2] || d4[3] != 1) return TPFA_EINVAL;
+    const bool full = d4[0] == d3[0] && d4[1] == d3[1] && d4[2] == d3[2];
+    coarse = d3[0] % 2 == 0 && d3[1] % 2 == 0 && d3[2] % 2 == 0 && d4[0] == d3[0] / 2 &&
+             d4[1] == d3[1] / 2 && d4[2] == d3[2] / 2;
+    if (!(full || coarse) || d4[3] != 1) return TPFA_EINVAL;
   }
   const double inner_rtol = tpfa::ctx_option(c, TPFA_OPT_INNER_RTOL);
   const int max_outer = (int)tpfa::ctx_option(c, TPFA_OPT_MAX_OUTER);
@@ -545,10 +620,23 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     w.s = (cudaStream_t)stream;
     w.n = n;
     w.m = (int)tpfa::ctx_option(c, TPFA_OPT_FCG_M);
+    w.coarse = coarse;
+    for (int i = 0; i < 3; ++i) w.dims[i] = (int)d3[i];
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     w.nb = 4 * nsm;
-    if (!w.alloc()) {
+    bool ok = w.alloc();
+    if (ok && coarse) {
+      const size_t nc = (size_t)(n / 8) * 4;
+      ok = cudaMalloc(&w.rc, nc) == cudaSuccess && cudaMalloc(&w.uc, nc) == cudaSuccess &&
+           cudaMalloc(&w.lnkc, nc) == cudaSuccess;
+      if (ok) {
+        restrict2_kernel<<<w.nb, kT, 0, w.s>>>(lnk, w.lnkc, w.dims[0], w.dims[1], w.dims[2], 1,
+                                               0.125f);
+        ok = cudaGetLastError() == cudaSuccess;
+      }
+    }
+    if (!ok) {
       cudaGetLastError();
       rc = TPFA_ENOMEM;
     } else {
@@ -637,4 +725,33 @@ extern "C" int tpfa_jacobi_split(tpfa_ctx* c, const float* coef, const float* r,
   cudaFreeAsync(t1, st);
   cudaFreeAsync(t2, st);
   return rc;
+}
+
+// coarse = scale * (sum of the 8 children) on the 2x coarser grid; fine
+// nx x ny x nz (even) per sample, ns samples; dev FP32.  Asynchronous.
+extern "C" int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, int nz, int ns,
+                              float scale, void* stream) {
+  if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || ns < 1) return TPFA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
+  const size_t n = (size_t)nx * ny * nz * ns;
+  if (!tpfa::dev_ok(fine, n * 4, 8, dev) || !tpfa::dev_ok(coarse, n / 8 * 4, 4, dev))
+    return TPFA_EINVAL;
+  const int nb = (int)((n / 8 + kT - 1) / kT < 4096 ? (n / 8 + kT - 1) / kT : 4096);
+  restrict2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(fine, coarse, nx, ny, nz, ns, scale);
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
+// fine = coarse value of each cell's parent (nearest prolongation).  Asynchronous.
+extern "C" int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, int nz, int ns,
+                             void* stream) {
+  if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || ns < 1) return TPFA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
+  const size_t n = (size_t)nx * ny * nz * ns;
+  if (!tpfa::dev_ok(fine, n * 4, 4, dev) || !tpfa::dev_ok(coarse, n / 8 * 4, 4, dev))
+    return TPFA_EINVAL;
+  const int nb = (int)((n + kT - 1) / kT < 4096 ? (n + kT - 1) / kT : 4096);
+  prolong2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(coarse, fine, nx, ny, nz, ns);
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
 }

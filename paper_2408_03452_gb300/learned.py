@@ -13,7 +13,9 @@ satisfies A e_k = r_k -- the residuals plain CG itself generates (k = 0 gives
 
 The network output u enters the preconditioner as the Jacobi blend
 z = D^-1 r + c u with the A-norm-optimal weight c (flexible CG in the
-library).  Loss: the A-norm error of that blend relative to ||e||_A,
+library).  By default the network runs on the 2x coarser grid,
+u = P net(R r, R ln K): Jacobi takes the high frequencies, the network the
+smooth error, at an eighth of the cost.  Loss: the A-norm error of that blend relative to ||e||_A,
   min_c ||D^-1 r + c u - e||_A^2 / ||e||_A^2 = (w'Aw - (u's)^2 / (u'Au)) / (e'Ae),
 w = e - D^-1 r, s = A w = r - A D^-1 r, per sample, summed over the batch
 (Adam is invariant to a constant factor).  Minimising over the weight makes
@@ -75,6 +77,8 @@ class Dataset:
         self.problems: list[Problem] = []
 
     def finish(self):
+        n = self.n
+        self.lnk_c = torch.stack([tpfa.restrict2(p.lnk, (n, n, n, 1)) for p in self.problems])
         self.R = torch.stack(self.R)
         self.E = torch.stack(self.E)
         self.S = torch.stack(self.S)
@@ -126,8 +130,12 @@ def make_dataset(n_real=50, snaps=40, n=64, sigma=1.5, seed=1000, tol=1e-10, log
     return ds
 
 
-def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, log=None):
-    """Adam on the A-norm loss.  Returns (params, history dict)."""
+def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse=True,
+          log=None):
+    """Adam on the blended A-norm loss.  coarse: the network runs on the 2x
+    coarser grid, u = P net(R r, R ln K) (R: 2x2x2 mean, P: nearest
+    prolongation; its gradient is the sum over each cell's 8 children).
+    Returns (params, history dict)."""
     dev = ds.R.device
     n = ds.n
     N = n ** 3
@@ -137,30 +145,36 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, log=No
     val_real = set(range(nreal - n_val, nreal))
     idx_train = np.array([i for i in range(len(ds.real)) if ds.real[i] not in val_real])
     idx_val = np.array([i for i in range(len(ds.real)) if ds.real[i] in val_real])
-    net = tpfa.UNet(n, n, n, ns=batch, train=True, device=dev)
+    nn = n // 2 if coarse else n
+    net = tpfa.UNet(nn, nn, nn, ns=batch, train=True, device=dev)
     P = init_params(seed).to(dev)
     M = torch.zeros_like(P)
     V = torch.zeros_like(P)
     G = torch.empty(batch * N, dtype=torch.float32, device=dev)
     q = torch.empty(N, dtype=torch.float32, device=dev)
     stats = torch.zeros((batch, 2), dtype=torch.float64, device=dev)
-    hist = {"epoch_loss": [], "val_loss": [], "seconds": [],
+    hist = {"epoch_loss": [], "val_loss": [], "seconds": [], "coarse": coarse,
             "jacobi_loss": float((ds.wAw / ds.eae).mean().item())}
     t = 0
     t0 = time.perf_counter()
+    shape = (n, n, n, batch)
 
     def batch_loss(idx, backward):
         nonlocal t
         Rb = ds.R[idx].reshape(-1)
         Sb = ds.S[idx].reshape(-1)
-        Lb = ds.lnk[ds.real[idx]].reshape(-1)
-        Z = net.forward(Rb, Lb)
+        if coarse:
+            Lb = ds.lnk_c[ds.real[idx]].reshape(-1)
+            Z = tpfa.prolong2(net.forward(tpfa.restrict2(Rb, shape), Lb), shape)
+        else:
+            Lb = ds.lnk[ds.real[idx]].reshape(-1)
+            Z = net.forward(Rb, Lb)
         for j, s in enumerate(idx):
             ctx.anorm_loss_grad(ds.problems[ds.real[s]].coef, Z[j * N:(j + 1) * N],
                                 Sb[j * N:(j + 1) * N], ds.eae[s:s + 1], q, G[j * N:(j + 1) * N],
                                 stats[j])
         if backward:
-            grad = net.backward(G)
+            grad = net.backward(tpfa.restrict2(G, shape, scale=1.0) if coarse else G)
             t += 1
             tpfa.adam_step(P, grad, M, V, t, lr)
         st = stats[:len(idx)]
@@ -189,7 +203,7 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, log=No
     return P, hist
 
 
-def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, log=None):
+def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, coarse=True, log=None):
     """Plain CG, Jacobi PCG and U-Net FCG on one held-out realization."""
     ctx = tpfa.Context(n, n, n)
     pr = Problem(ctx, seed, n, sigma)
@@ -210,23 +224,13 @@ def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, log=None)
     _, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=maxit)
     rec("jacobi_pcg", info)
     ctx.set_option("precond", 0)
-    net = tpfa.UNet(n, n, n, device=ctx.device)
+    nn = n // 2 if coarse else n
+    net = tpfa.UNet(nn, nn, nn, device=ctx.device)
     net.set_params(P.to(ctx.device))
     _, info = ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, tol=tol, maxit=maxit)
     rec("unet_fcg", info)
-    # time of one preconditioner application
-    r = torch.randn(n ** 3, dtype=torch.float32, device=ctx.device)
-    z = torch.empty_like(r)
-    for _ in range(3):
-        net.forward(r, pr.lnk, z)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(10):
-        net.forward(r, pr.lnk, z)
-    e1.record()
-    torch.cuda.synchronize()
-    out["unet_apply_ms"] = e0.elapsed_time(e1) / 10
+    out["unet_apply_ms"] = apply_bench(nn, 10)["apply_ms"]
+    out["coarse"] = coarse
     return out
 
 
@@ -261,6 +265,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-n", type=int, default=256)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--full", action="store_true",
+                    help="run the network on the full grid instead of the 2x coarser one")
     ap.add_argument("--apply-bench", type=int, default=0,
                     help="only time preconditioner applications on an N^3 grid")
     ap.add_argument("--reps", type=int, default=10)
@@ -270,10 +276,10 @@ def main(argv=None):
         print(json.dumps(apply_bench(a.apply_bench, a.reps)))
         return
     ds = make_dataset(a.n_real, a.snaps, a.n, log=log)
-    P, hist = train(ds, a.epochs, a.batch, a.lr, log=log)
+    P, hist = train(ds, a.epochs, a.batch, a.lr, coarse=not a.full, log=log)
     if a.save:
         np.save(a.save, P.cpu().numpy())
-    res = evaluate(P, n=a.eval_n, log=log)
+    res = evaluate(P, n=a.eval_n, coarse=not a.full, log=log)
     res["train"] = hist
     print(json.dumps(res))
 

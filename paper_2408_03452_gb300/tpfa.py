@@ -77,6 +77,8 @@ SIGNATURES = {
                                  C.c_double, C.c_double, _P]),
     "tpfa_anorm_loss_grad": (C.c_int, [_P] * 9),
     "tpfa_jacobi_split": (C.c_int, [_P] * 7),
+    "tpfa_restrict2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _P]),
+    "tpfa_prolong2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
     "fcg_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64,
                             C.POINTER(_Info), C.POINTER(C.c_int), _P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
@@ -481,6 +483,34 @@ class UNet:
                                             _ptr(grad, torch.float32, grad.numel(), dev, "grad"),
                                             _stream(dev)), "tpfa_unet_backward")
         return grad
+
+
+def restrict2(fine, shape, scale=0.125, coarse=None):
+    """coarse = scale * (sum of each cell's 8 children); shape = (nx, ny, nz, ns) of the fine grid."""
+    nx, ny, nz, ns = shape
+    dev = fine.device
+    nc = (nx // 2) * (ny // 2) * (nz // 2) * ns
+    if coarse is None:
+        coarse = torch.empty(nc, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_restrict2(_ptr(fine, torch.float32, nc * 8, dev, "fine"),
+                                    _ptr(coarse, torch.float32, nc, dev, "coarse"), nx, ny, nz, ns,
+                                    float(scale), _stream(dev)), "tpfa_restrict2")
+    return coarse
+
+
+def prolong2(coarse, shape, fine=None):
+    """fine[c] = coarse[parent(c)]; shape = (nx, ny, nz, ns) of the fine grid."""
+    nx, ny, nz, ns = shape
+    dev = coarse.device
+    n = nx * ny * nz * ns
+    if fine is None:
+        fine = torch.empty(n, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_prolong2(_ptr(coarse, torch.float32, n // 8, dev, "coarse"),
+                                   _ptr(fine, torch.float32, n, dev, "fine"), nx, ny, nz, ns,
+                                   _stream(dev)), "tpfa_prolong2")
+    return fine
 
 
 def adam_step(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

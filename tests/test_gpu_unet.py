@@ -260,6 +260,40 @@ def test_fcg_with_unet_converges(tp, oracle_mod, shape):
     assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-8 * 1.01
 
 
+def test_restrict_prolong_match_oracle(tp):
+    rng = np.random.default_rng(21)
+    nx, ny, nz, ns = 8, 6, 4, 2
+    f = rng.standard_normal((ns, nz, ny, nx)).astype(np.float32)
+    dev = torch.device("cuda")
+    F = torch.from_numpy(f.ravel()).to(dev)
+    rc = tp.restrict2(F, (nx, ny, nz, ns)).cpu().double().numpy()
+    ref = U.restrict2(f.astype(np.float64)).ravel()
+    np.testing.assert_allclose(rc, ref, rtol=1e-6, atol=1e-7)
+    rs = tp.restrict2(F, (nx, ny, nz, ns), scale=1.0).cpu().double().numpy()
+    np.testing.assert_allclose(rs, 8.0 * ref, rtol=1e-6, atol=1e-6)
+    c = rng.standard_normal(ref.size).astype(np.float32)
+    pf = tp.prolong2(torch.from_numpy(c).to(dev), (nx, ny, nz, ns)).cpu().numpy()
+    assert np.array_equal(pf, U.prolong2(c.reshape(ns, nz // 2, ny // 2, nx // 2)).ravel()
+                          .astype(np.float32))
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 24, 40)])
+def test_fcg_with_coarse_unet_converges(tp, oracle_mod, shape):
+    """A network created for the 2x coarser grid is applied as P net(R r, R ln K)
+    inside the blend; the solve reaches the FP64 tolerance."""
+    O = oracle_mod
+    K, mask, pD = _problem(shape, seed=5, sigma=1.5)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    _, flat = params_case(9)
+    dev = torch.device("cuda")
+    net = tp.UNet(*(d // 2 for d in shape))
+    net.set_params(torch.from_numpy(flat).to(dev))
+    lnk = torch.from_numpy(np.log(K).astype(np.float32)).to(dev)
+    x, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, tol=1e-8, maxit=20000)
+    assert info["code"] == tp.OK
+    assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-8 * 1.01
+
+
 def test_fcg_rejects_mismatched_network(tp):
     shape = (16, 16, 16)
     K, mask, pD = _problem(shape)
