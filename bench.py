@@ -44,6 +44,7 @@ UNIT = "cell-updates/s"
 SWEEP_BYTES_PER_CELL = 48
 FALLBACK_HBM_GBS = 6800.0
 LEARNED_METRIC = "U-Net FCG cell-iterations/s"
+LEARNED_FCG_M = 8  # retained directions of flexible CG in the learned workload
 LEARNED_UNIT = "cell-iterations/s"
 # useful FLOPs per cell of one U-Net application (true layer shapes: 2->16,
 # 16->16 and 16->1 at full resolution, 16->32 and 32->16 at 1/8, 32->64 and
@@ -468,6 +469,7 @@ def run_learned(a, dev, rank, local, barrier):
     del ds
     torch.cuda.empty_cache()
     ctx = tpfa.Context(n, n, n, device=dev)
+    ctx.set_option("fcg_m", LEARNED_FCG_M)
     pr = learned.Problem(ctx, 777001 + a.seed, n, 1.5)
     nn = n // 2  # the network runs on the 2x coarser grid
     net = tpfa.UNet(nn, nn, nn, device=dev)
@@ -522,7 +524,7 @@ def run_learned(a, dev, rank, local, barrier):
             "dtype": "bf16-net/f32-fcg/f64-refine", "data": "synthetic",
             "config": {
                 "workload": (f"learned preconditioner: U-Net trained at 64^3 on {n_pairs} plain-CG "
-                             f"pairs, applied on the 2x coarser grid inside flexible CG (m = 4, "
+                             f"pairs, applied on the 2x coarser grid inside flexible CG (m = {LEARNED_FCG_M}, "
                              f"Jacobi blend) on a held-out {n}^3 lognormal sigma-1.5 "
                              f"realization with Dirichlet x ends, FP64 relative residual "
                              f"{a.tol:g}"),

@@ -72,52 +72,11 @@ __global__ void start_kernel(const double* __restrict__ r64, double scale, float
   block_sum3(rr, 0.0, 0.0, part);
 }
 
-// partial a'b
-__global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
-                           double* part) {
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    s += (double)a[i] * b[i];
-  block_sum3(s, 0.0, 0.0, part);
-}
-
-// p = z + beta p (p = z when first); partial p'r
-__global__ void dir_kernel(const float* __restrict__ z, float* __restrict__ p,
-                           const float* __restrict__ r, float beta, int first, int64_t n,
-                           double* part) {
-  double pr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    const float v = first ? z[i] : fmaf(beta, p[i], z[i]);
-    p[i] = v;
-    pr += (double)v * r[i];
-  }
-  block_sum3(pr, 0.0, 0.0, part);
-}
-
-// e += alpha p; r -= alpha q; partial r'r
-__global__ void update_kernel(float* __restrict__ e, float* __restrict__ r,
-                              const float* __restrict__ p, const float* __restrict__ q, float alpha,
-                              int64_t n, double* part) {
-  double rr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    e[i] = fmaf(alpha, p[i], e[i]);
-    const float v = fmaf(-alpha, q[i], r[i]);
-    r[i] = v;
-    rr += (double)v * v;
-  }
-  block_sum3(rr, 0.0, 0.0, part);
-}
-
 // x += e / scale
 __global__ void correct_kernel(double* __restrict__ x, const float* __restrict__ e, double inv_scale,
                                int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
     x[i] += inv_scale * (double)e[i];
-}
-
-__global__ void copy_kernel(const float* __restrict__ a, float* __restrict__ b, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    b[i] = a[i];
 }
 
 // Block sums of M per-thread FP64 values (warp shuffles, then the warps in
@@ -144,81 +103,197 @@ __device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) 
 constexpr int kMaxDirs = 16;
 struct Dirs {
   const float* v[kMaxDirs];
-  float beta[kMaxDirs];
 };
 
-// partials of z'v_j, j < M
+// Device-resident scalars of the inner iteration: written by one-block finish
+// kernels from fixed-order partial sums, read by the vector kernels, so the
+// host need not take part in an iteration.
+struct Scal {
+  double c;                // blend weight of the current preconditioned residual
+  double beta[kMaxDirs];   // coefficients against the retained directions, newest first
+  double pq[kMaxDirs];     // p_j'q_j by ring slot
+  double alpha;
+  double pr;
+  int bad;                 // p'q <= 0 or a non-finite value since the host last looked
+  int pad;
+};
+
+// One pass for the preconditioned residual z = w + c u (w = r / D with Jacobi,
+// else r; u the network term when net) and its A-orthogonalisation against M
+// retained directions q_j = A p_j:
+//   s0 = u'r, s1 = (Au)'w, a_j = w'q_j, b_j = u'q_j   (z'q_j = a_j + c b_j).
 template <int M>
-__global__ void mdot_kernel(const float* __restrict__ z, Dirs d, int64_t n, double* part) {
-  double s[M];
+__global__ void dots_kernel(const float* __restrict__ r, const float4* __restrict__ coef,
+                            const float* __restrict__ u, const float* __restrict__ au, Dirs qd,
+                            int jac, int net, int64_t n, double* part) {
+  // FP32 sums per thread (about a hundred terms each), FP64 across threads
+  // and blocks: FP64 arithmetic per element would cost more than the memory
+  constexpr int K = 2 + 2 * M;
+  float s[K];
 #pragma unroll
-  for (int j = 0; j < M; ++j) s[j] = 0.0;
+  for (int j = 0; j < K; ++j) s[j] = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    const float zi = z[i];
+    const float ri = r[i];
+    const float wi = jac ? ri / coef[i].w : ri;
+    const float ui = net ? u[i] : 0.f;
+    if (net) {
+      s[0] = fmaf(ui, ri, s[0]);
+      s[1] = fmaf(au[i], wi, s[1]);
+    }
 #pragma unroll
-    for (int j = 0; j < M; ++j) s[j] += (double)zi * d.v[j][i];
+    for (int j = 0; j < M; ++j) {
+      const float qj = qd.v[j][i];
+      s[2 + j] = fmaf(wi, qj, s[2 + j]);
+      s[2 + M + j] = fmaf(ui, qj, s[2 + M + j]);
+    }
   }
-  block_sum_m<M>(s, part);
+  double d[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) d[j] = s[j];
+  block_sum_m<K>(d, part);
 }
 
-// p = z + sum_j beta_j v_j (p may be one of the v_j); partial p'r
-template <int M>
-__global__ void mdir_kernel(const float* __restrict__ z, Dirs d, float* p,
-                            const float* __restrict__ r, int64_t n, double* part) {
-  double pr[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    float v = z[i];
+// c = (u'r - (Au)'w) / u'Au (0 without network, or when u'Au is not positive)
+// and beta_j = -(a_j + c b_j) / (p_j'q_j) for the M retained directions
+__global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int M, int net,
+                                   const double* __restrict__ uau, Scal* sc, int head, int m) {
+  __shared__ double tot[2 + 2 * kMaxDirs];
+  const int K = 2 + 2 * M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < K; k += nw) {
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += part[(size_t)b * K + k];
 #pragma unroll
-    for (int j = 0; j < M; ++j) v = fmaf(d.beta[j], d.v[j][i], v);
-    p[i] = v;
-    pr[0] += (double)v * r[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[k] = t;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0;
+    if (net && nb > 0) {
+      const double d = *uau;
+      c = (d > 0.0 && isfinite(d)) ? (tot[0] - tot[1]) / d : 0.0;
+      if (!isfinite(c)) c = 0.0;
+    }
+    sc->c = c;
+    for (int j = 0; j < M; ++j) {
+      const int slot = (head - 1 - j + m) % m;
+      double b = -(tot[2 + j] + c * tot[2 + M + j]) / sc->pq[slot];
+      if (!isfinite(b)) {
+        sc->bad = 1;
+        b = 0.0;
+      }
+      sc->beta[j] = b;
+    }
+  }
+}
+
+// p = w + c u + sum_j beta_j p_j; partial p'r
+template <int M>
+__global__ void dir_kernel(const float* __restrict__ r, const float4* __restrict__ coef,
+                           const float* __restrict__ u, Dirs pd, const Scal* __restrict__ sc,
+                           int jac, int net, float* p, int64_t n, double* part) {
+  // p may be the oldest retained direction (read, then overwritten, per element)
+  const float c = (float)sc->c;
+  float beta[M > 0 ? M : 1];
+#pragma unroll
+  for (int j = 0; j < M; ++j) beta[j] = (float)sc->beta[j];
+  float prf = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+    const float ri = r[i];
+    float v = jac ? ri / coef[i].w : ri;
+    if (net) v = fmaf(c, u[i], v);
+#pragma unroll
+    for (int j = 0; j < M; ++j) v = fmaf(beta[j], pd.v[j][i], v);
+    p[i] = v;
+    prf = fmaf(v, ri, prf);
+  }
+  double pr[1] = {prf};
   block_sum_m<1>(pr, part);
 }
 
-#define TPFA_FCG_M(X) \
-  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+// fixed-order sum of nb block partials by one block of kT threads
+__device__ __forceinline__ double block_total(const double* __restrict__ part, int nb) {
+  __shared__ double sh[kT];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) t += part[b];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = kT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  return sh[0];
+}
 
-void launch_mdot(int m, int nb, cudaStream_t s, const float* z, const Dirs& d, int64_t n,
-                 double* part) {
-  switch (m) {
-#define X(M) \
-  case M: mdot_kernel<M><<<nb, kT, 0, s>>>(z, d, n, part); break;
-    TPFA_FCG_M(X)
-#undef X
-    default: break;
+// alpha = p'r / p'q (0 and the bad flag when p'q is not positive or a value
+// is not finite); records p'q of the new direction in its slot
+__global__ void finish_alpha_kernel(const double* __restrict__ part, int nb,
+                                    const double* __restrict__ pq_dev, Scal* sc, int head) {
+  const double pr = block_total(part, nb);
+  if (threadIdx.x == 0) {
+    const double pq = *pq_dev;
+    sc->pr = pr;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(pr)) {
+      sc->bad = 1;
+      sc->alpha = 0.0;
+      sc->pq[head] = 1.0;
+    } else {
+      sc->alpha = pr / pq;
+      sc->pq[head] = pq;
+    }
   }
 }
 
-void launch_mdir(int m, int nb, cudaStream_t s, const float* z, const Dirs& d, float* p,
-                 const float* r, int64_t n, double* part) {
-  switch (m) {
-#define X(M) \
-  case M: mdir_kernel<M><<<nb, kT, 0, s>>>(z, d, p, r, n, part); break;
-    TPFA_FCG_M(X)
-#undef X
-    default: break;
-  }
-}
-
-// partials of u'r and (Au)'(r / D)
-__global__ void blend_dots_kernel(const float* __restrict__ u, const float* __restrict__ r,
-                                  const float* __restrict__ au, const float4* __restrict__ coef,
-                                  int64_t n, double* part) {
-  double s0 = 0.0, s1 = 0.0;
+// e += alpha p; r -= alpha q; partial r'r
+__global__ void update_kernel(float* __restrict__ e, float* __restrict__ r,
+                              const float* __restrict__ p, const float* __restrict__ q,
+                              const Scal* __restrict__ sc, int64_t n, double* part) {
+  const float alpha = (float)sc->alpha;
+  float rrf = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    const float ri = r[i];
-    s0 += (double)u[i] * ri;
-    s1 += (double)au[i] * (ri / coef[i].w);
+    e[i] = fmaf(alpha, p[i], e[i]);
+    const float v = fmaf(-alpha, q[i], r[i]);
+    r[i] = v;
+    rrf = fmaf(v, v, rrf);
   }
-  block_sum3(s0, s1, 0.0, part);
+  double rr[1] = {rrf};
+  block_sum_m<1>(rr, part);
 }
 
-// z = r / D + c u (in place over u)
-__global__ void blend_kernel(float* __restrict__ uz, const float* __restrict__ r,
-                             const float4* __restrict__ coef, float c, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
-    uz[i] = fmaf(c, uz[i], r[i] / coef[i].w);
+// r'r of this iteration into its history slot
+__global__ void finish_rr_kernel(const double* __restrict__ part, int nb, double* slot) {
+  const double rr = block_total(part, nb);
+  if (threadIdx.x == 0) *slot = rr;
+}
+
+// partial sums per block: the most any kernel writes (dots_kernel<kMaxDirs>)
+constexpr int kPartPerBlock = 2 + 2 * kMaxDirs;
+
+#define TPFA_FCG_M0(X) \
+  X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+void launch_dots(int m, int nb, cudaStream_t s, const float* r, const float4* coef, const float* u,
+                 const float* au, const Dirs& qd, int jac, int net, int64_t n, double* part) {
+  switch (m) {
+#define X(M) \
+  case M: dots_kernel<M><<<nb, kT, 0, s>>>(r, coef, u, au, qd, jac, net, n, part); break;
+    TPFA_FCG_M0(X)
+#undef X
+    default: break;
+  }
+}
+
+void launch_dir(int m, int nb, cudaStream_t s, const float* r, const float4* coef, const float* u,
+                const Dirs& pd, const Scal* sc, int jac, int net, float* p, int64_t n,
+                double* part) {
+  switch (m) {
+#define X(M) \
+  case M: dir_kernel<M><<<nb, kT, 0, s>>>(r, coef, u, pd, sc, jac, net, p, n, part); break;
+    TPFA_FCG_M0(X)
+#undef X
+    default: break;
+  }
 }
 
 // y = x / D
@@ -239,41 +314,42 @@ __global__ void sub_kernel(const float* a, const float* b, float* y, int64_t n) 
 __global__ void restrict2_kernel(const float* __restrict__ fine, float* __restrict__ coarse, int nx,
                                  int ny, int nz, int ns, float scale) {
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-  const int64_t nc = (int64_t)cx * cy * cz * ns;
-  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < nc; c += (int64_t)gridDim.x * kT) {
-    const int i = (int)(c % cx);
-    int64_t t = c / cx;
-    const int j = (int)(t % cy);
+  const int nc = cx * cy * cz * ns;  // grids with fewer than 2^31 cells
+  for (int c = blockIdx.x * kT + threadIdx.x; c < nc; c += gridDim.x * kT) {
+    const int i = c % cx;
+    int t = c / cx;
+    const int j = t % cy;
     t /= cy;
-    const int k = (int)(t % cz);
-    const int64_t s = t / cz;
-    const float* f = fine + s * ((int64_t)nx * ny * nz);
+    const int k = t % cz;
+    const int s = t / cz;
+    const float* f = fine + (size_t)s * nx * ny * nz;
     float acc = 0.f;
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy) {
         const float2 v = *reinterpret_cast<const float2*>(
-            f + ((int64_t)(2 * k + dz) * ny + 2 * j + dy) * nx + 2 * i);
+            f + ((size_t)(2 * k + dz) * ny + 2 * j + dy) * nx + 2 * i);
         acc += v.x + v.y;
       }
     coarse[c] = scale * acc;
   }
 }
 
-// fine[c] = coarse[parent(c)]
+// fine[c] = coarse[parent(c)]; each thread writes two x-neighbours (same parent)
 __global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restrict__ fine, int nx,
                                 int ny, int nz, int ns) {
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-  const int64_t n = (int64_t)nx * ny * nz * ns;
-  for (int64_t c = (int64_t)blockIdx.x * kT + threadIdx.x; c < n; c += (int64_t)gridDim.x * kT) {
-    const int i = (int)(c % nx);
-    int64_t t = c / nx;
-    const int j = (int)(t % ny);
+  const int n2 = nx / 2 * ny * nz * ns;
+  for (int c = blockIdx.x * kT + threadIdx.x; c < n2; c += gridDim.x * kT) {
+    const int i = c % cx;
+    int t = c / cx;
+    const int j = t % ny;
     t /= ny;
-    const int k = (int)(t % nz);
-    const int64_t s = t / nz;
-    fine[c] = coarse[((s * cz + k / 2) * cy + j / 2) * cx + i / 2];
+    const int k = t % nz;
+    const int s = t / nz;
+    const float v = coarse[((s * cz + k / 2) * cy + j / 2) * cx + i];
+    *reinterpret_cast<float2*>(fine + 2 * (size_t)c) = make_float2(v, v);
   }
 }
 
@@ -310,6 +386,11 @@ __global__ void loss_grad_kernel(const float* __restrict__ q, const float* __res
     g[i] = f * fmaf(ab, q[i], -r[i]);
 }
 
+// iterations between the host's looks at the device scalars (convergence,
+// breakdown, stagnation); at most this many iterations run past the one that
+// met the tolerance
+constexpr int kCheckEvery = 4;
+
 struct Work {
   cudaStream_t s = nullptr;
   int nb = 0;
@@ -319,12 +400,15 @@ struct Work {
   float *P = nullptr, *Q = nullptr;  // m directions and their images A p
   double* r64 = nullptr;
   double* uau = nullptr;     // dev, 1
-  double* part = nullptr;    // dev, kMaxDirs * nb
+  double* part = nullptr;    // dev, kPartPerBlock * nb
   double* hpart = nullptr;   // pinned host
   double* norms = nullptr;   // dev, 2
   double* hnorms = nullptr;  // pinned
   double* pq = nullptr;      // dev, 1
   // network on the 2x coarser grid: restricted residual, its image, ln K
+  Scal* sc = nullptr;        // dev, iteration scalars
+  double* hist = nullptr;    // dev, r'r of the iterations since the host last looked
+  double* hhist = nullptr;   // pinned copy
   bool coarse = false;
   int dims[3] = {0, 0, 0};
   float *rc = nullptr, *uc = nullptr, *lnkc = nullptr;
@@ -336,10 +420,14 @@ struct Work {
            cudaMalloc(&Q, (size_t)m * n * 4) == cudaSuccess &&
            cudaMalloc(&e, n * 4) == cudaSuccess && cudaMalloc(&r64, n * 8) == cudaSuccess &&
            cudaMalloc(&au, n * 4) == cudaSuccess && cudaMalloc(&uau, 8) == cudaSuccess &&
-           cudaMalloc(&part, sizeof(double) * kMaxDirs * nb) == cudaSuccess &&
+           cudaMalloc(&part, sizeof(double) * kPartPerBlock * nb) == cudaSuccess &&
            cudaMalloc(&norms, 16) == cudaSuccess && cudaMalloc(&pq, 8) == cudaSuccess &&
-           cudaMallocHost(&hpart, sizeof(double) * kMaxDirs * nb) == cudaSuccess &&
-           cudaMallocHost(&hnorms, 16) == cudaSuccess;
+           cudaMallocHost(&hpart, sizeof(double) * kPartPerBlock * nb) == cudaSuccess &&
+           cudaMallocHost(&hnorms, 16) == cudaSuccess &&
+           cudaMalloc(&sc, sizeof(Scal)) == cudaSuccess &&
+           cudaMalloc(&hist, sizeof(double) * kCheckEvery) == cudaSuccess &&
+           cudaMallocHost(&hhist, sizeof(double) * kCheckEvery) == cudaSuccess &&
+           cudaMemset(sc, 0, sizeof(Scal)) == cudaSuccess;
   }
   ~Work() {
     if (s) cudaStreamSynchronize(s);
@@ -359,6 +447,9 @@ struct Work {
     cudaFree(rc);
     cudaFree(uc);
     cudaFree(lnkc);
+    cudaFree(sc);
+    cudaFree(hist);
+    cudaFreeHost(hhist);
   }
   // sums of the three per-block partials, in block order
   bool fetch(double* out3) {
@@ -370,18 +461,6 @@ struct Work {
     out3[0] = out3[1] = out3[2] = 0.0;
     for (int b = 0; b < nb; ++b)
       for (int k = 0; k < 3; ++k) out3[k] += hpart[3 * b + k];
-    return true;
-  }
-  // sums of k per-block partials laid out [block][k], in block order
-  bool fetch_k(int k, double* out) {
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(hpart, part, sizeof(double) * k * nb, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return false;
-    for (int j = 0; j < k; ++j) out[j] = 0.0;
-    for (int b = 0; b < nb; ++b)
-      for (int j = 0; j < k; ++j) out[j] += hpart[(size_t)b * k + j];
     return true;
   }
   // k per-block partials ([block][k], or the 3-slot layout when k3) and one
@@ -419,22 +498,8 @@ struct Result {
 
 enum PrecMode { kIdentity = 0, kJacobi = 1, kBlend = 2 };
 
-// z = M(r) for the current mode
-int precondition(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
-                 PrecMode mode) {
-  const float4* c4 = reinterpret_cast<const float4*>(coef);
-  if (mode == kIdentity) {
-    copy_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.z, w.n);
-    ++w.launches;
-    return TPFA_OK;
-  }
-  if (mode == kJacobi) {
-    jacobi_kernel<<<w.nb, kT, 0, w.s>>>(w.r, c4, w.z, w.n);
-    ++w.launches;
-    return TPFA_OK;
-  }
-  // z = D^-1 r + c u, u = net(r) (or P net(R r) on the coarser grid), c the
-  // A-norm-optimal weight
+// the network term u of the blend (into w.z) and A u (into w.au, u'Au into w.uau)
+int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w) {
   int rc;
   if (w.coarse) {
     restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.rc, w.dims[0], w.dims[1], w.dims[2], 1, 0.125f);
@@ -448,65 +513,70 @@ int precondition(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* ln
     w.launches += 15;
   }
   rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
-  if (rc) return rc;
-  blend_dots_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, w.au, c4, w.n, w.part);
-  w.launches += 2;
-  double d3[3], uau = 0.0;
-  if (!w.fetch_with_scalar(2, true, d3, w.uau, &uau)) return TPFA_ECUDA;
-  double cw = uau > 0.0 && std::isfinite(uau) ? (d3[0] - d3[1]) / uau : 0.0;
-  if (!std::isfinite(cw)) cw = 0.0;
-  blend_kernel<<<w.nb, kT, 0, w.s>>>(w.z, w.r, c4, (float)cw, w.n);
   ++w.launches;
-  return TPFA_OK;
+  return rc;
 }
 
 constexpr int kStallWindow = 100;
 
-// Inner FCG on A e = r (r, e already set, r'r = rr0); returns a TPFA_* error or
-// TPFA_OK, with res->status = TPFA_EBREAKDOWN if the method without network
-// broke down.
+// Inner FCG on A e = r (r, e already set, r'r = rr0).  All scalars stay on the
+// device; every kCheckEvery iterations the host reads the r'r history and the
+// bad flag.  Returns a TPFA_* error or TPFA_OK, with res->status =
+// TPFA_EBREAKDOWN if the method without network broke down.
 int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
               double rr0, double target, int64_t maxit, PrecMode fallback_mode, Result* res) {
   const int m = w.m;
-  double dots[kMaxDirs], pqv[kMaxDirs];
+  const float4* c4 = reinterpret_cast<const float4*>(coef);
   double rr = rr0;
-  int stored = 0, head = 0;
+  int stored = 0, head = 0, pending = 0;
   PrecMode mode = net == nullptr ? kIdentity : (res->fallback ? fallback_mode : kBlend);
   std::vector<double> hist(1, rr);
+  if (cudaMemsetAsync(w.sc, 0, sizeof(Scal), w.s) != cudaSuccess) return TPFA_ECUDA;
   while (res->iters < maxit && rr > target * target * rr0) {
-    int rc = precondition(c, net, coef, lnk, w, mode);
-    if (rc) return rc;
-    // A-orthogonalise against the retained directions, newest first
-    Dirs d;
-    for (int j = 0; j < stored; ++j) d.v[j] = w.Q + (size_t)((head - 1 - j + m) % m) * w.n;
-    if (stored > 0) {
-      launch_mdot(stored, w.nb, w.s, w.z, d, w.n, w.part);
-      ++w.launches;
-      if (!w.fetch_k(stored, dots)) return TPFA_ECUDA;
+    const int jac = mode != kIdentity, with_net = mode == kBlend;
+    if (with_net) {
+      const int rc = network_term(c, net, coef, lnk, w);
+      if (rc) return rc;
     }
-    bool finite = true;
+    Dirs qd, pd;
     for (int j = 0; j < stored; ++j) {
-      const int slot = (head - 1 - j + m) % m;
-      const double beta = -dots[j] / pqv[slot];
-      finite = finite && std::isfinite(beta);
-      d.v[j] = w.P + (size_t)slot * w.n;
-      d.beta[j] = (float)beta;
+      const size_t slot = (size_t)((head - 1 - j + m) % m);
+      qd.v[j] = w.Q + slot * w.n;
+      pd.v[j] = w.P + slot * w.n;
+    }
+    if (stored > 0 || with_net) {
+      launch_dots(stored, w.nb, w.s, w.r, c4, w.z, w.au, qd, jac, with_net, w.n, w.part);
+      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, stored, with_net, w.uau, w.sc, head, m);
+    } else {
+      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, 0, 0, 0, w.uau, w.sc, head, m);
     }
     float* p = w.P + (size_t)head * w.n;
     float* q = w.Q + (size_t)head * w.n;
-    if (stored > 0)
-      launch_mdir(stored, w.nb, w.s, w.z, d, p, w.r, w.n, w.part);
-    else
-      dir_kernel<<<w.nb, kT, 0, w.s>>>(w.z, p, w.r, 0.f, 1, w.n, w.part);
-    ++w.launches;
-    double d3[3];
-    rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
+    launch_dir(stored, w.nb, w.s, w.r, c4, w.z, pd, w.sc, jac, with_net, p, w.n, w.part);
+    int rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
     if (rc) return rc;
-    ++w.launches;
-    double pq = 0.0;
-    if (!w.fetch_with_scalar(1, stored == 0, d3, w.pq, &pq)) return TPFA_ECUDA;
-    const double pr = d3[0];
-    const bool bad = !(pq > 0.0) || !std::isfinite(pq) || !std::isfinite(pr) || !finite;
+    finish_alpha_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, w.pq, w.sc, head);
+    update_kernel<<<w.nb, kT, 0, w.s>>>(w.e, w.r, p, q, w.sc, w.n, w.part);
+    finish_rr_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, w.hist + pending);
+    w.launches += 7;
+    ++pending;
+    ++res->iters;
+    head = (head + 1) % m;
+    if (stored < m) ++stored;
+    if (pending < kCheckEvery && res->iters < maxit) continue;
+    // the host looks: r'r history, bad flag
+    int bad = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(w.hhist, w.hist, sizeof(double) * pending, cudaMemcpyDeviceToHost,
+                        w.s) != cudaSuccess ||
+        cudaMemcpyAsync(&bad, &w.sc->bad, sizeof(int), cudaMemcpyDeviceToHost, w.s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(w.s) != cudaSuccess)
+      return TPFA_ECUDA;
+    for (int k = 0; k < pending; ++k) hist.push_back(w.hhist[k]);
+    rr = w.hhist[pending - 1];
+    pending = 0;
+    if (!std::isfinite(rr)) bad = 1;
     // stagnation: the smallest r'r of the last kStallWindow iterations is not
     // 1% below the smallest before them
     bool stalled = false;
@@ -525,18 +595,8 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
       res->fallback = true;
       stored = 0;
       hist.assign(1, rr);
-      continue;
+      if (cudaMemsetAsync(w.sc, 0, sizeof(Scal), w.s) != cudaSuccess) return TPFA_ECUDA;
     }
-    const float alpha = (float)(pr / pq);
-    update_kernel<<<w.nb, kT, 0, w.s>>>(w.e, w.r, p, q, alpha, w.n, w.part);
-    ++w.launches;
-    if (!w.fetch(d3)) return TPFA_ECUDA;
-    rr = d3[0];
-    hist.push_back(rr);
-    pqv[head] = pq;
-    head = (head + 1) % m;
-    if (stored < m) ++stored;
-    ++res->iters;
   }
   return TPFA_OK;
 }
@@ -604,7 +664,8 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     int d4[4];
     tpfa_unet_shape(net, d4);
     const bool full = d4[0] == d3[0] && d4[1] == d3[1] && d4[2] == d3[2];
-    coarse = d3[0] % 2 == 0 && d3[1] % 2 == 0 && d3[2] % 2 == 0 && d4[0] == d3[0] / 2 &&
+    coarse = n < 2147483647LL && d3[0] % 2 == 0 && d3[1] % 2 == 0 && d3[2] % 2 == 0 &&
+             d4[0] == d3[0] / 2 &&
              d4[1] == d3[1] / 2 && d4[2] == d3[2] / 2;
     if (!(full || coarse) || d4[3] != 1) return TPFA_EINVAL;
   }
@@ -732,6 +793,7 @@ extern "C" int tpfa_jacobi_split(tpfa_ctx* c, const float* coef, const float* r,
 extern "C" int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, int nz, int ns,
                               float scale, void* stream) {
   if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || ns < 1) return TPFA_EINVAL;
+  if ((double)nx * ny * nz * ns >= 2147483647.0) return TPFA_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
   const size_t n = (size_t)nx * ny * nz * ns;
@@ -746,6 +808,7 @@ extern "C" int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, 
 extern "C" int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, int nz, int ns,
                              void* stream) {
   if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2 || ns < 1) return TPFA_EINVAL;
+  if ((double)nx * ny * nz * ns >= 2147483647.0) return TPFA_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
   const size_t n = (size_t)nx * ny * nz * ns;
