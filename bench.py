@@ -44,7 +44,7 @@ UNIT = "cell-updates/s"
 SWEEP_BYTES_PER_CELL = 48
 FALLBACK_HBM_GBS = 6800.0
 LEARNED_METRIC = "U-Net FCG cell-iterations/s"
-LEARNED_FCG_M = 8  # retained directions of flexible CG in the learned workload
+LEARNED_FCG_M = 2  # retained directions of flexible CG in the learned workload
 LEARNED_UNIT = "cell-iterations/s"
 # useful FLOPs per cell of one U-Net application (true layer shapes: 2->16,
 # 16->16 and 16->1 at full resolution, 16->32 and 32->16 at 1/8, 32->64 and

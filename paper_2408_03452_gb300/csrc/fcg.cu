@@ -123,7 +123,7 @@ struct Scal {
 // retained directions q_j = A p_j:
 //   s0 = u'r, s1 = (Au)'w, a_j = w'q_j, b_j = u'q_j   (z'q_j = a_j + c b_j).
 template <int M>
-__global__ void dots_kernel(const float* __restrict__ r, const float4* __restrict__ coef,
+__global__ void dots_kernel(const float* __restrict__ r, const float* __restrict__ dinv,
                             const float* __restrict__ u, const float* __restrict__ au, Dirs qd,
                             int jac, int net, int64_t n, double* part) {
   // FP32 sums per thread (about a hundred terms each), FP64 across threads
@@ -134,7 +134,7 @@ __global__ void dots_kernel(const float* __restrict__ r, const float4* __restric
   for (int j = 0; j < K; ++j) s[j] = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
     const float ri = r[i];
-    const float wi = jac ? ri / coef[i].w : ri;
+    const float wi = jac ? ri * dinv[i] : ri;
     const float ui = net ? u[i] : 0.f;
     if (net) {
       s[0] = fmaf(ui, ri, s[0]);
@@ -190,7 +190,7 @@ __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int 
 
 // p = w + c u + sum_j beta_j p_j; partial p'r
 template <int M>
-__global__ void dir_kernel(const float* __restrict__ r, const float4* __restrict__ coef,
+__global__ void dir_kernel(const float* __restrict__ r, const float* __restrict__ dinv,
                            const float* __restrict__ u, Dirs pd, const Scal* __restrict__ sc,
                            int jac, int net, float* p, int64_t n, double* part) {
   // p may be the oldest retained direction (read, then overwritten, per element)
@@ -201,7 +201,7 @@ __global__ void dir_kernel(const float* __restrict__ r, const float4* __restrict
   float prf = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
     const float ri = r[i];
-    float v = jac ? ri / coef[i].w : ri;
+    float v = jac ? ri * dinv[i] : ri;
     if (net) v = fmaf(c, u[i], v);
 #pragma unroll
     for (int j = 0; j < M; ++j) v = fmaf(beta[j], pd.v[j][i], v);
@@ -273,7 +273,7 @@ constexpr int kPartPerBlock = 2 + 2 * kMaxDirs;
 #define TPFA_FCG_M0(X) \
   X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
-void launch_dots(int m, int nb, cudaStream_t s, const float* r, const float4* coef, const float* u,
+void launch_dots(int m, int nb, cudaStream_t s, const float* r, const float* coef, const float* u,
                  const float* au, const Dirs& qd, int jac, int net, int64_t n, double* part) {
   switch (m) {
 #define X(M) \
@@ -284,7 +284,7 @@ void launch_dots(int m, int nb, cudaStream_t s, const float* r, const float4* co
   }
 }
 
-void launch_dir(int m, int nb, cudaStream_t s, const float* r, const float4* coef, const float* u,
+void launch_dir(int m, int nb, cudaStream_t s, const float* r, const float* coef, const float* u,
                 const Dirs& pd, const Scal* sc, int jac, int net, float* p, int64_t n,
                 double* part) {
   switch (m) {
@@ -294,6 +294,12 @@ void launch_dir(int m, int nb, cudaStream_t s, const float* r, const float4* coe
 #undef X
     default: break;
   }
+}
+
+// dinv = 1 / D (the Jacobi scaling the blend uses)
+__global__ void dinv_kernel(const float4* __restrict__ coef, float* __restrict__ dinv, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    dinv[i] = 1.0f / coef[i].w;
 }
 
 // y = x / D
@@ -396,7 +402,7 @@ struct Work {
   int nb = 0;
   int64_t n = 0;
   int m = 1;                 // retained directions
-  float *r = nullptr, *z = nullptr, *e = nullptr, *au = nullptr;
+  float *r = nullptr, *z = nullptr, *e = nullptr, *au = nullptr, *dinv = nullptr;
   float *P = nullptr, *Q = nullptr;  // m directions and their images A p
   double* r64 = nullptr;
   double* uau = nullptr;     // dev, 1
@@ -420,6 +426,7 @@ struct Work {
            cudaMalloc(&Q, (size_t)m * n * 4) == cudaSuccess &&
            cudaMalloc(&e, n * 4) == cudaSuccess && cudaMalloc(&r64, n * 8) == cudaSuccess &&
            cudaMalloc(&au, n * 4) == cudaSuccess && cudaMalloc(&uau, 8) == cudaSuccess &&
+           cudaMalloc(&dinv, n * 4) == cudaSuccess &&
            cudaMalloc(&part, sizeof(double) * kPartPerBlock * nb) == cudaSuccess &&
            cudaMalloc(&norms, 16) == cudaSuccess && cudaMalloc(&pq, 8) == cudaSuccess &&
            cudaMallocHost(&hpart, sizeof(double) * kPartPerBlock * nb) == cudaSuccess &&
@@ -437,6 +444,7 @@ struct Work {
     cudaFree(Q);
     cudaFree(e);
     cudaFree(au);
+    cudaFree(dinv);
     cudaFree(uau);
     cudaFree(r64);
     cudaFree(part);
@@ -526,7 +534,6 @@ constexpr int kStallWindow = 100;
 int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
               double rr0, double target, int64_t maxit, PrecMode fallback_mode, Result* res) {
   const int m = w.m;
-  const float4* c4 = reinterpret_cast<const float4*>(coef);
   double rr = rr0;
   int stored = 0, head = 0, pending = 0;
   PrecMode mode = net == nullptr ? kIdentity : (res->fallback ? fallback_mode : kBlend);
@@ -545,14 +552,14 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
       pd.v[j] = w.P + slot * w.n;
     }
     if (stored > 0 || with_net) {
-      launch_dots(stored, w.nb, w.s, w.r, c4, w.z, w.au, qd, jac, with_net, w.n, w.part);
+      launch_dots(stored, w.nb, w.s, w.r, w.dinv, w.z, w.au, qd, jac, with_net, w.n, w.part);
       finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, stored, with_net, w.uau, w.sc, head, m);
     } else {
       finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, 0, 0, 0, w.uau, w.sc, head, m);
     }
     float* p = w.P + (size_t)head * w.n;
     float* q = w.Q + (size_t)head * w.n;
-    launch_dir(stored, w.nb, w.s, w.r, c4, w.z, pd, w.sc, jac, with_net, p, w.n, w.part);
+    launch_dir(stored, w.nb, w.s, w.r, w.dinv, w.z, pd, w.sc, jac, with_net, p, w.n, w.part);
     int rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
     if (rc) return rc;
     finish_alpha_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, w.pq, w.sc, head);
@@ -687,6 +694,10 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     w.nb = 4 * nsm;
     bool ok = w.alloc();
+    if (ok) {
+      dinv_kernel<<<w.nb, kT, 0, w.s>>>(reinterpret_cast<const float4*>(coef), w.dinv, n);
+      ok = cudaGetLastError() == cudaSuccess;
+    }
     if (ok && coarse) {
       const size_t nc = (size_t)(n / 8) * 4;
       ok = cudaMalloc(&w.rc, nc) == cudaSuccess && cudaMalloc(&w.uc, nc) == cudaSuccess &&
