@@ -45,6 +45,7 @@ SWEEP_BYTES_PER_CELL = 48
 FALLBACK_HBM_GBS = 6800.0
 LEARNED_METRIC = "U-Net FCG cell-iterations/s"
 LEARNED_FCG_M = 2  # retained directions of flexible CG in the learned workload
+LEARNED_LEVELS = 2  # the network runs on the 2^levels coarser grid
 LEARNED_UNIT = "cell-iterations/s"
 # useful FLOPs per cell of one U-Net application (true layer shapes: 2->16,
 # 16->16 and 16->1 at full resolution, 16->32 and 32->16 at 1/8, 32->64 and
@@ -165,8 +166,8 @@ SAMPLE_LEARNED = 32
 
 
 def oracle_fcg_step(iters, params=None):
-    """Oracle flexible CG with the Jacobi-blended U-Net (on the 2x coarser grid)
-    on a 32^3 lognormal
+    """Oracle flexible CG with the Jacobi-blended U-Net (on the 2^LEARNED_LEVELS
+    coarser grid) on a 32^3 lognormal
     (sigma 1.5) realization with Dirichlet x ends: CSR assembly, RHS, `iters`
     FCG iterations.  params: flat parameter vector (default: He
     initialisation of the oracle).  Returns cell-iterations done."""
@@ -198,7 +199,7 @@ def oracle_fcg_step(iters, params=None):
         dinv = 1.0 / diag
 
     def precond(r):
-        u = U.precondition_coarse(p, r.reshape(1, n, n, n), lnk).reshape(-1)
+        u = U.precondition_coarse(p, r.reshape(1, n, n, n), lnk, LEARNED_LEVELS).reshape(-1)
         return U.jacobi_blend(u, r, dinv, A.matvec)[0]
 
     _, it, _ = U.fcg(A.matvec, b, precond, 0.0, iters)
@@ -454,16 +455,16 @@ def time_conv(tpfa, dev, n, cin, cout, reps=10):
 def run_learned(a, dev, rank, local, barrier):
     """Learned-preconditioner workload.  Setup (untimed): 50 lognormal
     (sigma 1.5) 64^3 realizations x 40 pairs (r_k, e_k) from plain-CG iterates,
-    Adam on the blended A-norm loss with the network on the 2x coarser grid.
+    Adam on the blended A-norm loss with the network on the 4x coarser grid.
     Step: a held-out n^3 realization solved to FP64 relative residual tol by
-    flexible CG with z = D^-1 r + c P net(R r, R ln K).  Plain CG and Jacobi
+    flexible CG with z = D^-1 r + c P^2 net(R^2 r, R^2 ln K).  Plain CG and Jacobi
     PCG on the same system are timed beside it."""
     import torch
     from paper_2408_03452_gb300 import learned, tpfa
     n = a.nx
     t0 = time.perf_counter()
     ds = learned.make_dataset(a.n_real, a.snaps, 64)
-    P, hist = learned.train(ds, epochs=a.epochs, batch=16, lr=1e-3)
+    P, hist = learned.train(ds, epochs=a.epochs, batch=16, lr=1e-3, levels=LEARNED_LEVELS)
     train_s = time.perf_counter() - t0
     n_pairs = len(ds.real)
     del ds
@@ -471,7 +472,7 @@ def run_learned(a, dev, rank, local, barrier):
     ctx = tpfa.Context(n, n, n, device=dev)
     ctx.set_option("fcg_m", LEARNED_FCG_M)
     pr = learned.Problem(ctx, 777001 + a.seed, n, 1.5)
-    nn = n // 2  # the network runs on the 2x coarser grid
+    nn = n >> LEARNED_LEVELS  # the network runs on the 2^levels coarser grid
     net = tpfa.UNet(nn, nn, nn, device=dev)
     net.set_params(P)
     x = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
@@ -524,7 +525,8 @@ def run_learned(a, dev, rank, local, barrier):
             "dtype": "bf16-net/f32-fcg/f64-refine", "data": "synthetic",
             "config": {
                 "workload": (f"learned preconditioner: U-Net trained at 64^3 on {n_pairs} plain-CG "
-                             f"pairs, applied on the 2x coarser grid inside flexible CG (m = {LEARNED_FCG_M}, "
+                             f"pairs, applied on the {2 ** LEARNED_LEVELS}x coarser grid inside flexible CG "
+                             f"(m = {LEARNED_FCG_M}, "
                              f"Jacobi blend) on a held-out {n}^3 lognormal sigma-1.5 "
                              f"realization with Dirichlet x ends, FP64 relative residual "
                              f"{a.tol:g}"),

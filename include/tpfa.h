@@ -398,9 +398,9 @@ int tpfa_anorm_loss_grad(tpfa_ctx* ctx, const float* coef, const float* mr, cons
  * Preconditioner: net == NULL gives the identity (plain CG); otherwise the
  * Jacobi blend z = D^-1 r + c u with the A-norm-optimal weight
  * c = (u'r - (Au)'D^-1 r) / (u'Au) (one extra operator application), where
- * u = net(r, ln K) if net was created for this grid, or u = P net(R r, R ln K)
- * if it was created for the 2x coarser grid (R: mean of each 2x2x2 block,
- * P: nearest prolongation; grid extents even).  When p'Ap <= 0, a value is
+ * u = net(r, ln K) if net was created for this grid, or u = P^l net(R^l r, R^l ln K)
+ * if it was created for the 2^l coarser grid, l = 1, 2 or 3 (R: mean of each
+ * 2x2x2 block, P: nearest prolongation; grid extents divisible by 2^l).  When p'Ap <= 0, a value is
  * not finite, or the smallest r'r of the last 100 iterations is not 1% below
  * the smallest before them, the inner iteration drops the network
  * (TPFA_OPT_FCG_FALLBACK: plain CG by default) and restarts its directions

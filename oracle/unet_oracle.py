@@ -234,11 +234,16 @@ def prolong2(v: np.ndarray) -> np.ndarray:
     return upsample2(v[..., None])[..., 0]
 
 
-def precondition_coarse(p: dict, r: np.ndarray, lnk: np.ndarray) -> np.ndarray:
-    """The network applied on the 2x coarser grid: P net(R r, R ln K), with R
-    the 2x2x2 mean and P the nearest prolongation (homogeneous of degree one
-    in r, like precondition)."""
-    return prolong2(precondition(p, restrict2(r), restrict2(lnk)))
+def precondition_coarse(p: dict, r: np.ndarray, lnk: np.ndarray, levels: int = 1) -> np.ndarray:
+    """The network applied on the 2^levels coarser grid: P^l net(R^l r, R^l ln K),
+    with R the 2x2x2 mean and P the nearest prolongation (homogeneous of
+    degree one in r, like precondition)."""
+    for _ in range(levels):
+        r, lnk = restrict2(r), restrict2(lnk)
+    u = precondition(p, r, lnk)
+    for _ in range(levels):
+        u = prolong2(u)
+    return u
 
 
 # ----------------------------------------------------------------------------

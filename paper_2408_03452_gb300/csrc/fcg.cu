@@ -396,6 +396,7 @@ __global__ void loss_grad_kernel(const float* __restrict__ q, const float* __res
 // breakdown, stagnation); at most this many iterations run past the one that
 // met the tolerance
 constexpr int kCheckEvery = 4;
+constexpr int kMaxLevels = 3;  // the network's grid: up to 8x coarser than the solver's
 
 struct Work {
   cudaStream_t s = nullptr;
@@ -411,13 +412,16 @@ struct Work {
   double* norms = nullptr;   // dev, 2
   double* hnorms = nullptr;  // pinned
   double* pq = nullptr;      // dev, 1
-  // network on the 2x coarser grid: restricted residual, its image, ln K
   Scal* sc = nullptr;        // dev, iteration scalars
   double* hist = nullptr;    // dev, r'r of the iterations since the host last looked
   double* hhist = nullptr;   // pinned copy
-  bool coarse = false;
+  // network on the 2^levels coarser grid: restricted residuals and images per
+  // level (level 0 is the solver's grid: r and z), ln K on the network's grid
+  int levels = 0;
   int dims[3] = {0, 0, 0};
-  float *rc = nullptr, *uc = nullptr, *lnkc = nullptr;
+  float* rl[kMaxLevels + 1] = {};
+  float* ul[kMaxLevels + 1] = {};
+  float* lnkc = nullptr;
   int64_t launches = 0;
 
   bool alloc() {
@@ -452,8 +456,10 @@ struct Work {
     cudaFree(pq);
     cudaFreeHost(hpart);
     cudaFreeHost(hnorms);
-    cudaFree(rc);
-    cudaFree(uc);
+    for (int l = 1; l <= kMaxLevels; ++l) {
+      cudaFree(rl[l]);
+      cudaFree(ul[l]);
+    }
     cudaFree(lnkc);
     cudaFree(sc);
     cudaFree(hist);
@@ -509,12 +515,18 @@ enum PrecMode { kIdentity = 0, kJacobi = 1, kBlend = 2 };
 // the network term u of the blend (into w.z) and A u (into w.au, u'Au into w.uau)
 int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w) {
   int rc;
-  if (w.coarse) {
-    restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.r, w.rc, w.dims[0], w.dims[1], w.dims[2], 1, 0.125f);
-    rc = tpfa_unet_forward(net, w.rc, w.lnkc, w.uc, w.s);
+  if (w.levels > 0) {
+    w.rl[0] = w.r;
+    w.ul[0] = w.z;
+    for (int l = 1; l <= w.levels; ++l)
+      restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.rl[l - 1], w.rl[l], w.dims[0] >> (l - 1),
+                                             w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, 0.125f);
+    rc = tpfa_unet_forward(net, w.rl[w.levels], w.lnkc, w.ul[w.levels], w.s);
     if (rc) return rc;
-    prolong2_kernel<<<w.nb, kT, 0, w.s>>>(w.uc, w.z, w.dims[0], w.dims[1], w.dims[2], 1);
-    w.launches += 17;
+    for (int l = w.levels; l >= 1; --l)
+      prolong2_kernel<<<w.nb, kT, 0, w.s>>>(w.ul[l], w.ul[l - 1], w.dims[0] >> (l - 1),
+                                            w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1);
+    w.launches += 15 + 2 * w.levels;
   } else {
     rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
     if (rc) return rc;
@@ -666,15 +678,18 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     return TPFA_EINVAL;
   int64_t d3[3];
   tpfa::ctx_dims(c, d3);
-  bool coarse = false;
+  // the network's grid: the solver's grid or 2x / 4x / 8x coarser (extents divisible)
+  int levels = -1;
   if (net != nullptr) {
     int d4[4];
     tpfa_unet_shape(net, d4);
-    const bool full = d4[0] == d3[0] && d4[1] == d3[1] && d4[2] == d3[2];
-    coarse = n < 2147483647LL && d3[0] % 2 == 0 && d3[1] % 2 == 0 && d3[2] % 2 == 0 &&
-             d4[0] == d3[0] / 2 &&
-             d4[1] == d3[1] / 2 && d4[2] == d3[2] / 2;
-    if (!(full || coarse) || d4[3] != 1) return TPFA_EINVAL;
+    for (int l = 0; l <= kMaxLevels && levels < 0; ++l) {
+      const int64_t f = 1LL << l;
+      if (d3[0] % f == 0 && d3[1] % f == 0 && d3[2] % f == 0 && d4[0] == d3[0] / f &&
+          d4[1] == d3[1] / f && d4[2] == d3[2] / f && (l == 0 || n < 2147483647LL))
+        levels = l;
+    }
+    if (levels < 0 || d4[3] != 1) return TPFA_EINVAL;
   }
   const double inner_rtol = tpfa::ctx_option(c, TPFA_OPT_INNER_RTOL);
   const int max_outer = (int)tpfa::ctx_option(c, TPFA_OPT_MAX_OUTER);
@@ -688,7 +703,7 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
     w.s = (cudaStream_t)stream;
     w.n = n;
     w.m = (int)tpfa::ctx_option(c, TPFA_OPT_FCG_M);
-    w.coarse = coarse;
+    w.levels = levels > 0 ? levels : 0;
     for (int i = 0; i < 3; ++i) w.dims[i] = (int)d3[i];
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -698,13 +713,23 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
       dinv_kernel<<<w.nb, kT, 0, w.s>>>(reinterpret_cast<const float4*>(coef), w.dinv, n);
       ok = cudaGetLastError() == cudaSuccess;
     }
-    if (ok && coarse) {
-      const size_t nc = (size_t)(n / 8) * 4;
-      ok = cudaMalloc(&w.rc, nc) == cudaSuccess && cudaMalloc(&w.uc, nc) == cudaSuccess &&
-           cudaMalloc(&w.lnkc, nc) == cudaSuccess;
+    if (ok && w.levels > 0) {
+      for (int l = 1; l <= w.levels && ok; ++l) {
+        const size_t bytes = (size_t)(n >> (3 * l)) * 4;
+        ok = cudaMalloc(&w.rl[l], bytes) == cudaSuccess && cudaMalloc(&w.ul[l], bytes) == cudaSuccess;
+      }
+      ok = ok && cudaMalloc(&w.lnkc, (size_t)(n >> (3 * w.levels)) * 4) == cudaSuccess;
       if (ok) {
-        restrict2_kernel<<<w.nb, kT, 0, w.s>>>(lnk, w.lnkc, w.dims[0], w.dims[1], w.dims[2], 1,
-                                               0.125f);
+        // ln K on the network's grid (the mean over each 2^levels block), through the
+        // image buffers of the intermediate levels
+        const float* src = lnk;
+        for (int l = 1; l <= w.levels; ++l) {
+          float* dst = l == w.levels ? w.lnkc : w.ul[l];
+          restrict2_kernel<<<w.nb, kT, 0, w.s>>>(src, dst, w.dims[0] >> (l - 1),
+                                                 w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1,
+                                                 0.125f);
+          src = dst;
+        }
         ok = cudaGetLastError() == cudaSuccess;
       }
     }

@@ -15,7 +15,7 @@ The network output u enters the preconditioner as the Jacobi blend
 z = D^-1 r + c u with the A-norm-optimal weight c (flexible CG in the
 library).  By default the network runs on the 2x coarser grid,
 u = P net(R r, R ln K): Jacobi takes the high frequencies, the network the
-smooth error, at an eighth of the cost.  Loss: the A-norm error of that blend relative to ||e||_A,
+smooth error, at an eighth of the cost (levels = 2: the 4x coarser grid).  Loss: the A-norm error of that blend relative to ||e||_A,
   min_c ||D^-1 r + c u - e||_A^2 / ||e||_A^2 = (w'Aw - (u's)^2 / (u'Au)) / (e'Ae),
 w = e - D^-1 r, s = A w = r - A D^-1 r, per sample, summed over the batch
 (Adam is invariant to a constant factor).  Minimising over the weight makes
@@ -78,7 +78,13 @@ class Dataset:
 
     def finish(self):
         n = self.n
-        self.lnk_c = torch.stack([tpfa.restrict2(p.lnk, (n, n, n, 1)) for p in self.problems])
+        # ln K on the 2x, 4x and 8x coarser grids
+        self.lnk_l = [None]
+        cur = [pr.lnk for pr in self.problems]
+        for l in range(1, 4):
+            m = n >> (l - 1)
+            cur = [tpfa.restrict2(c, (m, m, m, 1)) for c in cur]
+            self.lnk_l.append(torch.stack(cur))
         self.R = torch.stack(self.R)
         self.E = torch.stack(self.E)
         self.S = torch.stack(self.S)
@@ -130,11 +136,26 @@ def make_dataset(n_real=50, snaps=40, n=64, sigma=1.5, seed=1000, tol=1e-10, log
     return ds
 
 
-def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse=True,
-          log=None):
-    """Adam on the blended A-norm loss.  coarse: the network runs on the 2x
-    coarser grid, u = P net(R r, R ln K) (R: 2x2x2 mean, P: nearest
-    prolongation; its gradient is the sum over each cell's 8 children).
+def restrict_to(v, n, batch, levels, scale=0.125):
+    """levels applications of the 2x restriction to batch samples of n^3."""
+    for l in range(levels):
+        m = n >> l
+        v = tpfa.restrict2(v, (m, m, m, batch), scale=scale)
+    return v
+
+
+def prolong_from(v, n, batch, levels):
+    """levels applications of the nearest prolongation, ending on n^3."""
+    for l in range(levels, 0, -1):
+        m = n >> (l - 1)
+        v = tpfa.prolong2(v, (m, m, m, batch))
+    return v
+
+
+def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, levels=1, log=None):
+    """Adam on the blended A-norm loss.  levels: the network runs on the 2^levels
+    coarser grid, u = P^l net(R^l r, R^l ln K) (R: 2x2x2 mean, P: nearest
+    prolongation; the gradient passes back through P^T = 8 R per level).
     Returns (params, history dict)."""
     dev = ds.R.device
     n = ds.n
@@ -145,7 +166,7 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse
     val_real = set(range(nreal - n_val, nreal))
     idx_train = np.array([i for i in range(len(ds.real)) if ds.real[i] not in val_real])
     idx_val = np.array([i for i in range(len(ds.real)) if ds.real[i] in val_real])
-    nn = n // 2 if coarse else n
+    nn = n >> levels
     net = tpfa.UNet(nn, nn, nn, ns=batch, train=True, device=dev)
     P = init_params(seed).to(dev)
     M = torch.zeros_like(P)
@@ -153,19 +174,18 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse
     G = torch.empty(batch * N, dtype=torch.float32, device=dev)
     q = torch.empty(N, dtype=torch.float32, device=dev)
     stats = torch.zeros((batch, 2), dtype=torch.float64, device=dev)
-    hist = {"epoch_loss": [], "val_loss": [], "seconds": [], "coarse": coarse,
+    hist = {"epoch_loss": [], "val_loss": [], "seconds": [], "levels": levels,
             "jacobi_loss": float((ds.wAw / ds.eae).mean().item())}
     t = 0
     t0 = time.perf_counter()
-    shape = (n, n, n, batch)
 
     def batch_loss(idx, backward):
         nonlocal t
         Rb = ds.R[idx].reshape(-1)
         Sb = ds.S[idx].reshape(-1)
-        if coarse:
-            Lb = ds.lnk_c[ds.real[idx]].reshape(-1)
-            Z = tpfa.prolong2(net.forward(tpfa.restrict2(Rb, shape), Lb), shape)
+        if levels > 0:
+            Lb = ds.lnk_l[levels][ds.real[idx]].reshape(-1)
+            Z = prolong_from(net.forward(restrict_to(Rb, n, batch, levels), Lb), n, batch, levels)
         else:
             Lb = ds.lnk[ds.real[idx]].reshape(-1)
             Z = net.forward(Rb, Lb)
@@ -174,7 +194,7 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse
                                 Sb[j * N:(j + 1) * N], ds.eae[s:s + 1], q, G[j * N:(j + 1) * N],
                                 stats[j])
         if backward:
-            grad = net.backward(tpfa.restrict2(G, shape, scale=1.0) if coarse else G)
+            grad = net.backward(restrict_to(G, n, batch, levels, scale=1.0) if levels > 0 else G)
             t += 1
             tpfa.adam_step(P, grad, M, V, t, lr)
         st = stats[:len(idx)]
@@ -203,7 +223,8 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, coarse
     return P, hist
 
 
-def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, coarse=True, log=None):
+def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, levels=1, fcg_m=2,
+             log=None):
     """Plain CG, Jacobi PCG and U-Net FCG on one held-out realization."""
     ctx = tpfa.Context(n, n, n)
     pr = Problem(ctx, seed, n, sigma)
@@ -224,13 +245,14 @@ def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, coarse=Tr
     _, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=maxit)
     rec("jacobi_pcg", info)
     ctx.set_option("precond", 0)
-    nn = n // 2 if coarse else n
+    nn = n >> levels
     net = tpfa.UNet(nn, nn, nn, device=ctx.device)
     net.set_params(P.to(ctx.device))
+    ctx.set_option("fcg_m", fcg_m)
     _, info = ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, tol=tol, maxit=maxit)
     rec("unet_fcg", info)
     out["unet_apply_ms"] = apply_bench(nn, 10)["apply_ms"]
-    out["coarse"] = coarse
+    out["levels"] = levels
     return out
 
 
@@ -265,8 +287,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-n", type=int, default=256)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
-    ap.add_argument("--full", action="store_true",
-                    help="run the network on the full grid instead of the 2x coarser one")
+    ap.add_argument("--levels", type=int, default=1,
+                    help="the network runs on the 2^levels coarser grid (0 to 3)")
     ap.add_argument("--apply-bench", type=int, default=0,
                     help="only time preconditioner applications on an N^3 grid")
     ap.add_argument("--reps", type=int, default=10)
@@ -276,10 +298,10 @@ def main(argv=None):
         print(json.dumps(apply_bench(a.apply_bench, a.reps)))
         return
     ds = make_dataset(a.n_real, a.snaps, a.n, log=log)
-    P, hist = train(ds, a.epochs, a.batch, a.lr, coarse=not a.full, log=log)
+    P, hist = train(ds, a.epochs, a.batch, a.lr, levels=a.levels, log=log)
     if a.save:
         np.save(a.save, P.cpu().numpy())
-    res = evaluate(P, n=a.eval_n, coarse=not a.full, log=log)
+    res = evaluate(P, n=a.eval_n, levels=a.levels, log=log)
     res["train"] = hist
     print(json.dumps(res))
 

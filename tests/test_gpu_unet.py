@@ -277,16 +277,17 @@ def test_restrict_prolong_match_oracle(tp):
                           .astype(np.float32))
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (16, 24, 40)])
-def test_fcg_with_coarse_unet_converges(tp, oracle_mod, shape):
-    """A network created for the 2x coarser grid is applied as P net(R r, R ln K)
-    inside the blend; the solve reaches the FP64 tolerance."""
+@pytest.mark.parametrize("shape,f", [((32, 32, 32), 2), ((16, 24, 40), 2), ((32, 16, 48), 4)])
+def test_fcg_with_coarse_unet_converges(tp, oracle_mod, shape, f):
+    """A network created for the f-times coarser grid is applied as
+    P^l net(R^l r, R^l ln K) inside the blend; the solve reaches the FP64
+    tolerance."""
     O = oracle_mod
     K, mask, pD = _problem(shape, seed=5, sigma=1.5)
     ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
     _, flat = params_case(9)
     dev = torch.device("cuda")
-    net = tp.UNet(*(d // 2 for d in shape))
+    net = tp.UNet(*(d // f for d in shape))
     net.set_params(torch.from_numpy(flat).to(dev))
     lnk = torch.from_numpy(np.log(K).astype(np.float32)).to(dev)
     x, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, tol=1e-8, maxit=20000)
