@@ -13,9 +13,9 @@ satisfies A e_k = r_k -- the residuals plain CG itself generates (k = 0 gives
 
 The network output u enters the preconditioner as the Jacobi blend
 z = D^-1 r + c u with the A-norm-optimal weight c (flexible CG in the
-library).  By default the network runs on the 2x coarser grid,
-u = P net(R r, R ln K): Jacobi takes the high frequencies, the network the
-smooth error, at an eighth of the cost (levels = 2: the 4x coarser grid).  Loss: the A-norm error of that blend relative to ||e||_A,
+library).  By default the network runs on the 4x coarser grid,
+u = P^2 net(R^2 r, R^2 ln K) (levels = 2): Jacobi takes the high frequencies,
+the network the smooth error CG is slow on, at 1/64 of the full-grid cost.  Loss: the A-norm error of that blend relative to ||e||_A,
   min_c ||D^-1 r + c u - e||_A^2 / ||e||_A^2 = (w'Aw - (u's)^2 / (u'Au)) / (e'Ae),
 w = e - D^-1 r, s = A w = r - A D^-1 r, per sample, summed over the batch
 (Adam is invariant to a constant factor).  Minimising over the weight makes
@@ -152,7 +152,7 @@ def prolong_from(v, n, batch, levels):
     return v
 
 
-def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, levels=1, log=None):
+def train(ds: Dataset, epochs=12, batch=16, lr=1e-3, seed=0, holdout=0.1, levels=2, log=None):
     """Adam on the blended A-norm loss.  levels: the network runs on the 2^levels
     coarser grid, u = P^l net(R^l r, R^l ln K) (R: 2x2x2 mean, P: nearest
     prolongation; the gradient passes back through P^T = 8 R per level).
@@ -223,7 +223,7 @@ def train(ds: Dataset, epochs=20, batch=16, lr=1e-3, seed=0, holdout=0.1, levels
     return P, hist
 
 
-def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, levels=1, fcg_m=2,
+def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, levels=2, fcg_m=2,
              log=None):
     """Plain CG, Jacobi PCG and U-Net FCG on one held-out realization."""
     ctx = tpfa.Context(n, n, n)
@@ -282,12 +282,12 @@ def main(argv=None):
     ap.add_argument("--n-real", type=int, default=50)
     ap.add_argument("--snaps", type=int, default=40)
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-n", type=int, default=256)
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
-    ap.add_argument("--levels", type=int, default=1,
+    ap.add_argument("--levels", type=int, default=2,
                     help="the network runs on the 2^levels coarser grid (0 to 3)")
     ap.add_argument("--apply-bench", type=int, default=0,
                     help="only time preconditioner applications on an N^3 grid")

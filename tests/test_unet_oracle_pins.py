@@ -201,6 +201,14 @@ def test_precondition_coarse_homogeneous_and_smooth():
                                atol=1e-14)
     # constant on every 2x2x2 block
     assert np.all(m1[:, 0::2, 0::2, 0::2] == m1[:, 1::2, 1::2, 1::2])
+    # two levels: constant on 4x4x4 blocks, equal to one level applied to R r
+    r2 = rng.standard_normal((1, 16, 16, 16))
+    l2 = rng.standard_normal((1, 16, 16, 16))
+    m2 = U.precondition_coarse(p, r2, l2, levels=2)
+    assert np.all(m2[:, 0::4, 0::4, 0::4] == m2[:, 3::4, 3::4, 3::4])
+    np.testing.assert_allclose(
+        m2, U.prolong2(U.precondition_coarse(p, U.restrict2(r2), U.restrict2(l2), levels=1)),
+        rtol=1e-13, atol=1e-15)
 
 
 def _tpfa_problem(oracle_mod, nx=6, ny=5, nz=4, seed=3):
