@@ -511,6 +511,23 @@ def run_learned(a, dev, rank, local, barrier):
     plain = cg(0)
     cg(1)
     jac = cg(1)
+    # further held-out realizations (untimed by the step clock): learned vs Jacobi
+    others = []
+    for k in range(1, 4):
+        pk = learned.Problem(ctx, 777001 + a.seed + 1000 * k, n, 1.5)
+        x.zero_()
+        _, fi = ctx.fcg_solve(pk.coef, pk.coef64, pk.b, net=net, lnk=pk.lnk, x=x, tol=a.tol,
+                              maxit=a.maxit)
+        ctx.set_option("precond", 1)
+        x.zero_()
+        _, ji = ctx.cg_solve(pk.coef, pk.coef64, pk.b, x=x, tol=a.tol, maxit=a.maxit)
+        ctx.set_option("precond", 0)
+        others.append({"seed": 777001 + a.seed + 1000 * k,
+                       "unet_fcg": {"iters": fi["iters"], "s": fi["total_ms"] / 1e3,
+                                    "rel_res_fp64": fi["rel_res_fp64"], "code": fi["code"],
+                                    "fell_back": fi["fell_back"]},
+                       "jacobi_pcg": {"iters": ji["iters"], "s": ji["total_ms"] / 1e3}})
+        del pk
     apply = learned.apply_bench(nn, 10)
     conv_ms = time_conv(tpfa, dev, nn, 16, 16)
     if rank == 0:
@@ -538,6 +555,7 @@ def run_learned(a, dev, rank, local, barrier):
                                  "plain_cg": plain["rel_res_fp64"],
                                  "jacobi_pcg": jac["rel_res_fp64"]},
                 "fell_back": infos[-1]["fell_back"],
+                "other_realizations": others,
                 "unet_apply_ms": apply["apply_ms"], "unet_grid": [nn, nn, nn],
                 "unet_flop_per_cell": UNET_FLOP_PER_CELL,
                 "training": {"pairs": n_pairs, "epochs": a.epochs, "steps": hist["steps"],
