@@ -42,6 +42,9 @@ UNIT = "cell-updates/s"
 # algorithmic DRAM bytes per cell of one fused CG sweep: read r, p, q, x and
 # the 16-byte coefficient record, write r, p, q, x (FP32)
 SWEEP_BYTES_PER_CELL = 48
+# algorithmic DRAM bytes per cell of one operator application: read p and the
+# 16-byte coefficient record, write A p
+APPLY_BYTES_PER_CELL = 24
 FALLBACK_HBM_GBS = 6800.0
 LEARNED_METRIC = "U-Net FCG cell-iterations/s"
 LEARNED_FCG_M = 2  # retained directions of flexible CG in the learned workload
@@ -207,10 +210,16 @@ def oracle_fcg_step(iters, params=None):
 
 
 def oracle_sample_iters(O, target_s=12.0, workload="paper"):
+    """Iterations that make one oracle step last about target_s: the per-iteration
+    cost is the slope between a 5- and a 15-iteration run (setup excluded)."""
     t = time.perf_counter()
     oracle_step(O, 5, workload)
-    per = (time.perf_counter() - t) / 5
-    return max(5, int(target_s / per))
+    t5 = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle_step(O, 15, workload)
+    t15 = time.perf_counter() - t
+    per = max((t15 - t5) / 10, 1e-6)
+    return max(5, int((target_s - t5) / per) + 5)
 
 
 def sample_desc(workload):
@@ -530,9 +539,24 @@ def run_learned(a, dev, rank, local, barrier):
         del pk
     apply = learned.apply_bench(nn, 10)
     conv_ms = time_conv(tpfa, dev, nn, 16, 16)
+    # the operator application: two per FCG iteration, the largest kernel time
+    pv = torch.rand(n ** 3, dtype=torch.float32, device=dev)
+    av = torch.empty_like(pv)
+    for _ in range(3):
+        ctx.apply(pr.coef, pv, av)
+    stream = torch.cuda.current_stream(dev)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(10):
+        ctx.apply(pr.coef, pv, av)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e2.elapsed_time(e3) / 10
     if rank == 0:
         cells = n ** 3
         tpeak, tkind = measured_tensor_peak()
+        hpeak, hkind = measured_hbm_peak()
         flop = 2 * 27 * 16 * 16 * nn ** 3
         achieved = flop / (conv_ms / 1e3) / 1e12
         out = {
@@ -563,11 +587,19 @@ def run_learned(a, dev, rank, local, barrier):
                              "final_val_loss": hist["val_loss"][-1],
                              "jacobi_loss": hist["jacobi_loss"]},
                 "l2": "inputs larger than L2 (no flush needed)"},
-            "roofline": {"kernel": f"tensor-core 3x3x3 convolution 16->16 on the network's "
-                                   f"finest level ({nn}^3)",
-                         "bound": "tensor", "achieved": achieved, "peak": tpeak,
-                         "unit": "TFLOP/s", "frac": achieved / tpeak, "peak_source": tkind,
-                         "flop_per_launch": flop, "launch_ms": conv_ms, "traffic": None},
+            "roofline": {"kernel": "operator application A p (tpfa_apply, two per FCG "
+                                   "iteration)", "bound": "hbm",
+                         "achieved": APPLY_BYTES_PER_CELL * cells / (apply_ms / 1e3) / 1e9,
+                         "peak": hpeak, "unit": "GB/s",
+                         "frac": APPLY_BYTES_PER_CELL * cells / (apply_ms / 1e3) / 1e9 / hpeak,
+                         "peak_source": hkind, "bytes_per_cell": APPLY_BYTES_PER_CELL,
+                         "launch_ms": apply_ms, "traffic": None},
+            "roofline_network": {"kernel": f"tensor-core 3x3x3 convolution 16->16 on the "
+                                           f"network's finest level ({nn}^3)",
+                                 "bound": "tensor", "achieved": achieved, "peak": tpeak,
+                                 "unit": "TFLOP/s", "frac": achieved / tpeak,
+                                 "peak_source": tkind, "flop_per_launch": flop,
+                                 "launch_ms": conv_ms},
             "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
             "clocks": clk,
         }
