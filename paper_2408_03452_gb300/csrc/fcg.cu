@@ -127,25 +127,54 @@ __global__ void dots_kernel(const float* __restrict__ r, const float* __restrict
                             const float* __restrict__ u, const float* __restrict__ au, Dirs qd,
                             int jac, int net, int64_t n, double* part) {
   // FP32 sums per thread (about a hundred terms each), FP64 across threads
-  // and blocks: FP64 arithmetic per element would cost more than the memory
+  // and blocks: FP64 arithmetic per element would cost more than the memory.
+  // Four elements per step (float4), a scalar tail for n % 4.
   constexpr int K = 2 + 2 * M;
   float s[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) s[j] = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    const float ri = r[i];
-    const float wi = jac ? ri * dinv[i] : ri;
-    const float ui = net ? u[i] : 0.f;
+  auto one = [&](float ri, float di, float ui, float aui, const float* qv) {
+    const float wi = jac ? ri * di : ri;
     if (net) {
       s[0] = fmaf(ui, ri, s[0]);
-      s[1] = fmaf(au[i], wi, s[1]);
+      s[1] = fmaf(aui, wi, s[1]);
     }
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-      const float qj = qd.v[j][i];
-      s[2 + j] = fmaf(wi, qj, s[2 + j]);
-      s[2 + M + j] = fmaf(ui, qj, s[2 + M + j]);
+      s[2 + j] = fmaf(wi, qv[j], s[2 + j]);
+      s[2 + M + j] = fmaf(ui, qv[j], s[2 + M + j]);
     }
+  };
+  const int64_t n4 = n / 4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kT) {
+    const float4 r4 = reinterpret_cast<const float4*>(r)[i];
+    const float4 d4 = jac ? reinterpret_cast<const float4*>(dinv)[i] : z4;
+    const float4 u4 = net ? reinterpret_cast<const float4*>(u)[i] : z4;
+    const float4 a4 = net ? reinterpret_cast<const float4*>(au)[i] : z4;
+    float4 q4[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) q4[j] = reinterpret_cast<const float4*>(qd.v[j])[i];
+    float qv[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) qv[j] = q4[j].x;
+    one(r4.x, d4.x, u4.x, a4.x, qv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) qv[j] = q4[j].y;
+    one(r4.y, d4.y, u4.y, a4.y, qv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) qv[j] = q4[j].z;
+    one(r4.z, d4.z, u4.z, a4.z, qv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) qv[j] = q4[j].w;
+    one(r4.w, d4.w, u4.w, a4.w, qv);
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * kT + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kT) {
+    float qv[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) qv[j] = qd.v[j][i];
+    one(r[i], jac ? dinv[i] : 0.f, net ? u[i] : 0.f, net ? au[i] : 0.f, qv);
   }
   double d[K];
 #pragma unroll
@@ -188,7 +217,7 @@ __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int 
   }
 }
 
-// p = w + c u + sum_j beta_j p_j; partial p'r
+// p = w + c u + sum_j beta_j p_j; partial p'r (four elements per step)
 template <int M>
 __global__ void dir_kernel(const float* __restrict__ r, const float* __restrict__ dinv,
                            const float* __restrict__ u, Dirs pd, const Scal* __restrict__ sc,
@@ -199,14 +228,45 @@ __global__ void dir_kernel(const float* __restrict__ r, const float* __restrict_
 #pragma unroll
   for (int j = 0; j < M; ++j) beta[j] = (float)sc->beta[j];
   float prf = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
-    const float ri = r[i];
-    float v = jac ? ri * dinv[i] : ri;
-    if (net) v = fmaf(c, u[i], v);
+  auto one = [&](float ri, float di, float ui, const float* pv) {
+    float v = jac ? ri * di : ri;
+    if (net) v = fmaf(c, ui, v);
 #pragma unroll
-    for (int j = 0; j < M; ++j) v = fmaf(beta[j], pd.v[j][i], v);
-    p[i] = v;
+    for (int j = 0; j < M; ++j) v = fmaf(beta[j], pv[j], v);
     prf = fmaf(v, ri, prf);
+    return v;
+  };
+  const int64_t n4 = n / 4;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kT) {
+    const float4 r4 = reinterpret_cast<const float4*>(r)[i];
+    const float4 d4 = jac ? reinterpret_cast<const float4*>(dinv)[i] : z4;
+    const float4 u4 = net ? reinterpret_cast<const float4*>(u)[i] : z4;
+    float4 p4[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) p4[j] = reinterpret_cast<const float4*>(pd.v[j])[i];
+    float pv[M > 0 ? M : 1];
+    float4 o;
+#pragma unroll
+    for (int j = 0; j < M; ++j) pv[j] = p4[j].x;
+    o.x = one(r4.x, d4.x, u4.x, pv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) pv[j] = p4[j].y;
+    o.y = one(r4.y, d4.y, u4.y, pv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) pv[j] = p4[j].z;
+    o.z = one(r4.z, d4.z, u4.z, pv);
+#pragma unroll
+    for (int j = 0; j < M; ++j) pv[j] = p4[j].w;
+    o.w = one(r4.w, d4.w, u4.w, pv);
+    reinterpret_cast<float4*>(p)[i] = o;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * kT + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kT) {
+    float pv[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) pv[j] = pd.v[j][i];
+    p[i] = one(r[i], jac ? dinv[i] : 0.f, net ? u[i] : 0.f, pv);
   }
   double pr[1] = {prf};
   block_sum_m<1>(pr, part);
@@ -245,13 +305,35 @@ __global__ void finish_alpha_kernel(const double* __restrict__ part, int nb,
   }
 }
 
-// e += alpha p; r -= alpha q; partial r'r
+// e += alpha p; r -= alpha q; partial r'r (four elements per step)
 __global__ void update_kernel(float* __restrict__ e, float* __restrict__ r,
                               const float* __restrict__ p, const float* __restrict__ q,
                               const Scal* __restrict__ sc, int64_t n, double* part) {
   const float alpha = (float)sc->alpha;
   float rrf = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT) {
+  const int64_t n4 = n / 4;
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kT) {
+    float4 e4 = reinterpret_cast<float4*>(e)[i];
+    float4 r4 = reinterpret_cast<float4*>(r)[i];
+    const float4 p4 = reinterpret_cast<const float4*>(p)[i];
+    const float4 q4 = reinterpret_cast<const float4*>(q)[i];
+    e4.x = fmaf(alpha, p4.x, e4.x);
+    e4.y = fmaf(alpha, p4.y, e4.y);
+    e4.z = fmaf(alpha, p4.z, e4.z);
+    e4.w = fmaf(alpha, p4.w, e4.w);
+    r4.x = fmaf(-alpha, q4.x, r4.x);
+    r4.y = fmaf(-alpha, q4.y, r4.y);
+    r4.z = fmaf(-alpha, q4.z, r4.z);
+    r4.w = fmaf(-alpha, q4.w, r4.w);
+    reinterpret_cast<float4*>(e)[i] = e4;
+    reinterpret_cast<float4*>(r)[i] = r4;
+    rrf = fmaf(r4.x, r4.x, rrf);
+    rrf = fmaf(r4.y, r4.y, rrf);
+    rrf = fmaf(r4.z, r4.z, rrf);
+    rrf = fmaf(r4.w, r4.w, rrf);
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * kT + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kT) {
     e[i] = fmaf(alpha, p[i], e[i]);
     const float v = fmaf(-alpha, q[i], r[i]);
     r[i] = v;
@@ -424,10 +506,14 @@ struct Work {
   float* lnkc = nullptr;
   int64_t launches = 0;
 
+  // distance between retained directions: n rounded up to 4 floats, so that
+  // every slot starts on a 16-byte boundary (the vector kernels read float4)
+  int64_t slot_stride() const { return (n + 3) / 4 * 4; }
+
   bool alloc() {
     return cudaMalloc(&r, n * 4) == cudaSuccess && cudaMalloc(&z, n * 4) == cudaSuccess &&
-           cudaMalloc(&P, (size_t)m * n * 4) == cudaSuccess &&
-           cudaMalloc(&Q, (size_t)m * n * 4) == cudaSuccess &&
+           cudaMalloc(&P, (size_t)m * slot_stride() * 4) == cudaSuccess &&
+           cudaMalloc(&Q, (size_t)m * slot_stride() * 4) == cudaSuccess &&
            cudaMalloc(&e, n * 4) == cudaSuccess && cudaMalloc(&r64, n * 8) == cudaSuccess &&
            cudaMalloc(&au, n * 4) == cudaSuccess && cudaMalloc(&uau, 8) == cudaSuccess &&
            cudaMalloc(&dinv, n * 4) == cudaSuccess &&
@@ -560,8 +646,8 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
     Dirs qd, pd;
     for (int j = 0; j < stored; ++j) {
       const size_t slot = (size_t)((head - 1 - j + m) % m);
-      qd.v[j] = w.Q + slot * w.n;
-      pd.v[j] = w.P + slot * w.n;
+      qd.v[j] = w.Q + slot * w.slot_stride();
+      pd.v[j] = w.P + slot * w.slot_stride();
     }
     if (stored > 0 || with_net) {
       launch_dots(stored, w.nb, w.s, w.r, w.dinv, w.z, w.au, qd, jac, with_net, w.n, w.part);
@@ -569,8 +655,8 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
     } else {
       finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, 0, 0, 0, w.uau, w.sc, head, m);
     }
-    float* p = w.P + (size_t)head * w.n;
-    float* q = w.Q + (size_t)head * w.n;
+    float* p = w.P + (size_t)head * w.slot_stride();
+    float* q = w.Q + (size_t)head * w.slot_stride();
     launch_dir(stored, w.nb, w.s, w.r, w.dinv, w.z, pd, w.sc, jac, with_net, p, w.n, w.part);
     int rc = tpfa_apply(c, coef, p, q, w.pq, w.s);
     if (rc) return rc;

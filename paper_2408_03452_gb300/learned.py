@@ -276,6 +276,24 @@ def apply_bench(n: int, reps: int = 10, seed: int = 0) -> dict:
     return {"grid": n, "reps": reps, "apply_ms": e0.elapsed_time(e1) / reps}
 
 
+def fcg_bench(n: int, levels: int = 2, iters: int = 12, seed: int = 0) -> dict:
+    """Two flexible-CG solves capped at `iters` iterations (initial weights; the
+    cost of an iteration does not depend on them): a profiling target."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = tpfa.Context(n, n, n, device=dev)
+    ctx.set_option("fcg_m", 2)
+    pr = Problem(ctx, 777001 + seed, n, 1.5)
+    nn = n >> levels
+    net = tpfa.UNet(nn, nn, nn, device=dev)
+    net.set_params(init_params(seed).to(dev))
+    info = None
+    for _ in range(2):
+        _, info = ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, tol=1e-12,
+                                maxit=iters, check=False)
+    return {"grid": n, "levels": levels, "iters": info["iters"],
+            "ms_per_iter": info["inner_ms"] / max(info["iters"], 1)}
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="train and evaluate the U-Net preconditioner")
@@ -291,11 +309,18 @@ def main(argv=None):
                     help="the network runs on the 2^levels coarser grid (0 to 3)")
     ap.add_argument("--apply-bench", type=int, default=0,
                     help="only time preconditioner applications on an N^3 grid")
+    ap.add_argument("--fcg-bench", type=int, default=0,
+                    help="only run two flexible-CG solves capped at --iters iterations on an "
+                         "N^3 problem with the network on the 2^levels coarser grid")
+    ap.add_argument("--iters", type=int, default=12)
     ap.add_argument("--reps", type=int, default=10)
     a = ap.parse_args(argv)
     log = lambda m: print(m, flush=True)  # noqa: E731
     if a.apply_bench:
         print(json.dumps(apply_bench(a.apply_bench, a.reps)))
+        return
+    if a.fcg_bench:
+        print(json.dumps(fcg_bench(a.fcg_bench, a.levels, a.iters)))
         return
     ds = make_dataset(a.n_real, a.snaps, a.n, log=log)
     P, hist = train(ds, a.epochs, a.batch, a.lr, levels=a.levels, log=log)

@@ -277,6 +277,20 @@ def test_restrict_prolong_match_oracle(tp):
                           .astype(np.float32))
 
 
+@pytest.mark.parametrize("shape", [(13, 11, 7), (9, 5, 3)])
+def test_fcg_ragged_sizes(tp, oracle_mod, shape):
+    """Cell counts that are not a multiple of 4 (vector kernels' scalar tail,
+    padded direction slots), with and without Jacobi fallback settings."""
+    O = oracle_mod
+    K, mask, pD = _problem(shape, seed=7)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    for m in (1, 3):
+        ctx.set_option("fcg_m", m)
+        x, info = ctx.fcg_solve(coef, coef64, b, tol=1e-10, maxit=5000)
+        assert info["code"] == tp.OK
+        assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-10 * 1.01
+
+
 @pytest.mark.parametrize("shape,f", [((32, 32, 32), 2), ((16, 24, 40), 2), ((32, 16, 48), 4)])
 def test_fcg_with_coarse_unet_converges(tp, oracle_mod, shape, f):
     """A network created for the f-times coarser grid is applied as
