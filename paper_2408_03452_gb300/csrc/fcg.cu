@@ -563,29 +563,6 @@ struct Work {
       for (int k = 0; k < 3; ++k) out3[k] += hpart[3 * b + k];
     return true;
   }
-  // k per-block partials ([block][k], or the 3-slot layout when k3) and one
-  // device scalar, with a single synchronisation
-  bool fetch_with_scalar(int k, bool k3, double* out, const double* dev, double* sc) {
-    const int per = k3 ? 3 : k;
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(hpart, part, sizeof(double) * per * nb, cudaMemcpyDeviceToHost, s) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(hnorms, dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return false;
-    for (int j = 0; j < k; ++j) out[j] = 0.0;
-    for (int b = 0; b < nb; ++b)
-      for (int j = 0; j < k; ++j) out[j] += hpart[(size_t)b * per + j];
-    *sc = hnorms[0];
-    return true;
-  }
-  bool fetch_scalar(const double* dev, double* out) {
-    if (cudaMemcpyAsync(hnorms, dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return false;
-    *out = hnorms[0];
-    return true;
-  }
 };
 
 struct Result {
