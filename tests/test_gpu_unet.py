@@ -309,6 +309,29 @@ def test_fcg_with_coarse_unet_converges(tp, oracle_mod, shape, f):
     assert _oracle_rel_residual(O, shape, K, mask, pD, x.cpu().numpy()) <= 1e-8 * 1.01
 
 
+def test_fcg_iteration_cap_zero_rhs_and_status(tp):
+    """The inner iteration stops exactly at maxit (TPFA_NOTCONV, checked
+    between the host's looks as well); a zero right-hand side converges with
+    no iteration; the returned x is always finite."""
+    shape = (24, 16, 16)
+    K, mask, pD = _problem(shape, seed=8)
+    ctx, coef, coef64, b = _gpu_problem(tp, shape, K, mask, pD)
+    for cap in (1, 6, 9):
+        x, info = ctx.fcg_solve(coef, coef64, b, tol=1e-12, maxit=cap, check=False)
+        assert info["code"] == tp.NOTCONV and info["iters"] == cap
+        assert torch.isfinite(x).all()
+    z = torch.zeros_like(b)
+    x, info = ctx.fcg_solve(coef, coef64, z, tol=1e-8)
+    assert info["code"] == tp.OK and info["iters"] == 0 and float(x.abs().max()) == 0.0
+    # with a network on the 2x coarser grid the cap holds too
+    _, flat = params_case(2)
+    net = tp.UNet(12, 8, 8)
+    net.set_params(torch.from_numpy(flat).cuda())
+    lnk = torch.from_numpy(np.log(K).astype(np.float32)).cuda()
+    _, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, tol=1e-12, maxit=7, check=False)
+    assert info["code"] == tp.NOTCONV and info["iters"] == 7
+
+
 def test_fcg_rejects_mismatched_network(tp):
     shape = (16, 16, 16)
     K, mask, pD = _problem(shape)
