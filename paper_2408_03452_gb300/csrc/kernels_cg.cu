@@ -464,8 +464,10 @@ Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms) {
   int zc = zc_opt;
   if (zc <= 0) {
     // longest run (at most 128 planes; each run re-reads two halo planes)
-    // that still gives about four waves of eight resident warps per SM
-    const int64_t target = (int64_t)num_sms * 8 * 4;
+    // that still gives about four warps per SM: on 128^3 and 256^3 grids the
+    // sweep is 20% faster with these runs (32 and 128 planes) than with the
+    // shorter ones that would give several waves of resident warps
+    const int64_t target = (int64_t)num_sms * 4;
     const int64_t cols = s.nwx * s.nwy;
     zc = 128;
     while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc /= 2;
