@@ -537,6 +537,9 @@ def run_learned(a, dev, rank, local, barrier):
                                     "fell_back": fi["fell_back"]},
                        "jacobi_pcg": {"iters": ji["iters"], "s": ji["total_ms"] / 1e3}})
         del pk
+    # the batched form: the uneven 96-instance ensemble with the same network
+    ensemble = learned.evaluate_ensemble(P, seed=a.seed, levels=LEARNED_LEVELS,
+                                         fcg_m=LEARNED_FCG_M, tol=a.tol)
     apply = learned.apply_bench(nn, 10)
     conv_ms = time_conv(tpfa, dev, nn, 16, 16)
     # the operator application: two per FCG iteration, the largest kernel time
@@ -580,6 +583,7 @@ def run_learned(a, dev, rank, local, barrier):
                                  "jacobi_pcg": jac["rel_res_fp64"]},
                 "fell_back": infos[-1]["fell_back"],
                 "other_realizations": others,
+                "ensemble": ensemble,
                 "unet_apply_ms": apply["apply_ms"], "unet_grid": [nn, nn, nn],
                 "unet_flop_per_cell": UNET_FLOP_PER_CELL,
                 "training": {"pairs": n_pairs, "epochs": a.epochs, "steps": hist["steps"],

@@ -266,7 +266,8 @@ int tpfa_batch_destroy(tpfa_batch* batch);
 int tpfa_batch_offsets(const tpfa_batch* batch, int64_t* offsets);
 /* zc: host, n_inst entries: the z-run length each instance uses. */
 int tpfa_batch_zc(const tpfa_batch* batch, int* zc);
-/* TPFA_OPT_INNER_RTOL, TPFA_OPT_MAX_OUTER, TPFA_OPT_PRECOND. */
+/* TPFA_OPT_INNER_RTOL, TPFA_OPT_MAX_OUTER, TPFA_OPT_PRECOND; for fcg_solve_batch
+ * also TPFA_OPT_FCG_M and TPFA_OPT_FCG_FALLBACK. */
 int tpfa_batch_set_option(tpfa_batch* batch, int option, double value);
 /* As tpfa_build_trans / tpfa_build_rhs over the concatenated arrays. */
 int tpfa_batch_build_trans(tpfa_batch* batch, const double* K, const uint8_t* dirichlet,
@@ -429,6 +430,38 @@ int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, int nz, int 
 int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* coef64,
               const float* lnk, const double* b, double* x, double tol, int64_t maxit,
               tpfa_cg_info* info, int* fell_back, void* stream);
+
+/* fcg_solve over the instances of a batch (the learned-preconditioned,
+ * mixed-precision, batched form): every instance is refined and iterated as
+ * fcg_solve would do it alone, with its own tolerance target, iteration
+ * limit, preconditioner mode, fallback and convergence flag, but each FCG
+ * step is one launch per vector pass over all instances that still iterate
+ * (per-instance partial sums in a fixed order, so an instance's iterates do
+ * not depend on the others), and the batched operator application skips
+ * finished instances.  The inner solve of an instance stops as soon as its
+ * r'r meets its target (not only at the host's periodic look).
+ *   nets: host array of n_nets U-Net handles (n_nets = 0: no network; nets
+ *         and net_of may then be NULL).  Network k serves the instances i
+ *         with net_of[i] == k, which must all have the same grid; its sample
+ *         count ns is their number and its grid that grid or the 2x / 4x /
+ *         8x coarser one (extents divisible; sample j = the j-th of those
+ *         instances in index order).  net_of[i] = -1: no network for
+ *         instance i (TPFA_OPT_FCG_FALLBACK's preconditioner from the start).
+ *   lnk:  dev FP32 ln K over the concatenated cells (8-byte aligned when a
+ *         network runs on a coarser grid; ignored without networks).
+ *   coef, coef64, b, x: as cg_solve_batch.  Options of the batch:
+ *   TPFA_OPT_INNER_RTOL, TPFA_OPT_MAX_OUTER, TPFA_OPT_FCG_M (default 4),
+ *   TPFA_OPT_FCG_FALLBACK.  A network instance's cells must start at an even
+ *   offset when it runs on a coarser grid.
+ *   infos / total: as cg_solve_batch (rel_res_inner is NaN).  fell_back:
+ *   host, n_inst ints (1 where the instance dropped its network), or NULL.
+ * Calls on one batch must not overlap (they share its workspaces).  Waits for
+ * the stream.  Returns as cg_solve_batch, or TPFA_EINTERNAL when a
+ * tensor-core wait of a network gave up. */
+int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_nets, const int* net_of,
+                    const float* coef, const double* coef64, const float* lnk, const double* b,
+                    double* x, double tol, int64_t maxit, tpfa_cg_info* infos,
+                    tpfa_cg_info* total, int* fell_back, void* stream);
 
 /*
  * tpfa_apply_noalloc -- tpfa_apply for callers that cannot allocate device

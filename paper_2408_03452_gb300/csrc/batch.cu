@@ -13,38 +13,10 @@
 #include <new>
 #include <vector>
 
-#include "tpfa_internal.cuh"
+#include "batch_internal.cuh"
 
 using namespace tpfa;
 
-struct tpfa_batch {
-  int ninst;
-  int device;
-  int num_sms;
-  std::vector<tpfa_grid> geo;
-  std::vector<Grid> g;
-  std::vector<int64_t> off;  // ninst + 1
-  std::vector<BatchInst> inst;
-  int64_t cells;
-  int64_t sweep_blocks;
-  double inner_rtol;
-  int max_outer;
-  int precond;
-  BatchInst* inst_dev;
-  CgState* st;
-  CgState* host_st;
-  double* partials;
-  unsigned int* counters;  // ninst for the sweep + 1 for the per-instance helper kernels
-  long long* sweeps;
-  float* vec;
-  double* r64;
-  CgVecs v;
-  cudaGraphExec_t loop_exec;
-  const void* loop_key_coef;
-  int loop_key_precond;
-  cudaStream_t cap_stream;
-  cudaEvent_t ev[4];
-};
 
 namespace {
 
@@ -143,6 +115,8 @@ int tpfa_batch_create(const tpfa_grid* grids, int n_inst, const int* zc, tpfa_ba
   b->inner_rtol = 1e-6;
   b->max_outer = 20;
   b->precond = 0;
+  b->fcg_m = 4;
+  b->fcg_fallback = 0;
   int rc = TPFA_ECUDA;
   size_t pcap = 0;
   int64_t maxelem = 1;
@@ -276,6 +250,14 @@ int tpfa_batch_set_option(tpfa_batch* b, int option, double value) {
     case TPFA_OPT_PRECOND:
       if (value != 0 && value != 1) return TPFA_EINVAL;
       b->precond = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_FCG_M:
+      if (value != (int)value || value < 1 || value > 16) return TPFA_EINVAL;
+      b->fcg_m = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_FCG_FALLBACK:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      b->fcg_fallback = (int)value;
       return TPFA_OK;
     default:
       return TPFA_EINVAL;

@@ -1,0 +1,39 @@
+// The batch object shared by the batched solvers (batch.cu: plain and
+// Jacobi CG sweeps; fcg.cu: flexible CG with the learned preconditioner).
+#pragma once
+
+#include <vector>
+
+#include "tpfa_internal.cuh"
+
+struct tpfa_batch {
+  int ninst;
+  int device;
+  int num_sms;
+  std::vector<tpfa_grid> geo;
+  std::vector<tpfa::Grid> g;
+  std::vector<int64_t> off;  // ninst + 1
+  std::vector<tpfa::BatchInst> inst;
+  int64_t cells;
+  int64_t sweep_blocks;
+  double inner_rtol;
+  int max_outer;
+  int precond;
+  int fcg_m;         // fcg_solve_batch: retained directions
+  int fcg_fallback;  // fcg_solve_batch: 0 = plain CG after a network failure, 1 = Jacobi
+  tpfa::BatchInst* inst_dev;
+  tpfa::CgState* st;
+  tpfa::CgState* host_st;
+  double* partials;
+  unsigned int* counters;  // ninst for the sweep + 1 for the per-instance helper kernels
+  long long* sweeps;
+  float* vec;
+  double* r64;
+  tpfa::CgVecs v;
+  cudaGraphExec_t loop_exec;
+  const void* loop_key_coef;
+  int loop_key_precond;
+  cudaStream_t cap_stream;
+  cudaEvent_t ev[4];
+};
+

@@ -38,7 +38,9 @@ struct SweepArgs {
   // plain operator
   const float* p;
   float* Ap;
-  double* pAp;
+  double* pAp;            // batched: one value per instance
+  const int* act;         // batched operator: instance i is swept iff (act[i] & need) == need
+  int need;
   // fused CG iteration
   CgVecs v;
   CgState* st;
@@ -92,18 +94,22 @@ __device__ __forceinline__ float ty_word(const unsigned char* base, int lane) {
 // BATCH: one launch sweeps every instance of a batch; each block finds its
 // instance in the table (blocks of one instance are contiguous) and uses that
 // instance's grid, tiling, cell offset, CG state, completion counter and
-// partial sums.  A finished instance's blocks return at once.
+// partial sums.  A finished instance's blocks return at once.  Without CG it
+// is the plain operator of every instance whose activity flags hold the
+// requested bits, with p'Ap per instance.
 template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false, bool BATCH = false>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 sweep_kernel(const SweepArgs a) {
   static_assert(S >= 3, "the plane pipeline needs at least three stages");
   static_assert(!JAC || (CG && !B16), "Jacobi preconditioning is for FP32-record CG sweeps");
-  static_assert(!BATCH || (CG && !B16 && !COND), "batched sweeps are FP32-record CG sweeps");
+  static_assert(!BATCH || (!B16 && !COND), "batched sweeps use FP32 records, no graph condition");
+  static_assert(!BATCH || !JAC || CG, "the batched operator has no preconditioner");
   using LY = StageLayout<VY, B16, JAC>;
   extern __shared__ __align__(16) unsigned char smem[];
   Grid g = a.g;
   int64_t nwx = a.nwx, nwy = a.nwy, nwarps = a.nwarps, zcr = a.zc, off = 0;
   int64_t lb = blockIdx.x, pstart = 0, pcount = gridDim.x;
+  int inst = 0;
   CgState* st = a.st;
   unsigned int* counter = a.counter;
   if (BATCH) {
@@ -115,14 +121,17 @@ sweep_kernel(const SweepArgs a) {
     const BatchInst& I = a.inst[lo];
     g = I.g; nwx = I.nwx; nwy = I.nwy; nwarps = I.nwarps; zcr = I.zc; off = I.off;
     lb = blockIdx.x - I.bstart; pstart = I.bstart; pcount = I.nblocks;
-    st = a.st + lo;
+    inst = lo;
     counter = a.counter + lo;
+    if (CG) st = a.st + lo;
+    else if ((a.act[lo] & a.need) != a.need) return;  // every block of the instance returns
   }
   const float4* coefp = a.coef != nullptr ? a.coef + off : nullptr;
   float* ep = CG ? a.v.e + off : nullptr;
   float alpha = 0.f, beta = 0.f;
-  const float *rin = nullptr, *qin = nullptr, *pin = a.p;
+  const float *rin = nullptr, *qin = nullptr, *pin = CG ? nullptr : a.p + off;
   float *rout = nullptr, *qout = nullptr, *pout = nullptr;
+  float* apo = CG ? nullptr : a.Ap + off;
   if (CG) {
     if (*(volatile int*)&st->done != kRunning) {
       if (lb == 0 && threadIdx.x == 0) {
@@ -300,7 +309,7 @@ sweep_kernel(const SweepArgs a) {
             if (JAC) s3 = fmaf(q, q * jac_inv(cf.w), s3);
             else s3 = fmaf(q, q, s3);
           } else {
-            a.Ap[id] = q;
+            apo[id] = q;
             s1 = fmaf(pc, q, s1);
           }
         }
@@ -334,7 +343,8 @@ sweep_kernel(const SweepArgs a) {
     double v[1] = {kval(acc[1])};
     block_partial<1>(v, a.partials);
     double tot[1];
-    if (last_block_total<1>(a.partials, a.counter, tot) && threadIdx.x == 0) *a.pAp = tot[0];
+    if (last_block_range<1>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0)
+      a.pAp[inst] = tot[0];
   }
 }
 
@@ -604,6 +614,26 @@ cudaError_t launch_cg_sweep_batch(const BatchInst* inst, int ninst, int64_t nblo
   sw.nblocks = nblocks;
   if (jac) return launch_t<4, 4, true, false, false, true, true>(a, sw, s);
   return launch_t<4, 4, true, false, false, false, true>(a, sw, s);
+}
+
+cudaError_t launch_apply_batch(const BatchInst* inst, int ninst, int64_t nblocks,
+                               const float4* coef, const float* p, float* Ap, double* pAp,
+                               const int* act, int need, double* partials,
+                               unsigned int* counters, cudaStream_t s) {
+  SweepArgs a{};
+  a.inst = inst;
+  a.ninst = ninst;
+  a.coef = coef;
+  a.p = p;
+  a.Ap = Ap;
+  a.pAp = pAp;
+  a.act = act;
+  a.need = need;
+  a.partials = partials;
+  a.counter = counters;
+  Sweep sw{};
+  sw.nblocks = nblocks;
+  return launch_t<4, 4, false, false, false, false, true>(a, sw, s);
 }
 
 cudaError_t launch_batch_cond(const CgState* st, int ninst, unsigned long long cond,

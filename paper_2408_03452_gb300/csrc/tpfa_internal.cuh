@@ -141,6 +141,13 @@ cudaError_t launch_cg_sweep_batch(const BatchInst* inst, int ninst, int64_t nblo
                                   unsigned int* counters, bool jac, cudaStream_t s);
 cudaError_t launch_batch_cond(const CgState* st, int ninst, unsigned long long cond,
                               long long* sweeps, long long limit, cudaStream_t s);
+// Batched operator Ap = A p over every instance i with (act[i] & need) ==
+// need (the others are left untouched), pAp[i] = p_i'(A p)_i when pAp is
+// given (partials: nblocks doubles; counters: one per instance, zero).
+cudaError_t launch_apply_batch(const BatchInst* inst, int ninst, int64_t nblocks,
+                               const float4* coef, const float* p, float* Ap, double* pAp,
+                               const int* act, int need, double* partials,
+                               unsigned int* counters, cudaStream_t s);
 
 // Argument checks shared by the entry points: a device (or managed)
 // allocation on `device` that holds [p, p + bytes) and is `align`-aligned.

@@ -256,6 +256,88 @@ def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, levels=2,
     return out
 
 
+def net_levels(shape, levels: int):
+    """The coarsest level l <= levels whose grid suits the network (extents
+    divisible by 2^l, and multiples of 4 on the network's grid), or None."""
+    for l in range(levels, -1, -1):
+        f = 1 << l
+        if all(d % f == 0 and (d // f) % 4 == 0 for d in shape):
+            return l
+    return None
+
+
+def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m: int = 2,
+                      tol: float = 1e-8, maxit: int = 200000, log=None) -> dict:
+    """The batched ensemble of synth.ensemble (uneven sizes, sigma ~ U(0.5, 2.5),
+    Dirichlet ends on a random axis) solved to tol three ways on one batch
+    object: flexible CG with the Jacobi-blended U-Net (one network per size
+    class, on the coarsest suitable grid up to 2^levels coarser), Jacobi PCG
+    and plain CG (cg_solve_batch).  Each solver runs once untimed, then once
+    timed with CUDA events."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ens = synth.ensemble(seed=seed, n_inst=n_inst)
+    grids = [(w["nx"], w["ny"], w["nz"]) for w in ens]
+
+    def cat(k):
+        return torch.from_numpy(np.concatenate([w[k] for w in ens])).to(dev)
+
+    K, mask, pD = cat("K"), cat("mask"), cat("pD")
+    bc = tpfa.BatchContext(grids, device=dev)
+    coef, coef64 = bc.build_trans(K, mask, None, 0.0)
+    b = bc.build_rhs(K, mask, None, pD)
+    lnk = torch.log(K).float()
+    del K, mask, pD
+    classes = sorted(set(grids))
+    nets, idx, lv = [], {}, {}
+    for g in classes:
+        l = net_levels(g, levels)
+        lv["%dx%dx%d" % g] = l
+        if l is None:
+            continue
+        u = tpfa.UNet(*(d >> l for d in g), ns=sum(gi == g for gi in grids), device=dev)
+        u.set_params(P.to(dev))
+        idx[g] = len(nets)
+        nets.append(u)
+    net_of = [idx.get(g, -1) for g in grids]
+    bc.set_option("fcg_m", fcg_m)
+    x = torch.zeros(bc.n, dtype=torch.float64, device=dev)
+
+    def fcg():
+        x.zero_()
+        return bc.fcg_solve(coef, coef64, b, nets=nets, net_of=net_of, lnk=lnk, x=x, tol=tol,
+                            maxit=maxit)[1:]
+
+    def cg(precond):
+        def run():
+            bc.set_option("precond", precond)
+            x.zero_()
+            return bc.cg_solve(coef, coef64, b, x=x, tol=tol, maxit=maxit)[1:]
+        return run
+
+    out = {"instances": n_inst, "cells": bc.n, "tol": tol, "fcg_m": fcg_m,
+           "sizes": {"%dx%dx%d" % g: sum(gi == g for gi in grids) for g in classes},
+           "levels_per_size": lv}
+    for name, fn in (("unet_fcg_batched", fcg), ("jacobi_pcg_batched", cg(1)),
+                     ("plain_cg_batched", cg(0))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        per, tot = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        its = [p["iters"] for p in per]
+        out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters_min_max": [min(its), max(its)],
+                     "iters_sum": int(sum(its)), "rel_res_fp64_max": tot["rel_res_fp64"],
+                     "code": int(tot["code"]), "kernel_launches": int(tot["kernel_launches"])}
+        if name == "unet_fcg_batched":
+            out[name]["fell_back"] = int(sum(p["fell_back"] for p in per))
+        if log:
+            log(f"{name}: {out[name]}")
+    bc.close()
+    return out
+
+
 def apply_bench(n: int, reps: int = 10, seed: int = 0) -> dict:
     """Time M(r) on an n^3 grid (initial weights; the cost does not depend on them)."""
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -313,6 +395,9 @@ def main(argv=None):
                     help="only run two flexible-CG solves capped at --iters iterations on an "
                          "N^3 problem with the network on the 2^levels coarser grid")
     ap.add_argument("--iters", type=int, default=12)
+    ap.add_argument("--ensemble", action="store_true",
+                    help="also solve the 96-instance batched ensemble with the trained network "
+                         "(fcg_solve_batch) against batched Jacobi PCG and plain CG")
     ap.add_argument("--reps", type=int, default=10)
     a = ap.parse_args(argv)
     log = lambda m: print(m, flush=True)  # noqa: E731
@@ -328,6 +413,8 @@ def main(argv=None):
         np.save(a.save, P.cpu().numpy())
     res = evaluate(P, n=a.eval_n, levels=a.levels, log=log)
     res["train"] = hist
+    if a.ensemble:
+        res["ensemble"] = evaluate_ensemble(P, levels=a.levels, log=log)
     print(json.dumps(res))
 
 

@@ -93,6 +93,8 @@ SIGNATURES = {
     "tpfa_batch_build_rhs": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cg_solve_batch": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_int64, _P,
                                  C.POINTER(_Info), _P]),
+    "fcg_solve_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P, _P, _P, C.c_double,
+                                  C.c_int64, _P, C.POINTER(_Info), _P, _P]),
 }
 
 
@@ -616,6 +618,45 @@ class BatchContext:
         if check:
             _check(code, "cg_solve_batch", allow=(OK, NOTCONV))
         per = [{f: getattr(infos[i], f) for f, _ in _Info._fields_} for i in range(self.ninst)]
+        total = {f: getattr(tot, f) for f, _ in _Info._fields_}
+        total["code"] = code
+        return x, per, total
+
+    def fcg_solve(self, coef, coef64, b, nets=(), net_of=None, lnk=None, x=None, tol=1e-8,
+                  maxit=100000, check=True):
+        """Flexible CG over every instance (fcg_solve_batch).  nets: UNet
+        objects; net_of[i]: index into nets of instance i's network, or -1.
+        Returns (x, per-instance info list with 'fell_back', total info)."""
+        dev, n = self.device, self.n
+        if x is None:
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+        nets = list(nets)
+        harr = (C.c_void_p * max(1, len(nets)))(*[u._h.value for u in nets])
+        oarr = None
+        if nets:
+            if net_of is None or len(net_of) != self.ninst:
+                raise ValueError("net_of needs one entry per instance")
+            oarr = (C.c_int * self.ninst)(*[int(k) for k in net_of])
+        infos = (_Info * self.ninst)()
+        tot = _Info()
+        fb = (C.c_int * self.ninst)()
+        with torch.cuda.device(dev):
+            code = lib().fcg_solve_batch(
+                self._h, C.cast(harr, C.c_void_p) if nets else None, len(nets),
+                C.cast(oarr, C.c_void_p) if oarr is not None else None,
+                _ptr(coef, torch.float32, 4 * n, dev, "coef"),
+                _ptr(coef64, torch.float64, 4 * n, dev, "coef64"),
+                _ptr(lnk, torch.float32, n, dev, "lnk") if nets else None,
+                _ptr(b, torch.float64, n, dev, "b"), _ptr(x, torch.float64, n, dev, "x"),
+                float(tol), int(maxit), C.cast(infos, C.c_void_p), C.byref(tot),
+                C.cast(fb, C.c_void_p), _stream(dev))
+        if check:
+            _check(code, "fcg_solve_batch", allow=(OK, NOTCONV))
+        per = []
+        for i in range(self.ninst):
+            d = {f: getattr(infos[i], f) for f, _ in _Info._fields_}
+            d["fell_back"] = bool(fb[i])
+            per.append(d)
         total = {f: getattr(tot, f) for f, _ in _Info._fields_}
         total["code"] = code
         return x, per, total

@@ -100,3 +100,5 @@ def test_unet_parameter_layout_without_a_gpu(tp):
     assert L.tpfa_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == tp.EINVAL
     assert L.fcg_solve(None, None, None, None, None, None, None, 1e-8, 10, None, None,
                        None) == tp.EINVAL
+    assert L.fcg_solve_batch(None, None, 0, None, None, None, None, None, None, 1e-8, 10, None,
+                             None, None, None) == tp.EINVAL
