@@ -1349,10 +1349,17 @@ struct BNet {
   float* rl[kMaxLevels + 1] = {};  // restricted residuals per level (level 0: gathered copy)
   float* ul[kMaxLevels + 1] = {};  // network term per level (level 0: before the scatter)
   float* lnkc = nullptr;           // ln K on the network's grid, member after member
+  cudaStream_t st = nullptr;       // the networks are independent: each runs on its own stream
+  cudaEvent_t done = nullptr;
   BNet() = default;
   BNet(const BNet&) = delete;
   BNet& operator=(const BNet&) = delete;
   ~BNet() {
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+    if (done) cudaEventDestroy(done);
     cudaFree(soff);
     for (int l = 0; l <= kMaxLevels; ++l) {
       cudaFree(rl[l]);
@@ -1375,6 +1382,7 @@ struct BWork {
   float *P = nullptr, *Q = nullptr;
   double *part = nullptr, *uau = nullptr, *pq = nullptr, *norms = nullptr, *hnorms = nullptr;
   double *hist = nullptr, *hhist = nullptr;
+  cudaEvent_t fork = nullptr;  // the networks' streams start after it
   int64_t launches = 0;
 
   bool alloc() {
@@ -1397,7 +1405,8 @@ struct BWork {
               cudaMalloc(&norms, sizeof(double) * 2 * ninst) == cudaSuccess &&
               cudaMallocHost(&hnorms, sizeof(double) * 2 * ninst) == cudaSuccess &&
               cudaMalloc(&hist, sizeof(double) * kCheckEvery * ninst) == cudaSuccess &&
-              cudaMallocHost(&hhist, sizeof(double) * kCheckEvery * ninst) == cudaSuccess;
+              cudaMallocHost(&hhist, sizeof(double) * kCheckEvery * ninst) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
     // defined contents everywhere (the network also reads the residuals of
     // instances that are not iterating)
     ok = ok && cudaMemsetAsync(r, 0, v, s) == cudaSuccess &&
@@ -1435,40 +1444,59 @@ struct BWork {
     cudaFreeHost(hnorms);
     cudaFree(hist);
     cudaFreeHost(hhist);
+    if (fork) cudaEventDestroy(fork);
   }
   unsigned nchunks() const { return (unsigned)chunks.size(); }
 };
 
+// u = P^l net(R^l r, R^l ln K) for the members of one network, on w.s
+int network_class(BNet& N, BWork& w) {
+  const int ns = (int)N.members.size();
+  int rc;
+  if (N.levels > 0) {
+    for (int l = 1; l <= N.levels; ++l)
+      restrict2_kernel<<<w.nb, kT, 0, w.s>>>(l == 1 ? w.r : N.rl[l - 1], N.rl[l],
+                                             N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
+                                             N.dims[2] >> (l - 1), ns, 0.125f,
+                                             l == 1 ? N.soff : nullptr);
+    rc = tpfa_unet_forward(N.net, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
+    if (rc) return rc;
+    for (int l = N.levels; l >= 1; --l)
+      prolong2_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[l], l == 1 ? w.z : N.ul[l - 1],
+                                            N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
+                                            N.dims[2] >> (l - 1), ns, l == 1 ? N.soff : nullptr);
+    w.launches += 15 + 2 * N.levels;
+  } else {
+    const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];
+    gather_kernel<<<w.nb, kT, 0, w.s>>>(w.r, N.soff, N.rl[0], n, ns, 0);
+    rc = tpfa_unet_forward(N.net, N.rl[0], N.lnkc, N.ul[0], w.s);
+    if (rc) return rc;
+    gather_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[0], N.soff, w.z, n, ns, 1);
+    w.launches += 17;
+  }
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
 // u = network term of every network with a member that iterates in blend
-// mode (into w.z at the members' cells)
+// mode (into w.z at the members' cells).  The networks touch disjoint cells
+// and their own buffers only: each runs on its own stream, forked from and
+// joined back to w.s, so that the small, latency-bound layers of the size
+// classes overlap.
 int batch_network_term(std::vector<BNet>& nets, const std::vector<int>& blend_active, BWork& w) {
+  if (cudaEventRecord(w.fork, w.s) != cudaSuccess) return TPFA_ECUDA;
+  const cudaStream_t main = w.s;
   for (BNet& N : nets) {
     bool any = false;
     for (int i : N.members) any = any || blend_active[i];
     if (!any) continue;
-    const int ns = (int)N.members.size();
-    int rc;
-    if (N.levels > 0) {
-      for (int l = 1; l <= N.levels; ++l)
-        restrict2_kernel<<<w.nb, kT, 0, w.s>>>(l == 1 ? w.r : N.rl[l - 1], N.rl[l],
-                                               N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
-                                               N.dims[2] >> (l - 1), ns, 0.125f,
-                                               l == 1 ? N.soff : nullptr);
-      rc = tpfa_unet_forward(N.net, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
-      if (rc) return rc;
-      for (int l = N.levels; l >= 1; --l)
-        prolong2_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[l], l == 1 ? w.z : N.ul[l - 1],
-                                              N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
-                                              N.dims[2] >> (l - 1), ns, l == 1 ? N.soff : nullptr);
-      w.launches += 15 + 2 * N.levels;
-    } else {
-      const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];
-      gather_kernel<<<w.nb, kT, 0, w.s>>>(w.r, N.soff, N.rl[0], n, ns, 0);
-      rc = tpfa_unet_forward(N.net, N.rl[0], N.lnkc, N.ul[0], w.s);
-      if (rc) return rc;
-      gather_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[0], N.soff, w.z, n, ns, 1);
-      w.launches += 17;
-    }
+    if (cudaStreamWaitEvent(N.st, w.fork, 0) != cudaSuccess) return TPFA_ECUDA;
+    w.s = N.st;
+    const int rc = network_class(N, w);
+    w.s = main;
+    if (rc) return rc;
+    if (cudaEventRecord(N.done, N.st) != cudaSuccess ||
+        cudaStreamWaitEvent(main, N.done, 0) != cudaSuccess)
+      return TPFA_ECUDA;
   }
   return TPFA_OK;
 }
@@ -1582,7 +1610,9 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       std::vector<int64_t> so(ns);
       for (int j = 0; j < ns; ++j) so[j] = batch->off[B.members[j]];
       const int64_t nf = (int64_t)B.dims[0] * B.dims[1] * B.dims[2];
-      ok = cudaMalloc(&B.soff, sizeof(int64_t) * ns) == cudaSuccess &&
+      ok = cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming) == cudaSuccess &&
+           cudaMalloc(&B.soff, sizeof(int64_t) * ns) == cudaSuccess &&
            cudaMemcpyAsync(B.soff, so.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, s) ==
                cudaSuccess;
       for (int l = B.levels > 0 ? 1 : 0; l <= B.levels && ok; ++l) {

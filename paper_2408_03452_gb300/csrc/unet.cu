@@ -93,7 +93,15 @@ __host__ __device__ __forceinline__ int cells(const Vol& g) { return g.nx * g.ny
 int blocks_for(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
 // ---- per-sample root mean square (fixed-order reduction) ------------------
-constexpr int kRmsBlocks = 1024;  // blocks per sample
+constexpr int kRmsBlocks = 1024;  // most blocks per sample
+
+// blocks per sample of the sum of squares: about eight cells per thread, so
+// that small samples do not launch mostly idle blocks (depends only on the
+// sample's size, so a sample's rms is the same alone or in a batch)
+int rms_blocks(int per) {
+  const int b = (per + kThreads * 8 - 1) / (kThreads * 8);
+  return b < 1 ? 1 : (b > kRmsBlocks ? kRmsBlocks : b);
+}
 
 __global__ void sumsq_partial_kernel(const float* __restrict__ r, int n, double* partials) {
   __shared__ double sh[kThreads];
@@ -559,8 +567,9 @@ int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z, 
     return TPFA_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int per = g0.nx * g0.ny * g0.nz;
-  sumsq_partial_kernel<<<dim3(kRmsBlocks, g0.ns), kThreads, 0, s>>>(r, per, u->partials);
-  rms_finish_kernel<<<g0.ns, kThreads, 0, s>>>(u->partials, kRmsBlocks, per, u->rms);
+  const int nrb = rms_blocks(per);
+  sumsq_partial_kernel<<<dim3(nrb, g0.ns), kThreads, 0, s>>>(r, per, u->partials);
+  rms_finish_kernel<<<g0.ns, kThreads, 0, s>>>(u->partials, nrb, per, u->rms);
   prep_input_kernel<<<blocks_for(n0), kThreads, 0, s>>>(r, lnk, u->rms, u->in16, g0);
   if (elem_launch_ok()) return TPFA_ECUDA;
   using tpfa::net::kConvRelu;

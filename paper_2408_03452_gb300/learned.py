@@ -266,14 +266,10 @@ def net_levels(shape, levels: int):
     return None
 
 
-def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m: int = 2,
-                      tol: float = 1e-8, maxit: int = 200000, log=None) -> dict:
-    """The batched ensemble of synth.ensemble (uneven sizes, sigma ~ U(0.5, 2.5),
-    Dirichlet ends on a random axis) solved to tol three ways on one batch
-    object: flexible CG with the Jacobi-blended U-Net (one network per size
-    class, on the coarsest suitable grid up to 2^levels coarser), Jacobi PCG
-    and plain CG (cg_solve_batch).  Each solver runs once untimed, then once
-    timed with CUDA events."""
+def ensemble_problem(P, seed: int = 0, n_inst: int = 96, levels: int = 2):
+    """The ensemble of synth.ensemble on one batch object, with one network
+    (parameters P) per size class on the coarsest suitable grid.  Returns
+    (batch, coef, coef64, b, lnk, nets, net_of, grids, levels per size)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     ens = synth.ensemble(seed=seed, n_inst=n_inst)
     grids = [(w["nx"], w["ny"], w["nz"]) for w in ens]
@@ -299,6 +295,20 @@ def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m
         idx[g] = len(nets)
         nets.append(u)
     net_of = [idx.get(g, -1) for g in grids]
+    return bc, coef, coef64, b, lnk, nets, net_of, grids, lv
+
+
+def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m: int = 2,
+                      tol: float = 1e-8, maxit: int = 200000, log=None) -> dict:
+    """The batched ensemble of synth.ensemble (uneven sizes, sigma ~ U(0.5, 2.5),
+    Dirichlet ends on a random axis) solved to tol three ways on one batch
+    object: flexible CG with the Jacobi-blended U-Net (one network per size
+    class, on the coarsest suitable grid up to 2^levels coarser), Jacobi PCG
+    and plain CG (cg_solve_batch).  Each solver runs once untimed, then once
+    timed with CUDA events."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bc, coef, coef64, b, lnk, nets, net_of, grids, lv = ensemble_problem(P, seed, n_inst, levels)
+    classes = sorted(set(grids))
     bc.set_option("fcg_m", fcg_m)
     x = torch.zeros(bc.n, dtype=torch.float64, device=dev)
 
@@ -336,6 +346,22 @@ def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m
             log(f"{name}: {out[name]}")
     bc.close()
     return out
+
+
+def ensemble_bench(iters: int = 12, seed: int = 0, levels: int = 2, fcg_m: int = 2) -> dict:
+    """Two batched flexible-CG solves of the 96-instance ensemble capped at
+    `iters` iterations (initial weights; the cost of an iteration does not
+    depend on them): a profiling target."""
+    bc, coef, coef64, b, lnk, nets, net_of, _, _ = ensemble_problem(init_params(seed), seed,
+                                                                     96, levels)
+    bc.set_option("fcg_m", fcg_m)
+    tot = None
+    for _ in range(2):
+        _, per, tot = bc.fcg_solve(coef, coef64, b, nets=nets, net_of=net_of, lnk=lnk, tol=1e-12,
+                                   maxit=iters, check=False)
+    bc.close()
+    return {"instances": 96, "iters": iters, "ms_per_iter": tot["inner_ms"] / iters,
+            "launches_per_iter": tot["kernel_launches"] / iters}
 
 
 def apply_bench(n: int, reps: int = 10, seed: int = 0) -> dict:
@@ -395,6 +421,9 @@ def main(argv=None):
                     help="only run two flexible-CG solves capped at --iters iterations on an "
                          "N^3 problem with the network on the 2^levels coarser grid")
     ap.add_argument("--iters", type=int, default=12)
+    ap.add_argument("--ensemble-bench", action="store_true",
+                    help="only run two batched flexible-CG solves of the 96-instance ensemble "
+                         "capped at --iters iterations")
     ap.add_argument("--ensemble", action="store_true",
                     help="also solve the 96-instance batched ensemble with the trained network "
                          "(fcg_solve_batch) against batched Jacobi PCG and plain CG")
@@ -403,6 +432,9 @@ def main(argv=None):
     log = lambda m: print(m, flush=True)  # noqa: E731
     if a.apply_bench:
         print(json.dumps(apply_bench(a.apply_bench, a.reps)))
+        return
+    if a.ensemble_bench:
+        print(json.dumps(ensemble_bench(a.iters, levels=a.levels)))
         return
     if a.fcg_bench:
         print(json.dumps(fcg_bench(a.fcg_bench, a.levels, a.iters)))
