@@ -372,6 +372,13 @@ int tpfa_unet_set_params(tpfa_unet* net, const float* params, void* stream);
 /* z = M(r) for every sample (dev pointers).  Keeps the activations for a
  * following tpfa_unet_backward.  Asynchronous. */
 int tpfa_unet_forward(tpfa_unet* net, const float* r, const float* lnk, float* z, void* stream);
+/* tpfa_unet_forward on the first ns samples only (1 <= ns <= the network's
+ * sample count): r, lnk, z hold ns samples.  Each sample's output is the
+ * same as in a full forward pass.  After a pass on fewer samples than the
+ * network has, tpfa_unet_backward returns TPFA_EINVAL until the next full
+ * forward pass.  Asynchronous. */
+int tpfa_unet_forward_samples(tpfa_unet* net, int ns, const float* r, const float* lnk, float* z,
+                              void* stream);
 /* grad (dev, param_count FP32, overwritten) = d(sum gz . z)/d(params) at the
  * last forward pass; gz dev.  Requires train.  Asynchronous. */
 int tpfa_unet_backward(tpfa_unet* net, const float* gz, float* grad, void* stream);

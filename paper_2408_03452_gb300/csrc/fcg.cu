@@ -34,6 +34,8 @@
 struct tpfa_unet;
 extern "C" int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z,
                                  void* stream);
+extern "C" int tpfa_unet_forward_samples(tpfa_unet* u, int ns, const float* r, const float* lnk,
+                                         float* z, void* stream);
 extern "C" int tpfa_net_status(void* stream);
 extern "C" int tpfa_unet_shape(const tpfa_unet* u, int* dims4);
 
@@ -1339,16 +1341,22 @@ void launch_bdir(int M, unsigned nchunks, cudaStream_t s, const BChunk* ch, cons
 }
 
 // One network of the batched solve: the instances (members) that share it,
-// which all have the same grid; the network runs on the 2^levels coarser grid.
+// which all have the same grid; the network runs on the 2^levels coarser grid,
+// and only on the members that still iterate with it (the active ones, as a
+// prefix of its samples).
 struct BNet {
   tpfa_unet* net = nullptr;
   int levels = 0;
   int dims[3] = {0, 0, 0};  // the members' grid
+  int64_t ncoarse = 0;      // cells of one sample on the network's grid
   std::vector<int> members;
-  int64_t* soff = nullptr;  // dev: cell offset of each member in the concatenated arrays
+  std::vector<int> active;  // indices into members of the samples the network runs on
+  int64_t* soff = nullptr;  // dev: cell offset of each active member in the concatenated arrays
+  int64_t* coff = nullptr;  // dev: offset of each active member's sample in lnk_all
   float* rl[kMaxLevels + 1] = {};  // restricted residuals per level (level 0: gathered copy)
   float* ul[kMaxLevels + 1] = {};  // network term per level (level 0: before the scatter)
-  float* lnkc = nullptr;           // ln K on the network's grid, member after member
+  float* lnk_all = nullptr;        // ln K on the network's grid, member after member
+  float* lnkc = nullptr;           // the same for the active members, in their order
   cudaStream_t st = nullptr;       // the networks are independent: each runs on its own stream
   cudaEvent_t done = nullptr;
   BNet() = default;
@@ -1361,6 +1369,8 @@ struct BNet {
     }
     if (done) cudaEventDestroy(done);
     cudaFree(soff);
+    cudaFree(coff);
+    cudaFree(lnk_all);
     for (int l = 0; l <= kMaxLevels; ++l) {
       cudaFree(rl[l]);
       cudaFree(ul[l]);
@@ -1449,9 +1459,40 @@ struct BWork {
   unsigned nchunks() const { return (unsigned)chunks.size(); }
 };
 
-// u = P^l net(R^l r, R^l ln K) for the members of one network, on w.s
+// The members of each network that iterate in blend mode (blend[i]): when
+// the set changes, their cell offsets and the offsets of their ln K samples
+// are uploaded and their ln K gathered into the network's input prefix.
+// Called with every stream idle (outer-step start, the host's looks).
+int update_active(std::vector<BNet>& nets, const std::vector<int>& blend,
+                  const std::vector<int64_t>& off, BWork& w) {
+  for (BNet& N : nets) {
+    std::vector<int> act;
+    for (int j = 0; j < (int)N.members.size(); ++j)
+      if (blend[N.members[j]]) act.push_back(j);
+    if (act == N.active) continue;
+    N.active = act;
+    if (act.empty()) continue;
+    const int ns = (int)act.size();
+    std::vector<int64_t> so(ns), co(ns);
+    for (int k = 0; k < ns; ++k) {
+      so[k] = off[N.members[act[k]]];
+      co[k] = (int64_t)act[k] * N.ncoarse;
+    }
+    if (cudaMemcpyAsync(N.soff, so.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, w.s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(N.coff, co.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, w.s) !=
+            cudaSuccess)
+      return TPFA_ECUDA;
+    gather_kernel<<<w.nb, kT, 0, w.s>>>(N.lnk_all, N.coff, N.lnkc, N.ncoarse, ns, 0);
+    ++w.launches;
+    if (cudaGetLastError() != cudaSuccess) return TPFA_ECUDA;
+  }
+  return TPFA_OK;
+}
+
+// u = P^l net(R^l r, R^l ln K) for the active members of one network, on w.s
 int network_class(BNet& N, BWork& w) {
-  const int ns = (int)N.members.size();
+  const int ns = (int)N.active.size();
   int rc;
   if (N.levels > 0) {
     for (int l = 1; l <= N.levels; ++l)
@@ -1459,7 +1500,7 @@ int network_class(BNet& N, BWork& w) {
                                              N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
                                              N.dims[2] >> (l - 1), ns, 0.125f,
                                              l == 1 ? N.soff : nullptr);
-    rc = tpfa_unet_forward(N.net, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
+    rc = tpfa_unet_forward_samples(N.net, ns, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
     if (rc) return rc;
     for (int l = N.levels; l >= 1; --l)
       prolong2_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[l], l == 1 ? w.z : N.ul[l - 1],
@@ -1469,7 +1510,7 @@ int network_class(BNet& N, BWork& w) {
   } else {
     const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];
     gather_kernel<<<w.nb, kT, 0, w.s>>>(w.r, N.soff, N.rl[0], n, ns, 0);
-    rc = tpfa_unet_forward(N.net, N.rl[0], N.lnkc, N.ul[0], w.s);
+    rc = tpfa_unet_forward_samples(N.net, ns, N.rl[0], N.lnkc, N.ul[0], w.s);
     if (rc) return rc;
     gather_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[0], N.soff, w.z, n, ns, 1);
     w.launches += 17;
@@ -1482,13 +1523,11 @@ int network_class(BNet& N, BWork& w) {
 // and their own buffers only: each runs on its own stream, forked from and
 // joined back to w.s, so that the small, latency-bound layers of the size
 // classes overlap.
-int batch_network_term(std::vector<BNet>& nets, const std::vector<int>& blend_active, BWork& w) {
+int batch_network_term(std::vector<BNet>& nets, BWork& w) {
   if (cudaEventRecord(w.fork, w.s) != cudaSuccess) return TPFA_ECUDA;
   const cudaStream_t main = w.s;
   for (BNet& N : nets) {
-    bool any = false;
-    for (int i : N.members) any = any || blend_active[i];
-    if (!any) continue;
+    if (N.active.empty()) continue;
     if (cudaStreamWaitEvent(N.st, w.fork, 0) != cudaSuccess) return TPFA_ECUDA;
     w.s = N.st;
     const int rc = network_class(N, w);
@@ -1619,16 +1658,19 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
         const size_t bytes = (size_t)(nf >> (3 * l)) * ns * 4;
         ok = cudaMalloc(&B.rl[l], bytes) == cudaSuccess && cudaMalloc(&B.ul[l], bytes) == cudaSuccess;
       }
-      ok = ok && cudaMalloc(&B.lnkc, (size_t)(nf >> (3 * B.levels)) * ns * 4) == cudaSuccess;
+      B.ncoarse = nf >> (3 * B.levels);
+      ok = ok && cudaMalloc(&B.lnkc, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
+           cudaMalloc(&B.lnk_all, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
+           cudaMalloc(&B.coff, sizeof(int64_t) * ns) == cudaSuccess;
       if (!ok) break;
       // ln K on the network's grid (mean over each 2^levels block), member
       // after member, through the image buffers of the intermediate levels
       if (B.levels == 0) {
-        gather_kernel<<<w.nb, kT, 0, s>>>(lnk, B.soff, B.lnkc, nf, ns, 0);
+        gather_kernel<<<w.nb, kT, 0, s>>>(lnk, B.soff, B.lnk_all, nf, ns, 0);
       } else {
         for (int l = 1; l <= B.levels; ++l)
           restrict2_kernel<<<w.nb, kT, 0, s>>>(l == 1 ? lnk : B.ul[l - 1],
-                                               l == B.levels ? B.lnkc : B.ul[l],
+                                               l == B.levels ? B.lnk_all : B.ul[l],
                                                B.dims[0] >> (l - 1), B.dims[1] >> (l - 1),
                                                B.dims[2] >> (l - 1), ns, 0.125f,
                                                l == 1 ? B.soff : nullptr);
@@ -1708,12 +1750,14 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       int64_t giters = 0;
       bool running = true;
       for (int i = 0; i < N; ++i) blend[i] = (w.hflags[i] & kNet) != 0;
+      rc = update_active(bn, blend, batch->off, w);
+      if (rc) break;
       bool first = true;
       while (running && rc == TPFA_OK) {
         bool any_blend = false;
         for (int i = 0; i < N; ++i) any_blend = any_blend || blend[i];
         if (any_blend) {
-          rc = batch_network_term(bn, blend, w);
+          rc = batch_network_term(bn, w);
           if (rc) break;
           if (launch_apply_batch(batch->inst_dev, N, batch->sweep_blocks, cf4, w.z, w.au, w.uau,
                                  w.flags, kAct | kNet, batch->partials, batch->counters,
@@ -1769,6 +1813,7 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
         bool changed = false;
         running = false;
         for (int i = 0; i < N; ++i) {
+          blend[i] = 0;
           if (!(w.hflags[i] & kOuter) || status[i] != TPFA_OK) continue;
           BScal& S = w.hsc[i];
           if (first) hist[i].assign(1, S.rr0);
@@ -1824,6 +1869,9 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
           rc = TPFA_ECUDA;
           break;
         }
+        // the networks run on the members that still iterate with them
+        rc = update_active(bn, blend, batch->off, w);
+        if (rc) break;
         if (giters > maxit + kCheckEvery) break;  // every instance has its own limit below this
       }
       if (rc) break;

@@ -433,10 +433,10 @@ bool vol_buf(uint16_t** p, const Vol& g, int C) {
     if ((x) != cudaSuccess) return TPFA_ECUDA;  \
   } while (0)
 
-int conv(tpfa_unet* u, int layer, const uint16_t* x, const uint16_t* mask, uint16_t* y, int flags,
-         bool backward, cudaStream_t s) {
+int conv(tpfa_unet* u, const Vol* gv, int layer, const uint16_t* x, const uint16_t* mask,
+         uint16_t* y, int flags, bool backward, cudaStream_t s) {
   const LayerDef& d = kDefs[layer];
-  const Vol& g = u->g[d.level];
+  const Vol& g = gv[d.level];
   cudaError_t e;
   if (!backward)
     e = tpfa::net::conv_fwd(x, u->wf[layer], u->bias[layer], mask, y, g, d.cip, d.cop, flags, s);
@@ -557,10 +557,14 @@ int tpfa_unet_set_params(tpfa_unet* u, const float* params, void* stream) {
   return TPFA_OK;
 }
 
-int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z, void* stream) {
-  if (u == nullptr || !u->have_params) return TPFA_EINVAL;
+int tpfa_unet_forward_samples(tpfa_unet* u, int ns, const float* r, const float* lnk, float* z,
+                              void* stream) {
+  if (u == nullptr || !u->have_params || ns < 1 || ns > u->g[0].ns) return TPFA_EINVAL;
   if (cudaSetDevice(u->device) != cudaSuccess) return TPFA_ECUDA;
-  const Vol &g0 = u->g[0], &g1 = u->g[1], &g2 = u->g[2];
+  // the first ns samples: a prefix of every volume (samples are whole haloed blocks)
+  Vol gv[3];
+  for (int l = 0; l < 3; ++l) gv[l] = make_vol(u->g[l].nx, u->g[l].ny, u->g[l].nz, ns);
+  const Vol &g0 = gv[0], &g1 = gv[1], &g2 = gv[2];
   const int n0 = cells(g0);
   if (!tpfa::dev_ok(r, (size_t)n0 * 4, 4, u->device) || !tpfa::dev_ok(lnk, (size_t)n0 * 4, 4, u->device) ||
       !tpfa::dev_ok(z, (size_t)n0 * 4, 4, u->device))
@@ -574,25 +578,32 @@ int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z, 
   if (elem_launch_ok()) return TPFA_ECUDA;
   using tpfa::net::kConvRelu;
   int rc;
-  if ((rc = conv(u, 0, u->in16, nullptr, u->e0, kConvRelu, false, s))) return rc;
+  u->have_forward = false;
+  if ((rc = conv(u, gv, 0, u->in16, nullptr, u->e0, kConvRelu, false, s))) return rc;
   pool_kernel<<<blocks_for((long long)cells(g1) * 2), kThreads, 0, s>>>(u->e0, u->p0, 16, g0, g1);
   if ((rc = elem_launch_ok())) return rc;
-  if ((rc = conv(u, 1, u->p0, nullptr, u->e1, kConvRelu, false, s))) return rc;
+  if ((rc = conv(u, gv, 1, u->p0, nullptr, u->e1, kConvRelu, false, s))) return rc;
   pool_kernel<<<blocks_for((long long)cells(g2) * 4), kThreads, 0, s>>>(u->e1, u->p1, 32, g1, g2);
   if ((rc = elem_launch_ok())) return rc;
-  if ((rc = conv(u, 2, u->p1, nullptr, u->e2, kConvRelu, false, s))) return rc;
-  if ((rc = conv(u, 3, u->e2, nullptr, u->d2, kConvRelu, false, s))) return rc;
+  if ((rc = conv(u, gv, 2, u->p1, nullptr, u->e2, kConvRelu, false, s))) return rc;
+  if ((rc = conv(u, gv, 3, u->e2, nullptr, u->d2, kConvRelu, false, s))) return rc;
   upadd_kernel<<<blocks_for((long long)cells(g1) * 4), kThreads, 0, s>>>(u->d2, u->e1, u->s1, 32, g1, g2);
   if ((rc = elem_launch_ok())) return rc;
-  if ((rc = conv(u, 4, u->s1, nullptr, u->d1, kConvRelu, false, s))) return rc;
+  if ((rc = conv(u, gv, 4, u->s1, nullptr, u->d1, kConvRelu, false, s))) return rc;
   upadd_kernel<<<blocks_for((long long)n0 * 2), kThreads, 0, s>>>(u->d1, u->e0, u->s0, 16, g0, g1);
   if ((rc = elem_launch_ok())) return rc;
-  if ((rc = conv(u, 5, u->s0, nullptr, u->d0, kConvRelu, false, s))) return rc;
-  if ((rc = conv(u, 6, u->d0, nullptr, u->o16, 0, false, s))) return rc;
+  if ((rc = conv(u, gv, 5, u->s0, nullptr, u->d0, kConvRelu, false, s))) return rc;
+  if ((rc = conv(u, gv, 6, u->d0, nullptr, u->o16, 0, false, s))) return rc;
   out_extract_kernel<<<blocks_for(n0), kThreads, 0, s>>>(u->o16, u->rms, z, g0);
   if ((rc = elem_launch_ok())) return rc;
-  u->have_forward = true;
+  // the backward pass needs the activations of every sample
+  u->have_forward = ns == u->g[0].ns;
   return TPFA_OK;
+}
+
+int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z, void* stream) {
+  if (u == nullptr) return TPFA_EINVAL;
+  return tpfa_unet_forward_samples(u, u->g[0].ns, r, lnk, z, stream);
 }
 
 int tpfa_unet_backward(tpfa_unet* u, const float* gz, float* grad, void* stream) {
@@ -610,32 +621,32 @@ int tpfa_unet_backward(tpfa_unet* u, const float* gz, float* grad, void* stream)
   if ((rc = elem_launch_ok())) return rc;
   // layer 6: z = conv(d0)
   if ((rc = layer_grads(u, 6, u->d0, u->g16, grad, s))) return rc;
-  if ((rc = conv(u, 6, u->g16, u->d0, u->dd0, kConvMask, true, s))) return rc;
+  if ((rc = conv(u, u->g, 6, u->g16, u->d0, u->dd0, kConvMask, true, s))) return rc;
   // layer 5: d0 = relu(conv(s0))
   if ((rc = layer_grads(u, 5, u->s0, u->dd0, grad, s))) return rc;
-  if ((rc = conv(u, 5, u->dd0, nullptr, u->ds0, 0, true, s))) return rc;
+  if ((rc = conv(u, u->g, 5, u->dd0, nullptr, u->ds0, 0, true, s))) return rc;
   // s0 = up(d1) + e0
   upadj_mask_kernel<<<blocks_for((long long)cells(g1) * 2), kThreads, 0, s>>>(u->ds0, u->d1, u->dd1, 16, g0, g1);
   if ((rc = elem_launch_ok())) return rc;
   // layer 4: d1 = relu(conv(s1))
   if ((rc = layer_grads(u, 4, u->s1, u->dd1, grad, s))) return rc;
-  if ((rc = conv(u, 4, u->dd1, nullptr, u->ds1, 0, true, s))) return rc;
+  if ((rc = conv(u, u->g, 4, u->dd1, nullptr, u->ds1, 0, true, s))) return rc;
   // s1 = up(d2) + e1
   upadj_mask_kernel<<<blocks_for((long long)cells(g2) * 4), kThreads, 0, s>>>(u->ds1, u->d2, u->dd2, 32, g1, g2);
   if ((rc = elem_launch_ok())) return rc;
   // layer 3: d2 = relu(conv(e2))
   if ((rc = layer_grads(u, 3, u->e2, u->dd2, grad, s))) return rc;
-  if ((rc = conv(u, 3, u->dd2, u->e2, u->de2, kConvMask, true, s))) return rc;
+  if ((rc = conv(u, u->g, 3, u->dd2, u->e2, u->de2, kConvMask, true, s))) return rc;
   // layer 2: e2 = relu(conv(p1))
   if ((rc = layer_grads(u, 2, u->p1, u->de2, grad, s))) return rc;
-  if ((rc = conv(u, 2, u->de2, nullptr, u->dp1, 0, true, s))) return rc;
+  if ((rc = conv(u, u->g, 2, u->de2, nullptr, u->dp1, 0, true, s))) return rc;
   // e1 feeds s1 (skip) and p1 = pool(e1)
   pooladj_add_mask_kernel<<<blocks_for((long long)cells(g1) * 4), kThreads, 0, s>>>(
       u->ds1, u->dp1, u->e1, u->de1, 32, g1, g2);
   if ((rc = elem_launch_ok())) return rc;
   // layer 1: e1 = relu(conv(p0))
   if ((rc = layer_grads(u, 1, u->p0, u->de1, grad, s))) return rc;
-  if ((rc = conv(u, 1, u->de1, nullptr, u->dp0, 0, true, s))) return rc;
+  if ((rc = conv(u, u->g, 1, u->de1, nullptr, u->dp0, 0, true, s))) return rc;
   // e0 feeds s0 (skip) and p0 = pool(e0)
   pooladj_add_mask_kernel<<<blocks_for((long long)n0 * 2), kThreads, 0, s>>>(
       u->ds0, u->dp0, u->e0, u->de0, 16, g0, g1);

@@ -340,6 +340,11 @@ def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m
         out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters_min_max": [min(its), max(its)],
                      "iters_sum": int(sum(its)), "rel_res_fp64_max": tot["rel_res_fp64"],
                      "code": int(tot["code"]), "kernel_launches": int(tot["kernel_launches"])}
+        by = {}
+        for g in classes:
+            gi = [it for it, gg in zip(its, grids) if gg == g]
+            by["%dx%dx%d" % g] = [min(gi), max(gi)]
+        out[name]["iters_by_size"] = by
         if name == "unet_fcg_batched":
             out[name]["fell_back"] = int(sum(p["fell_back"] for p in per))
         if log:

@@ -72,6 +72,7 @@ SIGNATURES = {
     "tpfa_unet_shape": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "tpfa_unet_set_params": (C.c_int, [_P, _P, _P]),
     "tpfa_unet_forward": (C.c_int, [_P, _P, _P, _P, _P]),
+    "tpfa_unet_forward_samples": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
     "tpfa_unet_backward": (C.c_int, [_P, _P, _P, _P]),
     "tpfa_adam_step": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, C.c_double, C.c_double,
                                  C.c_double, C.c_double, _P]),
@@ -465,15 +466,19 @@ class UNet:
                 self._h, _ptr(params, torch.float32, unet_param_count(), dev, "params"),
                 _stream(dev)), "tpfa_unet_set_params")
 
-    def forward(self, r, lnk, z=None):
-        dev, n = self.device, self.n
+    def forward(self, r, lnk, z=None, samples=None):
+        """z = M(r); samples: run on the first `samples` samples only (r, lnk, z
+        then hold that many)."""
+        dev = self.device
+        ns = self.shape[3] if samples is None else int(samples)
+        n = self.n // self.shape[3] * ns
         if z is None:
             z = torch.empty(n, dtype=torch.float32, device=dev)
         with torch.cuda.device(dev):
-            _check(lib().tpfa_unet_forward(self._h, _ptr(r, torch.float32, n, dev, "r"),
-                                           _ptr(lnk, torch.float32, n, dev, "lnk"),
-                                           _ptr(z, torch.float32, n, dev, "z"), _stream(dev)),
-                   "tpfa_unet_forward")
+            _check(lib().tpfa_unet_forward_samples(
+                self._h, ns, _ptr(r, torch.float32, n, dev, "r"),
+                _ptr(lnk, torch.float32, n, dev, "lnk"), _ptr(z, torch.float32, n, dev, "z"),
+                _stream(dev)), "tpfa_unet_forward_samples")
         return z
 
     def backward(self, gz, grad=None):

@@ -95,6 +95,7 @@ def test_unet_parameter_layout_without_a_gpu(tp):
     assert L.tpfa_unet_destroy(None) == tp.EINVAL
     assert L.tpfa_unet_set_params(None, None, None) == tp.EINVAL
     assert L.tpfa_unet_forward(None, None, None, None, None) == tp.EINVAL
+    assert L.tpfa_unet_forward_samples(None, 1, None, None, None, None) == tp.EINVAL
     assert L.tpfa_unet_backward(None, None, None, None) == tp.EINVAL
     assert L.tpfa_conv3d_select(7) == tp.EINVAL
     assert L.tpfa_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == tp.EINVAL

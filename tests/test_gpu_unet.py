@@ -122,7 +122,7 @@ def test_unet_homogeneous_and_samples_independent(tp):
     r, lnk = field_case(shape, ns, 7)
     dev = torch.device("cuda")
     P = torch.from_numpy(flat).to(dev)
-    net = tp.UNet(*shape, ns=ns)
+    net = tp.UNet(*shape, ns=ns, train=True)
     net.set_params(P)
     R = torch.from_numpy(r.ravel().astype(np.float32)).to(dev)
     LK = torch.from_numpy(lnk.ravel().astype(np.float32)).to(dev)
@@ -135,6 +135,15 @@ def test_unet_homogeneous_and_samples_independent(tp):
     for s in range(ns):
         zs = one.forward(R[s * n:(s + 1) * n].contiguous(), LK[s * n:(s + 1) * n].contiguous())
         assert torch.equal(zs, z1[s * n:(s + 1) * n])
+    # a forward pass over the first k samples gives those samples' outputs,
+    # and leaves the network without activations for a backward pass
+    for k in (1, 2):
+        zk = net.forward(R[:k * n].contiguous(), LK[:k * n].contiguous(), samples=k)
+        assert torch.equal(zk, z1[:k * n])
+    with pytest.raises(tp.TpfaError):
+        net.backward(torch.ones_like(R))
+    net.forward(R, LK)
+    net.backward(torch.ones_like(R))  # a full pass restores it
 
 
 def test_adam_matches_oracle(tp):
