@@ -450,9 +450,12 @@ int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* co
  *   nets: host array of n_nets U-Net handles (n_nets = 0: no network; nets
  *         and net_of may then be NULL).  Network k serves the instances i
  *         with net_of[i] == k, which must all have the same grid; its sample
- *         count ns is their number and its grid that grid or the 2x / 4x /
- *         8x coarser one (extents divisible; sample j = the j-th of those
- *         instances in index order).  net_of[i] = -1: no network for
+ *         count ns is their number (sample j = the j-th of those instances in
+ *         index order) and its grid that grid, or the 2x / 4x / 8x coarser one
+ *         (extents divisible) with each extent rounded up to a multiple of 4:
+ *         the extra cells are zero padding that the restriction never
+ *         writes and the prolongation never reads.  The finest level whose
+ *         grid matches is used.  net_of[i] = -1: no network for
  *         instance i (TPFA_OPT_FCG_FALLBACK's preconditioner from the start).
  *   lnk:  dev FP32 ln K over the concatenated cells (8-byte aligned when a
  *         network runs on a coarser grid; ignored without networks).

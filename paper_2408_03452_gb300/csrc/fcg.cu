@@ -404,11 +404,14 @@ __global__ void sub_kernel(const float* a, const float* b, float* y, int64_t n) 
 
 // coarse[C] = scale * sum of the 8 children of C (fine grid nx x ny x nz, all
 // even, ns samples in the solver's x-fastest order; sample s of the fine
-// vector starts at soff[s] when soff is given (even offsets), else at s n)
+// vector starts at soff[s] when soff is given (even offsets), else at s n).
+// The coarse samples are stored qx x qy x qz (>= the coarse extents; 0: not
+// padded); padding cells are not written.
 __global__ void restrict2_kernel(const float* __restrict__ fine, float* __restrict__ coarse, int nx,
                                  int ny, int nz, int ns, float scale,
-                                 const int64_t* __restrict__ soff) {
+                                 const int64_t* __restrict__ soff, int qx, int qy, int qz) {
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const int px = qx > 0 ? qx : cx, py = qy > 0 ? qy : cy, pz = qz > 0 ? qz : cz;
   const int nc = cx * cy * cz * ns;  // grids with fewer than 2^31 cells
   for (int c = blockIdx.x * kT + threadIdx.x; c < nc; c += gridDim.x * kT) {
     const int i = c % cx;
@@ -427,16 +430,19 @@ __global__ void restrict2_kernel(const float* __restrict__ fine, float* __restri
             f + ((size_t)(2 * k + dz) * ny + 2 * j + dy) * nx + 2 * i);
         acc += v.x + v.y;
       }
-    coarse[c] = scale * acc;
+    coarse[((size_t)(s * pz + k) * py + j) * px + i] = scale * acc;
   }
 }
 
 // fine[c] = coarse[parent(c)]; each thread writes two x-neighbours (same
 // parent); sample s of the fine vector starts at soff[s] when soff is given
-// (even offsets), else at s n
+// (even offsets), else at s n; coarse samples stored qx x qy x qz as in
+// restrict2_kernel (0: not padded)
 __global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restrict__ fine, int nx,
-                                int ny, int nz, int ns, const int64_t* __restrict__ soff) {
-  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+                                int ny, int nz, int ns, const int64_t* __restrict__ soff, int qx,
+                                int qy, int qz) {
+  const int cx = nx / 2;
+  const int px = qx > 0 ? qx : cx, py = qy > 0 ? qy : ny / 2, pz = qz > 0 ? qz : nz / 2;
   const int per = nx / 2 * ny * nz;  // float2 pairs per sample
   const int n2 = per * ns;
   for (int c = blockIdx.x * kT + threadIdx.x; c < n2; c += gridDim.x * kT) {
@@ -446,7 +452,7 @@ __global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restr
     t /= ny;
     const int k = t % nz;
     const int s = t / nz;
-    const float v = coarse[((s * cz + k / 2) * cy + j / 2) * cx + i];
+    const float v = coarse[((size_t)(s * pz + k / 2) * py + j / 2) * px + i];
     float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * 2 * per);
     *reinterpret_cast<float2*>(f + 2 * (size_t)(c - s * per)) = make_float2(v, v);
   }
@@ -595,12 +601,13 @@ int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* ln
     for (int l = 1; l <= w.levels; ++l)
       restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.rl[l - 1], w.rl[l], w.dims[0] >> (l - 1),
                                              w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, 0.125f,
-                                             nullptr);
+                                             nullptr, 0, 0, 0);
     rc = tpfa_unet_forward(net, w.rl[w.levels], w.lnkc, w.ul[w.levels], w.s);
     if (rc) return rc;
     for (int l = w.levels; l >= 1; --l)
       prolong2_kernel<<<w.nb, kT, 0, w.s>>>(w.ul[l], w.ul[l - 1], w.dims[0] >> (l - 1),
-                                            w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, nullptr);
+                                            w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, nullptr,
+                                            0, 0, 0);
     w.launches += 15 + 2 * w.levels;
   } else {
     rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
@@ -804,7 +811,7 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
           float* dst = l == w.levels ? w.lnkc : w.ul[l];
           restrict2_kernel<<<w.nb, kT, 0, w.s>>>(src, dst, w.dims[0] >> (l - 1),
                                                  w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1,
-                                                 0.125f, nullptr);
+                                                 0.125f, nullptr, 0, 0, 0);
           src = dst;
         }
         ok = cudaGetLastError() == cudaSuccess;
@@ -914,7 +921,7 @@ extern "C" int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, 
     return TPFA_EINVAL;
   const int nb = (int)((n / 8 + kT - 1) / kT < 4096 ? (n / 8 + kT - 1) / kT : 4096);
   restrict2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(fine, coarse, nx, ny, nz, ns, scale,
-                                                        nullptr);
+                                                        nullptr, 0, 0, 0);
   return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
 }
 
@@ -929,7 +936,8 @@ extern "C" int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, i
   if (!tpfa::dev_ok(fine, n * 4, 4, dev) || !tpfa::dev_ok(coarse, n / 8 * 4, 4, dev))
     return TPFA_EINVAL;
   const int nb = (int)((n + kT - 1) / kT < 4096 ? (n + kT - 1) / kT : 4096);
-  prolong2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(coarse, fine, nx, ny, nz, ns, nullptr);
+  prolong2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(coarse, fine, nx, ny, nz, ns, nullptr, 0,
+                                                       0, 0);
   return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
 }
 
@@ -1348,7 +1356,14 @@ struct BNet {
   tpfa_unet* net = nullptr;
   int levels = 0;
   int dims[3] = {0, 0, 0};  // the members' grid
+  int pdims[3] = {0, 0, 0}; // the network's grid: the 2^levels coarser grid, each extent
+                            // rounded up to a multiple of 4 (zero padding beyond the grid)
   int64_t ncoarse = 0;      // cells of one sample on the network's grid
+  // stored extents of level l (0: unpadded), for the restriction into level l
+  // and the prolongation out of it
+  int qx(int l) const { return l == levels ? pdims[0] : 0; }
+  int qy(int l) const { return l == levels ? pdims[1] : 0; }
+  int qz(int l) const { return l == levels ? pdims[2] : 0; }
   std::vector<int> members;
   std::vector<int> active;  // indices into members of the samples the network runs on
   int64_t* soff = nullptr;  // dev: cell offset of each active member in the concatenated arrays
@@ -1499,13 +1514,14 @@ int network_class(BNet& N, BWork& w) {
       restrict2_kernel<<<w.nb, kT, 0, w.s>>>(l == 1 ? w.r : N.rl[l - 1], N.rl[l],
                                              N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
                                              N.dims[2] >> (l - 1), ns, 0.125f,
-                                             l == 1 ? N.soff : nullptr);
+                                             l == 1 ? N.soff : nullptr, N.qx(l), N.qy(l), N.qz(l));
     rc = tpfa_unet_forward_samples(N.net, ns, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
     if (rc) return rc;
     for (int l = N.levels; l >= 1; --l)
       prolong2_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[l], l == 1 ? w.z : N.ul[l - 1],
                                             N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
-                                            N.dims[2] >> (l - 1), ns, l == 1 ? N.soff : nullptr);
+                                            N.dims[2] >> (l - 1), ns, l == 1 ? N.soff : nullptr,
+                                            N.qx(l), N.qy(l), N.qz(l));
     w.launches += 15 + 2 * N.levels;
   } else {
     const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];
@@ -1582,14 +1598,21 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
     const Grid& g0 = batch->g[B.members[0]];
     int d4[4];
     if (tpfa_unet_shape(B.net, d4) != TPFA_OK || d4[3] != (int)B.members.size()) return TPFA_EINVAL;
+    // the network's level: its grid is the members' grid (l = 0) or the 2^l
+    // coarser one with each extent rounded up to a multiple of 4; the finest
+    // level that fits is taken
     B.levels = -1;
+    auto up4 = [](int64_t v) { return (v + 3) / 4 * 4; };
     for (int l = 0; l <= kMaxLevels && B.levels < 0; ++l) {
       const int64_t f = 1LL << l;
-      if (g0.nx % f == 0 && g0.ny % f == 0 && g0.nz % f == 0 && d4[0] == g0.nx / f &&
-          d4[1] == g0.ny / f && d4[2] == g0.nz / f)
-        B.levels = l;
+      if (g0.nx % f != 0 || g0.ny % f != 0 || g0.nz % f != 0) continue;
+      const int64_t c[3] = {g0.nx / f, g0.ny / f, g0.nz / f};
+      bool fits = true;
+      for (int a = 0; a < 3; ++a) fits = fits && d4[a] == (l == 0 ? c[a] : up4(c[a]));
+      if (fits) B.levels = l;
     }
     if (B.levels < 0) return TPFA_EINVAL;
+    for (int a = 0; a < 3; ++a) B.pdims[a] = d4[a];
     if ((double)g0.n * B.members.size() >= 2147483647.0) return TPFA_EINVAL;
     for (int i : B.members) {
       const Grid& gi = batch->g[i];
@@ -1654,13 +1677,17 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
            cudaMalloc(&B.soff, sizeof(int64_t) * ns) == cudaSuccess &&
            cudaMemcpyAsync(B.soff, so.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, s) ==
                cudaSuccess;
+      // the network's level is stored padded; its padding stays zero (the
+      // restriction writes only the grid's cells)
+      B.ncoarse = (int64_t)B.pdims[0] * B.pdims[1] * B.pdims[2];
       for (int l = B.levels > 0 ? 1 : 0; l <= B.levels && ok; ++l) {
-        const size_t bytes = (size_t)(nf >> (3 * l)) * ns * 4;
-        ok = cudaMalloc(&B.rl[l], bytes) == cudaSuccess && cudaMalloc(&B.ul[l], bytes) == cudaSuccess;
+        const size_t bytes = (l == B.levels ? (size_t)B.ncoarse : (size_t)(nf >> (3 * l))) * ns * 4;
+        ok = cudaMalloc(&B.rl[l], bytes) == cudaSuccess && cudaMalloc(&B.ul[l], bytes) == cudaSuccess &&
+             cudaMemsetAsync(B.rl[l], 0, bytes, s) == cudaSuccess;
       }
-      B.ncoarse = nf >> (3 * B.levels);
       ok = ok && cudaMalloc(&B.lnkc, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
            cudaMalloc(&B.lnk_all, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
+           cudaMemsetAsync(B.lnk_all, 0, (size_t)B.ncoarse * ns * 4, s) == cudaSuccess &&
            cudaMalloc(&B.coff, sizeof(int64_t) * ns) == cudaSuccess;
       if (!ok) break;
       // ln K on the network's grid (mean over each 2^levels block), member
@@ -1673,7 +1700,8 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
                                                l == B.levels ? B.lnk_all : B.ul[l],
                                                B.dims[0] >> (l - 1), B.dims[1] >> (l - 1),
                                                B.dims[2] >> (l - 1), ns, 0.125f,
-                                               l == 1 ? B.soff : nullptr);
+                                               l == 1 ? B.soff : nullptr, B.qx(l), B.qy(l),
+                                               B.qz(l));
       }
       ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     }

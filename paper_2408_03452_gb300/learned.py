@@ -256,19 +256,26 @@ def evaluate(P, n=256, sigma=1.5, seed=777001, tol=1e-8, maxit=200000, levels=2,
     return out
 
 
-def net_levels(shape, levels: int):
-    """The coarsest level l <= levels whose grid suits the network (extents
-    divisible by 2^l, and multiples of 4 on the network's grid), or None."""
+def net_grid(shape, levels: int):
+    """(l, grid) of the network for instances of `shape`: the coarsest level
+    l <= levels with extents divisible by 2^l, and the network's grid, the
+    2^l coarser grid with each extent rounded up to a multiple of 4 (the
+    extra cells are zero padding; two poolings need multiples of 4).  At
+    l = 0 no padding is allowed.  None when no level fits."""
     for l in range(levels, -1, -1):
         f = 1 << l
-        if all(d % f == 0 and (d // f) % 4 == 0 for d in shape):
-            return l
+        if any(d % f for d in shape):
+            continue
+        c = [d // f for d in shape]
+        if l == 0 and any(v % 4 for v in c):
+            continue
+        return l, tuple((v + 3) // 4 * 4 for v in c)
     return None
 
 
 def ensemble_problem(P, seed: int = 0, n_inst: int = 96, levels: int = 2):
     """The ensemble of synth.ensemble on one batch object, with one network
-    (parameters P) per size class on the coarsest suitable grid.  Returns
+    (parameters P) per size class on its grid from net_grid.  Returns
     (batch, coef, coef64, b, lnk, nets, net_of, grids, levels per size)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     ens = synth.ensemble(seed=seed, n_inst=n_inst)
@@ -286,11 +293,11 @@ def ensemble_problem(P, seed: int = 0, n_inst: int = 96, levels: int = 2):
     classes = sorted(set(grids))
     nets, idx, lv = [], {}, {}
     for g in classes:
-        l = net_levels(g, levels)
-        lv["%dx%dx%d" % g] = l
-        if l is None:
+        ng = net_grid(g, levels)
+        lv["%dx%dx%d" % g] = None if ng is None else {"level": ng[0], "net_grid": list(ng[1])}
+        if ng is None:
             continue
-        u = tpfa.UNet(*(d >> l for d in g), ns=sum(gi == g for gi in grids), device=dev)
+        u = tpfa.UNet(*ng[1], ns=sum(gi == g for gi in grids), device=dev)
         u.set_params(P.to(dev))
         idx[g] = len(nets)
         nets.append(u)

@@ -122,6 +122,24 @@ def test_fcg_batch_with_networks_matches_oracle(tp, oracle_mod):
     bc.close()
 
 
+def test_fcg_batch_with_padded_network_grids(tp, oracle_mod):
+    """Networks on the 4x coarser grid padded to multiples of 4 (16x16x8 ->
+    4x4x2 stored 4x4x4; 24x16x24 -> 6x4x6 stored 8x4x8), next to an unpadded
+    one: every instance reaches the FP64 tolerance."""
+    O = oracle_mod
+    insts = [_inst((16, 16, 8), 51, 1.5), _inst((24, 16, 24), 52, 1.5, "z"),
+             _inst((16, 16, 8), 53, 1.0, "y"), _inst((16, 16, 16), 54, 1.5)]
+    bc, coef, coef64, b, lnk = _setup(tp, insts)
+    nets = _nets(tp, [((4, 4, 4), 2), ((8, 4, 8), 1), ((4, 4, 4), 1)])
+    bc.set_option("fcg_m", 2)
+    x, per, total = bc.fcg_solve(coef, coef64, b, nets=nets, net_of=[0, 1, 0, 2], lnk=lnk,
+                                 tol=1e-8, maxit=20000)
+    assert total["code"] == tp.OK, (total, per)
+    for i, xi in enumerate(_parts(bc, x)):
+        assert _oracle_rel(O, insts[i], xi) <= 1e-8 * 1.01, (i, per[i])
+    bc.close()
+
+
 def test_fcg_batch_instance_independent_of_the_batch(tp):
     """The last instance of the mixed batch, solved alone with its own
     one-sample network and the same tiling: bit-identical solution, same
