@@ -1,0 +1,127 @@
+// Pieces shared by the two flexible-CG solvers (fcg.cu: one grid; fcg_batch.cu:
+// the instances of a batch): block reductions, the retained-direction table,
+// the Jacobi diagonal, restriction to and prolongation from the network's
+// coarser grid, and the solvers' constants.  Each translation unit gets its
+// own copy (anonymous namespace).
+#pragma once
+
+#include <stdint.h>
+
+#include "tpfa_internal.cuh"
+
+struct tpfa_unet;
+extern "C" int tpfa_unet_forward(tpfa_unet* u, const float* r, const float* lnk, float* z,
+                                 void* stream);
+extern "C" int tpfa_unet_forward_samples(tpfa_unet* u, int ns, const float* r, const float* lnk,
+                                         float* z, void* stream);
+extern "C" int tpfa_net_status(void* stream);
+extern "C" int tpfa_unet_shape(const tpfa_unet* u, int* dims4);
+
+namespace {
+
+constexpr int kT = 256;
+
+// Block sums of M per-thread FP64 values (warp shuffles, then the warps in
+// order): part[blockIdx.x * M + j].
+template <int M>
+__device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) {
+  __shared__ double sh[M][kT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[j][wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += sh[threadIdx.x][w];
+    part[(size_t)blockIdx.x * M + threadIdx.x] = t;
+  }
+}
+
+constexpr int kMaxDirs = 16;
+struct Dirs {
+  const float* v[kMaxDirs];
+};
+
+// partial sums per block: the most any kernel writes (dots_kernel<kMaxDirs>)
+constexpr int kPartPerBlock = 2 + 2 * kMaxDirs;
+
+#define TPFA_FCG_M0(X) \
+  X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+// dinv = 1 / D (the Jacobi scaling the blend uses)
+__global__ void dinv_kernel(const float4* __restrict__ coef, float* __restrict__ dinv, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kT)
+    dinv[i] = 1.0f / coef[i].w;
+}
+
+// coarse[C] = scale * sum of the 8 children of C (fine grid nx x ny x nz, all
+// even, ns samples in the solver's x-fastest order; sample s of the fine
+// vector starts at soff[s] when soff is given (even offsets), else at s n).
+// The coarse samples are stored qx x qy x qz (>= the coarse extents; 0: not
+// padded); padding cells are not written.
+__global__ void restrict2_kernel(const float* __restrict__ fine, float* __restrict__ coarse, int nx,
+                                 int ny, int nz, int ns, float scale,
+                                 const int64_t* __restrict__ soff, int qx, int qy, int qz) {
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const int px = qx > 0 ? qx : cx, py = qy > 0 ? qy : cy, pz = qz > 0 ? qz : cz;
+  const int nc = cx * cy * cz * ns;  // grids with fewer than 2^31 cells
+  for (int c = blockIdx.x * kT + threadIdx.x; c < nc; c += gridDim.x * kT) {
+    const int i = c % cx;
+    int t = c / cx;
+    const int j = t % cy;
+    t /= cy;
+    const int k = t % cz;
+    const int s = t / cz;
+    const float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * nx * ny * nz);
+    float acc = 0.f;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float2 v = *reinterpret_cast<const float2*>(
+            f + ((size_t)(2 * k + dz) * ny + 2 * j + dy) * nx + 2 * i);
+        acc += v.x + v.y;
+      }
+    coarse[((size_t)(s * pz + k) * py + j) * px + i] = scale * acc;
+  }
+}
+
+// fine[c] = coarse[parent(c)]; each thread writes two x-neighbours (same
+// parent); sample s of the fine vector starts at soff[s] when soff is given
+// (even offsets), else at s n; coarse samples stored qx x qy x qz as in
+// restrict2_kernel (0: not padded)
+__global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restrict__ fine, int nx,
+                                int ny, int nz, int ns, const int64_t* __restrict__ soff, int qx,
+                                int qy, int qz) {
+  const int cx = nx / 2;
+  const int px = qx > 0 ? qx : cx, py = qy > 0 ? qy : ny / 2, pz = qz > 0 ? qz : nz / 2;
+  const int per = nx / 2 * ny * nz;  // float2 pairs per sample
+  const int n2 = per * ns;
+  for (int c = blockIdx.x * kT + threadIdx.x; c < n2; c += gridDim.x * kT) {
+    const int i = c % cx;
+    int t = c / cx;
+    const int j = t % ny;
+    t /= ny;
+    const int k = t % nz;
+    const int s = t / nz;
+    const float v = coarse[((size_t)(s * pz + k / 2) * py + j / 2) * px + i];
+    float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * 2 * per);
+    *reinterpret_cast<float2*>(f + 2 * (size_t)(c - s * per)) = make_float2(v, v);
+  }
+}
+
+// iterations between the host's looks at the device scalars (convergence,
+// breakdown, stagnation); at most this many iterations run past the one that
+// met the tolerance
+constexpr int kCheckEvery = 4;
+constexpr int kMaxLevels = 3;  // the network's grid: up to 8x coarser than the solver's
+
+// stagnation window of the fallback test (iterations)
+constexpr int kStallWindow = 100;
+
+}  // namespace
