@@ -140,6 +140,27 @@ def test_fcg_batch_with_padded_network_grids(tp, oracle_mod):
     bc.close()
 
 
+def test_fcg_batch_networks_with_ragged_offsets(tp, oracle_mod):
+    """An 18-cell instance first: every later instance starts at an even
+    offset that is not a multiple of 4, so the vector passes take their
+    scalar path while networks run on the 4x coarser grids (padded); a
+    ragged instance without a network at the end."""
+    O = oracle_mod
+    insts = [_inst((3, 3, 2), 60, 1.0), _inst((16, 16, 16), 61, 1.5),
+             _inst((16, 16, 8), 62, 1.5, "z"), _inst((16, 16, 16), 63, 1.0, "y"),
+             _inst((13, 11, 7), 64, 1.0)]
+    bc, coef, coef64, b, lnk = _setup(tp, insts)
+    assert all(o % 2 == 0 and o % 4 != 0 for o in bc.offsets[1:4])
+    nets = _nets(tp, [((4, 4, 4), 2), ((4, 4, 4), 1)])
+    bc.set_option("fcg_m", 2)
+    x, per, total = bc.fcg_solve(coef, coef64, b, nets=nets, net_of=[-1, 0, 1, 0, -1], lnk=lnk,
+                                 tol=1e-8, maxit=20000)
+    assert total["code"] == tp.OK, (total, per)
+    for i, xi in enumerate(_parts(bc, x)):
+        assert _oracle_rel(O, insts[i], xi) <= 1e-8 * 1.01, (i, per[i])
+    bc.close()
+
+
 def test_fcg_batch_instance_independent_of_the_batch(tp):
     """The last instance of the mixed batch, solved alone with its own
     one-sample network and the same tiling: bit-identical solution, same
