@@ -404,8 +404,8 @@ struct Work {
   Scal* sc = nullptr;        // dev, iteration scalars
   double* hist = nullptr;    // dev, r'r of the iterations since the host last looked
   double* hhist = nullptr;   // pinned copy
-  // network on the 2^levels coarser grid: restricted residuals and images per
-  // level (level 0 is the solver's grid: r and z), ln K on the network's grid
+  // network on the 2^levels coarser grid: the restricted residual and the
+  // network's output there (index levels), ln K on the network's grid
   int levels = 0;
   int dims[3] = {0, 0, 0};
   float* rl[kMaxLevels + 1] = {};
@@ -486,19 +486,14 @@ enum PrecMode { kIdentity = 0, kJacobi = 1, kBlend = 2 };
 int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w) {
   int rc;
   if (w.levels > 0) {
-    w.rl[0] = w.r;
-    w.ul[0] = w.z;
-    for (int l = 1; l <= w.levels; ++l)
-      restrict2_kernel<<<w.nb, kT, 0, w.s>>>(w.rl[l - 1], w.rl[l], w.dims[0] >> (l - 1),
-                                             w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, 0.125f,
-                                             nullptr, 0, 0, 0);
-    rc = tpfa_unet_forward(net, w.rl[w.levels], w.lnkc, w.ul[w.levels], w.s);
+    const int L = w.levels;
+    launch_restrict_levels(L, w.nb, w.s, w.r, w.rl[L], w.dims[0], w.dims[1], w.dims[2], 1,
+                           nullptr, 0, 0, 0);
+    rc = tpfa_unet_forward(net, w.rl[L], w.lnkc, w.ul[L], w.s);
     if (rc) return rc;
-    for (int l = w.levels; l >= 1; --l)
-      prolong2_kernel<<<w.nb, kT, 0, w.s>>>(w.ul[l], w.ul[l - 1], w.dims[0] >> (l - 1),
-                                            w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1, nullptr,
-                                            0, 0, 0);
-    w.launches += 15 + 2 * w.levels;
+    launch_prolong_levels(L, w.nb, w.s, w.ul[L], w.z, w.dims[0], w.dims[1], w.dims[2], 1, nullptr,
+                          0, 0, 0);
+    w.launches += 17;
   } else {
     rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
     if (rc) return rc;
@@ -686,22 +681,14 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
       ok = cudaGetLastError() == cudaSuccess;
     }
     if (ok && w.levels > 0) {
-      for (int l = 1; l <= w.levels && ok; ++l) {
-        const size_t bytes = (size_t)(n >> (3 * l)) * 4;
-        ok = cudaMalloc(&w.rl[l], bytes) == cudaSuccess && cudaMalloc(&w.ul[l], bytes) == cudaSuccess;
-      }
-      ok = ok && cudaMalloc(&w.lnkc, (size_t)(n >> (3 * w.levels)) * 4) == cudaSuccess;
+      const int L = w.levels;
+      const size_t bytes = (size_t)(n >> (3 * L)) * 4;
+      ok = cudaMalloc(&w.rl[L], bytes) == cudaSuccess && cudaMalloc(&w.ul[L], bytes) == cudaSuccess &&
+           cudaMalloc(&w.lnkc, bytes) == cudaSuccess;
       if (ok) {
-        // ln K on the network's grid (the mean over each 2^levels block), through the
-        // image buffers of the intermediate levels
-        const float* src = lnk;
-        for (int l = 1; l <= w.levels; ++l) {
-          float* dst = l == w.levels ? w.lnkc : w.ul[l];
-          restrict2_kernel<<<w.nb, kT, 0, w.s>>>(src, dst, w.dims[0] >> (l - 1),
-                                                 w.dims[1] >> (l - 1), w.dims[2] >> (l - 1), 1,
-                                                 0.125f, nullptr, 0, 0, 0);
-          src = dst;
-        }
+        // ln K on the network's grid: the mean over each 2^levels block
+        launch_restrict_levels(L, w.nb, w.s, lnk, w.lnkc, w.dims[0], w.dims[1], w.dims[2], 1,
+                               nullptr, 0, 0, 0);
         ok = cudaGetLastError() == cudaSuccess;
       }
     }

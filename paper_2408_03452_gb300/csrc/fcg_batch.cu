@@ -426,17 +426,12 @@ struct BNet {
   int pdims[3] = {0, 0, 0}; // the network's grid: the 2^levels coarser grid, each extent
                             // rounded up to a multiple of 4 (zero padding beyond the grid)
   int64_t ncoarse = 0;      // cells of one sample on the network's grid
-  // stored extents of level l (0: unpadded), for the restriction into level l
-  // and the prolongation out of it
-  int qx(int l) const { return l == levels ? pdims[0] : 0; }
-  int qy(int l) const { return l == levels ? pdims[1] : 0; }
-  int qz(int l) const { return l == levels ? pdims[2] : 0; }
   std::vector<int> members;
   std::vector<int> active;  // indices into members of the samples the network runs on
   int64_t* soff = nullptr;  // dev: cell offset of each active member in the concatenated arrays
   int64_t* coff = nullptr;  // dev: offset of each active member's sample in lnk_all
-  float* rl[kMaxLevels + 1] = {};  // restricted residuals per level (level 0: gathered copy)
-  float* ul[kMaxLevels + 1] = {};  // network term per level (level 0: before the scatter)
+  float* rl[kMaxLevels + 1] = {};  // rl[levels]: restricted residuals (level 0: gathered copy)
+  float* ul[kMaxLevels + 1] = {};  // ul[levels]: network output (level 0: before the scatter)
   float* lnk_all = nullptr;        // ln K on the network's grid, member after member
   float* lnkc = nullptr;           // the same for the active members, in their order
   cudaStream_t st = nullptr;       // the networks are independent: each runs on its own stream
@@ -577,19 +572,14 @@ int network_class(BNet& N, BWork& w) {
   const int ns = (int)N.active.size();
   int rc;
   if (N.levels > 0) {
-    for (int l = 1; l <= N.levels; ++l)
-      restrict2_kernel<<<w.nb, kT, 0, w.s>>>(l == 1 ? w.r : N.rl[l - 1], N.rl[l],
-                                             N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
-                                             N.dims[2] >> (l - 1), ns, 0.125f,
-                                             l == 1 ? N.soff : nullptr, N.qx(l), N.qy(l), N.qz(l));
-    rc = tpfa_unet_forward_samples(N.net, ns, N.rl[N.levels], N.lnkc, N.ul[N.levels], w.s);
+    const int L = N.levels;
+    launch_restrict_levels(L, w.nb, w.s, w.r, N.rl[L], N.dims[0], N.dims[1], N.dims[2], ns, N.soff,
+                           N.pdims[0], N.pdims[1], N.pdims[2]);
+    rc = tpfa_unet_forward_samples(N.net, ns, N.rl[L], N.lnkc, N.ul[L], w.s);
     if (rc) return rc;
-    for (int l = N.levels; l >= 1; --l)
-      prolong2_kernel<<<w.nb, kT, 0, w.s>>>(N.ul[l], l == 1 ? w.z : N.ul[l - 1],
-                                            N.dims[0] >> (l - 1), N.dims[1] >> (l - 1),
-                                            N.dims[2] >> (l - 1), ns, l == 1 ? N.soff : nullptr,
-                                            N.qx(l), N.qy(l), N.qz(l));
-    w.launches += 15 + 2 * N.levels;
+    launch_prolong_levels(L, w.nb, w.s, N.ul[L], w.z, N.dims[0], N.dims[1], N.dims[2], ns, N.soff,
+                          N.pdims[0], N.pdims[1], N.pdims[2]);
+    w.launches += 17;
   } else {
     const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];
     gather_kernel<<<w.nb, kT, 0, w.s>>>(w.r, N.soff, N.rl[0], n, ns, 0);
@@ -747,10 +737,12 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       // the network's level is stored padded; its padding stays zero (the
       // restriction writes only the grid's cells)
       B.ncoarse = (int64_t)B.pdims[0] * B.pdims[1] * B.pdims[2];
-      for (int l = B.levels > 0 ? 1 : 0; l <= B.levels && ok; ++l) {
-        const size_t bytes = (l == B.levels ? (size_t)B.ncoarse : (size_t)(nf >> (3 * l))) * ns * 4;
-        ok = cudaMalloc(&B.rl[l], bytes) == cudaSuccess && cudaMalloc(&B.ul[l], bytes) == cudaSuccess &&
-             cudaMemsetAsync(B.rl[l], 0, bytes, s) == cudaSuccess;
+      {
+        const int L = B.levels;
+        const size_t bytes = (size_t)B.ncoarse * ns * 4;
+        ok = ok && cudaMalloc(&B.rl[L], bytes) == cudaSuccess &&
+             cudaMalloc(&B.ul[L], bytes) == cudaSuccess &&
+             cudaMemsetAsync(B.rl[L], 0, bytes, s) == cudaSuccess;
       }
       ok = ok && cudaMalloc(&B.lnkc, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
            cudaMalloc(&B.lnk_all, (size_t)B.ncoarse * ns * 4) == cudaSuccess &&
@@ -758,18 +750,12 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
            cudaMalloc(&B.coff, sizeof(int64_t) * ns) == cudaSuccess;
       if (!ok) break;
       // ln K on the network's grid (mean over each 2^levels block), member
-      // after member, through the image buffers of the intermediate levels
-      if (B.levels == 0) {
+      // after member
+      if (B.levels == 0)
         gather_kernel<<<w.nb, kT, 0, s>>>(lnk, B.soff, B.lnk_all, nf, ns, 0);
-      } else {
-        for (int l = 1; l <= B.levels; ++l)
-          restrict2_kernel<<<w.nb, kT, 0, s>>>(l == 1 ? lnk : B.ul[l - 1],
-                                               l == B.levels ? B.lnk_all : B.ul[l],
-                                               B.dims[0] >> (l - 1), B.dims[1] >> (l - 1),
-                                               B.dims[2] >> (l - 1), ns, 0.125f,
-                                               l == 1 ? B.soff : nullptr, B.qx(l), B.qy(l),
-                                               B.qz(l));
-      }
+      else
+        launch_restrict_levels(B.levels, w.nb, s, lnk, B.lnk_all, B.dims[0], B.dims[1], B.dims[2],
+                               ns, B.soff, B.pdims[0], B.pdims[1], B.pdims[2]);
       ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     }
     ok = ok && cudaMemsetAsync(batch->counters, 0, sizeof(unsigned int) * (N + 1), s) == cudaSuccess;

@@ -115,6 +115,101 @@ __global__ void prolong2_kernel(const float* __restrict__ coarse, float* __restr
   }
 }
 
+// Value of one cell of the 2^L coarser grid: the block mean over its 2^L
+// children per axis, formed level by level in the order of L successive
+// restrict2_kernel passes with scale 1/8.  Each level's product is rounded
+// on its own (__fmul_rn, no contraction into a later add), so the result is
+// bit-identical to those passes.  (x, y, z): the block's first fine cell.
+template <int L>
+__device__ __forceinline__ float block_mean(const float* __restrict__ f, int nx, int ny, int x,
+                                            int y, int z) {
+  float acc = 0.f;
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      if constexpr (L == 1) {
+        const float2 v =
+            *reinterpret_cast<const float2*>(f + ((size_t)(z + dz) * ny + y + dy) * nx + x);
+        acc += v.x + v.y;
+      } else {
+        constexpr int h = 1 << (L - 1);
+        const float a = block_mean<L - 1>(f, nx, ny, x, y + dy * h, z + dz * h);
+        const float b = block_mean<L - 1>(f, nx, ny, x + h, y + dy * h, z + dz * h);
+        acc += a + b;
+      }
+    }
+  return __fmul_rn(0.125f, acc);
+}
+
+// The 2^L coarser grid in one pass (block means, as L restrict2_kernel passes
+// with scale 1/8 would give them; fine extents divisible by 2^L).  Sample
+// offsets and the padded coarse layout as in restrict2_kernel.
+template <int L>
+__global__ void restrict_levels_kernel(const float* __restrict__ fine, float* __restrict__ coarse,
+                                       int nx, int ny, int nz, int ns,
+                                       const int64_t* __restrict__ soff, int qx, int qy, int qz) {
+  const int cx = nx >> L, cy = ny >> L, cz = nz >> L;
+  const int px = qx > 0 ? qx : cx, py = qy > 0 ? qy : cy, pz = qz > 0 ? qz : cz;
+  const int nc = cx * cy * cz * ns;  // grids with fewer than 2^31 cells
+  for (int c = blockIdx.x * kT + threadIdx.x; c < nc; c += gridDim.x * kT) {
+    const int i = c % cx;
+    int t = c / cx;
+    const int j = t % cy;
+    t /= cy;
+    const int k = t % cz;
+    const int s = t / cz;
+    const float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * nx * ny * nz);
+    coarse[((size_t)(s * pz + k) * py + j) * px + i] = block_mean<L>(f, nx, ny, i << L, j << L, k << L);
+  }
+}
+
+// fine[c] = coarse value of c's ancestor on the 2^L coarser grid (L nearest
+// prolongations in one pass); two x-neighbours per thread.  Sample offsets
+// and the padded coarse layout as in prolong2_kernel.
+template <int L>
+__global__ void prolong_levels_kernel(const float* __restrict__ coarse, float* __restrict__ fine,
+                                      int nx, int ny, int nz, int ns,
+                                      const int64_t* __restrict__ soff, int qx, int qy, int qz) {
+  const int hx = nx / 2;
+  const int px = qx > 0 ? qx : nx >> L, py = qy > 0 ? qy : ny >> L, pz = qz > 0 ? qz : nz >> L;
+  const int per = hx * ny * nz;  // float2 pairs per sample
+  const int n2 = per * ns;
+  for (int c = blockIdx.x * kT + threadIdx.x; c < n2; c += gridDim.x * kT) {
+    const int i = c % hx;
+    int t = c / hx;
+    const int j = t % ny;
+    t /= ny;
+    const int k = t % nz;
+    const int s = t / nz;
+    const float v = coarse[((size_t)(s * pz + (k >> L)) * py + (j >> L)) * px + ((2 * i) >> L)];
+    float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * 2 * per);
+    *reinterpret_cast<float2*>(f + 2 * (size_t)(c - s * per)) = make_float2(v, v);
+  }
+}
+
+// launchers for L = 1, 2, 3 (kMaxLevels)
+inline void launch_restrict_levels(int L, int nb, cudaStream_t st, const float* fine, float* coarse,
+                                   int nx, int ny, int nz, int ns, const int64_t* soff, int qx,
+                                   int qy, int qz) {
+  switch (L) {
+    case 1: restrict_levels_kernel<1><<<nb, kT, 0, st>>>(fine, coarse, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    case 2: restrict_levels_kernel<2><<<nb, kT, 0, st>>>(fine, coarse, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    case 3: restrict_levels_kernel<3><<<nb, kT, 0, st>>>(fine, coarse, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    default: break;
+  }
+}
+inline void launch_prolong_levels(int L, int nb, cudaStream_t st, const float* coarse, float* fine,
+                                  int nx, int ny, int nz, int ns, const int64_t* soff, int qx,
+                                  int qy, int qz) {
+  switch (L) {
+    case 1: prolong_levels_kernel<1><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    case 2: prolong_levels_kernel<2><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    case 3: prolong_levels_kernel<3><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    default: break;
+  }
+}
+
 // iterations between the host's looks at the device scalars (convergence,
 // breakdown, stagnation); at most this many iterations run past the one that
 // met the tolerance
