@@ -431,9 +431,22 @@ int tpfa_jacobi_split(tpfa_ctx* ctx, const float* coef, const float* r, const fl
  * 8-byte aligned; coarse: ns (nx/2)(ny/2)(nz/2) FP32, dev.  Asynchronous. */
 int tpfa_restrict2(const float* fine, float* coarse, int nx, int ny, int nz, int ns, float scale,
                    void* stream);
-/* Nearest prolongation: fine[c] = coarse[parent(c)] (shapes as tpfa_restrict2).
- * Asynchronous. */
+/* Nearest prolongation: fine[c] = coarse[parent(c)] (shapes as tpfa_restrict2;
+ * fine 8-byte aligned).  Asynchronous. */
 int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, int nz, int ns, void* stream);
+/* The 2^levels coarser grid in one pass (levels 1 to 3; extents divisible by
+ * 2^levels): coarse = the mean over each 2^levels block, bit-identical to
+ * `levels` successive tpfa_restrict2 calls with scale 1/8 (the same sums in
+ * the same order).  fine 8-byte aligned; shapes as tpfa_restrict2 with
+ * coarse ns (nx/2^l)(ny/2^l)(nz/2^l).  The solvers restrict to and prolong
+ * from a network's coarser grid with these passes.  Asynchronous. */
+int tpfa_restrict_levels(const float* fine, float* coarse, int nx, int ny, int nz, int ns,
+                         int levels, void* stream);
+/* fine[c] = coarse value of c's ancestor on the 2^levels coarser grid
+ * (`levels` nearest prolongations in one pass).  fine 8-byte aligned.
+ * Asynchronous. */
+int tpfa_prolong_levels(const float* coarse, float* fine, int nx, int ny, int nz, int ns,
+                        int levels, void* stream);
 int fcg_solve(tpfa_ctx* ctx, tpfa_unet* net, const float* coef, const double* coef64,
               const float* lnk, const double* b, double* x, double tol, int64_t maxit,
               tpfa_cg_info* info, int* fell_back, void* stream);

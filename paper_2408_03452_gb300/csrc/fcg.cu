@@ -808,10 +808,49 @@ extern "C" int tpfa_prolong2(const float* coarse, float* fine, int nx, int ny, i
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
   const size_t n = (size_t)nx * ny * nz * ns;
-  if (!tpfa::dev_ok(fine, n * 4, 4, dev) || !tpfa::dev_ok(coarse, n / 8 * 4, 4, dev))
+  // the kernel writes two x-neighbours at a time
+  if (!tpfa::dev_ok(fine, n * 4, 8, dev) || !tpfa::dev_ok(coarse, n / 8 * 4, 4, dev))
     return TPFA_EINVAL;
   const int nb = (int)((n + kT - 1) / kT < 4096 ? (n + kT - 1) / kT : 4096);
   prolong2_kernel<<<nb, kT, 0, (cudaStream_t)stream>>>(coarse, fine, nx, ny, nz, ns, nullptr, 0,
                                                        0, 0);
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
+// The 2^levels coarser grid in one pass: the block means, bit-identical to
+// `levels` successive tpfa_restrict2 calls with scale 1/8.  Asynchronous.
+extern "C" int tpfa_restrict_levels(const float* fine, float* coarse, int nx, int ny, int nz, int ns,
+                                    int levels, void* stream) {
+  if (levels < 1 || levels > kMaxLevels || ns < 1) return TPFA_EINVAL;
+  const int f = 1 << levels;
+  if (nx < f || ny < f || nz < f || nx % f || ny % f || nz % f) return TPFA_EINVAL;
+  if ((double)nx * ny * nz * ns >= 2147483647.0) return TPFA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
+  const size_t n = (size_t)nx * ny * nz * ns, nc = n >> (3 * levels);
+  if (!tpfa::dev_ok(fine, n * 4, 8, dev) || !tpfa::dev_ok(coarse, nc * 4, 4, dev))
+    return TPFA_EINVAL;
+  const int nb = (int)((nc + kT - 1) / kT < 4096 ? (nc + kT - 1) / kT : 4096);
+  launch_restrict_levels(levels, nb, (cudaStream_t)stream, fine, coarse, nx, ny, nz, ns, nullptr, 0,
+                         0, 0);
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
+// fine = value of each cell's ancestor on the 2^levels coarser grid (levels
+// nearest prolongations in one pass).  Asynchronous.
+extern "C" int tpfa_prolong_levels(const float* coarse, float* fine, int nx, int ny, int nz, int ns,
+                                   int levels, void* stream) {
+  if (levels < 1 || levels > kMaxLevels || ns < 1) return TPFA_EINVAL;
+  const int f = 1 << levels;
+  if (nx < f || ny < f || nz < f || nx % f || ny % f || nz % f) return TPFA_EINVAL;
+  if ((double)nx * ny * nz * ns >= 2147483647.0) return TPFA_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPFA_ECUDA;
+  const size_t n = (size_t)nx * ny * nz * ns, nc = n >> (3 * levels);
+  if (!tpfa::dev_ok(fine, n * 4, 8, dev) || !tpfa::dev_ok(coarse, nc * 4, 4, dev))
+    return TPFA_EINVAL;
+  const int nb = (int)((n / 2 + kT - 1) / kT < 4096 ? (n / 2 + kT - 1) / kT : 4096);
+  launch_prolong_levels(levels, nb, (cudaStream_t)stream, coarse, fine, nx, ny, nz, ns, nullptr, 0,
+                        0, 0);
   return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
 }

@@ -80,6 +80,8 @@ SIGNATURES = {
     "tpfa_jacobi_split": (C.c_int, [_P] * 7),
     "tpfa_restrict2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _P]),
     "tpfa_prolong2": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
+    "tpfa_restrict_levels": (C.c_int, [_P, _P] + [C.c_int] * 5 + [_P]),
+    "tpfa_prolong_levels": (C.c_int, [_P, _P] + [C.c_int] * 5 + [_P]),
     "fcg_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int64,
                             C.POINTER(_Info), C.POINTER(C.c_int), _P]),
     "tpfa_build_trans_bf16": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
@@ -517,6 +519,35 @@ def prolong2(coarse, shape, fine=None):
         _check(lib().tpfa_prolong2(_ptr(coarse, torch.float32, n // 8, dev, "coarse"),
                                    _ptr(fine, torch.float32, n, dev, "fine"), nx, ny, nz, ns,
                                    _stream(dev)), "tpfa_prolong2")
+    return fine
+
+
+def restrict_levels(fine, shape, levels, coarse=None):
+    """The 2^levels coarser grid in one pass (block means); shape = (nx, ny, nz, ns)."""
+    nx, ny, nz, ns = shape
+    dev = fine.device
+    nc = (nx * ny * nz * ns) >> (3 * levels)
+    if coarse is None:
+        coarse = torch.empty(nc, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_restrict_levels(_ptr(fine, torch.float32, nx * ny * nz * ns, dev, "fine"),
+                                          _ptr(coarse, torch.float32, nc, dev, "coarse"), nx, ny,
+                                          nz, ns, int(levels), _stream(dev)), "tpfa_restrict_levels")
+    return coarse
+
+
+def prolong_levels(coarse, shape, levels, fine=None):
+    """fine[c] = coarse value of c's ancestor on the 2^levels coarser grid."""
+    nx, ny, nz, ns = shape
+    dev = coarse.device
+    n = nx * ny * nz * ns
+    if fine is None:
+        fine = torch.empty(n, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_prolong_levels(_ptr(coarse, torch.float32, n >> (3 * levels), dev,
+                                              "coarse"),
+                                         _ptr(fine, torch.float32, n, dev, "fine"), nx, ny, nz, ns,
+                                         int(levels), _stream(dev)), "tpfa_prolong_levels")
     return fine
 
 

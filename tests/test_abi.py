@@ -96,6 +96,8 @@ def test_unet_parameter_layout_without_a_gpu(tp):
     assert L.tpfa_unet_set_params(None, None, None) == tp.EINVAL
     assert L.tpfa_unet_forward(None, None, None, None, None) == tp.EINVAL
     assert L.tpfa_unet_forward_samples(None, 1, None, None, None, None) == tp.EINVAL
+    assert L.tpfa_restrict_levels(None, None, 8, 8, 8, 1, 0, None) == tp.EINVAL
+    assert L.tpfa_prolong_levels(None, None, 8, 8, 8, 1, 4, None) == tp.EINVAL
     assert L.tpfa_unet_backward(None, None, None, None) == tp.EINVAL
     assert L.tpfa_conv3d_select(7) == tp.EINVAL
     assert L.tpfa_adam_step(None, None, None, None, 0, 1, 1e-3, 0.9, 0.999, 1e-8, None) == tp.EINVAL

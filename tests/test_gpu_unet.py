@@ -286,6 +286,43 @@ def test_restrict_prolong_match_oracle(tp):
                           .astype(np.float32))
 
 
+@pytest.mark.parametrize("levels,shape", [(1, (8, 6, 4, 2)), (2, (16, 8, 12, 2)),
+                                          (3, (16, 16, 8, 1))])
+def test_restrict_prolong_levels_equal_repeated_single_level(tp, levels, shape):
+    """The one-pass restriction to the 2^levels coarser grid (what the solvers
+    use) is bit-identical to `levels` tpfa_restrict2 passes, the one-pass
+    prolongation to `levels` tpfa_prolong2 passes; and both agree with the
+    oracle's restrict2 / prolong2 applied `levels` times."""
+    nx, ny, nz, ns = shape
+    rng = np.random.default_rng(31 + levels)
+    f = rng.standard_normal(nx * ny * nz * ns).astype(np.float32)
+    F = torch.from_numpy(f).cuda()
+    c = F
+    for l in range(levels):
+        c = tp.restrict2(c, (nx >> l, ny >> l, nz >> l, ns))
+    fused = tp.restrict_levels(F, shape, levels)
+    assert torch.equal(fused, c)
+    ref = f.astype(np.float64).reshape(ns, nz, ny, nx)
+    for _ in range(levels):
+        ref = U.restrict2(ref)
+    np.testing.assert_allclose(fused.cpu().double().numpy(), ref.ravel(), rtol=1e-5, atol=1e-6)
+    cc = rng.standard_normal(c.numel()).astype(np.float32)
+    CC = torch.from_numpy(cc).cuda()
+    p = CC
+    for l in reversed(range(levels)):
+        p = tp.prolong2(p, (nx >> l, ny >> l, nz >> l, ns))
+    fused_p = tp.prolong_levels(CC, shape, levels)
+    assert torch.equal(fused_p, p)
+    up = cc.astype(np.float64).reshape(ns, nz >> levels, ny >> levels, nx >> levels)
+    for _ in range(levels):
+        up = U.prolong2(up)
+    assert np.array_equal(fused_p.cpu().double().numpy(), up.ravel())
+    # the prolongations write pairs of cells: a fine vector off an 8-byte boundary is refused
+    buf = torch.zeros(nx * ny * nz * ns + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(tp.TpfaError):
+        tp.prolong2(c if levels == 1 else tp.restrict2(F, shape), shape, fine=buf[1:])
+
+
 @pytest.mark.parametrize("shape", [(13, 11, 7), (9, 5, 3)])
 def test_fcg_ragged_sizes(tp, oracle_mod, shape):
     """Cell counts that are not a multiple of 4 (vector kernels' scalar tail,
