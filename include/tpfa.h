@@ -341,6 +341,13 @@ int tpfa_conv3d_select(int kernel);
 /* Waits for the stream; TPFA_EINTERNAL (and clears the flag) if any
  * tensor-core wait of the convolution kernels gave up since the last call. */
 int tpfa_net_status(void* stream);
+/* Test hook for that failure path: one block waits, with the same bounded
+ * wait the tensor-core kernels use, on an mbarrier phase that nothing
+ * completes, gives up after `polls` polls (1 <= polls <= 2^22) and records
+ * the timeout as a stalled tensor-core kernel would; the next
+ * tpfa_net_status returns TPFA_EINTERNAL and clears it.  Allocates no
+ * tensor memory; the context stays usable.  Asynchronous. */
+int tpfa_tc_wait_probe(uint32_t polls, void* stream);
 
 /*
  * The 3-level U-Net preconditioner M(r) = rms(r) * net(r / rms(r), ln K):

@@ -767,6 +767,29 @@ extern "C" int tpfa_conv3d_select(int kernel) {
   return TPFA_OK;
 }
 
+namespace tpfa {
+namespace net {
+// One block waits, with the bounded wait of every tensor-core kernel here, for
+// an mbarrier phase that no thread completes (one arrival expected, none
+// made): the wait gives up after `polls` polls and records the timeout the way
+// a stalled tensor-core kernel does.  No tensor memory, no tensor-core work.
+__global__ void wait_probe_kernel(uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = tc::mbar_wait(&bar, 0, polls);
+  if (!ok && threadIdx.x == 0) atomicOr(&g_tc_timeout, 1);
+}
+}  // namespace net
+}  // namespace tpfa
+
+// Test hook for the failure path of the bounded waits (see the header).
+extern "C" int tpfa_tc_wait_probe(uint32_t polls, void* stream) {
+  if (polls < 1 || polls > tpfa::net::kWaitLimit) return TPFA_EINVAL;
+  tpfa::net::wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(polls);
+  return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
+}
+
 // Waits for the stream, then reports (and clears) a tensor-core wait that
 // gave up in any kernel of this library since the last call.
 extern "C" int tpfa_net_status(void* stream) {

@@ -65,6 +65,7 @@ SIGNATURES = {
     "tpfa_conv3d_bf16": (C.c_int, [_P, _P, _P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_conv3d_wgrad_bf16": (C.c_int, [_P, _P, _P] + [C.c_int] * 7 + [_P]),
     "tpfa_net_status": (C.c_int, [_P]),
+    "tpfa_tc_wait_probe": (C.c_int, [C.c_uint32, _P]),
     "tpfa_conv3d_select": (C.c_int, [C.c_int]),
     "tpfa_unet_param_count": (C.c_int64, []),
     "tpfa_unet_create": (C.c_int, [C.c_int] * 5 + [C.POINTER(C.c_void_p)]),

@@ -97,6 +97,8 @@ def test_unet_parameter_layout_without_a_gpu(tp):
     assert L.tpfa_unet_forward(None, None, None, None, None) == tp.EINVAL
     assert L.tpfa_unet_forward_samples(None, 1, None, None, None, None) == tp.EINVAL
     assert L.tpfa_restrict_levels(None, None, 8, 8, 8, 1, 0, None) == tp.EINVAL
+    assert L.tpfa_tc_wait_probe(0, None) == tp.EINVAL
+    assert L.tpfa_tc_wait_probe((1 << 22) + 1, None) == tp.EINVAL
     assert L.tpfa_prolong_levels(None, None, 8, 8, 8, 1, 4, None) == tp.EINVAL
     assert L.tpfa_unet_backward(None, None, None, None) == tp.EINVAL
     assert L.tpfa_conv3d_select(7) == tp.EINVAL

@@ -148,3 +148,23 @@ def test_conv_rejects_bad_arguments(tp):
     host = torch.zeros((tp.halo_voxels(4, 4, 4), 16), dtype=torch.bfloat16)
     assert lib.tpfa_conv3d_bf16(host.data_ptr(), w.data_ptr(), None, None, Y.data_ptr(), 4, 4, 4,
                                 1, 16, 16, 0, st) == tp.EINVAL
+
+
+def test_bounded_wait_timeout_is_reported_and_cleared(tp):
+    """Failure path of the tensor-core kernels' bounded mbarrier waits: a wait
+    that nothing completes gives up, the host reads TPFA_EINTERNAL from
+    tpfa_net_status, the flag is cleared, and the context keeps working."""
+    dev = torch.device("cuda")
+    stream = tp._stream(dev)
+    tp.net_status()  # nothing pending
+    assert tp.lib().tpfa_tc_wait_probe(1000, stream) == tp.OK
+    assert tp.lib().tpfa_net_status(stream) == tp.EINTERNAL
+    assert tp.lib().tpfa_net_status(stream) == tp.OK  # reported once, then cleared
+    # the context is still usable: a convolution runs and reports no timeout
+    V = tp.halo_voxels(8, 8, 8, 1)
+    x = torch.ones(V * 16, dtype=torch.bfloat16, device=dev)
+    w = torch.ones(27 * 16 * 16, dtype=torch.bfloat16, device=dev)
+    y = torch.zeros(V * 16, dtype=torch.bfloat16, device=dev)
+    tp.conv3d_bf16(x, w, y, (8, 8, 8, 1), 16, 16)
+    tp.net_status()
+    assert float(y.float().max()) > 0.0
