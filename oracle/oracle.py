@@ -28,14 +28,14 @@ _LIB_OVERRIDE = os.environ.get("TPFA_ORACLE_LIB")
 
 def compile_to(src: str, out: str) -> str:
     tmp = out + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                            "-o", tmp, src, "-lm"])
     os.replace(tmp, out)
     return out
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add, -O2)."""
+    """Compile the oracle with gcc (no fused multiply-add, -O2, OpenMP)."""
     if _LIB_OVERRIDE:
         return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -70,6 +70,10 @@ def _L():
         _lib.orc_cg.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_double), P, C.c_int64]
         _lib.orc_cg.restype = C.c_int
+        _lib.orc_pcg_jacobi.argtypes = _lib.orc_cg.argtypes
+        _lib.orc_pcg_jacobi.restype = C.c_int
+        _lib.orc_threads.argtypes = []
+        _lib.orc_threads.restype = C.c_int
         _lib.orc_cholesky_solve.argtypes = [C.c_int64, P, P, P]
         _lib.orc_cholesky_solve.restype = C.c_int
     return _lib
@@ -226,6 +230,26 @@ def cg(A: CSR, b, x0=None, tol=1e-12, maxit=None, history=0):
     return x, st, it.value, rr.value
 
 
+def pcg_jacobi(A: CSR, b, x0=None, tol=1e-12, maxit=None, history=0):
+    """CG preconditioned with diag(A).  Returns (x, status, iterations,
+    recursive relative residual[, history]) like cg()."""
+    b = _f64(b)
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    maxit = 10 * A.n + 10 if maxit is None else int(maxit)
+    it, rr = C.c_int64(0), C.c_double(0.0)
+    hist = np.zeros((history, A.n)) if history else None
+    st = _L().orc_pcg_jacobi(A.n, _p(A.rowptr), _p(A.cols), _p(A.vals), _p(b), _p(x),
+                             float(tol), maxit, C.byref(it), C.byref(rr), _p(hist), int(history))
+    if history:
+        return x, st, it.value, rr.value, hist
+    return x, st, it.value, rr.value
+
+
+def threads():
+    """Host threads the oracle's parallel loops use (OpenMP)."""
+    return int(_L().orc_threads())
+
+
 def cholesky_solve(Adense, b):
     A = np.array(Adense, dtype=np.float64, order="C")
     x = np.empty(A.shape[0])
@@ -235,11 +259,13 @@ def cholesky_solve(Adense, b):
     return x
 
 
-def solve(g: Grid, K, mask=None, d=None, q=None, pD=None, tol=1e-12, maxit=None, x0=None):
-    """Assemble and solve A p = b; returns (p, iterations)."""
+def solve(g: Grid, K, mask=None, d=None, q=None, pD=None, tol=1e-12, maxit=None, x0=None,
+          jacobi=False):
+    """Assemble and solve A p = b (plain CG, or Jacobi PCG with jacobi=True);
+    returns (p, iterations)."""
     A = assemble(g, K, mask, d)
     b = rhs(g, K, mask, q, pD)
-    x, st, it, _ = cg(A, b, x0=x0, tol=tol, maxit=maxit)
+    x, st, it, _ = (pcg_jacobi if jacobi else cg)(A, b, x0=x0, tol=tol, maxit=maxit)
     if st < 0:
         raise RuntimeError(f"oracle CG failed with status {st}")
     return x, it

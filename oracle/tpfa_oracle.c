@@ -35,12 +35,33 @@
  * Layout: flat index c = i + nx*(j + ny*k), X innermost, Z outermost
  * (Section IV).  Face order for every sum: -x, +x, -y, +y, -z, +z.
  *
- * Compile with -ffp-contract=off so that no multiply-add is fused.
+ * Compile with -ffp-contract=off so that no multiply-add is fused, and with
+ * -fopenmp: the matrix-vector product, the vector updates and the CSR
+ * assembly run their rows on all host threads (each row is computed by one
+ * thread, so the values do not depend on the thread count); dot products add
+ * fixed blocks of DOT_BLOCK terms each, then the block sums in order, so
+ * they do not depend on the thread count either.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define DOT_BLOCK 4096
+/* loops over fewer rows run on one thread (thread start-up would dominate) */
+#define PAR_MIN 65536
+
+/* threads the parallel loops use */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 typedef struct {
   int64_t nx, ny, nz;
@@ -122,18 +143,31 @@ static int orc_row_literal(const orc_grid* g, const double* K, const uint8_t* ma
   return m;
 }
 
-/* CSR assembly.  rowptr has N+1 entries, cols/vals room for 7N. Returns nnz. */
+/* CSR assembly.  rowptr has N+1 entries, cols/vals room for 7N. Returns nnz.
+ * Rows are first built at a fixed stride of 7 (in parallel), then packed in
+ * row order. */
 int64_t orc_assemble(const orc_grid* g, const double* K, const uint8_t* mask, const double* d,
                      double d0, int literal, int64_t* rowptr, int64_t* cols, double* vals) {
-  int64_t N = ncells(g), nnz = 0;
-  rowptr[0] = 0;
+  int64_t N = ncells(g);
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
   for (int64_t c = 0; c < N; ++c) {
-    int m = literal ? orc_row_literal(g, K, mask, d, d0, c, cols + nnz, vals + nnz)
-                    : orc_row(g, K, mask, d, d0, c, cols + nnz, vals + nnz);
-    nnz += m;
-    rowptr[c + 1] = nnz;
+    int m = literal ? orc_row_literal(g, K, mask, d, d0, c, cols + 7 * c, vals + 7 * c)
+                    : orc_row(g, K, mask, d, d0, c, cols + 7 * c, vals + 7 * c);
+    rowptr[c + 1] = m;
   }
-  return nnz;
+  rowptr[0] = 0;
+  for (int64_t c = 0; c < N; ++c) rowptr[c + 1] += rowptr[c];
+  /* pack: row c moves from 7c down to rowptr[c] <= 7c, so rows are moved in
+   * increasing order and never overwrite a row not yet moved */
+  for (int64_t c = 0; c < N; ++c) {
+    int64_t m = rowptr[c + 1] - rowptr[c];
+    if (rowptr[c] == 7 * c) continue;
+    for (int64_t e = 0; e < m; ++e) {
+      cols[rowptr[c] + e] = cols[7 * c + e];
+      vals[rowptr[c] + e] = vals[7 * c + e];
+    }
+  }
+  return rowptr[N];
 }
 
 /* Right-hand side of A p = b: Dirichlet rows carry p^D (Eq. 3); interior rows
@@ -253,6 +287,7 @@ void orc_net_flux(const orc_grid* g, const double* K, const double* x, double* y
 
 void orc_spmv(int64_t N, const int64_t* rowptr, const int64_t* cols, const double* vals,
               const double* x, double* y) {
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
   for (int64_t r = 0; r < N; ++r) {
     double s = 0.0;
     for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) s += vals[e] * x[cols[e]];
@@ -260,9 +295,36 @@ void orc_spmv(int64_t N, const int64_t* rowptr, const int64_t* cols, const doubl
   }
 }
 
+/* sum of a[i] b[i]: each block of DOT_BLOCK terms is summed in index order,
+ * then the block sums in block order */
 static double dot(int64_t N, const double* a, const double* b) {
+  int64_t nb = (N + DOT_BLOCK - 1) / DOT_BLOCK;
+  if (nb <= 1) {
+    double s = 0.0;
+    for (int64_t i = 0; i < N; ++i) s += a[i] * b[i];
+    return s;
+  }
+  double* part = (double*)malloc(sizeof(double) * (size_t)nb);
+  if (part == NULL) {
+    double s = 0.0;
+    for (int64_t blk = 0; blk < nb; ++blk) {
+      double t = 0.0;
+      int64_t e = (blk + 1) * DOT_BLOCK < N ? (blk + 1) * DOT_BLOCK : N;
+      for (int64_t i = blk * DOT_BLOCK; i < e; ++i) t += a[i] * b[i];
+      s += t;
+    }
+    return s;
+  }
+#pragma omp parallel for schedule(static) if (nb >= PAR_MIN / DOT_BLOCK)
+  for (int64_t blk = 0; blk < nb; ++blk) {
+    double t = 0.0;
+    int64_t e = (blk + 1) * DOT_BLOCK < N ? (blk + 1) * DOT_BLOCK : N;
+    for (int64_t i = blk * DOT_BLOCK; i < e; ++i) t += a[i] * b[i];
+    part[blk] = t;
+  }
   double s = 0.0;
-  for (int64_t i = 0; i < N; ++i) s += a[i] * b[i];
+  for (int64_t blk = 0; blk < nb; ++blk) s += part[blk];
+  free(part);
   return s;
 }
 
@@ -290,6 +352,7 @@ int orc_cg(int64_t N, const int64_t* rowptr, const int64_t* cols, const double* 
     return 0;
   }
   orc_spmv(N, rowptr, cols, vals, x, Ap);
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
   for (int64_t i = 0; i < N; ++i) { r[i] = b[i] - Ap[i]; p[i] = r[i]; }
   double rr = dot(N, r, r);
   for (k = 0; k < maxit; ++k) {
@@ -298,9 +361,11 @@ int orc_cg(int64_t N, const int64_t* rowptr, const int64_t* cols, const double* 
     double pAp = dot(N, p, Ap);
     if (!(pAp > 0.0)) { status = -4; break; }
     double alpha = rr / pAp;
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
     for (int64_t i = 0; i < N; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * Ap[i]; }
     double rr_new = dot(N, r, r);
     double beta = rr_new / rr;
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
     for (int64_t i = 0; i < N; ++i) p[i] = r[i] + beta * p[i];
     rr = rr_new;
     if (hist_x != NULL && k < hist_len) memcpy(hist_x + k * N, x, sizeof(double) * (size_t)N);
@@ -309,6 +374,78 @@ int orc_cg(int64_t N, const int64_t* rowptr, const int64_t* cols, const double* 
   *iters = k;
   *relres = sqrt(rr) / bn;
   free(r); free(p); free(Ap);
+  return status;
+}
+
+/* Conjugate gradient preconditioned with M = diag(A) (Jacobi), in the
+ * textbook order:
+ *   r0 = b - A x0, z0 = M^-1 r0, p0 = z0;
+ *   alpha = r'z / p'Ap;  x += alpha p;  r -= alpha Ap;  z+ = M^-1 r+;
+ *   beta = r+'z+ / r'z;  p = z+ + beta p.
+ * Not part of the paper (Alg. 1 is unpreconditioned); the oracle uses it to
+ * reach its FP64 reference solution on high-contrast fields, where plain CG
+ * needs far more iterations.  M is read from the diagonal entries of the
+ * CSR.  Stopping rule, return codes and history as orc_cg. */
+int orc_pcg_jacobi(int64_t N, const int64_t* rowptr, const int64_t* cols, const double* vals,
+                   const double* b, double* x, double tol, int64_t maxit, int64_t* iters,
+                   double* relres, double* hist_x, int64_t hist_len) {
+  double* r = (double*)malloc(sizeof(double) * (size_t)N);
+  double* z = (double*)malloc(sizeof(double) * (size_t)N);
+  double* p = (double*)malloc(sizeof(double) * (size_t)N);
+  double* Ap = (double*)malloc(sizeof(double) * (size_t)N);
+  double* minv = (double*)malloc(sizeof(double) * (size_t)N);
+  if (!r || !z || !p || !Ap || !minv) {
+    free(r); free(z); free(p); free(Ap); free(minv);
+    return -2;
+  }
+  int status = 1;
+  int64_t k = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    double dg = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (cols[e] == i) dg += vals[e];
+    if (!(dg > 0.0)) status = -4;
+    minv[i] = 1.0 / dg;
+  }
+  double bn = sqrt(dot(N, b, b));
+  if (status == -4 || bn == 0.0) {
+    if (bn == 0.0 && status != -4) {
+      for (int64_t i = 0; i < N; ++i) x[i] = 0.0;
+      status = 0;
+    }
+    *iters = 0; *relres = bn == 0.0 ? 0.0 : NAN;
+    free(r); free(z); free(p); free(Ap); free(minv);
+    return status;
+  }
+  orc_spmv(N, rowptr, cols, vals, x, Ap);
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
+  for (int64_t i = 0; i < N; ++i) { r[i] = b[i] - Ap[i]; z[i] = minv[i] * r[i]; p[i] = z[i]; }
+  double rz = dot(N, r, z);
+  double rr = dot(N, r, r);
+  for (k = 0; k < maxit; ++k) {
+    if (sqrt(rr) <= tol * bn) { status = 0; break; }
+    orc_spmv(N, rowptr, cols, vals, p, Ap);
+    double pAp = dot(N, p, Ap);
+    if (!(pAp > 0.0)) { status = -4; break; }
+    double alpha = rz / pAp;
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
+    for (int64_t i = 0; i < N; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+      z[i] = minv[i] * r[i];
+    }
+    double rz_new = dot(N, r, z);
+    rr = dot(N, r, r);
+    double beta = rz_new / rz;
+#pragma omp parallel for schedule(static) if (N >= PAR_MIN)
+    for (int64_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz_new;
+    if (hist_x != NULL && k < hist_len) memcpy(hist_x + k * N, x, sizeof(double) * (size_t)N);
+  }
+  if (status == 1 && sqrt(rr) <= tol * bn) status = 0;
+  *iters = k;
+  *relres = sqrt(rr) / bn;
+  free(r); free(z); free(p); free(Ap); free(minv);
   return status;
 }
 

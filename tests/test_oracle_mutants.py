@@ -31,6 +31,11 @@ MUTANTS = [
      "b[c] = 0.0; continue;", 1),
     ("cg_beta_inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;", 1),
     ("cg_residual_update", "r[i] -= alpha * Ap[i]; }", "r[i] -= alpha * p[i]; }", 1),
+    ("pcg_unpreconditioned_z", "      z[i] = minv[i] * r[i];\n", "      z[i] = r[i];\n", 1),
+    ("pcg_beta_inverted", "double beta = rz_new / rz;", "double beta = rz / rz_new;", 1),
+    ("pcg_direction_from_r", "p[i] = z[i] + beta * p[i];", "p[i] = r[i] + beta * p[i];", 1),
+    ("dot_block_dropped", "for (int64_t blk = 0; blk < nb; ++blk) s += part[blk];",
+     "for (int64_t blk = 1; blk < nb; ++blk) s += part[blk];", 1),
 ]
 
 

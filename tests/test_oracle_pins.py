@@ -240,6 +240,137 @@ def test_literal_eq6_gives_same_iterates(oracle_mod):
     np.testing.assert_allclose(xs, xl, rtol=0, atol=1e-10)
 
 
+# --- Jacobi-preconditioned CG (the oracle's reference solver on high contrast)
+
+@pytest.mark.parametrize("shape,seed", [((5, 4, 3), 0), ((8, 6, 5), 1)])
+def test_pcg_jacobi_matches_library_dense_solve(oracle_mod, shape, seed):
+    O = oracle_mod
+    nx, ny, nz = shape
+    g = _grid(O, nx, ny, nz, dx=0.8, dy=1.3, dz=1.0, mu=0.9)
+    K = synth.channelized_field(nx, ny, nz, 2.0, seed, n_channels=1, width=2, thickness=2,
+                                amplitude=1.0, wavelength=8.0, contrast=1e4)
+    mask, pD = synth.dirichlet_faces(nx, ny, nz, "y", 1.5, 0.0)
+    A = O.assemble(g, K, mask, 1e-3)
+    b = O.rhs(g, K, mask, None, pD)
+    ref = np.linalg.solve(A.dense(), b)
+    x, st, it, rel = O.pcg_jacobi(A, b, tol=1e-14)
+    assert st == 0 and rel <= 1e-14
+    np.testing.assert_allclose(x, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_pcg_jacobi_iterates_are_cg_on_the_scaled_system(oracle_mod):
+    """PCG with M = diag(A) produces x_k = S xh_k, where xh_k are the iterates
+    of plain CG on the symmetrically scaled system (S A S) xh = S b with
+    S = diag(A)^(-1/2) (the textbook equivalence of preconditioned CG).  The
+    scaled system is assembled here by scaling the CSR values and solved by
+    the oracle's plain CG, which the pins above tie to a library solve."""
+    O = oracle_mod
+    nx, ny, nz = 6, 5, 4
+    g = _grid(O, nx, ny, nz)
+    K = synth.lognormal_field(nx, ny, nz, 2.0, 9)
+    mask, pD = synth.dirichlet_faces(nx, ny, nz, "z", 1.0, 0.5)
+    A = O.assemble(g, K, mask, 0.02)
+    b = O.rhs(g, K, mask, None, pD)
+    diag = A.dense().diagonal()
+    S = 1.0 / np.sqrt(diag)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    As = O.CSR(A.n, A.rowptr, A.cols, A.vals * S[rows] * S[A.cols])
+    H = 10
+    _, _, _, _, hp = O.pcg_jacobi(A, b, tol=0.0, maxit=H, history=H)
+    _, _, _, _, hc = O.cg(As, S * b, tol=0.0, maxit=H, history=H)
+    np.testing.assert_allclose(hp, hc * S[None, :], rtol=0, atol=1e-12 * np.abs(hp).max())
+
+
+@pytest.mark.parametrize("solver", ["cg", "pcg_jacobi"])
+def test_solvers_match_library_sparse_solve_beyond_one_dot_block(oracle_mod, solver):
+    """A grid of 72,000 cells (many blocks of the blocked dot products and
+    above the threshold of the parallel loops; two layers keep the library's
+    sparse factorisation fast): CG and Jacobi PCG agree with scipy's sparse
+    direct solve of the same CSR."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    O = oracle_mod
+    nx, ny, nz = 200, 180, 2
+    g = _grid(O, nx, ny, nz)
+    K = synth.lognormal_field(nx, ny, nz, 1.0, 12)
+    mask, pD = synth.dirichlet_faces(nx, ny, nz, "x", 1.0, 0.0)
+    A = O.assemble(g, K, mask, 1e-2)
+    b = O.rhs(g, K, mask, None, pD)
+    ref = sla.spsolve(sp.csr_matrix((A.vals, A.cols, A.rowptr), shape=(A.n, A.n)).tocsc(), b)
+    x, st, it, rel = getattr(O, solver)(A, b, tol=1e-13)
+    assert st == 0 and rel <= 1e-13
+    np.testing.assert_allclose(x, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    # the recursive residual the solver reports is the true one (dot products intact)
+    assert np.linalg.norm(b - A.matvec(x)) <= 2e-13 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("solver", ["cg", "pcg_jacobi"])
+def test_iterates_are_galerkin_solutions_on_krylov_spaces(oracle_mod, solver):
+    """The k-th CG iterate (x0 = 0) minimises the A-norm of the error over the
+    Krylov space span{z0, B z0, ..., B^(k-1) z0}, with B = A, z0 = b for CG and
+    B = M^-1 A, z0 = M^-1 b for Jacobi PCG: the defining property of the
+    method, independent of its recurrences.  Here the projected system is
+    solved with numpy on an orthonormal basis of the space, for k = 1..5, on a
+    72,000-cell grid (so every dot product of the solver spans many blocks)."""
+    O = oracle_mod
+    nx, ny, nz = 200, 180, 2
+    g = _grid(O, nx, ny, nz)
+    K = synth.lognormal_field(nx, ny, nz, 1.0, 13)
+    A = O.assemble(g, K, None, 0.05)
+    b = synth.uniform(13, 4, np.arange(g.n)) - 0.5
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    dg = np.zeros(A.n)
+    np.add.at(dg, rows[A.cols == rows], A.vals[A.cols == rows])
+    minv = 1.0 / dg
+    pre = (lambda v: minv * v) if solver == "pcg_jacobi" else (lambda v: v)
+    H = 5
+    _, _, _, _, hist = getattr(O, solver)(A, b, tol=0.0, maxit=H, history=H)
+    V = [pre(b)]
+    for k in range(1, H + 1):
+        Q, _ = np.linalg.qr(np.stack(V, axis=1))
+        AQ = np.stack([A.matvec(Q[:, i]) for i in range(k)], axis=1)
+        y = np.linalg.solve(Q.T @ AQ, Q.T @ b)
+        xk = Q @ y
+        np.testing.assert_allclose(hist[k - 1], xk, rtol=0, atol=1e-9 * np.abs(xk).max())
+        V.append(pre(A.matvec(V[-1])))
+
+
+def test_pcg_jacobi_terminates_within_n(oracle_mod):
+    O = oracle_mod
+    g = _grid(O, 4, 4, 4)
+    K = synth.lognormal_field(4, 4, 4, 3.0, 2)
+    A = O.assemble(g, K, None, 0.05)
+    b = synth.uniform(2, 5, np.arange(g.n))
+    x, st, it, rel = O.pcg_jacobi(A, b, tol=1e-12)
+    assert st == 0 and it <= g.n
+    assert np.linalg.norm(b - A.matvec(x)) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_parallel_loops_do_not_depend_on_the_thread_count(oracle_mod, tmp_path):
+    """Dot products sum fixed blocks in a fixed order and every row is
+    computed by one thread: a solve gives bit-identical iterates with one
+    thread and with all of them (a subprocess with OMP_NUM_THREADS=1)."""
+    import os
+    import subprocess
+    import sys
+    code = ("import numpy as np, sys; sys.path.insert(0, %r)\n"
+            "from oracle import oracle as O\n"
+            "from paper_2408_03452_gb300 import synth\n"
+            "g = O.Grid(50, 40, 35); K = synth.lognormal_field(50, 40, 35, 1.5, 4)\n"
+            "A = O.assemble(g, K, None, 1e-3); b = synth.uniform(1, 2, np.arange(g.n))\n"
+            "x, _, it, _ = O.pcg_jacobi(A, b, tol=1e-10)\n"
+            "y, _, it2, _ = O.cg(A, b, tol=1e-8)\n"
+            "np.save(sys.argv[1], np.concatenate([x, y, [it, it2]]))\n"
+            % os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    outs = []
+    for nt in ("1", str(max(2, os.cpu_count() or 2))):
+        f = str(tmp_path / f"out{nt}.npy")
+        subprocess.run([sys.executable, "-c", code, f], check=True,
+                       env=dict(os.environ, OMP_NUM_THREADS=nt))
+        outs.append(np.load(f))
+    assert np.array_equal(outs[0], outs[1])
+
+
 # --- consistency of the oracle's own views of the operator ------------------
 
 def test_coefficients_rows_and_apply_agree(oracle_mod):
