@@ -46,6 +46,9 @@ SWEEP_BYTES_PER_CELL = 48
 # 16-byte coefficient record, write A p
 APPLY_BYTES_PER_CELL = 24
 FALLBACK_HBM_GBS = 6800.0
+# nominal HBM3e bandwidth of one GB300 (the north star's "~8 TB/s"), for a
+# second roofline fraction beside the measured copy peak
+NOMINAL_HBM_GBS = 8000.0
 LEARNED_METRIC = "U-Net FCG cell-iterations/s"
 LEARNED_FCG_M = 2  # retained directions of flexible CG in the learned workload
 LEARNED_LEVELS = 2  # the network runs on the 2^levels coarser grid
@@ -89,13 +92,19 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="solves timed end to end with host buffers (0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="paper workload: skip the time-to-1e-8 solver comparison")
+    ap.add_argument("--window", type=int, default=1,
+                    help="paper workload: also time the oracle on the full grid (a 10-iteration "
+                         "window) when host memory allows (0 = skip)")
     ap.add_argument("--tile-vy", type=int, default=0)
     ap.add_argument("--tile-zc", type=int, default=-1)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--loop", type=int, default=0,
                     help="0: CUDA-graph while loop; 1: host-polled graph chunks")
-    ap.add_argument("--scheme", type=int, default=-1,
-                    help="CG sweep: 0 stores q = Ap (48 B/cell), 1 recomputes it (40 B/cell)")
+    ap.add_argument("--sweep", type=int, default=0,
+                    help="CG sweep kernel: 0 automatic, 1 cp.async-staged, 2 TMA-staged")
+    ap.add_argument("--tma-tile", type=int, default=-1, help="tile of the TMA-staged sweep")
     ap.add_argument("--probe-iters", type=int, default=0,
                     help="profiling aid: build the workload, run one solve capped at this many "
                          "CG iterations (host-polled chunks of 4), print its info, no timing")
@@ -132,15 +141,16 @@ def finish_args(a):
 # CPU oracle leg
 # ----------------------------------------------------------------------------
 
-SAMPLE = (128, 128, 64)
+SAMPLE = (256, 256, 128)
 SAMPLE_CHANNELS = (64, 64, 64)
 
 
 def oracle_step(O, iters, workload="paper"):
     """Oracle on a bounded sample of the same recipe: assemble the CSR of a
-    128x128x64 block (64^3 for the channelized recipe), build the
-    right-hand side, run `iters` CG iterations, evaluate the FP64 residual.
-    Returns cell-updates done."""
+    256x256x128 block (64^3 for the channelized recipe), build the
+    right-hand side, run `iters` CG iterations (Jacobi PCG on the
+    channelized recipe, whose plain CG barely moves), evaluate the FP64
+    residual.  Returns cell-updates done."""
     if workload == "learned":
         return oracle_fcg_step(iters)
     if workload == "channelized":
@@ -149,7 +159,7 @@ def oracle_step(O, iters, workload="paper"):
         g = O.Grid(nx, ny, nz)
         A = O.assemble(g, w["K"], w["mask"], 0.0)
         b = O.rhs(g, w["K"], w["mask"], None, w["pD"])
-        x, st, it, _ = O.cg(A, b, tol=0.0, maxit=iters)
+        x, st, it, _ = O.pcg_jacobi(A, b, tol=0.0, maxit=iters)
         float(np.linalg.norm(b - A.matvec(x)))
         return nx * ny * nz * it
     nx, ny, nz = SAMPLE
@@ -237,8 +247,52 @@ def metric_unit(workload):
 
 
 def oracle_cores(workload):
-    # the learned-preconditioner oracle runs numpy matrix products (BLAS threads)
-    return os.cpu_count() if workload == "learned" else 1
+    # the C oracle runs its rows on all host threads (OpenMP); the learned-
+    # preconditioner oracle runs numpy matrix products (BLAS threads)
+    if workload == "learned":
+        return os.cpu_count()
+    from oracle import oracle as O
+    return O.threads()
+
+
+def mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def oracle_window_estimate(w, iters=10):
+    """The oracle on the full benchmark grid: CSR assembly of all cells, the
+    right-hand side, then a window of `iters` CG iterations, timed.  A full
+    oracle solve at this size would take hours; the per-iteration time of the
+    window is reported as an estimate of its rate."""
+    from oracle import oracle as O
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    n = nx * ny * nz
+    need_gb = n * (7 * 16 + 8 + 7 * 8) / 1e9 + 4
+    have = mem_available_gb()
+    if have < need_gb:
+        return {"skipped": f"needs about {need_gb:.0f} GB of host memory, {have:.0f} GB available"}
+    O.build()
+    g = O.Grid(nx, ny, nz)
+    t = time.perf_counter()
+    A = O.assemble(g, w["K"], None, w["d"])
+    q = synth.dense_sources(n, w["src_idx"], w["src_val"])
+    b = O.rhs(g, w["K"], None, q, None)
+    t_asm = time.perf_counter() - t
+    t = time.perf_counter()
+    _, _, it, _ = O.cg(A, b, tol=0.0, maxit=iters)
+    t_cg = time.perf_counter() - t
+    del A, b, q
+    return {"kind": "estimate", "grid": [nx, ny, nz], "iterations": it,
+            "value": n * it / t_cg, "unit": UNIT, "s_per_iteration": t_cg / max(it, 1),
+            "assembly_and_rhs_s": t_asm, "cores": O.threads(),
+            "what": f"oracle CSR CG on the full grid: a window of {it} iterations of the solve, "
+                    f"timed after assembly; the per-iteration rate stands for the whole solve"}
 
 
 def cpu_baseline(target_s=12.0, workload="paper"):
@@ -249,7 +303,7 @@ def cpu_baseline(target_s=12.0, workload="paper"):
     units = oracle_step(O, iters, workload)
     dt = time.perf_counter() - t
     what = "FCG" if workload == "learned" else "CG"
-    how = "numpy" if workload == "learned" else "single-threaded C"
+    how = "numpy" if workload == "learned" else "C with OpenMP"
     return {"value": units / dt, "unit": metric_unit(workload)[1], "cores": oracle_cores(workload),
             "kind": "oracle",
             "sample": f"{sample_desc(workload)}: CSR assembly, RHS, {iters} {what} iterations, "
@@ -459,6 +513,131 @@ def time_conv(tpfa, dev, n, cin, cout, reps=10):
     e1.record(stream)
     tpfa.net_status(dev)
     return e0.elapsed_time(e1) / reps
+
+
+def time_to_1e8(dev, seed=0, n=256, tol=1e-8, ensemble=True, maxit=200000):
+    """The metric's comparison of solvers by time to an FP64 relative residual
+    of 1e-8, on one GPU, on a held-out n^3 lognormal (sigma 1.5) realization
+    with Dirichlet x ends: plain CG (Alg. 1), Jacobi PCG, Jacobi PCG on BF16
+    records (mixed precision) and flexible CG with the U-Net preconditioner
+    (trained first, untimed, at 64^3), each run once untimed and once timed
+    (CUDA events inside the call); with ensemble=True the same comparison on
+    the batched 96-instance ensemble."""
+    import torch
+    from paper_2408_03452_gb300 import learned, tpfa
+    t0 = time.perf_counter()
+    ds = learned.make_dataset(50, 40, 64)
+    P, hist = learned.train(ds, epochs=12, batch=16, lr=1e-3, levels=LEARNED_LEVELS)
+    train_s = time.perf_counter() - t0
+    n_pairs = len(ds.real)
+    del ds
+    torch.cuda.empty_cache()
+    ctx = tpfa.Context(n, n, n, device=dev)
+    ctx.set_option("fcg_m", LEARNED_FCG_M)
+    pr = learned.Problem(ctx, 777001 + seed, n, 1.5)
+    Kh, mh, _ = learned.realization(777001 + seed, n, 1.5)
+    c16 = ctx.build_trans_bf16(torch.from_numpy(Kh).to(dev), torch.from_numpy(mh).to(dev))
+    del Kh, mh
+    nn = n >> LEARNED_LEVELS
+    net = tpfa.UNet(nn, nn, nn, device=dev)
+    net.set_params(P)
+    x = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
+
+    def fcg():
+        x.zero_()
+        return ctx.fcg_solve(pr.coef, pr.coef64, pr.b, net=net, lnk=pr.lnk, x=x, tol=tol,
+                             maxit=maxit)[1]
+
+    def cg(precond, coef):
+        def run():
+            ctx.set_option("precond", precond)
+            x.zero_()
+            info = ctx.cg_solve(coef, pr.coef64, pr.b, x=x, tol=tol, maxit=maxit)[1]
+            ctx.set_option("precond", 0)
+            return info
+        return run
+
+    out = {"grid": [n, n, n], "tol": tol,
+           "workload": f"held-out {n}^3 lognormal sigma-1.5 realization, Dirichlet x ends",
+           "time_s": {}, "iters": {}, "rel_res_fp64": {}, "converged": {}}
+    for name, fn in (("plain_cg", cg(0, pr.coef)), ("jacobi_pcg", cg(1, pr.coef)),
+                     ("jacobi_pcg_bf16_records", cg(1, c16)), ("unet_fcg", fcg)):
+        fn()
+        info = fn()
+        out["time_s"][name] = info["total_ms"] / 1e3
+        out["iters"][name] = info["iters"]
+        out["rel_res_fp64"][name] = info["rel_res_fp64"]
+        out["converged"][name] = info["code"] == tpfa.OK
+    out["chosen"] = "unet_fcg"
+    out["speedup_vs_plain_cg"] = {k: out["time_s"]["plain_cg"] / v for k, v in out["time_s"].items()}
+    out["training"] = {"pairs": n_pairs, "seconds": train_s, "final_val_loss": hist["val_loss"][-1],
+                       "jacobi_loss": hist["jacobi_loss"], "untimed": True}
+    ctx.close()
+    del pr, net, x, c16
+    torch.cuda.empty_cache()
+    if ensemble:
+        e = learned.evaluate_ensemble(P, seed=seed, levels=LEARNED_LEVELS, fcg_m=LEARNED_FCG_M,
+                                      tol=tol)
+        out["ensemble"] = {k: e[k] for k in ("instances", "cells", "sizes")}
+        for k in ("plain_cg_batched", "jacobi_pcg_batched", "unet_fcg_batched"):
+            out["ensemble"][k] = {"s": e[k]["s"], "iters_min_max": e[k]["iters_min_max"],
+                                  "rel_res_fp64_max": e[k]["rel_res_fp64_max"],
+                                  "code": e[k]["code"]}
+    return out
+
+
+def channelized_steps(a, dev, n=64):
+    """GPU iterates after each FP64 refinement step on an n^3 grid of the
+    channelized recipe, with BF16 records and with FP32 records (Jacobi inner
+    CG both): one refinement step per call, each call continuing from the
+    previous iterate (which is what the refinement loop does)."""
+    import torch
+    from paper_2408_03452_gb300 import tpfa
+    w = synth.channelized(seed=a.seed, n=n)
+    runs = {}
+    with tpfa.Context(n, n, n, device=dev) as ctx:
+        ctx.set_option("precond", 1)
+        ctx.set_option("max_outer", 1)
+        K, mask, pD = (torch.from_numpy(w[k]).to(dev) for k in ("K", "mask", "pD"))
+        coef, coef64 = ctx.build_trans(K, mask, None, 0.0)
+        c16 = ctx.build_trans_bf16(K, mask, None, 0.0)
+        b = ctx.build_rhs(K, mask, None, pD)
+        for name, inner in (("bf16_records", c16), ("fp32_records", coef)):
+            x = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
+            steps = []
+            for _ in range(40):
+                x, info = ctx.cg_solve(inner, coef64, b, x=x, tol=a.tol, maxit=a.maxit, check=False)
+                steps.append({"x": x.cpu().numpy().copy(), "inner_iters": info["iters"],
+                              "rel_res_fp64": info["rel_res_fp64"]})
+                if info["code"] != tpfa.NOTCONV:
+                    break
+            runs[name] = steps
+    return {"n": n, "w": w, "runs": runs}
+
+
+def refinement_errors(sg):
+    """CPU-baseline leg of the channelized workload: the oracle's FP64
+    solution of the same grid (Jacobi PCG to 1e-13) and the error of every
+    GPU refinement step against it."""
+    from oracle import oracle as O
+    O.build()
+    n, w = sg["n"], sg["w"]
+    g = O.Grid(n, n, n)
+    t = time.perf_counter()
+    A = O.assemble(g, w["K"], w["mask"], 0.0)
+    b = O.rhs(g, w["K"], w["mask"], None, w["pD"])
+    xr, st, it, rel = O.pcg_jacobi(A, b, tol=1e-13)
+    dt = time.perf_counter() - t
+    nr = float(np.linalg.norm(xr))
+    out = {"grid": [n, n, n], "tol": None,
+           "oracle": {"solver": "FP64 Jacobi PCG to 1e-13", "iters": it, "status": st,
+                      "rel_res": rel, "seconds": dt, "cores": O.threads()}}
+    for name, steps in sg["runs"].items():
+        out[name] = [{"step": k + 1, "inner_iters": s_["inner_iters"],
+                      "rel_res_fp64": s_["rel_res_fp64"],
+                      "rel_err_vs_oracle": float(np.linalg.norm(s_["x"] - xr)) / nr}
+                     for k, s_ in enumerate(steps)]
+    return out
 
 
 def run_learned(a, dev, rank, local, barrier):
@@ -823,8 +1002,9 @@ def main():
     if a.tile_zc >= 0:
         ctx.set_option("tile_zc", a.tile_zc)
     ctx.set_option("loop", a.loop)
-    if a.scheme >= 0:
-        ctx.set_option("scheme", a.scheme)
+    ctx.set_option("sweep", a.sweep)
+    if a.tma_tile >= 0:
+        ctx.set_option("tma_tile", a.tma_tile)
     ctx.set_option("precond", a.precond)
     coef = torch.empty((n, 4), dtype=torch.float32, device=dev)
     coef64 = torch.empty((n, 4), dtype=torch.float64, device=dev)
@@ -909,6 +1089,28 @@ def main():
 
     ms_max, iters_all, e2e_ms_max, e2e_iters_all = combine_ranks(
         ms, iters, e2e[1] if e2e else 0.0, e2e[0] if e2e else 0.0, dev)
+    tiling = ctx.tiling(1 if coef16 is not None else 0)
+
+    # beside the timed steps (their clock has stopped): the metric's
+    # time-to-1e-8 comparison, and for the mixed-precision workload the
+    # other record type and the per-refinement-step errors
+    extras, steps_gpu = {}, None
+    if rank == 0 and a.workload == "paper" and not a.no_ttt:
+        extras["time_to_1e8"] = time_to_1e8(dev, a.seed)
+    if rank == 0 and a.workload == "channelized":
+        other = "f32" if a.inner == "bf16" else "bf16"
+        oc = coef if other == "f32" else ctx.build_trans_bf16(K, inp.get("mask"), None, d0)
+        cmp = {}
+        for rep in range(2):
+            x.zero_()
+            _, oi = ctx.cg_solve(oc, coef64, b, x=x, tol=a.tol, maxit=a.maxit, check=False)
+        cmp[other + "_records"] = {"time_to_tol_s": oi["total_ms"] / 1e3, "iters": oi["iters"],
+                                   "refinements": oi["outer"], "rel_res_fp64": oi["rel_res_fp64"],
+                                   "converged": oi["code"] == 0,
+                                   "sweep_ms": oi["inner_ms"] / max(oi["iters"], 1)}
+        extras["other_records"] = cmp
+        if not a.no_cpu:
+            steps_gpu = channelized_steps(a, dev)
 
     if rank == 0:
         value = cell_updates_per_s(n, iters_all, ms_max)
@@ -934,9 +1136,13 @@ def main():
             "roofline": {"kernel": "cg sweep (fused CG iteration)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
+                         "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                         "sweep_kernel": ["", "cp.async-staged", "TMA-staged"][tiling["kernel"]],
+                         "tiling": tiling,
                          "bytes_per_cell": bpc, "sweep_ms": sweep_ms,
                          "traffic": (sweep_traffic(nx, ny, nz)
-                                     if (coef16 is None and a.precond == 0 and a.scheme <= 0)
+                                     if (coef16 is None and a.precond == 0 and a.sweep == 1)
                                      else None)},
             "gpu_launches": launches,
         }
@@ -946,8 +1152,14 @@ def main():
                                                         for v in host.values())),
                           "d2h_bytes_per_step": int(n * 8), "steps": a.e2e_steps}
         out["clocks"] = clk
+        if extras:
+            out["config"].update(extras)
         if not a.no_cpu:
             out["cpu_baseline"] = cpu_baseline(workload=a.workload)
+            if a.workload == "paper" and a.window:
+                out["cpu_baseline"]["full_grid_window"] = oracle_window_estimate(w)
+            if a.workload == "channelized" and steps_gpu is not None:
+                out["config"]["refinement_steps"] = refinement_errors(steps_gpu)
         print(json.dumps(out))
     ctx.close()
     if world > 1:

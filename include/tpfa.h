@@ -91,19 +91,36 @@ enum tpfa_option {
   TPFA_OPT_TILE_ZC = 5,      /* planes per warp in the stencil sweeps, 0 = automatic              */
   TPFA_OPT_CHUNK = 6,        /* CG iterations per graph launch when TPFA_OPT_LOOP = 1 (default 32) */
   TPFA_OPT_STAGES = 7,       /* shared-memory plane stages per warp: 3 or 4 (default 4; 4 needs VY = 4) */
-  TPFA_OPT_SCHEME = 8,       /* CG sweep: 0 = stores q = A p (48 B/cell, default), 1 = recomputes it (40 B/cell) */
-  TPFA_OPT_STAGES40 = 9,     /* stages of the scheme-1 sweep: 4, 5 or 6 with 2 warps/block, 4 or 5 with 4 (default 5) */
-  TPFA_OPT_WARPS40 = 10,     /* warps per block of the scheme-1 sweep: 2 (default) or 4                  */
+  /* 8, 9, 10: retired (a CG sweep that recomputed q = A p at 40 B/cell was
+     measured slower than the stored-q sweep); tpfa_set_option refuses them */
   TPFA_OPT_INNER_RTOL_BF16 = 11, /* lower bound on the inner relative tolerance of cg_solve_bf16 (1e-3) */
-  TPFA_OPT_PRECOND = 12,     /* inner CG of cg_solve: 0 = unpreconditioned (Alg. 1, default),
-                                1 = Jacobi, M = diag(D) (FP32 records only; cg_solve_bf16 with
-                                it set returns TPFA_EINVAL)                                       */
+  TPFA_OPT_PRECOND = 12,     /* inner CG of cg_solve and cg_solve_bf16: 0 = unpreconditioned
+                                (Alg. 1, default), 1 = Jacobi, M = diag(D) (with BF16 records D
+                                is the diagonal the BF16 sweep forms; cg_solve_bf16 then
+                                allocates one FP32 vector of M^-1 on its first call)            */
   TPFA_OPT_FCG_M = 13,       /* fcg_solve: previous directions each new one is A-orthogonalised
                                 against, 1..16 (default 4)                                        */
-  TPFA_OPT_FCG_FALLBACK = 14 /* fcg_solve with a network, after breakdown or stagnation:
+  TPFA_OPT_FCG_FALLBACK = 14, /* fcg_solve with a network, after breakdown or stagnation:
                                 0 = unpreconditioned CG (default); 1 = drop the network, keep
                                 Jacobi                                                            */
+  TPFA_OPT_SWEEP = 15,       /* CG sweep kernel of cg_solve: 0 = automatic (default: the TMA-staged
+                                sweep for unpreconditioned CG on FP32 records when nx % 4 == 0,
+                                else the cp.async-staged sweep), 1 = cp.async-staged sweep,
+                                2 = TMA-staged sweep (cg_solve returns TPFA_EINVAL where it
+                                cannot run)                                                       */
+  TPFA_OPT_TMA_TILE = 16     /* tile of the TMA-staged sweep, 32 columns x rows per block:
+                                0 = 4 warps x 4 rows, 3 stages (default); 1 = 4 x 4, 4 stages;
+                                2 = 4 x 2, 4 stages; 3 = 8 x 2, 3 stages                         */
 };
+
+/* The stencil-sweep tiling a context uses, for inspection and tests.
+ * which: 0 = the CG loop of cg_solve with FP32 records, 1 = the CG loop of
+ * cg_solve_bf16, 2 = tpfa_apply.  out: host array of 6 values:
+ * kernel (1 = cp.async-staged sweep, 2 = TMA-staged sweep), rows per warp,
+ * shared-memory stages, compute warps per block, z-planes per run (zc),
+ * blocks per launch.  Returns TPFA_EINVAL for a NULL argument, a bad `which`
+ * or a requested TMA sweep that cannot run for this grid. */
+int tpfa_sweep_tiling(const tpfa_ctx* ctx, int which, int64_t* out);
 
 /* Create a context for one grid on the current CUDA device.  Allocates the
  * small reduction workspace (partials, scalars); the CG vectors are
@@ -240,8 +257,12 @@ int tpfa_apply_bf16(tpfa_ctx* ctx, const uint16_t* coef16, const float* p, float
 /* cg_solve with the BF16 operator inside the FP32 CG sweeps: each refinement
  * step solves A_bf16 e = r (relative tolerance max(tol/2 / current relative
  * residual, TPFA_OPT_INNER_RTOL_BF16)), then x += e and r = b - A x in FP64
- * with coef64.  Stops when the FP64 relative residual <= tol.  Arguments
- * and return codes as cg_solve. */
+ * with coef64.  Stops when the FP64 relative residual <= tol.  With
+ * TPFA_OPT_PRECOND = 1 the inner CG is Jacobi-preconditioned: M^-1 = 1/D per
+ * cell, D formed from the BF16 faces and E exactly as the sweep forms it,
+ * computed into a context vector at the start of each call (the sweep then
+ * reads 8 + 4 bytes of coefficients per cell instead of 16).  Arguments and
+ * return codes as cg_solve. */
 int cg_solve_bf16(tpfa_ctx* ctx, const uint16_t* coef16, const double* coef64, const double* b,
                   double* x, double tol, int64_t maxit, tpfa_cg_info* info, void* stream);
 
@@ -511,16 +532,20 @@ int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_nets, const
  * image, which every GPU that loads the library holds until the process
  * exits.
  *
- * grid  host pointer to the grid (same rules as tpfa_create).
+ * grid  host pointer to the grid, checked by the same rules as tpfa_create
+ *       (nx, ny, nz >= 1, the same size limits, dx, dy, dz, mu finite and
+ *       > 0); the geometry fields do not enter the operator application.
  * coef, p, Ap, pAp, stream: as for tpfa_apply.
  *
  * Limits and behaviour:
  *  - the grid must be tiled with at most 16384 blocks of the sweep kernel
  *    (4 warps of 30 x 4 columns each, z-runs lengthened as needed), i.e.
  *    ceil(nx/30) * ceil(ny/4) <= 65536; larger grids get TPFA_EINVAL.
- *  - the first call on a device looks up the workspace's device address
- *    (cudaGetSymbolAddress, no allocation); make that first call before any
- *    stream capture on that device.
+ *  - every call looks up the workspace's device address in the current
+ *    context (cudaGetSymbolAddress, no allocation), so a device reset or a
+ *    re-created primary context cannot leave a stale address behind.  The
+ *    first call on a device may load the library's device code into that
+ *    context; make that first call before any stream capture on the device.
  *  - all calls share the one workspace: calls whose kernels overlap on the
  *    GPU (different streams, or different host threads without ordering)
  *    race and give wrong pAp values.  The completion counter is cleared on

@@ -65,6 +65,7 @@ def _L():
         _lib.orc_face_trans.argtypes = [G, P, P, P, P]
         _lib.orc_extra_diagonal.argtypes = [G, P, P, P, C.c_double, P]
         _lib.orc_apply_rows.argtypes = [G, P, P, P, C.c_double, P, C.c_int64, P, P]
+        _lib.orc_abs_apply_rows.argtypes = [G, P, P, P, C.c_double, P, C.c_int64, P, P]
         _lib.orc_net_flux.argtypes = [G, P, P, P]
         _lib.orc_spmv.argtypes = [C.c_int64, P, P, P, P, P]
         _lib.orc_cg.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_int64,
@@ -143,7 +144,8 @@ def assemble(g: Grid, K, mask=None, d=None, literal=False) -> CSR:
     vals = np.empty(7 * n, np.float64)
     nnz = _L().orc_assemble(g._c(), _p(K), _p(mask), _p(da), d0, int(bool(literal)),
                             _p(rowptr), _p(cols), _p(vals))
-    return CSR(n, rowptr, cols[:nnz].copy(), vals[:nnz].copy())
+    # views of the first nnz entries (no copy: the paper-scale matrix is tens of GB)
+    return CSR(n, rowptr, cols[:nnz], vals[:nnz])
 
 
 def rhs(g: Grid, K, mask=None, q=None, pD=None, literal=False):
@@ -207,6 +209,17 @@ def apply_rows(g: Grid, K, mask, d, rows, x):
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     y = np.empty(len(rows))
     _L().orc_apply_rows(g._c(), _p(K), _p(mask), _p(da), d0, _p(rows), len(rows), _p(x), _p(y))
+    return y
+
+
+def abs_apply_rows(g: Grid, K, mask, d, rows, x):
+    """(|A| |x|) at the listed rows: the rounding scale of (A x) there."""
+    K, mask, x = _f64(K), _u8(mask), _f64(x)
+    da, d0 = _dargs(d)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(len(rows))
+    _L().orc_abs_apply_rows(g._c(), _p(K), _p(mask), _p(da), d0, _p(rows), len(rows), _p(x),
+                            _p(y))
     return y
 
 

@@ -270,6 +270,20 @@ void orc_apply_rows(const orc_grid* g, const double* K, const uint8_t* mask, con
   }
 }
 
+/* |A| |x| for the rows listed in idx: the sum of |a_ij| |x_j| over row i, the
+ * scale of the rounding error of any evaluation of (A x)_i. */
+void orc_abs_apply_rows(const orc_grid* g, const double* K, const uint8_t* mask, const double* d,
+                        double d0, const int64_t* idx, int64_t n, const double* x, double* y) {
+  int64_t cols[7];
+  double vals[7];
+  for (int64_t t = 0; t < n; ++t) {
+    int m = orc_row(g, K, mask, d, d0, idx[t], cols, vals);
+    double s = 0.0;
+    for (int e = 0; e < m; ++e) s += fabs(vals[e]) * fabs(x[cols[e]]);
+    y[t] = s;
+  }
+}
+
 /* Sum of T_KL (x_K - x_L) over all faces of each cell, ignoring the
  * Dirichlet set: the net flux leaving each cell for a pressure field x. */
 void orc_net_flux(const orc_grid* g, const double* K, const double* x, double* y) {

@@ -19,9 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libtpfa.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["api.cu", "batch.cu", "kernels_build.cu", "kernels_cg.cu", "kernels_cg40.cu",
-           "noalloc.cu", "tc_gemm.cu", "conv3d.cu", "unet.cu", "fcg.cu",
-           "fcg_batch.cu"]
+SOURCES = ["api.cu", "batch.cu", "kernels_build.cu", "kernels_cg.cu", "sweep_tma.cu", "noalloc.cu",
+           "tc_gemm.cu", "conv3d.cu", "unet.cu", "fcg.cu", "fcg_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]

@@ -22,14 +22,13 @@ struct tpfa_ctx {
   int loop_mode;
   int vy;
   int stages;      // stages of the stored-q sweep and of tpfa_apply
-  int scheme;      // CG sweep: 0 = stored q (48 B/cell), 1 = recomputed q (40 B/cell)
   int precond;     // 0 = none (Alg. 1), 1 = Jacobi
   int fcg_m;       // directions retained by fcg_solve
   int fcg_fallback;  // fcg_solve fallback: 0 = unpreconditioned (default), 1 = Jacobi
-  int stages40;    // stages of the recomputed-q sweep
-  int warps40;     // warps per block of the recomputed-q sweep
   int zc;
   int chunk;
+  int sweep_sel;   // CG sweep kernel: 0 = automatic, 1 = cp.async staged, 2 = TMA staged
+  int tma_tile;    // tile choice of the TMA-staged sweep
   // reduction workspace
   CgState* st;
   CgState* host_st;  // pinned
@@ -40,14 +39,17 @@ struct tpfa_ctx {
   // CG vectors (allocated on first solve)
   float* vec;
   double* r64;
+  float* dinv;  // Jacobi with BF16 records: M^-1 per cell (allocated on first use)
   CgVecs v;
   // iteration-loop graph
   cudaGraphExec_t loop_exec;
   const void* loop_key_coef;
   bool loop_key_b16;
   int loop_key_precond;
-  int loop_key_vy, loop_key_stages, loop_key_scheme, loop_key_stages40, loop_key_warps40;
-  int loop_key_zc, loop_key_mode, loop_key_chunk;
+  int loop_key_vy, loop_key_stages;
+  int loop_key_zc, loop_key_mode, loop_key_chunk, loop_key_sweep, loop_key_tile;
+  TmaMaps* maps;     // tensor maps of the TMA-staged sweep (host copy, built with the loop)
+  TmaPlan tplan;
   cudaStream_t cap_stream;
   cudaEvent_t ev[4];
 };
@@ -122,28 +124,25 @@ int use_device(const tpfa_ctx* c) {
 
 Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->stages, c->zc, c->num_sms); }
 
-int cg_scheme(const tpfa_ctx* c, bool b16);
-
 // the sweep the CG loop runs
-Sweep ctx_cg_sweep(const tpfa_ctx* c, bool b16 = false) {
-  return cg_scheme(c, b16) == 1 ? plan_sweep40(c->g, c->stages40, c->warps40, c->zc, c->num_sms)
-                                : ctx_sweep(c);
-}
+Sweep ctx_cg_sweep(const tpfa_ctx* c) { return ctx_sweep(c); }
 
-// scheme 1 has neither a BF16 nor a preconditioned variant: those solves
-// always run the stored-q sweep
-int cg_scheme(const tpfa_ctx* c, bool b16) { return (b16 || c->precond) ? 0 : c->scheme; }
+// The CG loop runs the TMA-staged sweep for plain CG on FP32 records when the
+// grid allows it (nx % 4 == 0), unless the cp.async sweep is requested.
+bool use_tma(const tpfa_ctx* c, bool b16) {
+  return !b16 && c->precond == 0 && c->sweep_sel != 1 && c->vy == 4 && tma_sweep_ok(c->g);
+}
 
 cudaError_t launch_cg(const tpfa_ctx* c, const Sweep& sw, const void* coef, bool b16,
                       unsigned long long cond, int use_cond, cudaStream_t s) {
+  if (use_tma(c, b16))
+    return launch_cg_sweep_tma(c->g, c->tplan, *c->maps, c->v, c->st, c->partials, c->counter,
+                               cond, use_cond, s);
   if (c->precond == 1)
-    return launch_cg_sweep_jacobi(c->g, sw, static_cast<const float4*>(coef), c->v, c->st,
+    return launch_cg_sweep_jacobi(c->g, sw, coef, b16, b16 ? c->dinv : nullptr, c->v, c->st,
                                   c->partials, c->counter, cond, use_cond, s);
-  return cg_scheme(c, b16) == 1
-      ? launch_cg40_sweep(c->g, sw, static_cast<const float4*>(coef), c->v, c->st, c->partials,
-                          c->counter, cond, use_cond, s)
-      : launch_cg_sweep(c->g, sw, coef, b16, c->v, c->st, c->partials, c->counter, cond,
-                        use_cond, s);
+  return launch_cg_sweep(c->g, sw, coef, b16, c->v, c->st, c->partials, c->counter, cond,
+                         use_cond, s);
 }
 
 int ensure_partials(tpfa_ctx* c, size_t need) {
@@ -201,19 +200,30 @@ void drop_loop(tpfa_ctx* c) {
 int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
   if (c->loop_exec && c->loop_key_coef == coef && c->loop_key_b16 == b16 &&
       c->loop_key_precond == c->precond && c->loop_key_vy == c->vy &&
-      c->loop_key_stages == c->stages && c->loop_key_scheme == c->scheme &&
-      c->loop_key_stages40 == c->stages40 && c->loop_key_warps40 == c->warps40 &&
-      c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk)
+      c->loop_key_stages == c->stages &&
+      c->loop_key_zc == c->zc && c->loop_key_mode == c->loop_mode && c->loop_key_chunk == c->chunk &&
+      c->loop_key_sweep == c->sweep_sel && c->loop_key_tile == c->tma_tile)
     return TPFA_OK;
   drop_loop(c);
   if ((b16 || c->precond) && c->vy != 4) return TPFA_EINVAL;  // 4-row warp tiles only
-  if (b16 && c->precond) return TPFA_EINVAL;  // Jacobi needs D, which BF16 records do not store
-  const Sweep sw = ctx_cg_sweep(c, b16);
-  int rc = ensure_partials(c, (size_t)sw.nblocks * 4);
-  if (rc) return rc;
-  if ((cg_scheme(c, b16) == 1 ? sweep40_blocks_per_sm(c->stages40, c->warps40)
-                              : sweep_blocks_per_sm(c->vy, c->stages)) < 1)
-    return TPFA_ECUDA;
+  const Sweep sw = ctx_cg_sweep(c);
+  const bool tma = use_tma(c, b16);
+  if (c->sweep_sel == 2 && !tma) return TPFA_EINVAL;  // TMA sweep requested but not possible
+  int rc = TPFA_OK;
+  if (tma) {
+    c->tplan = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms);
+    if (c->maps == nullptr) c->maps = new (std::nothrow) TmaMaps();
+    if (c->maps == nullptr) return TPFA_ENOMEM;
+    if (!make_tma_maps(c->g, c->tplan, static_cast<const float4*>(coef), c->v, c->maps))
+      return TPFA_ECUDA;
+    rc = ensure_partials(c, (size_t)c->tplan.nblocks * 4);
+    if (rc) return rc;
+    if (tma_blocks_per_sm(c->tplan.tile) < 1) return TPFA_ECUDA;
+  } else {
+    rc = ensure_partials(c, (size_t)sw.nblocks * 4);
+    if (rc) return rc;
+    if (sweep_blocks_per_sm(c->vy, c->stages) < 1) return TPFA_ECUDA;
+  }
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = c->cap_stream;
   const void* cf = coef;
@@ -272,12 +282,11 @@ int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
   c->loop_key_precond = c->precond;
   c->loop_key_vy = c->vy;
   c->loop_key_stages = c->stages;
-  c->loop_key_scheme = c->scheme;
-  c->loop_key_stages40 = c->stages40;
-  c->loop_key_warps40 = c->warps40;
   c->loop_key_zc = c->zc;
   c->loop_key_mode = c->loop_mode;
   c->loop_key_chunk = c->chunk;
+  c->loop_key_sweep = c->sweep_sel;
+  c->loop_key_tile = c->tma_tile;
   return TPFA_OK;
 }
 
@@ -354,10 +363,7 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   c->loop_mode = 0;
   c->vy = 4;
   c->stages = 4;
-  c->scheme = 0;
   c->precond = 0;
-  c->stages40 = 5;
-  c->warps40 = 2;
   c->zc = 0;
   c->chunk = 32;
   int rc = TPFA_ECUDA;
@@ -378,8 +384,6 @@ int tpfa_create(const tpfa_grid* grid, tpfa_ctx** out) {
   {
     const Sweep sw = ctx_sweep(c);
     size_t need = (size_t)sw.nblocks * 4;
-    const Sweep sw40 = ctx_cg_sweep(c);
-    if ((size_t)sw40.nblocks * 4 > need) need = (size_t)sw40.nblocks * 4;
     if (need < (size_t)c->elem_nblocks * 2) need = (size_t)c->elem_nblocks * 2;
     rc = ensure_partials(c, need);
     if (rc) goto fail;
@@ -405,6 +409,8 @@ int tpfa_destroy(tpfa_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->vec) cudaFree(c->vec);
   if (c->r64) cudaFree(c->r64);
+  if (c->dinv) cudaFree(c->dinv);
+  delete c->maps;
   if (c->partials) cudaFree(c->partials);
   if (c->counter) cudaFree(c->counter);
   if (c->st) cudaFree(c->st);
@@ -456,18 +462,6 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
       if (value != 0 && value != 1) return TPFA_EINVAL;
       c->fcg_fallback = (int)value;
       return TPFA_OK;
-    case TPFA_OPT_SCHEME:
-      if (value != 0 && value != 1) return TPFA_EINVAL;
-      c->scheme = (int)value;
-      return TPFA_OK;
-    case TPFA_OPT_STAGES40:
-      if (!sweep40_config_ok((int)value, c->warps40) || value != floor(value)) return TPFA_EINVAL;
-      c->stages40 = (int)value;
-      return TPFA_OK;
-    case TPFA_OPT_WARPS40:
-      if (!sweep40_config_ok(c->stages40, (int)value) || value != floor(value)) return TPFA_EINVAL;
-      c->warps40 = (int)value;
-      return TPFA_OK;
     case TPFA_OPT_TILE_ZC:
       if (value < 0 || value > 1 << 20 || value != floor(value)) return TPFA_EINVAL;
       c->zc = (int)value;
@@ -476,9 +470,41 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
       if (value < 1 || value > 4096 || value != floor(value)) return TPFA_EINVAL;
       c->chunk = (int)value;
       return TPFA_OK;
+    case TPFA_OPT_SWEEP:
+      if (value != 0 && value != 1 && value != 2) return TPFA_EINVAL;
+      c->sweep_sel = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_TMA_TILE:
+      if (!(value >= 0 && value < tma_tile_count()) || value != floor(value)) return TPFA_EINVAL;
+      c->tma_tile = (int)value;
+      return TPFA_OK;
     default:
       return TPFA_EINVAL;
   }
+}
+
+int tpfa_sweep_tiling(const tpfa_ctx* c, int which, int64_t* out) {
+  if (c == nullptr || out == nullptr || which < 0 || which > 2) return TPFA_EINVAL;
+  const Sweep sw = ctx_sweep(c);
+  const bool b16 = which == 1;
+  if (which != 2 && use_tma(c, b16)) {
+    const TmaPlan p = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms);
+    out[0] = 2;
+    out[1] = p.vy;
+    out[2] = p.stages;
+    out[3] = p.w;
+    out[4] = p.zc;
+    out[5] = p.nblocks;
+    return TPFA_OK;
+  }
+  if (which != 2 && c->sweep_sel == 2) return TPFA_EINVAL;
+  out[0] = 1;
+  out[1] = sw.vy;
+  out[2] = sw.stages;
+  out[3] = sw.warps;
+  out[4] = sw.zc;
+  out[5] = sw.nblocks;
+  return TPFA_OK;
 }
 
 int tpfa_build_trans(tpfa_ctx* c, const double* K, const uint8_t* dirichlet, const double* d,
@@ -616,10 +642,22 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
   cudaStream_t s = (cudaStream_t)stream;
   rc = ensure_vectors(c);
   if (rc) return rc;
+  if (b16 && c->precond && c->dinv == nullptr) {
+    if (cudaMalloc(&c->dinv, n * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      c->dinv = nullptr;
+      return TPFA_ENOMEM;
+    }
+  }
   rc = ensure_loop(c, coef, b16);
   if (rc) return rc;
   CK(cudaMemsetAsync(c->counter, 0, 64, s));
   CK(cudaEventRecord(c->ev[0], s));
+  if (b16 && c->precond) {
+    // M^-1 from the BF16 records of this call (they may have changed since
+    // the last solve with the same pointer)
+    CK(launch_dinv_bf16(c->g, static_cast<const uint2*>(coef), c->dinv, s));
+  }
 
   CgState* hs = c->host_st;
   double inner_ms = 0.0;
@@ -673,11 +711,9 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
           inner_ms += ms;
           if (hs->done == kRunning) continue;
         }
-        if (cg_scheme(c, b16) == 1)
-          CK(launch_finalize40(c->g, c->v, c->st, c->elem_nblocks, s));
-        else
-          CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks,
-                             c->precond ? static_cast<const float4*>(coef) : nullptr, s));
+        CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks,
+                           c->precond && !b16 ? static_cast<const float4*>(coef) : nullptr,
+                           c->precond && b16 ? c->dinv : nullptr, s));
         launches += 1;
         rc = read_state(c, s);
         if (rc) return rc;
@@ -692,13 +728,7 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
       }
       total_iters += hs->iter;
       launches += hs->launches;
-      {
-        // scheme 1 does not advance the recursive residual in finalize: use
-        // the fused estimate when the loop stopped on it
-        const bool est = cg_scheme(c, b16) == 1 && (inner_status == kConvEst || inner_status == kMaxit);
-        const double rr_in = est ? hs->rho_est : hs->rho;
-        rel_inner = hs->rho0 > 0 ? sqrt(rr_in / hs->rho0) : 0.0;
-      }
+      rel_inner = hs->rho0 > 0 ? sqrt(hs->rho / hs->rho0) : 0.0;
       if (inner_status == kGuard) { status = TPFA_EINTERNAL; break; }
       if (inner_status == kNonFinite) { status = TPFA_ENONFINITE; break; }
       if (inner_status == kBreakdown && hs->iter == 0) { status = TPFA_EBREAKDOWN; break; }

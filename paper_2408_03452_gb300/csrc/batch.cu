@@ -397,7 +397,7 @@ int cg_solve_batch(tpfa_batch* b, const float* coef, const double* coef64, const
         if (!active[i]) continue;
         BK(launch_finalize(b->g[i], vecs_at(b->v, b->off[i]), b->st + i, b->partials, ecounter,
                            elem_blocks(b->g[i], b->num_sms),
-                           b->precond ? cf + b->off[i] : nullptr, s));
+                           b->precond ? cf + b->off[i] : nullptr, nullptr, s));
         ++launches;
       }
       rc = read_states();

@@ -10,10 +10,11 @@
 // 0 and 31 carry the x-halo), VY consecutive y-rows, and marches through zc
 // consecutive z-planes, keeping the z-neighbours in registers.  x-neighbours
 // come from warp shuffles, y-neighbours from the warp's own rows plus one
-// halo row on each side.  Every global access is a fully used 32-byte
-// sector; each input array is read once per sweep from DRAM, halos are
-// L1/L2 hits.  No shared memory staging and no block-level barrier inside
-// the march: warps are independent.
+// halo row on each side.  Every plane a warp needs is staged into a
+// per-warp shared-memory ring with cp.async (zero-filled outside the grid)
+// two planes ahead of the plane being computed; each input array is read
+// once per sweep from DRAM, halo rows and columns are L2 hits.  There is no
+// block-level barrier inside the march: warps are independent.
 //
 // Reductions are deterministic: per-thread compensated FP32 sums over a
 // fixed cell set, FP64 warp shuffles in a fixed tree, FP64 block sums in a
@@ -35,6 +36,7 @@ struct SweepArgs {
   int zc;
   const float4* coef;     // FP32 records (Tx, Ty, Tz, D)
   const uint2* coef16;    // BF16 records (Tx, Ty, Tz, E), D = sum of the six T + E
+  const float* dinv;      // Jacobi with BF16 records: M^-1 per cell (dinv_bf16_kernel)
   // plain operator
   const float* p;
   float* Ap;
@@ -53,8 +55,9 @@ struct SweepArgs {
 // of the warp's VY rows, r/q/p (or p alone) of rows -1..VY, x of the VY
 // rows, and the word holding Ty of row -1.  Lane-minor, each lane reads only
 // its own column.  Records are 16 bytes (FP32) or 8 bytes (BF16).
-// With Jacobi preconditioning the stage also holds D of the halo rows -1
-// and VY (the records of the own rows carry theirs).
+// With Jacobi preconditioning and FP32 records the stage also holds D of the
+// halo rows -1 and VY (the records of the own rows carry theirs); with BF16
+// records, which do not store D, it holds M^-1 of every row -1 .. VY.
 template <int VY, bool B16, bool JAC = false>
 struct StageLayout {
   static constexpr int kRec = B16 ? 8 : 16;
@@ -62,8 +65,9 @@ struct StageLayout {
   static constexpr int kVec = VY * 32 * kRec;                   // float [3][VY+2][32]
   static constexpr int kE = kVec + 3 * (VY + 2) * 32 * 4;       // float [VY][32]
   static constexpr int kTy = kE + VY * 32 * 4;                  // 32-bit word [32]
-  static constexpr int kDh = kTy + 32 * 4;                      // float [2][32] (JAC only)
-  static constexpr int kBytes = kDh + (JAC ? 2 * 32 * 4 : 0);
+  static constexpr int kDh = kTy + 32 * 4;                      // float [2 or VY+2][32] (JAC)
+  static constexpr int kDhRows = JAC ? (B16 ? VY + 2 : 2) : 0;
+  static constexpr int kBytes = kDh + kDhRows * 32 * 4;
 };
 
 template <int VY, int S, bool B16, bool JAC = false>
@@ -86,11 +90,12 @@ __device__ __forceinline__ float ty_word(const unsigned char* base, int lane) {
   return B16 ? bf16_hi(w) : __uint_as_float(w);
 }
 
-// JAC: Jacobi-preconditioned CG (M = diag(D)), FP32 records only.  The
-// preconditioned residual z = r / D is formed on the fly, p_k = z_k + beta
-// p_{k-1}, and the four dots become r'z, p'q, z'q, q'D^-1 q, which give
-// alpha = r'z / p'q and (r - alpha q)' D^-1 (r - alpha q) by the same
-// identity as the plain iteration.  No extra vector is read or written.
+// JAC: Jacobi-preconditioned CG (M = diag(D)).  The preconditioned residual
+// z = r / D is formed on the fly, p_k = z_k + beta p_{k-1}, and the four
+// dots become r'z, p'q, z'q, q'D^-1 q, which give alpha = r'z / p'q and
+// (r - alpha q)' D^-1 (r - alpha q) by the same identity as the plain
+// iteration.  With FP32 records no extra vector is read or written; with
+// BF16 records M^-1 is read from a per-cell FP32 array (4 B/cell).
 // BATCH: one launch sweeps every instance of a batch; each block finds its
 // instance in the table (blocks of one instance are contiguous) and uses that
 // instance's grid, tiling, cell offset, CG state, completion counter and
@@ -101,7 +106,7 @@ template <int VY, int S, bool CG, bool COND, bool B16, bool JAC = false, bool BA
 __global__ void __launch_bounds__(kSweepWarps * 32)
 sweep_kernel(const SweepArgs a) {
   static_assert(S >= 3, "the plane pipeline needs at least three stages");
-  static_assert(!JAC || (CG && !B16), "Jacobi preconditioning is for FP32-record CG sweeps");
+  static_assert(!JAC || CG, "Jacobi preconditioning is for CG sweeps");
   static_assert(!BATCH || (!B16 && !COND), "batched sweeps use FP32 records, no graph condition");
   static_assert(!BATCH || !JAC || CG, "the batched operator has no preconditioner");
   using LY = StageLayout<VY, B16, JAC>;
@@ -208,9 +213,11 @@ sweep_kernel(const SweepArgs a) {
             if (B16) cp4(sty + lane, a.coef16 + src, ok);  // word 0 = Tx | Ty << 16
             else cp4(sty + lane, reinterpret_cast<const float*>(coefp + src) + 1, ok);
           }
-          if (JAC && (jj == -1 || jj == VY))
+          if (JAC && !B16 && (jj == -1 || jj == VY))
             cp4(reinterpret_cast<float*>(sb + LY::kDh) + (jj == -1 ? 0 : 32) + lane,
                 reinterpret_cast<const float*>(coefp + src) + 3, ok);
+          if (JAC && B16)
+            cp4(reinterpret_cast<float*>(sb + LY::kDh) + (jj + 1) * 32 + lane, a.dinv + src, ok);
           if (jj >= 0 && jj < VY) {
             if (B16) cp8(reinterpret_cast<uint2*>(scf) + jj * 32 + lane, a.coef16 + src, ok);
             else cp16(reinterpret_cast<float4*>(scf) + jj * 32 + lane, coefp + src, ok);
@@ -240,7 +247,9 @@ sweep_kernel(const SweepArgs a) {
           const float q0 = sv[(1 * (VY + 2) + jj + 1) * 32 + lane];
           r_ = fmaf(-alpha, q0, r0);  // Alg. 1 line 7 (previous iteration)
           float z_ = r_;
-          if (JAC) {
+          if (JAC && B16) {
+            z_ = r_ * reinterpret_cast<const float*>(sb + LY::kDh)[(jj + 1) * 32 + lane];
+          } else if (JAC) {
             const float D = (jj == -1 || jj == VY)
                 ? reinterpret_cast<const float*>(sb + LY::kDh)[(jj == -1 ? 0 : 32) + lane]
                 : rec_at<false>(sb + LY::kCoef, jj * 32 + lane).w;
@@ -306,7 +315,9 @@ sweep_kernel(const SweepArgs a) {
             qout[id] = q;
             s1 = fmaf(pc, q, s1);
             s2 = fmaf(R0[jj], q, s2);
-            if (JAC) s3 = fmaf(q, q * jac_inv(cf.w), s3);
+            if (JAC && B16)
+              s3 = fmaf(q, q * reinterpret_cast<const float*>(sb + LY::kDh)[(jj + 1) * 32 + lane], s3);
+            else if (JAC) s3 = fmaf(q, q * jac_inv(cf.w), s3);
             else s3 = fmaf(q, q, s3);
           } else {
             apo[id] = q;
@@ -403,7 +414,7 @@ prepare_kernel(Grid g, const double* __restrict__ r64, CgVecs v, CgState* st, do
     st->scale = scale;
     st->iter = 0; st->maxit = maxit; st->launches = 0;
     st->guard_limit = 2 * maxit + 64;
-    st->parity = 0; st->done = kRunning;
+    st->parity = 0; st->done = kRunning; st->fault = 0;
   }
 }
 
@@ -413,7 +424,7 @@ prepare_kernel(Grid g, const double* __restrict__ r64, CgVecs v, CgState* st, do
 // loop with the exact CG continuation (alpha = 0, beta = r+'r+ / r'r).
 __global__ void __launch_bounds__(kElemThreads)
 finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* counter,
-                const float4* jac) {
+                const float4* jac, const float* dinv) {
   const int par = st->parity;
   const float af = (float)st->alpha_fin;
   float* r = v.r[par];
@@ -425,7 +436,9 @@ finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* c
     v.e[c] = fmaf(af, p[c], v.e[c]);
     const float rn = fmaf(-af, q[c], r[c]);
     r[c] = rn;
-    if (jac != nullptr) {  // preconditioned norm r' D^-1 r
+    if (dinv != nullptr) {  // preconditioned norm r' M^-1 r (BF16 records)
+      kadd(acc, rn * (rn * dinv[c]));
+    } else if (jac != nullptr) {  // preconditioned norm r' D^-1 r
       kadd(acc, rn * (rn * jac_inv(jac[c].w)));
     } else {
       kadd(acc, rn * rn);
@@ -448,6 +461,25 @@ finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* c
         st->done = kRunning;
       }
     }
+  }
+}
+
+// M^-1 = jac_inv(D) per cell for Jacobi with BF16 records, where D is the
+// diagonal the BF16 sweep forms: the six rounded face values and E added in
+// the sweep's order (zero for faces on the outer boundary), so that the
+// preconditioner is one fixed function of the operator the sweep applies.
+__global__ void __launch_bounds__(kElemThreads)
+dinv_bf16_kernel(Grid g, const uint2* __restrict__ coef16, float* __restrict__ dinv) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
+    const int64_t i = c % g.nx, j = (c / g.nx) % g.ny, k = c / g.plane;
+    const uint2 u = __ldg(coef16 + c);
+    const float txm = i > 0 ? bf16_lo(__ldg(&coef16[c - 1].x)) : 0.f;
+    const float tym = j > 0 ? bf16_hi(__ldg(&coef16[c - g.nx].x)) : 0.f;
+    const float tzm = k > 0 ? bf16_lo(__ldg(&coef16[c - g.plane].y)) : 0.f;
+    const float D = (((((txm + bf16_lo(u.x)) + tym) + bf16_hi(u.x)) + tzm) + bf16_lo(u.y)) +
+                    bf16_hi(u.y);
+    dinv[c] = jac_inv(D);
   }
 }
 
@@ -562,23 +594,36 @@ cudaError_t launch_apply(const Grid& g, const Sweep& sw, const void* coef, bool 
   return launch_sweep(a, sw, false, false, s);
 }
 
-cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
-                                   CgState* st, double* partials, unsigned int* counter,
-                                   unsigned long long cond, int use_cond, cudaStream_t s) {
-  SweepArgs a = sweep_args(g, sw, coef);
+template <int S, bool B16>
+static cudaError_t launch_jac(const SweepArgs& a, const Sweep& sw, bool cond, cudaStream_t s) {
+  return cond ? launch_t<4, S, true, true, B16, true>(a, sw, s)
+              : launch_t<4, S, true, false, B16, true>(a, sw, s);
+}
+
+cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                                   const float* dinv, CgVecs v, CgState* st, double* partials,
+                                   unsigned int* counter, unsigned long long cond, int use_cond,
+                                   cudaStream_t s) {
+  SweepArgs a = sweep_args_rec(g, sw, coef, b16);
+  a.dinv = dinv;
   a.v = v;
   a.st = st;
   a.partials = partials;
   a.counter = counter;
   a.cond = cond;
   const bool c = use_cond != 0;
-  if (sw.vy == 4 && sw.stages == 3)
-    return c ? launch_t<4, 3, true, true, false, true>(a, sw, s)
-             : launch_t<4, 3, true, false, false, true>(a, sw, s);
-  if (sw.vy == 4 && sw.stages == 4)
-    return c ? launch_t<4, 4, true, true, false, true>(a, sw, s)
-             : launch_t<4, 4, true, false, false, true>(a, sw, s);
+  if (b16 && dinv == nullptr) return cudaErrorInvalidValue;
+  if (sw.vy == 4 && sw.stages == 3) return b16 ? launch_jac<3, true>(a, sw, c, s) : launch_jac<3, false>(a, sw, c, s);
+  if (sw.vy == 4 && sw.stages == 4) return b16 ? launch_jac<4, true>(a, sw, c, s) : launch_jac<4, false>(a, sw, c, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dinv_bf16(const Grid& g, const uint2* coef16, float* dinv, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  dinv_bf16_kernel<<<elem_blocks(g, sms), kElemThreads, 0, s>>>(g, coef16, dinv);
+  return cudaGetLastError();
 }
 
 // Condition of the batched while loop: continue while any instance runs
@@ -696,8 +741,8 @@ cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* 
 
 cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
                             unsigned int* counter, int nblocks, const float4* jac,
-                            cudaStream_t s) {
-  finalize_kernel<<<nblocks, kElemThreads, 0, s>>>(g, v, st, partials, counter, jac);
+                            const float* dinv, cudaStream_t s) {
+  finalize_kernel<<<nblocks, kElemThreads, 0, s>>>(g, v, st, partials, counter, jac, dinv);
   return cudaGetLastError();
 }
 

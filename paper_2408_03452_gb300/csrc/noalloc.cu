@@ -9,8 +9,6 @@
 // context; this entry point needs none and allocates nothing.
 #include <math.h>
 
-#include <mutex>
-
 #include "tpfa_internal.cuh"
 
 namespace {
@@ -28,24 +26,19 @@ constexpr size_t kScratchBytes = kCounterBytes + (size_t)kNoAllocMaxBlocks * siz
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_apply_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_scratch_dev[kMaxDevices];  // device address of g_apply_scratch, per device
-
-// Once per device, with that device current: look up the device address of
-// the scratch array.  No allocation happens here.
-int scratch_for(int device, unsigned char** out) {
-  if (device < 0 || device >= kMaxDevices) return TPFA_EINVAL;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_dev[device] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_apply_scratch) != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return TPFA_ECUDA;
-    }
-    g_scratch_dev[device] = static_cast<unsigned char*>(p);
+// The device address of g_apply_scratch in the current device's context.
+// It is looked up on every call (a lookup, no allocation): the address
+// belongs to the module loaded in the current context, and a host program
+// that resets the device or re-creates its primary context gets the module
+// loaded again, possibly at another address, so a cached address could be
+// stale.
+int scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_apply_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return TPFA_ECUDA;
   }
-  *out = g_scratch_dev[device];
+  *out = static_cast<unsigned char*>(p);
   return TPFA_OK;
 }
 
@@ -55,6 +48,11 @@ extern "C" int tpfa_apply_noalloc(const tpfa_grid* grid, const float* coef, cons
                                   float* Ap, double* pAp, void* stream) {
   if (grid == nullptr) return TPFA_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return TPFA_EINVAL;
+  // geometry is not used by the operator application, but a grid that
+  // tpfa_create would refuse is refused here too
+  if (!(grid->dx > 0) || !(grid->dy > 0) || !(grid->dz > 0) || !(grid->mu > 0)) return TPFA_EINVAL;
+  if (!isfinite(grid->dx) || !isfinite(grid->dy) || !isfinite(grid->dz) || !isfinite(grid->mu))
+    return TPFA_EINVAL;
   if ((double)grid->nx * (double)grid->ny + 2.0 * (double)grid->nx > 2147483647.0) return TPFA_EINVAL;
   if ((double)grid->nx * (double)grid->ny * (double)grid->nz > 4.0e12) return TPFA_EINVAL;
   int device = -1, sms = 0;
@@ -80,7 +78,7 @@ extern "C" int tpfa_apply_noalloc(const tpfa_grid* grid, const float* coef, cons
     sw = plan_sweep(g, 4, 4, (int)(2 * (int64_t)sw.zc < g.nz ? 2 * sw.zc : g.nz), sms);
   if (sw.nblocks > kNoAllocMaxBlocks) return TPFA_EINVAL;
   unsigned char* scratch = nullptr;
-  int rc = scratch_for(device, &scratch);
+  int rc = scratch_address(&scratch);
   if (rc) return rc;
   unsigned int* counter = reinterpret_cast<unsigned int*>(scratch);
   double* partials = reinterpret_cast<double*>(scratch + kCounterBytes);

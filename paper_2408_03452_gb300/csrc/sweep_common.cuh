@@ -156,7 +156,7 @@ __device__ void cg_finish(CgState* st, const double (&t)[4], unsigned long long 
       st->beta = rn / rho;
     }
   }
-  if (st->launches > st->guard_limit) done = kGuard;
+  if (st->launches > st->guard_limit || st->fault) done = kGuard;
   st->parity ^= 1;
   st->done = done;
   if (use_cond) cudaGraphSetConditional(cond, done == kRunning ? 1u : 0u);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtpfa.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,7 +34,8 @@ struct CgState {
   long long guard_limit;
   int parity;          // which vector set (0/1) holds r_k, p_k, q_k
   int done;            // kRunning or one of the Done* codes
-  int pad0, pad1;
+  int fault;           // a bounded wait inside a sweep ran out (ends the loop: kGuard)
+  int pad1;
 };
 
 enum Done : int {
@@ -65,9 +67,6 @@ struct Sweep {
 
 Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms);
 bool sweep_config_ok(int vy, int stages);
-// CG sweep that recomputes q_{k-1} instead of storing q (kernels_cg40.cu)
-Sweep plan_sweep40(const Grid& g, int stages, int warps, int zc_opt, int num_sms);
-bool sweep40_config_ok(int stages, int warps);
 
 // One instance of a batched solve: its grid, its sweep tiling, where its
 // cells start in the concatenated arrays and which sweep blocks it owns.
@@ -88,6 +87,25 @@ struct CgVecs {
   float* e;  // correction being accumulated (x of the inner solve)
 };
 
+// Tiling of the TMA-staged CG sweep (sweep_tma.cu): blocks of w compute warps
+// (plus one producer warp) own 32 columns x (w * vy) rows and march through
+// zc planes with a ring of `stages` shared-memory stages.
+struct TmaPlan {
+  int tile;    // index of the (w, vy, stages) choice
+  int w, vy, stages, zc;
+  int64_t nbx, nby, nbz, nblocks;
+};
+// Tensor maps of the arrays the TMA sweep reads (both vector sets).
+struct TmaMaps {
+  CUtensorMap r[2], q[2], p[2], e, c;
+};
+bool tma_sweep_ok(const Grid& g);  // nx % 4 == 0 and the driver exposes the map encoder
+int tma_tile_count();
+TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms);
+int tma_blocks_per_sm(int tile);
+bool make_tma_maps(const Grid& g, const TmaPlan& p, const float4* coef, const CgVecs& v,
+                   TmaMaps* m);
+
 // ---- launchers (kernels_*.cu) ---------------------------------------------
 
 cudaError_t launch_build_trans(const Grid& g, const tpfa_grid& geo, const double* K,
@@ -105,21 +123,18 @@ cudaError_t launch_apply(const Grid& g, const Sweep& sw, const void* coef, bool 
 cudaError_t launch_cg_sweep(const Grid& g, const Sweep& sw, const void* coef, bool b16,
                             CgVecs v, CgState* st, double* partials, unsigned int* counter,
                             unsigned long long cond, int use_cond, cudaStream_t s);
-// Jacobi-preconditioned CG sweep (stored q, FP32 records, VY = 4)
-cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
-                                   CgState* st, double* partials, unsigned int* counter,
-                                   unsigned long long cond, int use_cond, cudaStream_t s);
+// Jacobi-preconditioned CG sweep (stored q, VY = 4).  FP32 records carry D;
+// BF16 records need dinv, M^-1 per cell from launch_dinv_bf16.
+cudaError_t launch_cg_sweep_jacobi(const Grid& g, const Sweep& sw, const void* coef, bool b16,
+                                   const float* dinv, CgVecs v, CgState* st, double* partials,
+                                   unsigned int* counter, unsigned long long cond, int use_cond,
+                                   cudaStream_t s);
+cudaError_t launch_dinv_bf16(const Grid& g, const uint2* coef16, float* dinv, cudaStream_t s);
 cudaError_t launch_accumulation(const Grid& g, const uint8_t* mask, const double* d, double d0,
                                 const double* p_prev, double* b, cudaStream_t s);
 cudaError_t launch_build_trans_bf16(const Grid& g, const tpfa_grid& geo, const double* K,
                                     const uint8_t* mask, const double* d, double d0,
                                     uint2* coef16, cudaStream_t s);
-cudaError_t launch_cg40_sweep(const Grid& g, const Sweep& sw, const float4* coef, CgVecs v,
-                              CgState* st, double* partials, unsigned int* counter,
-                              unsigned long long cond, int use_cond, cudaStream_t s);
-cudaError_t launch_finalize40(const Grid& g, CgVecs v, const CgState* st, int nblocks,
-                              cudaStream_t s);
-int sweep40_blocks_per_sm(int stages, int warps);
 cudaError_t launch_residual64(const Grid& g, const double* coef64, const double* b,
                               const double* x, double* r, double* norms, CgState* st,
                               double* partials, unsigned int* counter, int nblocks,
@@ -128,11 +143,15 @@ cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* 
                            double rtol, long long maxit, cudaStream_t s);
 cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
                             unsigned int* counter, int nblocks, const float4* jac,
-                            cudaStream_t s);
+                            const float* dinv, cudaStream_t s);
 cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
                            cudaStream_t s);
 
 int sweep_blocks_per_sm(int vy, int stages);
+// Plain FP32-record CG sweep through the TMA-staged kernel
+cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& m, CgVecs v,
+                                CgState* st, double* partials, unsigned int* counter,
+                                unsigned long long cond, int use_cond, cudaStream_t s);
 
 // Batched CG sweep over every instance (VY = 4, 4 stages, FP32 records) and
 // the one-block kernel that sets the while-loop condition after it.

@@ -21,8 +21,8 @@ OK, NOTCONV = 0, 1
 EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENONFINITE, EINTERNAL, ESTAGNATION = -1, -2, -3, -4, -5, -6, -7
 
 OPTIONS = {"inner_rtol": 1, "max_outer": 2, "loop": 3, "tile_vy": 4, "tile_zc": 5, "chunk": 6,
-           "stages": 7, "scheme": 8, "stages40": 9, "warps40": 10, "inner_rtol_bf16": 11,
-           "precond": 12, "fcg_m": 13, "fcg_fallback": 14}
+           "stages": 7, "inner_rtol_bf16": 11,
+           "precond": 12, "fcg_m": 13, "fcg_fallback": 14, "sweep": 15, "tma_tile": 16}
 
 
 class TpfaError(RuntimeError):
@@ -53,6 +53,7 @@ SIGNATURES = {
     "tpfa_strerror": (C.c_char_p, [C.c_int]),
     "tpfa_abi_version": (C.c_int, []),
     "tpfa_set_option": (C.c_int, [_P, C.c_int, C.c_double]),
+    "tpfa_sweep_tiling": (C.c_int, [_P, C.c_int, _P]),
     "tpfa_build_trans": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P, _P]),
     "tpfa_build_rhs": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     "tpfa_apply": (C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -247,6 +248,14 @@ class Context:
 
     def set_option(self, name: str, value: float):
         _check(lib().tpfa_set_option(self._h, OPTIONS[name], float(value)), f"set_option({name})")
+
+    def tiling(self, which: int = 0) -> dict:
+        """Sweep tiling: which = 0 (CG loop, FP32 records), 1 (CG loop, BF16
+        records), 2 (tpfa_apply).  kernel 1 = cp.async-staged, 2 = TMA-staged."""
+        out = (C.c_int64 * 6)()
+        _check(lib().tpfa_sweep_tiling(self._h, int(which), C.cast(out, C.c_void_p)),
+               "tpfa_sweep_tiling")
+        return dict(zip(("kernel", "vy", "stages", "warps", "zc", "blocks"), list(out)))
 
     # -- coefficient and right-hand side construction -----------------------
     def build_trans(self, K, dirichlet=None, d=None, d_uniform=0.0, coef=None, coef64=True):

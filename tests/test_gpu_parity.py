@@ -200,14 +200,9 @@ def test_residual64_matches_oracle(tp, oracle_mod, shape):
     assert nr[1] == pytest.approx(b @ b, rel=1e-12)
 
 
-def _solve(tp, c, tol, loop=0, maxit=200000, x0=None, tile=None, scheme=None, cg40=None):
+def _solve(tp, c, tol, loop=0, maxit=200000, x0=None, tile=None):
     with _ctx(tp, c) as ctx:
         ctx.set_option("loop", loop)
-        if scheme is not None:
-            ctx.set_option("scheme", scheme)
-        if cg40:
-            ctx.set_option("warps40", cg40[1])
-            ctx.set_option("stages40", cg40[0])
         if tile:
             ctx.set_option("tile_vy", tile[0])
             ctx.set_option("stages", tile[2])
@@ -224,20 +219,19 @@ def _oracle_rel(O, c, x):
     return O.rel_residual(_ogrid(O, c), c["K"], c["mask"], c["d"], c["q"], c["pD"], x)
 
 
-@pytest.mark.parametrize("scheme", [1, 0])
 @pytest.mark.parametrize("loop", [1, 0])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_cg_small_config(tp, oracle_mod, loop, seed, scheme):
+def test_cg_small_config(tp, oracle_mod, loop, seed):
     """32^3, ln K ~ N(0,1), Dirichlet x end layers: FP32 CG to 1e-6, then the
     refined solve to FP64 relative residual 1e-8; the oracle re-evaluates the
     residual of the GPU solution and compares with its own solution."""
     O = oracle_mod
     c = _case((32, 32, 32), seed=seed, sigma=1.0)
-    x6, info6 = _solve(tp, c, 1e-6, loop=loop, scheme=scheme)
+    x6, info6 = _solve(tp, c, 1e-6, loop=loop)
     assert info6["code"] == 0, info6
     assert _oracle_rel(O, c, x6) <= 1e-6 * 1.001
     assert info6["rel_res_fp64"] <= 1e-6
-    x8, info8 = _solve(tp, c, 1e-8, loop=loop, scheme=scheme)
+    x8, info8 = _solve(tp, c, 1e-8, loop=loop)
     assert info8["code"] == 0, info8
     rel = _oracle_rel(O, c, x8)
     assert rel <= 1e-8 * 1.001
@@ -247,23 +241,15 @@ def test_cg_small_config(tp, oracle_mod, loop, seed, scheme):
     assert info8["iters"] > 0 and info8["outer"] >= 1
 
 
-@pytest.mark.parametrize("scheme", [1, 0])
-def test_cg_loop_modes_and_tiles_agree_bitwise(tp, scheme):
+def test_cg_loop_modes_and_tiles_agree_bitwise(tp):
     c = _case((33, 17, 9), seed=3, sigma=1.5, dirichlet=None, d=1e-3, wells=True)
-    xa, ia = _solve(tp, c, 1e-8, loop=0, scheme=scheme)
-    xb, ib = _solve(tp, c, 1e-8, loop=1, scheme=scheme)
-    xc, ic = _solve(tp, c, 1e-8, loop=0, scheme=scheme)
+    xa, ia = _solve(tp, c, 1e-8, loop=0)
+    xb, ib = _solve(tp, c, 1e-8, loop=1)
+    xc, ic = _solve(tp, c, 1e-8, loop=0)
     assert np.array_equal(xa, xb) and np.array_equal(xa, xc)
     assert ia["iters"] == ib["iters"] == ic["iters"]
     # the stage count changes neither the arithmetic nor any summation
     # order: bit-identical; the block size regroups the FP64 partial sums
-    if scheme == 1:
-        for cfg in [(4, 2), (6, 2)]:
-            xs, _ = _solve(tp, c, 1e-8, loop=0, scheme=1, cg40=cfg)
-            assert np.array_equal(xa, xs), cfg
-        for cfg in [(4, 4), (5, 4)]:
-            xs, info = _solve(tp, c, 1e-8, loop=0, scheme=1, cg40=cfg)
-            assert info["code"] == 0 and info["rel_res_fp64"] <= 1e-8, cfg
     # a different warp tiling changes only the order of the dot-product
     # partial sums: same solution to the tolerance
     xd, idd = _solve(tp, c, 1e-8, loop=0, tile=(8, 3, 3))
@@ -272,13 +258,12 @@ def test_cg_loop_modes_and_tiles_agree_bitwise(tp, scheme):
     assert idd["code"] == 0 and idd["rel_res_fp64"] <= 1e-8
 
 
-@pytest.mark.parametrize("scheme", [1, 0])
 @pytest.mark.parametrize("shape", [(7, 5, 3), (61, 1, 1), (1, 1, 40), (95, 33, 20), (64, 9, 17),
                                    (2, 2, 2), (57, 6, 130)])
-def test_cg_odd_shapes(tp, oracle_mod, shape, scheme):
+def test_cg_odd_shapes(tp, oracle_mod, shape):
     O = oracle_mod
     c = _case(shape, seed=4, sigma=1.5, dirichlet=None, d=1e-3, wells=True, layer=2)
-    x, info = _solve(tp, c, 1e-8, scheme=scheme)
+    x, info = _solve(tp, c, 1e-8)
     assert info["code"] == 0, info
     assert _oracle_rel(O, c, x) <= 1e-8 * 1.001
 

@@ -395,6 +395,9 @@ def test_coefficients_rows_and_apply_agree(oracle_mod):
     rows = np.array([0, 7, 33, g.n - 1])
     np.testing.assert_allclose(O.apply_rows(g, K, mask, d, rows, x), A.matvec(x)[rows],
                                rtol=1e-15, atol=1e-15)
+    # |A| |x| at the same rows: the dense matrix's absolute values
+    np.testing.assert_allclose(O.abs_apply_rows(g, K, mask, d, rows, x),
+                               (np.abs(Ad) @ np.abs(x))[rows], rtol=1e-14, atol=0)
 
 
 def test_face_form_with_extra_diagonal_reproduces_csr(oracle_mod):
