@@ -1116,7 +1116,9 @@ def main():
         value = cell_updates_per_s(n, iters_all, ms_max)
         peak, peak_kind = measured_hbm_peak()
         sweep_ms = inner_ms / max(iters, 1)
-        bpc = SWEEP_BYTES_PER_CELL - (8 if coef16 is not None else 0)
+        # BF16 records save 8 B/cell; with Jacobi they need the 4 B/cell M^-1 array
+        bpc = SWEEP_BYTES_PER_CELL - (8 if coef16 is not None else 0) + \
+            (4 if coef16 is not None and a.precond else 0)
         algo = bpc * n
         achieved = algo / (sweep_ms / 1e3) / 1e9
         out = {

@@ -104,13 +104,15 @@ enum tpfa_option {
                                 0 = unpreconditioned CG (default); 1 = drop the network, keep
                                 Jacobi                                                            */
   TPFA_OPT_SWEEP = 15,       /* CG sweep kernel of cg_solve: 0 = automatic (default: the TMA-staged
-                                sweep for unpreconditioned CG on FP32 records when nx % 4 == 0,
-                                else the cp.async-staged sweep), 1 = cp.async-staged sweep,
-                                2 = TMA-staged sweep (cg_solve returns TPFA_EINVAL where it
-                                cannot run)                                                       */
+                                sweep for unpreconditioned CG on FP32 records, else the
+                                cp.async-staged sweep), 1 = cp.async-staged sweep, 2 = TMA-staged
+                                sweep (cg_solve returns TPFA_EINVAL where it cannot run: BF16
+                                records, Jacobi, or a driver without the tensor-map encoder).
+                                The TMA-staged sweep keeps r, q, p, x of a cell in one 16-byte
+                                record (32 B/cell of context memory, allocated on first use)   */
   TPFA_OPT_TMA_TILE = 16     /* tile of the TMA-staged sweep, 32 columns x rows per block:
-                                0 = 4 warps x 4 rows, 3 stages (default); 1 = 4 x 4, 4 stages;
-                                2 = 4 x 2, 4 stages; 3 = 8 x 2, 3 stages                         */
+                                0 = 4 warps x 4 rows, 4 stages (default); 1 = 4 x 4, 3 stages;
+                                2 = 8 x 4, 3 stages; 3 = 4 x 2, 6 stages                         */
 };
 
 /* The stencil-sweep tiling a context uses, for inspection and tests.
@@ -354,10 +356,19 @@ int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int
                            int nz, int ns, int cin, int cout, int accumulate, void* stream);
 /* Forward-convolution kernel for the calls that follow (process-wide):
  * 0 = 128-voxel tiles, each copying the nine row groups it reads;
- * 1 = z-marching (default): each CTA follows a 128-voxel plane segment
- *     through consecutive planes with a ring of row-group triples, loading
- *     each triple once, with two TMEM accumulators; (cin, cout) = (64, 32)
- *     always uses kernel 0. */
+ * 1 = z-marching: each CTA follows a 128-voxel plane segment through
+ *     consecutive planes with a ring of row-group triples, loading each
+ *     triple once, 27 MMAs of N = cout per output plane into two alternating
+ *     TMEM accumulators;
+ * 2 = z-marching with the z-taps folded into N: the loop runs over input
+ *     planes, and one MMA of N = 3 cout applies the three z-taps of one
+ *     (dy, dx) offset to the three output planes an input plane feeds
+ *     (accumulators in a TMEM ring), so every staged input row is read by the
+ *     tensor core 9 instead of 27 times;
+ * 3 = per layer shape, the faster of 1 and 2 on GB300 (default): 2 for
+ *     16 -> 16, 1 for the others.
+ * (cin, cout) = (64, 32) always uses kernel 0.  Returns TPFA_EINVAL for
+ * another value. */
 int tpfa_conv3d_select(int kernel);
 /* Waits for the stream; TPFA_EINTERNAL (and clears the flag) if any
  * tensor-core wait of the convolution kernels gave up since the last call. */
@@ -407,6 +418,9 @@ int tpfa_unet_forward(tpfa_unet* net, const float* r, const float* lnk, float* z
  * forward pass.  Asynchronous. */
 int tpfa_unet_forward_samples(tpfa_unet* net, int ns, const float* r, const float* lnk, float* z,
                               void* stream);
+/* The network's permeability input: lnk[i] = ln K[i] rounded to FP32, for
+ * n cells (K dev FP64 > 0, lnk dev FP32; the current device).  Asynchronous. */
+int tpfa_log_perm(const double* K, float* lnk, int64_t n, void* stream);
 /* grad (dev, param_count FP32, overwritten) = d(sum gz . z)/d(params) at the
  * last forward pass; gz dev.  Requires train.  Asynchronous. */
 int tpfa_unet_backward(tpfa_unet* net, const float* gz, float* grad, void* stream);

@@ -40,6 +40,7 @@ struct tpfa_ctx {
   float* vec;
   double* r64;
   float* dinv;  // Jacobi with BF16 records: M^-1 per cell (allocated on first use)
+  float4* vec4;  // interleaved vector records of the TMA-staged sweep (two sets, on first use)
   CgVecs v;
   // iteration-loop graph
   cudaGraphExec_t loop_exec;
@@ -133,11 +134,23 @@ bool use_tma(const tpfa_ctx* c, bool b16) {
   return !b16 && c->precond == 0 && c->sweep_sel != 1 && c->vy == 4 && tma_sweep_ok(c->g);
 }
 
+// The CG vectors of a solve: the separate arrays, or with the TMA-staged
+// sweep the interleaved records.
+CgVecs loop_vecs(const tpfa_ctx* c, bool b16) {
+  CgVecs v = c->v;
+  if (use_tma(c, b16)) {
+    const size_t pad = ((size_t)c->g.n + 15) / 16 * 16;
+    v.v4[0] = c->vec4;
+    v.v4[1] = c->vec4 + pad;
+  }
+  return v;
+}
+
 cudaError_t launch_cg(const tpfa_ctx* c, const Sweep& sw, const void* coef, bool b16,
                       unsigned long long cond, int use_cond, cudaStream_t s) {
   if (use_tma(c, b16))
-    return launch_cg_sweep_tma(c->g, c->tplan, *c->maps, c->v, c->st, c->partials, c->counter,
-                               cond, use_cond, s);
+    return launch_cg_sweep_tma(c->g, c->tplan, *c->maps, loop_vecs(c, b16), c->st, c->partials,
+                               c->counter, cond, use_cond, s);
   if (c->precond == 1)
     return launch_cg_sweep_jacobi(c->g, sw, coef, b16, b16 ? c->dinv : nullptr, c->v, c->st,
                                   c->partials, c->counter, cond, use_cond, s);
@@ -214,7 +227,16 @@ int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
     c->tplan = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms);
     if (c->maps == nullptr) c->maps = new (std::nothrow) TmaMaps();
     if (c->maps == nullptr) return TPFA_ENOMEM;
-    if (!make_tma_maps(c->g, c->tplan, static_cast<const float4*>(coef), c->v, c->maps))
+    if (c->vec4 == nullptr) {
+      const size_t pad = ((size_t)c->g.n + 15) / 16 * 16;  // 256-byte aligned second set
+      if (cudaMalloc(&c->vec4, 2 * pad * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        c->vec4 = nullptr;
+        return TPFA_ENOMEM;
+      }
+    }
+    if (!make_tma_maps(c->g, c->tplan, static_cast<const float4*>(coef), loop_vecs(c, b16),
+                       c->maps))
       return TPFA_ECUDA;
     rc = ensure_partials(c, (size_t)c->tplan.nblocks * 4);
     if (rc) return rc;
@@ -410,6 +432,7 @@ int tpfa_destroy(tpfa_ctx* c) {
   if (c->vec) cudaFree(c->vec);
   if (c->r64) cudaFree(c->r64);
   if (c->dinv) cudaFree(c->dinv);
+  if (c->vec4) cudaFree(c->vec4);
   delete c->maps;
   if (c->partials) cudaFree(c->partials);
   if (c->counter) cudaFree(c->counter);
@@ -651,6 +674,7 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
   }
   rc = ensure_loop(c, coef, b16);
   if (rc) return rc;
+  const CgVecs vecs = loop_vecs(c, b16);
   CK(cudaMemsetAsync(c->counter, 0, 64, s));
   CK(cudaEventRecord(c->ev[0], s));
   if (b16 && c->precond) {
@@ -691,7 +715,7 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
       const double floor_rtol = b16 ? c->inner_rtol_bf16 : c->inner_rtol;
       if (rtol < floor_rtol) rtol = floor_rtol;
       if (rtol > 0.5) rtol = 0.5;
-      CK(launch_prepare(c->g, c->r64, c->v, c->st, rtol, (long long)(maxit - total_iters), s));
+      CK(launch_prepare(c->g, c->r64, vecs, c->st, rtol, (long long)(maxit - total_iters), s));
       launches += 1;
       int inner_status = kRunning;
       // host-side bound on relaunches (the device guard normally ends the
@@ -711,7 +735,7 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
           inner_ms += ms;
           if (hs->done == kRunning) continue;
         }
-        CK(launch_finalize(c->g, c->v, c->st, c->partials, c->counter, c->elem_nblocks,
+        CK(launch_finalize(c->g, vecs, c->st, c->partials, c->counter, c->elem_nblocks,
                            c->precond && !b16 ? static_cast<const float4*>(coef) : nullptr,
                            c->precond && b16 ? c->dinv : nullptr, s));
         launches += 1;
@@ -733,7 +757,7 @@ static int solve_impl(tpfa_ctx* c, const void* coef, bool b16, const double* coe
       if (inner_status == kNonFinite) { status = TPFA_ENONFINITE; break; }
       if (inner_status == kBreakdown && hs->iter == 0) { status = TPFA_EBREAKDOWN; break; }
       // x += e / scale;  r64 = b - A x
-      CK(launch_correct(c->g, c->v.e, x, c->st, s));
+      CK(launch_correct(c->g, vecs, x, c->st, s));
       CK(launch_residual64(c->g, coef64, b, x, c->r64, nullptr, c->st, c->partials, c->counter,
                            c->elem_nblocks, s));
       launches += 2;

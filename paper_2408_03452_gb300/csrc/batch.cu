@@ -430,7 +430,7 @@ int cg_solve_batch(tpfa_batch* b, const float* coef, const double* coef64, const
     for (int i = 0; i < N; ++i) {
       if (!active[i]) continue;
       const int64_t o = b->off[i];
-      BK(launch_correct(b->g[i], b->v.e + o, x + o, b->st + i, s));
+      BK(launch_correct(b->g[i], vecs_at(b->v, o), x + o, b->st + i, s));
       BK(residual(i));
       launches += 2;
       ++outer[i];

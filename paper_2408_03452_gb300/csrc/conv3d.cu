@@ -439,6 +439,230 @@ conv_fwd_zm_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
   if (warp == 0) tc::tmem_dealloc(acc0, Cfg::kCols);
 }
 
+// ---- z-marching forward kernel with the z-taps folded into N ---------------
+// Same work units and row-group triples as the z-marching kernel, but the loop
+// runs over input planes instead of output planes.  Triple j (planes
+// kp0-2+j .. in the unit's numbering) feeds outputs j-2, j-1 and j through the
+// taps dz = 2, 1, 0, and for one (dy, dx) row-group offset the three tap
+// matrices sit side by side in shared memory, so one tcgen05.mma with
+// N = 3 COUT computes all three contributions from one read of the A operand
+// (the staged input rows): 9 MMAs of N = 48 per output plane for 16 -> 16
+// instead of 27 of N = 16, a third of the operand traffic from shared memory.
+// The accumulators of consecutive outputs are consecutive COUT-column slots of
+// a TMEM ring of R slots; an output range that wraps around the ring is split
+// into two MMAs, and an output's first contribution (triple j = k, first
+// (dy, dx, k16) step) is its own MMA with accumulation off.  Output k is final
+// after triple k+2: its epilogue runs while the tensor core works on triple
+// k+3.
+template <int CIN, int COUT>
+struct ZfCfg {
+  static constexpr int kST = zm_stages<CIN, COUT>();
+  static constexpr int kWTap = COUT * CIN * 2;
+  static constexpr int kWBytes = 27 * kWTap;
+  static constexpr int kRGBytes = kRG * CIN * 2;
+  static constexpr int kTriple = 3 * kRGBytes;
+  static constexpr int kSmem = kWBytes + kST * kTriple;
+  static constexpr int kR = 256 / COUT;  // accumulator slots: 256 TMEM columns
+  static constexpr uint32_t kCols = 256;
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+  static_assert(kR >= 4, "the ring must hold the three outputs in work and one in its epilogue");
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv_fwd_zf_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
+                   const float* __restrict__ bias, const uint16_t* __restrict__ mask,
+                   uint16_t* __restrict__ y, Vol g, int flags, ZmGrid zg) {
+  using Cfg = ZfCfg<CIN, COUT>;
+  constexpr int ST = Cfg::kST;
+  constexpr int R = Cfg::kR;
+  constexpr int kc = CIN / 8;
+  constexpr int kChunks = 3 * kRG * kc;            // 16-byte copies per triple
+  constexpr int kPer = (kChunks + 127) / 128;      // per thread
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tbase;
+  __shared__ float sbias[COUT];
+  unsigned char* sW = sm;
+  unsigned char* sR = sm + Cfg::kWBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // tap t = dz * 9 + dy * 3 + dx goes to tile (dy * 3 + dx) * 3 + (2 - dz): the
+  // taps of one (dy, dx) are consecutive K-major tiles in the order dz = 2, 1, 0,
+  // i.e. one B operand of N = 3 COUT rows
+  for (int i = tid; i < 27 * COUT * kc; i += 128) {
+    const int c = i % kc, r = (i / kc) % COUT, t = i / (kc * COUT);
+    const int tt = (t % 9) * 3 + (2 - t / 9);
+    const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
+    *reinterpret_cast<uint4*>(sW + tt * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
+  }
+  if (tid < COUT) sbias[tid] = bias ? bias[tid] : 0.f;
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, Cfg::kCols);
+  int roff[kPer], coff[kPer];
+  uint32_t soff[kPer];
+#pragma unroll
+  for (int m = 0; m < kPer; ++m) {
+    const int i = tid + 128 * m;
+    const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+    roff[m] = gi * g.wp + v;
+    coff[m] = c * 8;
+    soff[m] = (uint32_t)(gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t acc0 = tbase;
+  const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sR), kRG * 16, 128);
+  const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sW), 128, kc * 128);
+
+  bool abort = false;
+  int tg = 0;     // triples issued by this CTA (barrier phase)
+  int obase = 0;  // outputs of earlier units (accumulator ring position)
+  for (int u = blockIdx.x; u < zg.units && !abort; u += gridDim.x) {
+    const int bi = u % zg.nb, cz = u / zg.nb;
+    const int sidx = cz / zg.nzc;
+    const int z0 = (cz % zg.nzc) * zg.zc;
+    const int nout = min(zg.zc, g.nz - z0);
+    const int kp0 = sidx * g.dp + 1 + z0;  // padded plane of output 0
+    const int seg = bi * 128;
+    const int ntrip = nout + 2;            // triples: planes kp0-1 .. kp0+nout
+    const int poff = seg + warp * 32 + lane;
+    const int px = poff % g.wp, py = poff / g.wp;
+    const bool in_xy = poff < g.pp && px >= 1 && px <= g.nx && py >= 1 && py <= g.ny;
+    auto load_triple = [&](int j) {
+      if (j < ntrip) {
+        const int base = seg + (kp0 - 1 + j) * g.pp - g.wp - 1;
+        unsigned char* st = sR + (j % ST) * Cfg::kTriple;
+#pragma unroll
+        for (int m = 0; m < kPer; ++m) {
+          if (kChunks % 128 == 0 || tid + 128 * m < kChunks) {
+            const int row = base + roff[m];
+            const bool ok = row >= 0 && row < g.vp;
+            cp16z(st + soff[m], x + (size_t)(ok ? row : 0) * CIN + coff[m], ok);
+          }
+        }
+      }
+      cp_commit_group();
+    };
+    for (int j = 0; j < ST; ++j) load_triple(j);
+
+    auto epilogue = [&](int k) {
+      const size_t idx = (size_t)(kp0 + k) * g.pp + poff;
+      const uint32_t acc = acc0 + (uint32_t)(((obase + k) % R) * COUT);
+      float va[COUT];
+      tc::tmem_ld_cols<COUT>(acc + ((uint32_t)(warp * 32) << 16), va);
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 8) {
+        const float* v = va + c0;
+        if (in_xy) {
+          uint4 mk = make_uint4(0, 0, 0, 0);
+          if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + idx * COUT + c0);
+          const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+          uint32_t ov[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            float a = v[2 * h] + sbias[c0 + 2 * h], b = v[2 * h + 1] + sbias[c0 + 2 * h + 1];
+            if (flags & kConvRelu) {
+              a = fmaxf(a, 0.f);
+              b = fmaxf(b, 0.f);
+            }
+            if (flags & kConvMask) {
+              if (!bf16_positive(mw[h] & 0xffffu)) a = 0.f;
+              if (!bf16_positive(mw[h] >> 16)) b = 0.f;
+            }
+            ov[h] = pack_bf16(a, b);
+          }
+          *reinterpret_cast<uint4*>(y + idx * COUT + c0) = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        }
+      }
+    };
+
+    for (int j = 0; j < ntrip; ++j, ++tg) {
+      cp_wait_groups<ST - 2>();  // triple j is complete
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+        const int klo = max(0, j - 2), khi = min(nout - 1, j);
+        const uint64_t slot = adesc0 + (uint64_t)((j % ST) * (Cfg::kTriple >> 4));
+        // outputs ka..kb of this triple, one (dy, dx, k16) step: B tiles
+        // consecutive from the tile of output ka, D slots consecutive modulo R
+        auto mma_range = [&](int ka, int kb, uint64_t ad, int tile0, int ks, bool accum) {
+          int k = ka;
+          while (k <= kb) {
+            const int sl = (obase + k) % R;
+            const int n = min(kb - k + 1, R - sl);
+            const uint64_t bd =
+                bdesc0 + (uint64_t)(((tile0 + (k - ka)) * Cfg::kWTap + ks * 256) >> 4);
+            tc::mma_bf16(acc0 + (uint32_t)(sl * COUT), ad, bd, tc::idesc_bf16_f32(128, n * COUT),
+                         accum);
+            k += n;
+          }
+        };
+#pragma unroll 1
+        for (int gi = 0; gi < 3; ++gi)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+            for (int ks = 0; ks < CIN / 16; ++ks) {
+              const uint64_t ad =
+                  slot + (uint64_t)((gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16) >> 4);
+              // tile of output ka: (dy, dx) group, index 2 - dz with dz = j - ka
+              const int grp = (gi * 3 + dx) * 3 + 2 - j;
+              const bool first = (gi | dx | ks) == 0;
+              if (first && khi == j) {  // output j starts here: accumulation off for it
+                if (klo < j) mma_range(klo, j - 1, ad, grp + klo, ks, true);
+                mma_range(j, j, ad, grp + j, ks, false);
+              } else {
+                mma_range(klo, khi, ad, grp + klo, ks, true);
+              }
+            }
+        tc::mma_commit(&bars[tg & 1]);
+      }
+      if (j >= 1) {
+        // triple j-1's MMAs are done: its ring slot is free, and output j-3 is final
+        const bool ok = tc::mbar_wait(&bars[(tg - 1) & 1], ((tg - 1) >> 1) & 1, kWaitLimit);
+        if (__syncthreads_or(!ok)) {
+          abort = true;
+          break;
+        }
+        load_triple(j - 1 + ST);
+        if (j >= 3) {
+          tc::fence_after();
+          epilogue(j - 3);
+          tc::fence_before();
+        }
+      } else {
+        cp_commit_group();
+      }
+    }
+    if (abort) break;
+    {  // the last output of the unit
+      const bool ok = tc::mbar_wait(&bars[(tg - 1) & 1], ((tg - 1) >> 1) & 1, kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      tc::fence_after();
+      epilogue(nout - 1);
+      tc::fence_before();
+    }
+    obase += nout;
+    cp_wait_all();
+    __syncthreads();  // ring slots are rewritten by the next unit
+  }
+  cp_wait_all();
+  if (abort && tid == 0) atomicOr(&g_tc_timeout, 1);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(acc0, Cfg::kCols);
+}
+
 template <int CIN, int COUT>
 struct WgCfg {
   static constexpr int kTaps = 128 / CIN;                    // taps per 128-row tile
@@ -626,6 +850,29 @@ cudaError_t zm_launch(const uint16_t* x, const uint16_t* w, const float* bias,
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
+cudaError_t zf_launch(const uint16_t* x, const uint16_t* w, const float* bias,
+                      const uint16_t* mask, uint16_t* y, const Vol& g, int flags,
+                      cudaStream_t s) {
+  static int per_sm = -1, nsm = 0;
+  if (per_sm < 0)
+    per_sm = ctas_per_sm((const void*)conv_fwd_zf_kernel<CIN, COUT>, ZfCfg<CIN, COUT>::kSmem,
+                         ZfCfg<CIN, COUT>::kCols, &nsm);
+  const int ctas = per_sm * nsm;
+  ZmGrid zg;
+  zg.nb = (g.pp + 127) / 128;
+  zg.zc = g.nz;
+  // shorter z runs until there are at least two units per resident CTA
+  while (zg.zc > 4 && (long long)zg.nb * g.ns * ((g.nz + zg.zc - 1) / zg.zc) < 2LL * ctas)
+    zg.zc = (zg.zc + 1) / 2;
+  zg.nzc = (g.nz + zg.zc - 1) / zg.zc;
+  zg.units = zg.nb * g.ns * zg.nzc;
+  const int grid = zg.units < ctas ? zg.units : ctas;
+  conv_fwd_zf_kernel<CIN, COUT><<<grid, 128, ZfCfg<CIN, COUT>::kSmem, s>>>(x, w, bias, mask, y,
+                                                                           g, flags, zg);
+  return cudaGetLastError();
+}
+
 int wgrad_splits(int mtiles, int nchunks) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -670,13 +917,22 @@ bool conv_shape_ok(int cin, int cout) {
 
 #define TPFA_CONV_SHAPES(X) X(16, 16) X(16, 32) X(32, 16) X(32, 64) X(64, 32)
 
-// 0: tile kernel, 1: z-marching kernel (default; where its ring fits)
-static int g_conv_kernel = 1;
+// 0: tile kernel, 1: z-marching kernel, 2: z-marching kernel with the z-taps
+// folded into N (both where their ring fits), 3: per layer shape the faster
+// of 1 and 2 as measured on GB300 (default: 2 for 16 -> 16, 1 otherwise)
+static int g_conv_kernel = 3;
 
 cudaError_t conv_fwd(const uint16_t* x, const uint16_t* w, const float* bias, const uint16_t* mask,
                      uint16_t* y, const Vol& g, int cin, int cout, int flags, cudaStream_t s) {
   const bool ring = !(cin == 64 && cout == 32);
-  if (ring && g_conv_kernel == 1) {
+  const int kern = g_conv_kernel != 3 ? g_conv_kernel : (cin == 16 && cout == 16 ? 2 : 1);
+  if (ring && kern == 2) {
+#define X(CI, CO) \
+  if (cin == CI && cout == CO) return zf_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
+    X(16, 16) X(16, 32) X(32, 16) X(32, 64)
+#undef X
+  }
+  if (ring && kern == 1) {
 #define X(CI, CO) \
   if (cin == CI && cout == CO) return zm_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
     X(16, 16) X(16, 32) X(32, 16) X(32, 64)
@@ -760,9 +1016,10 @@ extern "C" int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, flo
 }
 
 // Selects the forward convolution kernel: 0 = 128-voxel tiles with all nine
-// row groups per tile, 1 = z-marching ring where it fits (default).
+// row groups per tile, 1 = z-marching ring where it fits, 2 = z-marching ring
+// with the z-taps folded into N, 3 = per layer shape (default).
 extern "C" int tpfa_conv3d_select(int kernel) {
-  if (kernel != 0 && kernel != 1) return TPFA_EINVAL;
+  if (kernel < 0 || kernel > 3) return TPFA_EINVAL;
   tpfa::net::g_conv_kernel = kernel;
   return TPFA_OK;
 }

@@ -402,10 +402,14 @@ prepare_kernel(Grid g, const double* __restrict__ r64, CgVecs v, CgState* st, do
   const double scale = rr > 0.0 ? 1.0 / sqrt(rr) : 1.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
-    v.r[0][c] = (float)(scale * r64[c]);
-    v.p[0][c] = 0.f;
-    v.q[0][c] = 0.f;
-    v.e[c] = 0.f;
+    if (v.v4[0] != nullptr) {  // interleaved records (r, q, p, x)
+      v.v4[0][c] = make_float4((float)(scale * r64[c]), 0.f, 0.f, 0.f);
+    } else {
+      v.r[0][c] = (float)(scale * r64[c]);
+      v.p[0][c] = 0.f;
+      v.q[0][c] = 0.f;
+      v.e[c] = 0.f;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->alpha = 0.0; st->beta = 0.0; st->rho = 0.0; st->rho0 = 0.0; st->rho_est = 0.0;
@@ -430,12 +434,22 @@ finalize_kernel(Grid g, CgVecs v, CgState* st, double* partials, unsigned int* c
   float* r = v.r[par];
   const float* p = v.p[par];
   const float* q = v.q[par];
+  float4* v4 = v.v4[par];
   Acc acc = {0.f, 0.f};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
-    v.e[c] = fmaf(af, p[c], v.e[c]);
-    const float rn = fmaf(-af, q[c], r[c]);
-    r[c] = rn;
+    float rn;
+    if (v4 != nullptr) {  // interleaved records (r, q, p, x)
+      float4 t = v4[c];
+      t.w = fmaf(af, t.z, t.w);
+      rn = fmaf(-af, t.y, t.x);
+      t.x = rn;
+      v4[c] = t;
+    } else {
+      v.e[c] = fmaf(af, p[c], v.e[c]);
+      rn = fmaf(-af, q[c], r[c]);
+      r[c] = rn;
+    }
     if (dinv != nullptr) {  // preconditioned norm r' M^-1 r (BF16 records)
       kadd(acc, rn * (rn * dinv[c]));
     } else if (jac != nullptr) {  // preconditioned norm r' D^-1 r
@@ -483,44 +497,20 @@ dinv_bf16_kernel(Grid g, const uint2* __restrict__ coef16, float* __restrict__ d
   }
 }
 
-// x64 += e / scale.
+// x64 += e / scale (e: the correction array, or the x component of the
+// current interleaved record set).
 __global__ void __launch_bounds__(kElemThreads)
-correct_kernel(Grid g, const float* __restrict__ e, double* __restrict__ x, const CgState* st) {
+correct_kernel(Grid g, CgVecs v, double* __restrict__ x, const CgState* st) {
   const double inv = 1.0 / st->scale;
+  const float4* v4 = v.v4[st->parity];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < g.n; c += stride)
-    x[c] = fma((double)e[c], inv, x[c]);
+    x[c] = fma((double)(v4 != nullptr ? v4[c].w : v.e[c]), inv, x[c]);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-
-Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms) {
-  Sweep s;
-  s.vy = vy;
-  s.stages = stages;
-  s.warps = kSweepWarps;
-  s.nwx = (g.nx + kTileX - 1) / kTileX;
-  s.nwy = (g.ny + vy - 1) / vy;
-  int zc = zc_opt;
-  if (zc <= 0) {
-    // longest run (at most 128 planes; each run re-reads two halo planes)
-    // that still gives about four warps per SM: on 128^3 and 256^3 grids the
-    // sweep is 20% faster with these runs (32 and 128 planes) than with the
-    // shorter ones that would give several waves of resident warps
-    const int64_t target = (int64_t)num_sms * 4;
-    const int64_t cols = s.nwx * s.nwy;
-    zc = 128;
-    while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc /= 2;
-  }
-  if (zc > g.nz) zc = (int)g.nz;
-  s.zc = zc;
-  s.nwz = (g.nz + zc - 1) / zc;
-  s.nwarps = s.nwx * s.nwy * s.nwz;
-  s.nblocks = (s.nwarps + kSweepWarps - 1) / kSweepWarps;
-  return s;
-}
 
 bool sweep_config_ok(int vy, int stages) {
   return (vy == 4 && (stages == 3 || stages == 4)) || (vy == 8 && stages == 3);
@@ -746,12 +736,12 @@ cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partia
   return cudaGetLastError();
 }
 
-cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
+cudaError_t launch_correct(const Grid& g, const CgVecs& v, double* x, const CgState* st,
                            cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  correct_kernel<<<elem_blocks(g, sms), kElemThreads, 0, s>>>(g, e, x, st);
+  correct_kernel<<<elem_blocks(g, sms), kElemThreads, 0, s>>>(g, v, x, st);
   return cudaGetLastError();
 }
 

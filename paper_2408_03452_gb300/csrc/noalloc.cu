@@ -16,8 +16,8 @@ namespace {
 using namespace tpfa;
 
 // Fixed workspace: one completion counter (first 256 bytes) and one FP64
-// partial sum per block.  It bounds the tiling to kNoAllocMaxBlocks blocks.
-constexpr int kNoAllocMaxBlocks = 16384;
+// partial sum per block.  It bounds the tiling to kNoAllocMaxBlocks blocks
+// (sweep_plan.h).
 constexpr size_t kCounterBytes = 256;
 constexpr size_t kScratchBytes = kCounterBytes + (size_t)kNoAllocMaxBlocks * sizeof(double);
 
@@ -73,10 +73,8 @@ extern "C" int tpfa_apply_noalloc(const tpfa_grid* grid, const float* coef, cons
   // Same tiling as tpfa_apply, with longer z-runs if needed so that the
   // block count fits the fixed workspace; grids whose single z-run still
   // needs more blocks are refused.
-  Sweep sw = plan_sweep(g, 4, 4, 0, sms);
-  while (sw.nblocks > kNoAllocMaxBlocks && sw.zc < g.nz)
-    sw = plan_sweep(g, 4, 4, (int)(2 * (int64_t)sw.zc < g.nz ? 2 * sw.zc : g.nz), sms);
-  if (sw.nblocks > kNoAllocMaxBlocks) return TPFA_EINVAL;
+  Sweep sw;
+  if (!plan_noalloc(g, sms, &sw)) return TPFA_EINVAL;
   unsigned char* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc) return rc;

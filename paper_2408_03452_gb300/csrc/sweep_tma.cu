@@ -1,35 +1,41 @@
 // Fused CG sweep with its planes staged by the tensor memory accelerator.
 //
-// Computes exactly what the plain FP32-record CG sweep of kernels_cg.cu
-// computes for one iteration of Alg. 1 (arXiv 2408.03452, Section II.A):
+// Computes what the plain FP32-record CG sweep of kernels_cg.cu computes for
+// one iteration of Alg. 1 (arXiv 2408.03452, Section II.A):
 // r_k = r_{k-1} - alpha q_{k-1}, p_k = r_k + beta p_{k-1},
 // x_k = x_{k-1} + alpha p_{k-1}, q_k = A p_k (Eq. 6 / Alg. 2 in the positive
 // form (A p)_K = D_K p_K - sum_f T_f p_nbr) and the four dot products r'r,
-// p'q, r'q, q'q, with the same per-cell arithmetic in the same order, so q,
-// r, p and x are bit-identical to that sweep's; only the grouping of the dot
-// products' partial sums differs (another tiling).
+// p'q, r'q, q'q, with the same per-cell arithmetic in the same order; only the
+// grouping of the dot products' partial sums differs (another tiling).
 //
-// Tiling: a block owns 32 consecutive x-columns (X0 = 32 bx, so every output
-// row a warp stores is one aligned 128-byte line) and TY = W * VY y-rows, and
-// marches through a run of zc z-planes.  Warp w (of W compute warps) owns
-// rows w*VY .. w*VY+VY-1 of the tile; lane l owns column X0 + l.  One more
-// warp is the producer: for every plane one of its threads issues five
+// Vector layout: the four CG vectors of a cell are one 16-byte record
+// (r, q, p, x) in FP32, and the sweep reads one set of records and writes the
+// other (two sets, ping-ponged).  With the coefficient records that makes
+// three DRAM streams per sweep (read records, read vectors, write vectors)
+// instead of nine: the same 48 bytes per cell, fewer concurrent access
+// streams (a plain copy kernel with this access pattern moves 48 B/cell at
+// 6.95 TB/s with three streams against 6.29 TB/s with nine on GB300).
+//
+// Tiling: a block owns 32 consecutive x-columns (X0 = 32 bx) and TY = W * VY
+// y-rows, and marches through a run of zc z-planes.  Warp w (of W compute
+// warps) owns rows w*VY .. w*VY+VY-1 of the tile; lane l owns column X0 + l,
+// so every output row a warp stores is 512 contiguous bytes.  One more warp
+// is the producer: for every plane one of its threads issues two
 // cp.async.bulk.tensor loads into a ring of S shared-memory stages,
-//   r, q, p   [TY+2 rows][40 columns] from (X0-4, Y0-1)  (x-halo and y-halo),
-//   records   [TY+1 rows][33 records] from (X0-1, Y0-1)  (Tx of x-1, Ty of y-1),
-//   x         [TY rows][32 columns]   from (X0, Y0),
-// with out-of-grid elements zero-filled by the copy engine, and the compute
-// warps find every neighbour in shared memory or registers: x-neighbours by
-// warp shuffles (the two x-halo columns formed by lanes 0 and 31), y-neighbours
-// from the stage, z-neighbours from registers carried plane to plane.
-// Stages are handed over by mbarriers: "full" (transaction bytes of the five
-// copies) and "empty" (one arrival per compute warp).  Every wait is bounded;
-// a wait that runs out records a fault in the CG state, which ends the loop
-// with the guard status instead of hanging the GPU.
+//   vectors   [TY+2 rows][34 records] from (X0-1, Y0-1)  (x-halo and y-halo),
+//   coefficients [TY+1 rows][33 records] from (X0-1, Y0-1) (Tx of x-1, Ty of y-1),
+// with out-of-grid elements zero-filled by the copy engine.  x-neighbours
+// come from warp shuffles (the two x-halo columns are formed by every lane
+// from the stage and used by lanes 0 and 31), y-neighbours from the stage,
+// z-neighbours from registers carried plane to plane.  Stages are handed
+// over by mbarriers: "full" (transaction bytes of the copies) and "empty"
+// (one arrival per compute warp).  Every wait is bounded; a wait that runs
+// out records a fault in the CG state, which ends the loop with the guard
+// status instead of hanging the GPU.
 //
-// Requirement of the copy engine: global row strides that are multiples of
-// 16 bytes, i.e. nx % 4 == 0 (tma_sweep_ok); other grids use the cp.async
-// sweep.
+// Requirement of the copy engine: global strides that are multiples of 16
+// bytes, which 16-byte records always satisfy (tma_sweep_ok checks the
+// driver's tensor-map encoder).
 #include <cuda.h>
 #include <math.h>
 #include <string.h>
@@ -45,16 +51,16 @@ using tc::mbar_init;
 using tc::mbar_wait;
 using tc::smem_addr;
 
-constexpr int kBoxX = 40;      // r, q, p box width: X0-4 .. X0+35
-constexpr int kRecX = 33;      // record box width: X0-1 .. X0+31
+constexpr int kVecX = 34;      // vector box width: X0-1 .. X0+32
+constexpr int kRecX = 33;      // coefficient box width: X0-1 .. X0+31
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls of one mbarrier wait before giving up
 
 struct TmaArgs {
-  CUtensorMap mr[2], mq[2], mp[2], me, mc;  // r, q, p (two vector sets), x, records
+  CUtensorMap mv[2], mc;  // vector records (two sets), coefficient records
   Grid g;
   int zc;
   int nbx, nby;  // blocks along x and y
-  CgVecs v;
+  float4* v4[2];
   CgState* st;
   double* partials;
   unsigned int* counter;
@@ -64,17 +70,13 @@ struct TmaArgs {
 template <int W, int VY>
 struct TmaLayout {
   static constexpr int TY = W * VY;
-  static constexpr int kVecBytes = (TY + 2) * kBoxX * 4;
+  static constexpr int kVecBytes = (TY + 2) * kVecX * 16;
   static constexpr int kRecBytes = (TY + 1) * kRecX * 16;
-  static constexpr int kEBytes = TY * 32 * 4;
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
-  static constexpr int kR = 0;
-  static constexpr int kQ = al(kVecBytes);
-  static constexpr int kP = 2 * al(kVecBytes);
-  static constexpr int kC = 3 * al(kVecBytes);
-  static constexpr int kE = kC + al(kRecBytes);
-  static constexpr int kStage = kE + al(kEBytes);
-  static constexpr uint32_t kTx = 3 * kVecBytes + kRecBytes + kEBytes;  // bytes per stage
+  static constexpr int kV = 0;
+  static constexpr int kC = al(kVecBytes);
+  static constexpr int kStage = kC + al(kRecBytes);
+  static constexpr uint32_t kTx = kVecBytes + kRecBytes;  // bytes per stage
 };
 
 template <int W, int VY, int S>
@@ -96,14 +98,6 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* m, uint64_t
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* m, uint64_t* bar, int c, int x,
-                                       int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(m)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -161,9 +155,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
   if (warp == W) {
     // ---- producer: one thread issues the copies of every plane -----------
     if (lane == 0) {
-      const CUtensorMap* mr = &a.mr[par];
-      const CUtensorMap* mq = &a.mq[par];
-      const CUtensorMap* mp = &a.mp[par];
+      const CUtensorMap* mv = &a.mv[par];
       int issued = 0;
       for (int j = 0; j < L; ++j) {
         const int s = j % S;
@@ -174,11 +166,9 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
         const int z = (int)(z0 - 1 + j);
         unsigned char* sb = smem + s * LY::kStage;
         mbar_expect_tx(&full[s], LY::kTx);
-        tma_3d(sb + LY::kR, mr, &full[s], X0 - 4, Y0 - 1, z);
-        tma_3d(sb + LY::kQ, mq, &full[s], X0 - 4, Y0 - 1, z);
-        tma_3d(sb + LY::kP, mp, &full[s], X0 - 4, Y0 - 1, z);
-        tma_4d(sb + LY::kC, &a.mc, &full[s], 0, X0 - 1, Y0 - 1, z);
-        tma_3d(sb + LY::kE, &a.me, &full[s], X0, Y0, z);
+        // x coordinate in floats: 4 (X0 - 1), a multiple of 4 (16 bytes)
+        tma_3d(sb + LY::kV, mv, &full[s], 4 * (X0 - 1), Y0 - 1, z);
+        tma_3d(sb + LY::kC, &a.mc, &full[s], 4 * (X0 - 1), Y0 - 1, z);
         issued = j + 1;
       }
       // every issued copy must have landed before the block exits: wait for
@@ -200,42 +190,29 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
     // in-plane offset of own row 0; own rows inside the grid stay below
     // nx * ny < 2^31 (checked at context creation)
     const unsigned o0 = (unsigned)(Y0 + jw) * (unsigned)nxi + (unsigned)gx;
-    const int hc = lane == 0 ? 3 : 4 + 32;  // box column of this lane's x-halo cell
-    float* ep = a.v.e;
-    float* rout = a.v.r[par ^ 1];
-    float* qout = a.v.q[par ^ 1];
-    float* pout = a.v.p[par ^ 1];
+    const int hc = lane == 0 ? 0 : 33;  // box column of this lane's x-halo cell
+    float4* vout = a.v4[par ^ 1];
 
-    // Form r_k and p_k of plane j (absolute z = z0 - 1 + j) for rows -1..VY of
-    // this lane's column and for the x-halo cell of the own rows; for own
-    // cells of planes inside the run also write r_k, p_k and x_k.
-    auto form = [&](int j, float (&P)[VY + 2], float (&R)[VY], float (&H)[VY], float& s0) {
-      const unsigned char* sb = smem + (j % S) * LY::kStage;
-      const float* sr = reinterpret_cast<const float*>(sb + LY::kR);
-      const float* sq = reinterpret_cast<const float*>(sb + LY::kQ);
-      const float* sp = reinterpret_cast<const float*>(sb + LY::kP);
-      const float* se = reinterpret_cast<const float*>(sb + LY::kE);
+    // Form r_k, p_k (and x_k on own rows) of plane j (absolute z = z0 - 1 + j)
+    // for rows -1..VY of this lane's column, and p_k of the x-halo cell of the
+    // own rows.
+    auto form = [&](int j, float (&P)[VY + 2], float (&R)[VY], float (&H)[VY], float (&E)[VY],
+                    float& s0) {
+      const float4* sv = reinterpret_cast<const float4*>(smem + (j % S) * LY::kStage + LY::kV);
       const int64_t z = z0 - 1 + j;
       const bool own = z >= z0 && z < z1;
-      const int64_t zo = g.plane * z;
 #pragma unroll
       for (int jj = -1; jj <= VY; ++jj) {
-        const int i = (jw + jj + 1) * kBoxX + lane + 4;
-        const float p0 = sp[i];
-        const float r_ = fmaf(-alpha, sq[i], sr[i]);  // Alg. 1 line 7 (previous iteration)
-        const float p_ = fmaf(beta, p0, r_);           // Alg. 1 line 10
+        const float4 v = sv[(jw + jj + 1) * kVecX + lane + 1];  // (r, q, p, x)
+        const float r_ = fmaf(-alpha, v.y, v.x);  // Alg. 1 line 7 (previous iteration)
+        const float p_ = fmaf(beta, v.z, r_);     // Alg. 1 line 10
         P[jj + 1] = p_;
         if (jj >= 0 && jj < VY) {
           R[jj] = r_;
-          const int h = (jw + jj + 1) * kBoxX + hc;
-          H[jj] = fmaf(beta, sp[h], fmaf(-alpha, sq[h], sr[h]));
-          if (own && ((rowok >> jj) & 1u)) {
-            const int64_t id = zo + (int64_t)(o0 + (unsigned)(jj * nxi));
-            ep[id] = fmaf(alpha, p0, se[(jw + jj) * 32 + lane]);  // Alg. 1 line 6
-            rout[id] = r_;
-            pout[id] = p_;
-            s0 = fmaf(r_, r_, s0);
-          }
+          E[jj] = fmaf(alpha, v.z, v.w);          // Alg. 1 line 6
+          const float4 h = sv[(jw + jj + 1) * kVecX + hc];
+          H[jj] = fmaf(beta, h.z, fmaf(-alpha, h.y, h.x));
+          if (own && ((rowok >> jj) & 1u)) s0 = fmaf(r_, r_, s0);
         }
       }
     };
@@ -247,12 +224,12 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
       if (lane == 0) mbar_arrive(&empty[j % S]);
     };
 
-    float Pm[VY], P0[VY + 2], R0[VY], H0[VY], Tzm[VY];
+    float Pm[VY], P0[VY + 2], R0[VY], H0[VY], E0[VY], Tzm[VY];
     float s0 = 0.f;
     if (!wait_full(0)) fault = true;
     if (!fault) {  // plane z0 - 1: direction below the first plane, and its Tz
-      float Pt[VY + 2], Rt[VY], Ht[VY];
-      form(0, Pt, Rt, Ht, s0);
+      float Pt[VY + 2], Rt[VY], Ht[VY], Et[VY];
+      form(0, Pt, Rt, Ht, Et, s0);
       const float4* sc = reinterpret_cast<const float4*>(smem + LY::kC);
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
@@ -262,16 +239,16 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
       release(0);
       if (!wait_full(1)) fault = true;
     }
-    if (!fault) form(1, P0, R0, H0, s0);
+    if (!fault) form(1, P0, R0, H0, E0, s0);
 
     for (int64_t z = z0; z < z1 && !fault; ++z) {
       const int jc = (int)(z - z0) + 1;  // plane z
       const int jf = jc + 1;             // plane z + 1
       if (!wait_full(jf)) { fault = true; break; }
-      float Pp[VY + 2], Rp[VY], Hp[VY];
-      form(jf, Pp, Rp, Hp, s0);
+      float Pp[VY + 2], Rp[VY], Hp[VY], Ep[VY];
+      form(jf, Pp, Rp, Hp, Ep, s0);
       const float4* sc = reinterpret_cast<const float4*>(smem + (jc % S) * LY::kStage + LY::kC);
-      const int64_t zo = g.plane * z;
+      float4* vz = vout + g.plane * z;
       float s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
@@ -287,7 +264,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
         const float q = stencil7(cf, txm, tym, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
                                  Pp[jj + 1], Pm[jj]);
         if ((rowok >> jj) & 1u) {
-          qout[zo + (int64_t)(o0 + (unsigned)(jj * nxi))] = q;
+          vz[o0 + (unsigned)(jj * nxi)] = make_float4(R0[jj], q, pc, E0[jj]);
           s1 = fmaf(pc, q, s1);
           s2 = fmaf(R0[jj], q, s2);
           s3 = fmaf(q, q, s3);
@@ -305,6 +282,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
       for (int jj = 0; jj < VY; ++jj) {
         R0[jj] = Rp[jj];
         H0[jj] = Hp[jj];
+        E0[jj] = Ep[jj];
       }
 #pragma unroll
       for (int jj = 0; jj < VY + 2; ++jj) P0[jj] = Pp[jj];
@@ -345,28 +323,18 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// FP32 field [nz][ny][nx] as a 3-D tensor, box (40, TY + 2, 1) or (32, TY, 1)
-bool encode_vec(CUtensorMap* m, const float* base, const Grid& g, int bx, int by) {
+// 16-byte records [nz][ny][nx][4 floats] as a 3-D FP32 tensor of rows of
+// 4 nx floats, box (4 bw, bh, 1): one box row is one contiguous request of
+// 16 bw bytes (a 4-D view with the record as the innermost dimension would
+// make the copy engine issue one 16-byte request per record)
+bool encode_rec(CUtensorMap* m, const float4* base, const Grid& g, int bw, int bh) {
   EncodeTiledFn fn = encode_fn();
   if (fn == nullptr) return false;
-  const cuuint64_t dim[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-  const cuuint64_t stride[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.plane * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint64_t dim[3] = {4 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)g.nx * 16, (cuuint64_t)g.plane * 16};
+  const cuuint32_t box[3] = {4 * (cuuint32_t)bw, (cuuint32_t)bh, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dim, stride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// FP32 records [nz][ny][nx][4] as a 4-D tensor, box (4, 33, TY + 1, 1)
-bool encode_rec(CUtensorMap* m, const float4* base, const Grid& g, int by) {
-  EncodeTiledFn fn = encode_fn();
-  if (fn == nullptr) return false;
-  const cuuint64_t dim[4] = {4, (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-  const cuuint64_t stride[3] = {16, (cuuint64_t)g.nx * 16, (cuuint64_t)g.plane * 16};
-  const cuuint32_t box[4] = {4, (cuuint32_t)kRecX, (cuuint32_t)by, 1};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float4*>(base), dim, stride, box, es,
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float4*>(base), dim, stride, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -398,14 +366,13 @@ int tma_blocks_per_sm_t() {
 struct TileShape {
   int w, vy, s;
 };
-constexpr TileShape kTmaTiles[] = {{4, 4, 3}, {4, 4, 4}, {4, 2, 4}, {8, 2, 3}};
+constexpr TileShape kTmaTiles[] = {{4, 4, 4}, {4, 4, 3}, {8, 4, 3}, {4, 2, 6}};
 constexpr int kNumTmaTiles = (int)(sizeof(kTmaTiles) / sizeof(kTmaTiles[0]));
 
 }  // namespace
 
 bool tma_sweep_ok(const Grid& g) {
-  return g.nx % 4 == 0 && g.nx < (1 << 30) && g.ny < (1 << 30) && g.nz < (1 << 30) &&
-         encode_fn() != nullptr;
+  return g.nx < (1 << 30) && g.ny < (1 << 30) && g.nz < (1 << 30) && encode_fn() != nullptr;
 }
 
 int tma_tile_count() { return kNumTmaTiles; }
@@ -439,10 +406,10 @@ TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms) {
 int tma_blocks_per_sm(int tile) {
   int nb = 0;
   switch (tile) {
-    case 0: nb = tma_blocks_per_sm_t<4, 4, 3>(); break;
-    case 1: nb = tma_blocks_per_sm_t<4, 4, 4>(); break;
-    case 2: nb = tma_blocks_per_sm_t<4, 2, 4>(); break;
-    case 3: nb = tma_blocks_per_sm_t<8, 2, 3>(); break;
+    case 0: nb = tma_blocks_per_sm_t<4, 4, 4>(); break;
+    case 1: nb = tma_blocks_per_sm_t<4, 4, 3>(); break;
+    case 2: nb = tma_blocks_per_sm_t<8, 4, 3>(); break;
+    case 3: nb = tma_blocks_per_sm_t<4, 2, 6>(); break;
     default: break;
   }
   if (nb == 0) cudaGetLastError();
@@ -452,14 +419,10 @@ int tma_blocks_per_sm(int tile) {
 bool make_tma_maps(const Grid& g, const TmaPlan& p, const float4* coef, const CgVecs& v,
                    TmaMaps* m) {
   const int ty = p.w * p.vy;
+  if (v.v4[0] == nullptr || v.v4[1] == nullptr) return false;
   bool ok = true;
-  for (int i = 0; i < 2; ++i) {
-    ok = ok && encode_vec(&m->r[i], v.r[i], g, kBoxX, ty + 2);
-    ok = ok && encode_vec(&m->q[i], v.q[i], g, kBoxX, ty + 2);
-    ok = ok && encode_vec(&m->p[i], v.p[i], g, kBoxX, ty + 2);
-  }
-  ok = ok && encode_vec(&m->e, v.e, g, 32, ty);
-  ok = ok && encode_rec(&m->c, coef, g, ty + 1);
+  for (int i = 0; i < 2; ++i) ok = ok && encode_rec(&m->v[i], v.v4[i], g, kVecX, ty + 2);
+  ok = ok && encode_rec(&m->c, coef, g, kRecX, ty + 1);
   return ok;
 }
 
@@ -469,27 +432,24 @@ cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& 
   TmaArgs a;
   memset(&a, 0, sizeof(a));
   for (int i = 0; i < 2; ++i) {
-    a.mr[i] = m.r[i];
-    a.mq[i] = m.q[i];
-    a.mp[i] = m.p[i];
+    a.mv[i] = m.v[i];
+    a.v4[i] = v.v4[i];
   }
-  a.me = m.e;
   a.mc = m.c;
   a.g = g;
   a.zc = p.zc;
   a.nbx = (int)p.nbx;
   a.nby = (int)p.nby;
-  a.v = v;
   a.st = st;
   a.partials = partials;
   a.counter = counter;
   a.cond = cond;
   const bool c = use_cond != 0;
   switch (p.tile) {
-    case 0: return c ? launch_tma_t<4, 4, 3, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 3, false>(a, p.nblocks, s);
-    case 1: return c ? launch_tma_t<4, 4, 4, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 4, false>(a, p.nblocks, s);
-    case 2: return c ? launch_tma_t<4, 2, 4, true>(a, p.nblocks, s) : launch_tma_t<4, 2, 4, false>(a, p.nblocks, s);
-    case 3: return c ? launch_tma_t<8, 2, 3, true>(a, p.nblocks, s) : launch_tma_t<8, 2, 3, false>(a, p.nblocks, s);
+    case 0: return c ? launch_tma_t<4, 4, 4, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 4, false>(a, p.nblocks, s);
+    case 1: return c ? launch_tma_t<4, 4, 3, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 3, false>(a, p.nblocks, s);
+    case 2: return c ? launch_tma_t<8, 4, 3, true>(a, p.nblocks, s) : launch_tma_t<8, 4, 3, false>(a, p.nblocks, s);
+    case 3: return c ? launch_tma_t<4, 2, 6, true>(a, p.nblocks, s) : launch_tma_t<4, 2, 6, false>(a, p.nblocks, s);
     default: return cudaErrorInvalidValue;
   }
 }

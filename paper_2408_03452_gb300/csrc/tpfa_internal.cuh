@@ -5,13 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sweep_plan.h"
 #include "tpfa.h"
 
 namespace tpfa {
 
 constexpr int kWarp = 32;
-constexpr int kTileX = 30;        // output columns per warp (lanes 1..30; lanes 0, 31 are halo)
-constexpr int kSweepWarps = 4;    // warps per block in the stencil sweeps
 constexpr int kElemThreads = 256; // threads per block in element-wise / per-cell kernels
 
 // Device-resident scalars of one solve.  Written only by the last block of a
@@ -48,24 +47,6 @@ enum Done : int {
   kGuard = -6,       // runaway-loop guard tripped
 };
 
-struct Grid {
-  int64_t nx, ny, nz;
-  int64_t plane;  // nx * ny
-  int64_t n;      // nx * ny * nz
-};
-
-// Warp tiling of the z-marching stencil sweeps.
-struct Sweep {
-  int vy;           // rows per warp (4 or 8)
-  int stages;       // shared-memory plane stages per warp
-  int warps;        // warps per block
-  int zc;           // planes per warp
-  int64_t nwx, nwy, nwz;
-  int64_t nwarps;
-  int64_t nblocks;  // blocks of `warps` warps
-};
-
-Sweep plan_sweep(const Grid& g, int vy, int stages, int zc_opt, int num_sms);
 bool sweep_config_ok(int vy, int stages);
 
 // One instance of a batched solve: its grid, its sweep tiling, where its
@@ -85,6 +66,10 @@ struct CgVecs {
   float* p[2];
   float* q[2];
   float* e;  // correction being accumulated (x of the inner solve)
+  // Interleaved layout of the TMA-staged sweep (used instead of the arrays
+  // above when set): per cell one record (r, q, p, x), two sets ping-ponged;
+  // the set st->parity holds the current iterate, x included.
+  float4* v4[2] = {nullptr, nullptr};
 };
 
 // Tiling of the TMA-staged CG sweep (sweep_tma.cu): blocks of w compute warps
@@ -95,11 +80,12 @@ struct TmaPlan {
   int w, vy, stages, zc;
   int64_t nbx, nby, nbz, nblocks;
 };
-// Tensor maps of the arrays the TMA sweep reads (both vector sets).
+// Tensor maps of the arrays the TMA sweep reads (both vector-record sets,
+// coefficient records).
 struct TmaMaps {
-  CUtensorMap r[2], q[2], p[2], e, c;
+  CUtensorMap v[2], c;
 };
-bool tma_sweep_ok(const Grid& g);  // nx % 4 == 0 and the driver exposes the map encoder
+bool tma_sweep_ok(const Grid& g);  // the driver exposes the tensor-map encoder
 int tma_tile_count();
 TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms);
 int tma_blocks_per_sm(int tile);
@@ -144,7 +130,7 @@ cudaError_t launch_prepare(const Grid& g, const double* r64, CgVecs v, CgState* 
 cudaError_t launch_finalize(const Grid& g, CgVecs v, CgState* st, double* partials,
                             unsigned int* counter, int nblocks, const float4* jac,
                             const float* dinv, cudaStream_t s);
-cudaError_t launch_correct(const Grid& g, const float* e, double* x, const CgState* st,
+cudaError_t launch_correct(const Grid& g, const CgVecs& v, double* x, const CgState* st,
                            cudaStream_t s);
 
 int sweep_blocks_per_sm(int vy, int stages);

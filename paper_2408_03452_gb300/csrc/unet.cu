@@ -466,11 +466,28 @@ int layer_grads(tpfa_unet* u, int layer, const uint16_t* x, const uint16_t* dpre
 
 int elem_launch_ok() { return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA; }
 
+// lnk = (float) ln K, the network's second input channel
+__global__ void log_perm_kernel(const double* __restrict__ K, float* __restrict__ lnk, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    lnk[i] = (float)log(K[i]);
+}
+
 }  // namespace
 
 extern "C" {
 
 int64_t tpfa_unet_param_count(void) { return kParams.total; }
+
+int tpfa_log_perm(const double* K, float* lnk, int64_t n, void* stream) {
+  int dev = -1;
+  if (n < 1 || cudaGetDevice(&dev) != cudaSuccess) return n < 1 ? TPFA_EINVAL : TPFA_ECUDA;
+  if (!tpfa::dev_ok(K, (size_t)n * 8, 8, dev) || !tpfa::dev_ok(lnk, (size_t)n * 4, 4, dev))
+    return TPFA_EINVAL;
+  const int64_t nb = (n + kThreads - 1) / kThreads;
+  log_perm_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), kThreads, 0, (cudaStream_t)stream>>>(K, lnk, n);
+  return elem_launch_ok();
+}
 
 int tpfa_unet_create(int nx, int ny, int nz, int ns, int train, tpfa_unet** out) {
   if (out == nullptr) return TPFA_EINVAL;

@@ -67,7 +67,7 @@ class Problem:
         md = torch.from_numpy(mask).to(dev)
         self.coef, self.coef64 = ctx.build_trans(Kd, md)
         self.b = ctx.build_rhs(Kd, md, pD=torch.from_numpy(pD).to(dev))
-        self.lnk = torch.from_numpy(np.log(K).astype(np.float32)).to(dev)
+        self.lnk = tpfa.log_perm(Kd)
 
 
 class Dataset:
@@ -288,7 +288,7 @@ def ensemble_problem(P, seed: int = 0, n_inst: int = 96, levels: int = 2):
     bc = tpfa.BatchContext(grids, device=dev)
     coef, coef64 = bc.build_trans(K, mask, None, 0.0)
     b = bc.build_rhs(K, mask, None, pD)
-    lnk = torch.log(K).float()
+    lnk = tpfa.log_perm(K)
     del K, mask, pD
     classes = sorted(set(grids))
     nets, idx, lv = [], {}, {}
@@ -382,7 +382,7 @@ def apply_bench(n: int, reps: int = 10, seed: int = 0) -> dict:
     net = tpfa.UNet(n, n, n, device=dev)
     net.set_params(init_params(seed).to(dev))
     r = torch.from_numpy(synth.uniform_field(n ** 3, seed).astype(np.float32)).to(dev)
-    lnk = torch.from_numpy(np.log(realization(seed, n, 1.5)[0]).astype(np.float32)).to(dev)
+    lnk = tpfa.log_perm(torch.from_numpy(realization(seed, n, 1.5)[0]).to(dev))
     z = torch.empty_like(r)
     for _ in range(2):
         net.forward(r, lnk, z)

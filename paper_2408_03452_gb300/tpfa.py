@@ -69,6 +69,7 @@ SIGNATURES = {
     "tpfa_tc_wait_probe": (C.c_int, [C.c_uint32, _P]),
     "tpfa_conv3d_select": (C.c_int, [C.c_int]),
     "tpfa_unet_param_count": (C.c_int64, []),
+    "tpfa_log_perm": (C.c_int, [_P, _P, C.c_int64, _P]),
     "tpfa_unet_create": (C.c_int, [C.c_int] * 5 + [C.POINTER(C.c_void_p)]),
     "tpfa_unet_destroy": (C.c_int, [_P]),
     "tpfa_unet_shape": (C.c_int, [_P, C.POINTER(C.c_int)]),
@@ -559,6 +560,18 @@ def prolong_levels(coarse, shape, levels, fine=None):
                                          _ptr(fine, torch.float32, n, dev, "fine"), nx, ny, nz, ns,
                                          int(levels), _stream(dev)), "tpfa_prolong_levels")
     return fine
+
+
+def log_perm(K, lnk=None):
+    """The network's permeability input ln K (FP32) from K (float64 CUDA tensor)."""
+    dev, n = K.device, K.numel()
+    if lnk is None:
+        lnk = torch.empty(n, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(lib().tpfa_log_perm(_ptr(K, torch.float64, n, dev, "K"),
+                                   _ptr(lnk, torch.float32, n, dev, "lnk"), n, _stream(dev)),
+               "tpfa_log_perm")
+    return lnk
 
 
 def adam_step(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -27,12 +27,14 @@ def tp():
     return tpfa
 
 
-@pytest.fixture(params=[1, 0], ids=["zmarch", "tiles"])
+@pytest.fixture(params=[2, 1, 0], ids=["zfold", "zmarch", "tiles"])
 def kernel(tp, request):
-    """Both forward kernels: the z-marching ring (default) and the tile kernel."""
+    """Every forward kernel, forced for every layer shape: the z-marching ring
+    with the z-taps folded into N, the z-marching ring with one MMA per tap,
+    the tile kernel (the default picks 2 or 1 per shape)."""
     tp.conv3d_select(request.param)
     yield request.param
-    tp.conv3d_select(1)
+    tp.conv3d_select(3)
 
 
 def bf16(a):

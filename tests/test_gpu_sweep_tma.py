@@ -14,7 +14,7 @@ the oracle:
     the two sweeps' iterates agree to 1e-5 for k <= 8 (same per-cell
     arithmetic);
   * solves: the oracle's FP64 residual of the GPU solution <= tol, for every
-    tile choice, both loop modes, ragged x / y tiles and z-runs.
+    tile choice, both loop modes, ragged x / y tiles and z-runs, any nx.
 """
 import numpy as np
 import pytest
@@ -68,46 +68,32 @@ def _solve(tp, shape, c, tol, maxit, opts):
 
 
 def test_tiling_selection(tp):
-    with tp.Context(64, 20, 9) as ctx:
-        assert tiling(tp, ctx)["kernel"] == 2          # nx % 4 == 0: TMA sweep
-        assert tiling(tp, ctx, 1)["kernel"] == 1       # BF16 records: cp.async sweep
-        assert tiling(tp, ctx, 2)["kernel"] == 1       # tpfa_apply
-        ctx.set_option("precond", 1)
-        assert tiling(tp, ctx)["kernel"] == 1
-        ctx.set_option("precond", 0)
-        ctx.set_option("sweep", 1)
-        assert tiling(tp, ctx)["kernel"] == 1
-        ctx.set_option("sweep", 2)
-        t = tiling(tp, ctx)
-        assert t["kernel"] == 2 and t["warps"] == 4 and t["vy"] == 4
-        for tile, (w, vy, s) in enumerate([(4, 4, 3), (4, 4, 4), (4, 2, 4), (8, 2, 3)]):
-            ctx.set_option("tma_tile", tile)
+    for shape in ((64, 20, 9), (66, 20, 9)):
+        with tp.Context(*shape) as ctx:
+            assert tiling(tp, ctx)["kernel"] == 2          # FP32 records: TMA sweep
+            assert tiling(tp, ctx, 1)["kernel"] == 1       # BF16 records: cp.async sweep
+            assert tiling(tp, ctx, 2)["kernel"] == 1       # tpfa_apply
+            ctx.set_option("precond", 1)
+            assert tiling(tp, ctx)["kernel"] == 1
+            ctx.set_option("precond", 0)
+            ctx.set_option("sweep", 1)
+            assert tiling(tp, ctx)["kernel"] == 1
+            ctx.set_option("sweep", 2)
             t = tiling(tp, ctx)
-            assert (t["warps"], t["vy"], t["stages"]) == (w, vy, s)
-            assert t["blocks"] == 2 * ((20 + w * vy - 1) // (w * vy)) * ((9 + t["zc"] - 1) // t["zc"])
-        with pytest.raises(tp.TpfaError):
-            ctx.set_option("tma_tile", 4)
-    with tp.Context(66, 20, 9) as ctx:
-        assert tiling(tp, ctx)["kernel"] == 1          # nx % 4 != 0
-        ctx.set_option("sweep", 2)
-        with pytest.raises(tp.TpfaError):
-            tiling(tp, ctx)
-
-
-def test_tma_sweep_refused_where_it_cannot_run(tp):
-    shape = (66, 8, 8)
-    c = _case(shape, 1, "wells")
-    with tp.Context(*shape) as ctx:
-        ctx.set_option("sweep", 2)
-        K = _dev(c["K"])
-        coef, coef64 = ctx.build_trans(K, None, None, 1e-3)
-        b = ctx.build_rhs(K, None, _dev(c["q"]), None)
-        with pytest.raises(tp.TpfaError):
-            ctx.cg_solve(coef, coef64, b, tol=1e-8)
+            assert t["kernel"] == 2 and t["warps"] == 4 and t["vy"] == 4 and t["stages"] == 4
+            nbx = (shape[0] + 31) // 32
+            for tile, (w, vy, st) in enumerate([(4, 4, 4), (4, 4, 3), (8, 4, 3), (4, 2, 6)]):
+                ctx.set_option("tma_tile", tile)
+                t = tiling(tp, ctx)
+                assert (t["warps"], t["vy"], t["stages"]) == (w, vy, st)
+                assert t["blocks"] == nbx * ((20 + w * vy - 1) // (w * vy)) * ((9 + t["zc"] - 1) // t["zc"])
+            with pytest.raises(tp.TpfaError):
+                ctx.set_option("tma_tile", 4)
 
 
 ITER_SHAPES = [((32, 32, 32), "dirx"), ((36, 17, 9), "wells"), ((4, 4, 4), "dirx"),
-               ((100, 30, 41), "wells"), ((64, 1, 7), "wells")]
+               ((100, 30, 41), "wells"), ((64, 1, 7), "wells"), ((33, 17, 9), "dirx"),
+               ((95, 33, 20), "wells")]
 
 
 @pytest.mark.parametrize("shape,kind", ITER_SHAPES)
@@ -135,14 +121,15 @@ def test_cg_iterates_match_oracle(tp, oracle_mod, shape, kind):
 
 
 SOLVE_SHAPES = [(32, 32, 32), (36, 17, 9), (4, 4, 4), (100, 30, 41), (64, 1, 7), (8, 50, 130),
-                (4, 1, 1), (128, 16, 3)]
+                (4, 1, 1), (128, 16, 3), (7, 5, 3), (1, 1, 1), (61, 1, 1), (1, 1, 40), (95, 33, 20),
+                (2, 40, 3)]
 
 
 @pytest.mark.parametrize("shape", SOLVE_SHAPES)
 @pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_tma_solve_matches_oracle(tp, oracle_mod, shape, tile):
     O = oracle_mod
-    kind = "dirx" if shape[0] > 1 and shape[0] % 8 == 0 else "wells"
+    kind = "dirx" if shape[0] > 2 and shape[0] % 8 == 0 else "wells"
     c = _case(shape, 3, kind)
     x, info, t = _solve(tp, shape, c, 1e-8, 400000, {"sweep": 2, "tma_tile": tile})
     assert t["kernel"] == 2

@@ -388,3 +388,18 @@ def test_fcg_rejects_mismatched_network(tp):
     lnk = torch.zeros(16 ** 3, dtype=torch.float32, device="cuda")
     _, info = ctx.fcg_solve(coef, coef64, b, net=net, lnk=lnk, check=False)
     assert info["code"] == tp.EINVAL
+
+
+def test_log_perm_is_the_rounded_natural_log(tp):
+    """The network's permeability input ln K: the FP64 natural logarithm
+    rounded to FP32, within one FP32 ulp of numpy's (CUDA's log is accurate to
+    a couple of FP64 ulps, so the rounding to FP32 agrees except where the
+    FP64 value sits within those ulps of a rounding boundary)."""
+    from paper_2408_03452_gb300 import synth
+    K = synth.lognormal_field(37, 19, 11, 2.5, 4)
+    K[:3] = [1.0, 1e-30, 7e30]
+    got = tp.log_perm(torch.from_numpy(K).cuda()).cpu().numpy()
+    ref = np.log(K).astype(np.float32)
+    ulp = np.abs(got.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 1 and (ulp == 0).mean() >= 0.999
+    assert got[0] == 0.0
