@@ -304,6 +304,8 @@ def cpu_baseline(target_s=12.0, workload="paper"):
     dt = time.perf_counter() - t
     what = "FCG" if workload == "learned" else "CG"
     how = "numpy" if workload == "learned" else "C with OpenMP"
+    if workload == "channelized":
+        what = "Jacobi PCG"
     return {"value": units / dt, "unit": metric_unit(workload)[1], "cores": oracle_cores(workload),
             "kind": "oracle",
             "sample": f"{sample_desc(workload)}: CSR assembly, RHS, {iters} {what} iterations, "
@@ -406,9 +408,11 @@ def measured_hbm_peak():
 
 
 def sweep_traffic(nx, ny, nz):
-    """DRAM bytes per cell of one CG sweep from the committed ncu summary, if
-    it was taken on the current kernel source; else None."""
-    src = os.path.join(ROOT, "paper_2408_03452_gb300", "csrc", "kernels_cg.cu")
+    """DRAM bytes of one CG sweep launch (TMA-staged, FP32 records, plain CG)
+    from the committed ncu summary (bytes per cell of a smaller capture with
+    the same 128-plane runs, times the cells), if it was taken on the current
+    kernel source; else None."""
+    src = os.path.join(ROOT, "paper_2408_03452_gb300", "csrc", "sweep_tma.cu")
     prof = os.path.join(ROOT, "profiles", "cg_sweep_traffic.json")
     try:
         rec = json.load(open(prof))
@@ -612,7 +616,7 @@ def channelized_steps(a, dev, n=64):
                 if info["code"] != tpfa.NOTCONV:
                     break
             runs[name] = steps
-    return {"n": n, "w": w, "runs": runs}
+    return {"n": n, "w": w, "runs": runs, "tol": a.tol}
 
 
 def refinement_errors(sg):
@@ -629,7 +633,7 @@ def refinement_errors(sg):
     xr, st, it, rel = O.pcg_jacobi(A, b, tol=1e-13)
     dt = time.perf_counter() - t
     nr = float(np.linalg.norm(xr))
-    out = {"grid": [n, n, n], "tol": None,
+    out = {"grid": [n, n, n], "tol": sg["tol"],
            "oracle": {"solver": "FP64 Jacobi PCG to 1e-13", "iters": it, "status": st,
                       "rel_res": rel, "seconds": dt, "cores": O.threads()}}
     for name, steps in sg["runs"].items():
@@ -805,11 +809,16 @@ def run_ensemble(a, dev, rank, world, local, barrier):
     with tpfa.BatchContext(grids) as bc0:
         coef, coef64 = bc0.build_trans(inp["K"], inp["mask"], None, 0.0)
         b = bc0.build_rhs(inp["K"], inp["mask"], None, inp["pD"])
+        bc0.set_option("precond", a.precond)
         zc_auto = bc0.zc
-    zc = zc_auto if a.no_autotune else autotune.tune(grids, coef, coef64, b, tol=a.tol,
-                                                      maxit=a.maxit, precond=a.precond)
+    shape = ({"sweep": 0, "tile": 0, "zc": zc_auto} if a.no_autotune else
+             autotune.tune_batch(grids, coef, coef64, b, tol=a.tol, maxit=a.maxit,
+                                 precond=a.precond))
+    zc = shape["zc"]
     bc = tpfa.BatchContext(grids, zc=zc, device=dev)
     bc.set_option("precond", a.precond)
+    bc.set_option("sweep", shape["sweep"])
+    bc.set_option("tma_tile", shape["tile"])
     x = torch.empty(bc.n, dtype=torch.float64, device=dev)
 
     def step(d):
@@ -896,6 +905,8 @@ def run_ensemble(a, dev, rank, world, local, barrier):
                        "parallelism": f"replicas{world}",
                        "precond": ["none", "jacobi"][a.precond],
                        "zc_per_size": {f"{g[0]}x{g[1]}x{g[2]}": z for g, z in zip(grids, zc)},
+                       "sweep_kernel": ["TMA-staged", "cp.async-staged"][shape["sweep"]],
+                       "tma_tile": shape["tile"],
                        "autotuned": not a.no_autotune,
                        "iters_min_max": [min(p["iters"] for p in per), max(p["iters"] for p in per)],
                        "time_to_tol_s": ms / 1e3 / a.steps,
@@ -1144,7 +1155,7 @@ def main():
                          "tiling": tiling,
                          "bytes_per_cell": bpc, "sweep_ms": sweep_ms,
                          "traffic": (sweep_traffic(nx, ny, nz)
-                                     if (coef16 is None and a.precond == 0 and a.sweep == 1)
+                                     if (coef16 is None and a.precond == 0 and tiling["kernel"] == 2)
                                      else None)},
             "gpu_launches": launches,
         }

@@ -128,10 +128,11 @@ Sweep ctx_sweep(const tpfa_ctx* c) { return plan_sweep(c->g, c->vy, c->stages, c
 // the sweep the CG loop runs
 Sweep ctx_cg_sweep(const tpfa_ctx* c) { return ctx_sweep(c); }
 
-// The CG loop runs the TMA-staged sweep for plain CG on FP32 records when the
-// grid allows it (nx % 4 == 0), unless the cp.async sweep is requested.
+// The CG loop runs the TMA-staged sweep (plain or Jacobi, FP32 or BF16
+// records) unless the cp.async sweep is requested or the grid does not allow
+// it (BF16 records need an even nx, BF16 Jacobi nx % 4 == 0).
 bool use_tma(const tpfa_ctx* c, bool b16) {
-  return !b16 && c->precond == 0 && c->sweep_sel != 1 && c->vy == 4 && tma_sweep_ok(c->g);
+  return c->sweep_sel != 1 && c->vy == 4 && tma_sweep_ok(c->g, b16, c->precond == 1);
 }
 
 // The CG vectors of a solve: the separate arrays, or with the TMA-staged
@@ -224,7 +225,7 @@ int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
   if (c->sweep_sel == 2 && !tma) return TPFA_EINVAL;  // TMA sweep requested but not possible
   int rc = TPFA_OK;
   if (tma) {
-    c->tplan = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms);
+    c->tplan = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms, b16, c->precond == 1);
     if (c->maps == nullptr) c->maps = new (std::nothrow) TmaMaps();
     if (c->maps == nullptr) return TPFA_ENOMEM;
     if (c->vec4 == nullptr) {
@@ -235,12 +236,11 @@ int ensure_loop(tpfa_ctx* c, const void* coef, bool b16) {
         return TPFA_ENOMEM;
       }
     }
-    if (!make_tma_maps(c->g, c->tplan, static_cast<const float4*>(coef), loop_vecs(c, b16),
-                       c->maps))
+    if (!make_tma_maps(c->g, c->tplan, coef, c->dinv, loop_vecs(c, b16), c->maps))
       return TPFA_ECUDA;
     rc = ensure_partials(c, (size_t)c->tplan.nblocks * 4);
     if (rc) return rc;
-    if (tma_blocks_per_sm(c->tplan.tile) < 1) return TPFA_ECUDA;
+    if (tma_blocks_per_sm(c->tplan) < 1) return TPFA_ECUDA;
   } else {
     rc = ensure_partials(c, (size_t)sw.nblocks * 4);
     if (rc) return rc;
@@ -511,7 +511,7 @@ int tpfa_sweep_tiling(const tpfa_ctx* c, int which, int64_t* out) {
   const Sweep sw = ctx_sweep(c);
   const bool b16 = which == 1;
   if (which != 2 && use_tma(c, b16)) {
-    const TmaPlan p = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms);
+    const TmaPlan p = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms, b16, c->precond == 1);
     out[0] = 2;
     out[1] = p.vy;
     out[2] = p.stages;

@@ -34,9 +34,104 @@ CgVecs vecs_at(const CgVecs& v, int64_t off) {
     o.r[k] = v.r[k] + off;
     o.p[k] = v.p[k] + off;
     o.q[k] = v.q[k] + off;
+    o.v4[k] = v.v4[k] != nullptr ? v.v4[k] + off : nullptr;
   }
   o.e = v.e + off;
   return o;
+}
+
+// The batched CG loop runs the TMA-staged sweep unless the cp.async sweep is
+// requested (or the driver lacks the tensor-map encoder).
+bool batch_tma(const tpfa_batch* b) {
+  if (b->sweep_sel == 1) return false;
+  for (const Grid& g : b->g)
+    if (!tma_sweep_ok(g, false, b->precond == 1)) return false;
+  return true;
+}
+
+// Automatic z-runs of the TMA-staged batched sweep: one common run length,
+// the longest (<= 128) that still gives the whole batch about four waves of
+// two blocks per SM (per-instance planning would give the small instances
+// one-plane runs, each re-reading two halo planes).
+int batch_tma_zauto(const tpfa_batch* b) {
+  const int64_t target = (int64_t)b->num_sms * 2 * 4;
+  int z = 128;
+  for (;;) {
+    int64_t blocks = 0;
+    for (const Grid& g : b->g)
+      blocks += plan_tma(g, b->tma_tile, z, b->num_sms, false, b->precond == 1).nblocks;
+    if (blocks >= target || z == 1) return z;
+    z /= 2;
+  }
+}
+
+// Per-instance tilings and tensor maps of the TMA-staged batched sweep for
+// one coefficient array, the interleaved vector records on first use, and
+// partial-sum room for its blocks.
+int setup_batch_tma(tpfa_batch* b, const float* coef) {
+  const int N = b->ninst;
+  const size_t pad = ((size_t)b->cells + 15) / 16 * 16;
+  if (b->vec4 == nullptr) {
+    if (cudaMalloc(&b->vec4, 2 * pad * sizeof(float4)) != cudaSuccess) {
+      cudaGetLastError();
+      b->vec4 = nullptr;
+      return TPFA_ENOMEM;
+    }
+  }
+  if (b->maps_dev == nullptr) {
+    if (cudaMalloc(&b->maps_dev, sizeof(CUtensorMap) * 4 * N) != cudaSuccess ||
+        cudaMalloc(&b->tinst_dev, sizeof(TmaInst) * N) != cudaSuccess) {
+      cudaGetLastError();
+      return TPFA_ENOMEM;
+    }
+  }
+  std::vector<CUtensorMap> maps(4 * (size_t)N);
+  b->tinst.assign(N, TmaInst());
+  const int zauto = batch_tma_zauto(b);
+  int64_t blocks = 0;
+  for (int i = 0; i < N; ++i) {
+    const TmaPlan p = plan_tma(b->g[i], b->tma_tile, b->zc_req[i] > 0 ? b->zc_req[i] : zauto,
+                               b->num_sms, false, b->precond == 1);
+    CgVecs vi{};
+    vi.v4[0] = b->vec4 + b->off[i];
+    vi.v4[1] = b->vec4 + pad + b->off[i];
+    TmaMaps m;
+    if (!make_tma_maps(b->g[i], p, reinterpret_cast<const float4*>(coef) + b->off[i], nullptr,
+                       vi, &m))
+      return TPFA_ECUDA;
+    maps[4 * i] = m.v[0];
+    maps[4 * i + 1] = m.v[1];
+    maps[4 * i + 2] = m.c;
+    maps[4 * i + 3] = m.c;  // no M^-1 map with FP32 records
+    TmaInst& I = b->tinst[i];
+    I.g = b->g[i];
+    I.zc = p.zc;
+    I.nbx = (int)p.nbx;
+    I.nby = (int)p.nby;
+    I.off = b->off[i];
+    I.bstart = blocks;
+    I.nblocks = p.nblocks;
+    I.maps = b->maps_dev + 4 * i;
+    blocks += p.nblocks;
+  }
+  if (blocks > 0x7fffffff) return TPFA_EINVAL;
+  b->tma_blocks = blocks;
+  if ((size_t)blocks * 4 > b->partials_cap) {
+    double* np = nullptr;
+    if (cudaMalloc(&np, (size_t)blocks * 4 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return TPFA_ENOMEM;
+    }
+    cudaDeviceSynchronize();
+    cudaFree(b->partials);
+    b->partials = np;
+    b->partials_cap = (size_t)blocks * 4;
+  }
+  BK(cudaMemcpy(b->maps_dev, maps.data(), sizeof(CUtensorMap) * 4 * N, cudaMemcpyHostToDevice));
+  BK(cudaMemcpy(b->tinst_dev, b->tinst.data(), sizeof(TmaInst) * N, cudaMemcpyHostToDevice));
+  b->v.v4[0] = b->vec4;
+  b->v.v4[1] = b->vec4 + pad;
+  return TPFA_OK;
 }
 
 int use_dev(const tpfa_batch* b) {
@@ -56,10 +151,18 @@ bool grid_ok(const tpfa_grid& g) {
 
 // While loop {batched sweep; condition} for one coefficient array.
 int ensure_batch_loop(tpfa_batch* b, const float* coef) {
-  if (b->loop_exec && b->loop_key_coef == coef && b->loop_key_precond == b->precond)
+  if (b->loop_exec && b->loop_key_coef == coef && b->loop_key_precond == b->precond &&
+      b->loop_key_sweep == b->sweep_sel && b->loop_key_tile == b->tma_tile)
     return TPFA_OK;
   if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
   b->loop_exec = nullptr;
+  const bool tma = batch_tma(b);
+  if (tma) {
+    const int rc = setup_batch_tma(b, coef);
+    if (rc) return rc;
+  } else {
+    b->v.v4[0] = b->v.v4[1] = nullptr;
+  }
   cudaGraph_t graph = nullptr;
   BK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle h;
@@ -76,10 +179,13 @@ int ensure_batch_loop(tpfa_batch* b, const float* coef) {
     e = cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = launch_cg_sweep_batch(b->inst_dev, b->ninst, b->sweep_blocks,
-                                             reinterpret_cast<const float4*>(coef), b->v, b->st,
-                                             b->partials, b->counters, b->precond == 1,
-                                             b->cap_stream);
+      cudaError_t e1 =
+          tma ? launch_cg_sweep_tma_batch(b->tinst_dev, b->ninst, b->tma_blocks, b->tma_tile,
+                                          b->precond == 1, b->v, b->st, b->partials, b->counters,
+                                          b->cap_stream)
+              : launch_cg_sweep_batch(b->inst_dev, b->ninst, b->sweep_blocks,
+                                      reinterpret_cast<const float4*>(coef), b->v, b->st,
+                                      b->partials, b->counters, b->precond == 1, b->cap_stream);
       cudaError_t e2 = launch_batch_cond(b->st, b->ninst, h, b->sweeps, 0, b->cap_stream);
       e = cudaStreamEndCapture(b->cap_stream, &body);
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
@@ -94,6 +200,8 @@ int ensure_batch_loop(tpfa_batch* b, const float* coef) {
   }
   b->loop_key_coef = coef;
   b->loop_key_precond = b->precond;
+  b->loop_key_sweep = b->sweep_sel;
+  b->loop_key_tile = b->tma_tile;
   return TPFA_OK;
 }
 
@@ -117,6 +225,11 @@ int tpfa_batch_create(const tpfa_grid* grids, int n_inst, const int* zc, tpfa_ba
   b->precond = 0;
   b->fcg_m = 4;
   b->fcg_fallback = 0;
+  b->sweep_sel = 0;
+  b->tma_tile = 0;
+  b->zc_req.assign(n_inst, 0);
+  if (zc != nullptr)
+    for (int i = 0; i < n_inst; ++i) b->zc_req[i] = zc[i];
   int rc = TPFA_ECUDA;
   size_t pcap = 0;
   int64_t maxelem = 1;
@@ -165,6 +278,7 @@ int tpfa_batch_create(const tpfa_grid* grids, int n_inst, const int* zc, tpfa_ba
   }
   pcap = (size_t)b->sweep_blocks * 4;
   if ((size_t)maxelem * 2 > pcap) pcap = (size_t)maxelem * 2;
+  b->partials_cap = pcap;
   rc = TPFA_ENOMEM;
   if (cudaMalloc(&b->inst_dev, sizeof(BatchInst) * n_inst) != cudaSuccess) goto fail;
   if (cudaMalloc(&b->st, sizeof(CgState) * n_inst) != cudaSuccess) goto fail;
@@ -211,6 +325,9 @@ int tpfa_batch_destroy(tpfa_batch* b) {
     if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaFree(b->vec);
+  cudaFree(b->vec4);
+  cudaFree(b->maps_dev);
+  cudaFree(b->tinst_dev);
   cudaFree(b->r64);
   cudaFree(b->partials);
   cudaFree(b->counters);
@@ -232,7 +349,15 @@ int tpfa_batch_offsets(const tpfa_batch* b, int64_t* offsets) {
 
 int tpfa_batch_zc(const tpfa_batch* b, int* zc) {
   if (b == nullptr || zc == nullptr) return TPFA_EINVAL;
-  for (int i = 0; i < b->ninst; ++i) zc[i] = (int)b->inst[i].zc;
+  const bool tma = batch_tma(b);
+  const int zauto = tma ? batch_tma_zauto(b) : 0;
+  for (int i = 0; i < b->ninst; ++i) {
+    if (tma)
+      zc[i] = plan_tma(b->g[i], b->tma_tile, b->zc_req[i] > 0 ? b->zc_req[i] : zauto, b->num_sms,
+                       false, b->precond == 1).zc;
+    else
+      zc[i] = (int)b->inst[i].zc;
+  }
   return TPFA_OK;
 }
 
@@ -258,6 +383,14 @@ int tpfa_batch_set_option(tpfa_batch* b, int option, double value) {
     case TPFA_OPT_FCG_FALLBACK:
       if (value != 0 && value != 1) return TPFA_EINVAL;
       b->fcg_fallback = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_SWEEP:
+      if (value != 0 && value != 1) return TPFA_EINVAL;
+      b->sweep_sel = (int)value;
+      return TPFA_OK;
+    case TPFA_OPT_TMA_TILE:
+      if (!(value >= 0 && value < tma_tile_count()) || value != floor(value)) return TPFA_EINVAL;
+      b->tma_tile = (int)value;
       return TPFA_OK;
     default:
       return TPFA_EINVAL;

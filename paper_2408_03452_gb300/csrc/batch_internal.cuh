@@ -30,9 +30,21 @@ struct tpfa_batch {
   float* vec;
   double* r64;
   tpfa::CgVecs v;
+  // TMA-staged batched sweep (the default): requested z-runs per instance,
+  // interleaved vector records, per-instance tilings and tensor maps
+  int sweep_sel;  // 0 = automatic (TMA), 1 = cp.async-staged sweep
+  int tma_tile;
+  std::vector<int> zc_req;
+  float4* vec4;
+  std::vector<tpfa::TmaInst> tinst;
+  tpfa::TmaInst* tinst_dev;
+  CUtensorMap* maps_dev;
+  int64_t tma_blocks;
+  size_t partials_cap;  // doubles
   cudaGraphExec_t loop_exec;
   const void* loop_key_coef;
   int loop_key_precond;
+  int loop_key_sweep, loop_key_tile;
   cudaStream_t cap_stream;
   cudaEvent_t ev[4];
 };

@@ -52,11 +52,30 @@ using tc::mbar_wait;
 using tc::smem_addr;
 
 constexpr int kVecX = 34;      // vector box width: X0-1 .. X0+32
-constexpr int kRecX = 33;      // coefficient box width: X0-1 .. X0+31
+constexpr int kDinvX = 40;     // M^-1 box width (BF16 Jacobi): X0-4 .. X0+35
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls of one mbarrier wait before giving up
 
+// Coefficient records staged per plane, by record type and preconditioner.
+//   FP32 records (Tx, Ty, Tz, D), 16 bytes: box from (X0-1, Y0-1), 33 wide and
+//   TY+1 rows (Tx of x-1 and Ty of y-1 for the own cells); with Jacobi 34 wide
+//   and TY+2 rows, so that D of the halo cells is there too.
+//   BF16 records (Tx, Ty, Tz, E), 8 bytes: box from (X0-2, Y0-1) (a 16-byte
+//   aligned start), 36 wide, TY+1 rows; D = the six faces + E is formed in the
+//   stencil, and with Jacobi M^-1 (from dinv_bf16_kernel) comes from its own
+//   FP32 box, 40 wide from (X0-4, Y0-1), TY+2 rows.
+template <bool B16, bool JAC>
+struct Rec {
+  static constexpr int kBytes = B16 ? 8 : 16;
+  static constexpr int kX = B16 ? 36 : (JAC ? 34 : 33);  // records per box row
+  static constexpr int kC0 = B16 ? 2 : 1;                // box column of x = X0
+  static constexpr int kRows = (JAC && !B16) ? 2 : 1;    // box rows beyond TY
+  static constexpr bool kDinv = B16 && JAC;
+};
+
 struct TmaArgs {
-  CUtensorMap mv[2], mc;  // vector records (two sets), coefficient records
+  CUtensorMap mv[2], mc, md;  // vector records (two sets), coefficients, M^-1 (BF16 Jacobi)
+  const TmaInst* inst;        // batched sweeps: instance table (ninst entries)
+  int ninst;
   Grid g;
   int zc;
   int nbx, nby;  // blocks along x and y
@@ -67,21 +86,24 @@ struct TmaArgs {
   unsigned long long cond;
 };
 
-template <int W, int VY>
+template <int W, int VY, bool B16, bool JAC>
 struct TmaLayout {
+  using RC = Rec<B16, JAC>;
   static constexpr int TY = W * VY;
   static constexpr int kVecBytes = (TY + 2) * kVecX * 16;
-  static constexpr int kRecBytes = (TY + 1) * kRecX * 16;
+  static constexpr int kRecBytes = (TY + RC::kRows) * RC::kX * RC::kBytes;
+  static constexpr int kDinvBytes = RC::kDinv ? (TY + 2) * kDinvX * 4 : 0;
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
   static constexpr int kV = 0;
   static constexpr int kC = al(kVecBytes);
-  static constexpr int kStage = kC + al(kRecBytes);
-  static constexpr uint32_t kTx = kVecBytes + kRecBytes;  // bytes per stage
+  static constexpr int kD = kC + al(kRecBytes);
+  static constexpr int kStage = kD + al(kDinvBytes);
+  static constexpr uint32_t kTx = kVecBytes + kRecBytes + kDinvBytes;  // bytes per stage
 };
 
-template <int W, int VY, int S>
+template <int W, int VY, int S, bool B16, bool JAC>
 constexpr int tma_smem_bytes() {
-  return S * TmaLayout<W, VY>::kStage + 2 * S * 8 + 128;  // stages + barriers + alignment
+  return S * TmaLayout<W, VY, B16, JAC>::kStage + 2 * S * 8 + 128;  // + barriers, alignment
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -101,10 +123,27 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* m, uint64_t
       : "memory");
 }
 
-template <int W, int VY, int S, bool COND>
+// staged record i as (Tx, Ty, Tz, w): w = D (FP32 records) or E (BF16 records)
+template <bool B16>
+__device__ __forceinline__ float4 srec(const unsigned char* base, int i) {
+  if (B16) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[i];
+    return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+  }
+  return reinterpret_cast<const float4*>(base)[i];
+}
+
+// BATCH: one launch sweeps every instance of a batch.  Blocks of an instance
+// are contiguous; each block finds its instance in the table and uses that
+// instance's grid, tiling, cell offset, tensor maps (in global memory), CG
+// state, completion counter and range of partial sums.  The blocks of an
+// instance that is not iterating return at once.
+template <int W, int VY, int S, bool COND, bool B16, bool JAC, bool BATCH = false>
 __global__ void __launch_bounds__((W + 1) * 32)
 cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
-  using LY = TmaLayout<W, VY>;
+  static_assert(!BATCH || (!COND && !B16), "batched sweeps: FP32 records, no graph condition");
+  using LY = TmaLayout<W, VY, B16, JAC>;
+  using RC = Rec<B16, JAC>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -112,15 +151,32 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
   uint64_t* empty = full + S;
 
   CgState* st = a.st;
-  const Grid g = a.g;
+  Grid g = a.g;
+  int nbx = a.nbx, nby = a.nby, zc = a.zc;
+  int64_t lb = blockIdx.x, pstart = 0, pcount = gridDim.x, off = 0;
+  unsigned int* counter = a.counter;
+  const CUtensorMap *mv0 = &a.mv[0], *mv1 = &a.mv[1], *mc = &a.mc, *md = &a.md;
+  if (BATCH) {
+    int lo = 0, hi = a.ninst - 1;  // last instance whose first block <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.inst[mid].bstart <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const TmaInst& I = a.inst[lo];
+    g = I.g; nbx = I.nbx; nby = I.nby; zc = I.zc; off = I.off;
+    lb = blockIdx.x - I.bstart; pstart = I.bstart; pcount = I.nblocks;
+    st = a.st + lo;
+    counter = a.counter + lo;
+    mv0 = I.maps; mv1 = I.maps + 1; mc = I.maps + 2; md = I.maps + 3;
+  }
   if (*(volatile int*)&st->done != kRunning) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (lb == 0 && threadIdx.x == 0) {
       st->launches += 1;
       if (COND) cudaGraphSetConditional(a.cond, 0u);
     }
     return;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lb == 0 && threadIdx.x == 0) {
     const long long n = st->launches + 1;
     st->launches = n;
     if (COND && n > st->guard_limit) cudaGraphSetConditional(a.cond, 0u);
@@ -131,13 +187,13 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int bx = blockIdx.x % a.nbx;
-  const int t = blockIdx.x / a.nbx;
-  const int by = t % a.nby;
-  const int bz = t / a.nby;
+  const int bx = (int)(lb % nbx);
+  const int t = (int)(lb / nbx);
+  const int by = t % nby;
+  const int bz = t / nby;
   const int X0 = 32 * bx, Y0 = LY::TY * by;
-  const int64_t z0 = (int64_t)bz * a.zc;
-  const int64_t z1 = min(z0 + (int64_t)a.zc, g.nz);
+  const int64_t z0 = (int64_t)bz * zc;
+  const int64_t z1 = min(z0 + (int64_t)zc, g.nz);
   const int L = (int)(z1 - z0) + 2;  // planes z0-1 .. z1
 
   if (threadIdx.x == 0) {
@@ -155,7 +211,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
   if (warp == W) {
     // ---- producer: one thread issues the copies of every plane -----------
     if (lane == 0) {
-      const CUtensorMap* mv = &a.mv[par];
+      const CUtensorMap* mv = par ? mv1 : mv0;
       int issued = 0;
       for (int j = 0; j < L; ++j) {
         const int s = j % S;
@@ -166,9 +222,10 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
         const int z = (int)(z0 - 1 + j);
         unsigned char* sb = smem + s * LY::kStage;
         mbar_expect_tx(&full[s], LY::kTx);
-        // x coordinate in floats: 4 (X0 - 1), a multiple of 4 (16 bytes)
+        // x coordinates in 4-byte elements, all multiples of 4 (16 bytes)
         tma_3d(sb + LY::kV, mv, &full[s], 4 * (X0 - 1), Y0 - 1, z);
-        tma_3d(sb + LY::kC, &a.mc, &full[s], 4 * (X0 - 1), Y0 - 1, z);
+        tma_3d(sb + LY::kC, mc, &full[s], (RC::kBytes / 4) * (X0 - RC::kC0), Y0 - 1, z);
+        if (RC::kDinv) tma_3d(sb + LY::kD, md, &full[s], X0 - 4, Y0 - 1, z);
         issued = j + 1;
       }
       // every issued copy must have landed before the block exits: wait for
@@ -190,29 +247,44 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
     // in-plane offset of own row 0; own rows inside the grid stay below
     // nx * ny < 2^31 (checked at context creation)
     const unsigned o0 = (unsigned)(Y0 + jw) * (unsigned)nxi + (unsigned)gx;
-    const int hc = lane == 0 ? 0 : 33;  // box column of this lane's x-halo cell
-    float4* vout = a.v4[par ^ 1];
+    const int hc = lane == 0 ? 0 : 33;  // vector box column of this lane's x-halo cell
+    float4* vout = a.v4[par ^ 1] + off;
+
+    // M^-1 of the staged cell at box row r, column c + (X0 - 1) offset of the
+    // vector box (Jacobi only)
+    auto minv = [&](const unsigned char* sb, int r, int cv) -> float {
+      if (RC::kDinv)
+        return reinterpret_cast<const float*>(sb + LY::kD)[r * kDinvX + cv + 3];
+      return jac_inv(srec<false>(sb + LY::kC, r * RC::kX + cv).w);
+    };
 
     // Form r_k, p_k (and x_k on own rows) of plane j (absolute z = z0 - 1 + j)
     // for rows -1..VY of this lane's column, and p_k of the x-halo cell of the
-    // own rows.
-    auto form = [&](int j, float (&P)[VY + 2], float (&R)[VY], float (&H)[VY], float (&E)[VY],
-                    float& s0) {
-      const float4* sv = reinterpret_cast<const float4*>(smem + (j % S) * LY::kStage + LY::kV);
+    // own rows.  With Jacobi p_k = z_k + beta p_{k-1}, z_k = M^-1 r_k.
+    auto form = [&](int j, float (&P)[VY + 2], float (&R)[VY], float (&Zd)[VY], float (&H)[VY],
+                    float (&E)[VY], float& s0) {
+      const unsigned char* sb = smem + (j % S) * LY::kStage;
+      const float4* sv = reinterpret_cast<const float4*>(sb + LY::kV);
       const int64_t z = z0 - 1 + j;
       const bool own = z >= z0 && z < z1;
 #pragma unroll
       for (int jj = -1; jj <= VY; ++jj) {
-        const float4 v = sv[(jw + jj + 1) * kVecX + lane + 1];  // (r, q, p, x)
-        const float r_ = fmaf(-alpha, v.y, v.x);  // Alg. 1 line 7 (previous iteration)
-        const float p_ = fmaf(beta, v.z, r_);     // Alg. 1 line 10
+        const int r = jw + jj + 1;
+        const float4 v = sv[r * kVecX + lane + 1];  // (r, q, p, x)
+        const float r_ = fmaf(-alpha, v.y, v.x);      // Alg. 1 line 7 (previous iteration)
+        float z_ = r_;
+        if (JAC) z_ = r_ * minv(sb, r, lane + 1);     // z = M^-1 r
+        const float p_ = fmaf(beta, v.z, z_);         // Alg. 1 line 10
         P[jj + 1] = p_;
         if (jj >= 0 && jj < VY) {
           R[jj] = r_;
-          E[jj] = fmaf(alpha, v.z, v.w);          // Alg. 1 line 6
-          const float4 h = sv[(jw + jj + 1) * kVecX + hc];
-          H[jj] = fmaf(beta, h.z, fmaf(-alpha, h.y, h.x));
-          if (own && ((rowok >> jj) & 1u)) s0 = fmaf(r_, r_, s0);
+          Zd[jj] = z_;
+          E[jj] = fmaf(alpha, v.z, v.w);              // Alg. 1 line 6
+          const float4 h = sv[r * kVecX + hc];
+          float hz = fmaf(-alpha, h.y, h.x);
+          if (JAC) hz = hz * minv(sb, r, hc);
+          H[jj] = fmaf(beta, h.z, hz);
+          if (own && ((rowok >> jj) & 1u)) s0 = fmaf(r_, z_, s0);
         }
       }
     };
@@ -224,38 +296,40 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
       if (lane == 0) mbar_arrive(&empty[j % S]);
     };
 
-    float Pm[VY], P0[VY + 2], R0[VY], H0[VY], E0[VY], Tzm[VY];
+    float Pm[VY], P0[VY + 2], R0[VY], Z0[VY], H0[VY], E0[VY], Tzm[VY];
     float s0 = 0.f;
     if (!wait_full(0)) fault = true;
     if (!fault) {  // plane z0 - 1: direction below the first plane, and its Tz
-      float Pt[VY + 2], Rt[VY], Ht[VY], Et[VY];
-      form(0, Pt, Rt, Ht, Et, s0);
-      const float4* sc = reinterpret_cast<const float4*>(smem + LY::kC);
+      float Pt[VY + 2], Rt[VY], Zt[VY], Ht[VY], Et[VY];
+      form(0, Pt, Rt, Zt, Ht, Et, s0);
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
         Pm[jj] = Pt[jj + 1];
-        Tzm[jj] = sc[(jw + jj + 1) * kRecX + lane + 1].z;
+        Tzm[jj] = srec<B16>(smem + LY::kC, (jw + jj + 1) * RC::kX + lane + RC::kC0).z;
       }
       release(0);
       if (!wait_full(1)) fault = true;
     }
-    if (!fault) form(1, P0, R0, H0, E0, s0);
+    if (!fault) form(1, P0, R0, Z0, H0, E0, s0);
 
     for (int64_t z = z0; z < z1 && !fault; ++z) {
       const int jc = (int)(z - z0) + 1;  // plane z
       const int jf = jc + 1;             // plane z + 1
       if (!wait_full(jf)) { fault = true; break; }
-      float Pp[VY + 2], Rp[VY], Hp[VY], Ep[VY];
-      form(jf, Pp, Rp, Hp, Ep, s0);
-      const float4* sc = reinterpret_cast<const float4*>(smem + (jc % S) * LY::kStage + LY::kC);
+      float Pp[VY + 2], Rp[VY], Zp[VY], Hp[VY], Ep[VY];
+      form(jf, Pp, Rp, Zp, Hp, Ep, s0);
+      const unsigned char* sb = smem + (jc % S) * LY::kStage;
       float4* vz = vout + g.plane * z;
       float s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
-        const int ri = (jw + jj + 1) * kRecX + lane + 1;
-        const float4 cf = sc[ri];
-        const float txm = sc[ri - 1].x;
-        const float tym = sc[ri - kRecX].y;
+        const int r = jw + jj + 1;
+        const int ri = r * RC::kX + lane + RC::kC0;
+        float4 cf = srec<B16>(sb + LY::kC, ri);
+        const float txm = srec<B16>(sb + LY::kC, ri - 1).x;
+        const float tym = srec<B16>(sb + LY::kC, ri - RC::kX).y;
+        // BF16 records: D = T(-x) + T(+x) + T(-y) + T(+y) + T(-z) + T(+z) + E
+        if (B16) cf.w = (((((txm + cf.x) + tym) + cf.y) + Tzm[jj]) + cf.z) + cf.w;
         const float pc = P0[jj + 1];
         float pxm = __shfl_up_sync(kFull, pc, 1);
         float pxp = __shfl_down_sync(kFull, pc, 1);
@@ -266,8 +340,10 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
         if ((rowok >> jj) & 1u) {
           vz[o0 + (unsigned)(jj * nxi)] = make_float4(R0[jj], q, pc, E0[jj]);
           s1 = fmaf(pc, q, s1);
-          s2 = fmaf(R0[jj], q, s2);
-          s3 = fmaf(q, q, s3);
+          s2 = fmaf(Z0[jj], q, s2);
+          if (JAC && B16) s3 = fmaf(q, q * minv(sb, r, lane + 1), s3);
+          else if (JAC) s3 = fmaf(q, q * jac_inv(cf.w), s3);
+          else s3 = fmaf(q, q, s3);
         }
         Tzm[jj] = cf.z;
         Pm[jj] = pc;
@@ -281,6 +357,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
         R0[jj] = Rp[jj];
+        Z0[jj] = Zp[jj];
         H0[jj] = Hp[jj];
         E0[jj] = Ep[jj];
       }
@@ -297,7 +374,7 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
   double v[4] = {kval(acc[0]), kval(acc[1]), kval(acc[2]), kval(acc[3])};
   block_partial<4>(v, a.partials);
   double tot[4];
-  if (last_block_range<4>(a.partials, a.counter, 0, gridDim.x, tot) && threadIdx.x == 0)
+  if (last_block_range<4>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0)
     cg_finish(st, tot, a.cond, COND);
 }
 
@@ -339,49 +416,105 @@ bool encode_rec(CUtensorMap* m, const float4* base, const Grid& g, int bw, int b
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int W, int VY, int S, bool COND>
+// FP32 field [nz][ny][nx] as a 3-D tensor, box (bw, bh, 1) (needs nx % 4 == 0)
+bool encode_f32(CUtensorMap* m, const float* base, const Grid& g, int bw, int bh) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.plane * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 8-byte BF16 records [nz][ny][nx][4 x bf16] as a 3-D tensor of 32-bit words,
+// rows of 2 nx words, box (2 bw, bh, 1) (needs nx % 2 == 0)
+bool encode_rec16(CUtensorMap* m, const uint2* base, const Grid& g, int bw, int bh) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) return false;
+  const cuuint64_t dim[3] = {2 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.plane * 8};
+  const cuuint32_t box[3] = {2 * (cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint2*>(base), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int W, int VY, int S, bool COND, bool B16, bool JAC>
 cudaError_t launch_tma_t(const TmaArgs& a, int64_t nblocks, cudaStream_t s) {
-  constexpr int smem = tma_smem_bytes<W, VY, S>();
-  cudaError_t e = cudaFuncSetAttribute(cg_sweep_tma_kernel<W, VY, S, COND>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  constexpr int smem = tma_smem_bytes<W, VY, S, B16, JAC>();
+  auto fn = cg_sweep_tma_kernel<W, VY, S, COND, B16, JAC>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  cg_sweep_tma_kernel<W, VY, S, COND><<<(unsigned)nblocks, (W + 1) * 32, smem, s>>>(a);
+  fn<<<(unsigned)nblocks, (W + 1) * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int W, int VY, int S>
+template <int W, int VY, int S, bool B16, bool JAC>
 int tma_blocks_per_sm_t() {
-  constexpr int smem = tma_smem_bytes<W, VY, S>();
-  if (cudaFuncSetAttribute(cg_sweep_tma_kernel<W, VY, S, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+  constexpr int smem = tma_smem_bytes<W, VY, S, B16, JAC>();
+  auto fn = cg_sweep_tma_kernel<W, VY, S, true, B16, JAC>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cg_sweep_tma_kernel<W, VY, S, true>,
-                                                    (W + 1) * 32, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (W + 1) * 32, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
-// (W, VY, S) of each tile choice
+// (W, VY, S) of each tile choice; the Jacobi and BF16 variants use tile 0
 struct TileShape {
   int w, vy, s;
 };
 constexpr TileShape kTmaTiles[] = {{4, 4, 4}, {4, 4, 3}, {8, 4, 3}, {4, 2, 6}};
 constexpr int kNumTmaTiles = (int)(sizeof(kTmaTiles) / sizeof(kTmaTiles[0]));
 
+template <int W, int VY, int S, bool JAC>
+cudaError_t launch_tma_batch_t(const TmaArgs& a, int64_t nblocks, cudaStream_t s) {
+  constexpr int smem = tma_smem_bytes<W, VY, S, false, JAC>();
+  auto fn = cg_sweep_tma_kernel<W, VY, S, false, false, JAC, true>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)nblocks, (W + 1) * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool COND>
+cudaError_t launch_variant(const TmaArgs& a, const TmaPlan& p, cudaStream_t s) {
+  if (p.b16 && p.jac) return launch_tma_t<4, 4, 4, COND, true, true>(a, p.nblocks, s);
+  if (p.b16) return launch_tma_t<4, 4, 4, COND, true, false>(a, p.nblocks, s);
+  if (p.jac) return launch_tma_t<4, 4, 4, COND, false, true>(a, p.nblocks, s);
+  switch (p.tile) {
+    case 0: return launch_tma_t<4, 4, 4, COND, false, false>(a, p.nblocks, s);
+    case 1: return launch_tma_t<4, 4, 3, COND, false, false>(a, p.nblocks, s);
+    case 2: return launch_tma_t<8, 4, 3, COND, false, false>(a, p.nblocks, s);
+    case 3: return launch_tma_t<4, 2, 6, COND, false, false>(a, p.nblocks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
-bool tma_sweep_ok(const Grid& g) {
-  return g.nx < (1 << 30) && g.ny < (1 << 30) && g.nz < (1 << 30) && encode_fn() != nullptr;
+bool tma_sweep_ok(const Grid& g, bool b16, bool jac) {
+  if (g.nx >= (1 << 30) || g.ny >= (1 << 30) || g.nz >= (1 << 30) || encode_fn() == nullptr)
+    return false;
+  if (b16 && g.nx % 2 != 0) return false;         // 8-byte records: 16-byte row strides
+  if (b16 && jac && g.nx % 4 != 0) return false;  // the FP32 M^-1 array: likewise
+  return true;
 }
 
 int tma_tile_count() { return kNumTmaTiles; }
 
-TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms) {
+TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac) {
   TmaPlan p{};
-  if (tile < 0 || tile >= kNumTmaTiles) tile = 0;
+  if (tile < 0 || tile >= kNumTmaTiles || b16 || jac) tile = 0;
   const TileShape ts = kTmaTiles[tile];
   p.tile = tile;
+  p.b16 = b16;
+  p.jac = jac;
   p.w = ts.w;
   p.vy = ts.vy;
   p.stages = ts.s;
@@ -403,26 +536,45 @@ TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms) {
   return p;
 }
 
-int tma_blocks_per_sm(int tile) {
+int tma_blocks_per_sm(const TmaPlan& p) {
   int nb = 0;
-  switch (tile) {
-    case 0: nb = tma_blocks_per_sm_t<4, 4, 4>(); break;
-    case 1: nb = tma_blocks_per_sm_t<4, 4, 3>(); break;
-    case 2: nb = tma_blocks_per_sm_t<8, 4, 3>(); break;
-    case 3: nb = tma_blocks_per_sm_t<4, 2, 6>(); break;
-    default: break;
+  if (p.b16 && p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, true, true>();
+  else if (p.b16) nb = tma_blocks_per_sm_t<4, 4, 4, true, false>();
+  else if (p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, false, true>();
+  else {
+    switch (p.tile) {
+      case 0: nb = tma_blocks_per_sm_t<4, 4, 4, false, false>(); break;
+      case 1: nb = tma_blocks_per_sm_t<4, 4, 3, false, false>(); break;
+      case 2: nb = tma_blocks_per_sm_t<8, 4, 3, false, false>(); break;
+      case 3: nb = tma_blocks_per_sm_t<4, 2, 6, false, false>(); break;
+      default: break;
+    }
   }
   if (nb == 0) cudaGetLastError();
   return nb;
 }
 
-bool make_tma_maps(const Grid& g, const TmaPlan& p, const float4* coef, const CgVecs& v,
-                   TmaMaps* m) {
+bool make_tma_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* dinv,
+                   const CgVecs& v, TmaMaps* m) {
   const int ty = p.w * p.vy;
   if (v.v4[0] == nullptr || v.v4[1] == nullptr) return false;
   bool ok = true;
   for (int i = 0; i < 2; ++i) ok = ok && encode_rec(&m->v[i], v.v4[i], g, kVecX, ty + 2);
-  ok = ok && encode_rec(&m->c, coef, g, kRecX, ty + 1);
+  if (p.b16 && p.jac) {
+    using RC = Rec<true, true>;
+    ok = ok && dinv != nullptr;
+    ok = ok && encode_rec16(&m->c, static_cast<const uint2*>(coef), g, RC::kX, ty + RC::kRows);
+    ok = ok && encode_f32(&m->d, dinv, g, kDinvX, ty + 2);
+  } else if (p.b16) {
+    using RC = Rec<true, false>;
+    ok = ok && encode_rec16(&m->c, static_cast<const uint2*>(coef), g, RC::kX, ty + RC::kRows);
+  } else if (p.jac) {
+    using RC = Rec<false, true>;
+    ok = ok && encode_rec(&m->c, static_cast<const float4*>(coef), g, RC::kX, ty + RC::kRows);
+  } else {
+    using RC = Rec<false, false>;
+    ok = ok && encode_rec(&m->c, static_cast<const float4*>(coef), g, RC::kX, ty + RC::kRows);
+  }
   return ok;
 }
 
@@ -436,6 +588,7 @@ cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& 
     a.v4[i] = v.v4[i];
   }
   a.mc = m.c;
+  a.md = m.d;
   a.g = g;
   a.zc = p.zc;
   a.nbx = (int)p.nbx;
@@ -444,12 +597,27 @@ cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& 
   a.partials = partials;
   a.counter = counter;
   a.cond = cond;
-  const bool c = use_cond != 0;
-  switch (p.tile) {
-    case 0: return c ? launch_tma_t<4, 4, 4, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 4, false>(a, p.nblocks, s);
-    case 1: return c ? launch_tma_t<4, 4, 3, true>(a, p.nblocks, s) : launch_tma_t<4, 4, 3, false>(a, p.nblocks, s);
-    case 2: return c ? launch_tma_t<8, 4, 3, true>(a, p.nblocks, s) : launch_tma_t<8, 4, 3, false>(a, p.nblocks, s);
-    case 3: return c ? launch_tma_t<4, 2, 6, true>(a, p.nblocks, s) : launch_tma_t<4, 2, 6, false>(a, p.nblocks, s);
+  return use_cond != 0 ? launch_variant<true>(a, p, s) : launch_variant<false>(a, p, s);
+}
+
+cudaError_t launch_cg_sweep_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int tile,
+                                      bool jac, CgVecs v, CgState* st, double* partials,
+                                      unsigned int* counters, cudaStream_t s) {
+  TmaArgs a;
+  memset(&a, 0, sizeof(a));
+  a.inst = inst;
+  a.ninst = ninst;
+  a.v4[0] = v.v4[0];
+  a.v4[1] = v.v4[1];
+  a.st = st;
+  a.partials = partials;
+  a.counter = counters;
+  if (jac) return launch_tma_batch_t<4, 4, 4, true>(a, nblocks, s);
+  switch (tile) {
+    case 0: return launch_tma_batch_t<4, 4, 4, false>(a, nblocks, s);
+    case 1: return launch_tma_batch_t<4, 4, 3, false>(a, nblocks, s);
+    case 2: return launch_tma_batch_t<8, 4, 3, false>(a, nblocks, s);
+    case 3: return launch_tma_batch_t<4, 2, 6, false>(a, nblocks, s);
     default: return cudaErrorInvalidValue;
   }
 }

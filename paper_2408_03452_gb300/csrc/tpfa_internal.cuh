@@ -74,23 +74,44 @@ struct CgVecs {
 
 // Tiling of the TMA-staged CG sweep (sweep_tma.cu): blocks of w compute warps
 // (plus one producer warp) own 32 columns x (w * vy) rows and march through
-// zc planes with a ring of `stages` shared-memory stages.
+// zc planes with a ring of `stages` shared-memory stages.  b16: BF16 records;
+// jac: Jacobi-preconditioned iteration (both use tile 0).
 struct TmaPlan {
   int tile;    // index of the (w, vy, stages) choice
+  bool b16, jac;
   int w, vy, stages, zc;
   int64_t nbx, nby, nbz, nblocks;
 };
-// Tensor maps of the arrays the TMA sweep reads (both vector-record sets,
-// coefficient records).
+// Tensor maps of the arrays the TMA sweep reads: both vector-record sets, the
+// coefficient records and (BF16 Jacobi) the M^-1 array.
 struct TmaMaps {
-  CUtensorMap v[2], c;
+  CUtensorMap v[2], c, d;
 };
-bool tma_sweep_ok(const Grid& g);  // the driver exposes the tensor-map encoder
+// the driver exposes the tensor-map encoder and the record rows have 16-byte
+// strides (BF16 records: nx even; BF16 Jacobi: nx % 4 == 0)
+bool tma_sweep_ok(const Grid& g, bool b16, bool jac);
 int tma_tile_count();
-TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms);
-int tma_blocks_per_sm(int tile);
-bool make_tma_maps(const Grid& g, const TmaPlan& p, const float4* coef, const CgVecs& v,
-                   TmaMaps* m);
+TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac);
+int tma_blocks_per_sm(const TmaPlan& p);
+bool make_tma_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* dinv,
+                   const CgVecs& v, TmaMaps* m);
+
+// One instance of a batched TMA-staged sweep (device table): its grid and
+// tiling, where its cells and blocks start, and its tensor maps (v[0], v[1],
+// c, d of TmaMaps, in device memory).
+struct TmaInst {
+  Grid g;
+  int zc, nbx, nby;
+  int64_t off;
+  int64_t bstart;
+  int64_t nblocks;
+  const CUtensorMap* maps;
+};
+// Batched CG sweep through the TMA-staged kernel: FP32 records, plain
+// (any tile) or Jacobi (tile 0); v.v4 are the batch's record sets.
+cudaError_t launch_cg_sweep_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int tile,
+                                      bool jac, CgVecs v, CgState* st, double* partials,
+                                      unsigned int* counters, cudaStream_t s);
 
 // ---- launchers (kernels_*.cu) ---------------------------------------------
 
@@ -134,7 +155,7 @@ cudaError_t launch_correct(const Grid& g, const CgVecs& v, double* x, const CgSt
                            cudaStream_t s);
 
 int sweep_blocks_per_sm(int vy, int stages);
-// Plain FP32-record CG sweep through the TMA-staged kernel
+// CG sweep through the TMA-staged kernel (the variant the plan names)
 cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& m, CgVecs v,
                                 CgState* st, double* partials, unsigned int* counter,
                                 unsigned long long cond, int use_cond, cudaStream_t s);

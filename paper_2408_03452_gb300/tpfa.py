@@ -610,9 +610,13 @@ class BatchContext:
         _check(lib().tpfa_batch_offsets(self._h, C.cast(off, C.c_void_p)), "tpfa_batch_offsets")
         self.offsets = [int(v) for v in off]
         self.n = self.offsets[-1]
+
+    @property
+    def zc(self):
+        """z-run length per instance of the batched sweep the options select."""
         z = (C.c_int * self.ninst)()
         _check(lib().tpfa_batch_zc(self._h, C.cast(z, C.c_void_p)), "tpfa_batch_zc")
-        self.zc = [int(v) for v in z]
+        return [int(v) for v in z]
 
     def close(self):
         if self._h:

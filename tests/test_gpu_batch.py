@@ -43,10 +43,11 @@ def _cat(insts, key):
     return torch.from_numpy(np.concatenate([w[key] for w in insts])).cuda()
 
 
-def _batch_solve(tp, insts, tol, zc=None, precond=0):
+def _batch_solve(tp, insts, tol, zc=None, precond=0, sweep=0):
     grids = [(w["nx"], w["ny"], w["nz"]) for w in insts]
     with tp.BatchContext(grids, zc=zc) as bc:
         bc.set_option("precond", precond)
+        bc.set_option("sweep", sweep)
         K, mask, pD = _cat(insts, "K"), _cat(insts, "mask"), _cat(insts, "pD")
         coef, coef64 = bc.build_trans(K, mask, None, 0.0)
         b = bc.build_rhs(K, mask, None, pD)
@@ -56,12 +57,13 @@ def _batch_solve(tp, insts, tol, zc=None, precond=0):
         return xs, per, total, bc.zc
 
 
-def _single_solve(tp, w, tol, zc, precond=0):
+def _single_solve(tp, w, tol, zc, precond=0, sweep=0):
     with tp.Context(w["nx"], w["ny"], w["nz"]) as ctx:
         ctx.set_option("tile_vy", 4)
         ctx.set_option("stages", 4)
         ctx.set_option("tile_zc", zc)
         ctx.set_option("precond", precond)
+        ctx.set_option("sweep", sweep)
         K, mask, pD = (torch.from_numpy(w[k]).cuda() for k in ("K", "mask", "pD"))
         coef, coef64 = ctx.build_trans(K, mask, None, 0.0)
         b = ctx.build_rhs(K, mask, None, pD)
@@ -70,17 +72,19 @@ def _single_solve(tp, w, tol, zc, precond=0):
         return x.cpu().numpy(), info
 
 
+@pytest.mark.parametrize("sweep", [0, 1], ids=["tma", "cpasync"])
 @pytest.mark.parametrize("precond", [0, 1])
-def test_batch_matches_oracle_and_single_solves(tp, oracle_mod, precond):
+def test_batch_matches_oracle_and_single_solves(tp, oracle_mod, precond, sweep):
+    """Both batched sweeps (TMA-staged, the default, and cp.async-staged)."""
     O = oracle_mod
     insts = _instances()
-    xs, per, total, zc = _batch_solve(tp, insts, 1e-8, precond=precond)
+    xs, per, total, zc = _batch_solve(tp, insts, 1e-8, precond=precond, sweep=sweep)
     assert total["code"] == 0, (total, per)
     for i, w in enumerate(insts):
         g = O.Grid(w["nx"], w["ny"], w["nz"])
         assert per[i]["status"] == 0, per[i]
         assert O.rel_residual(g, w["K"], w["mask"], 0.0, None, w["pD"], xs[i]) <= 1e-8 * 1.001
-        xi, info = _single_solve(tp, w, 1e-8, zc[i], precond)
+        xi, info = _single_solve(tp, w, 1e-8, zc[i], precond, sweep)
         assert np.array_equal(xs[i], xi), i
         assert per[i]["iters"] == info["iters"], i
     # the zero right-hand side instance: x = 0 without iterating
@@ -89,10 +93,11 @@ def test_batch_matches_oracle_and_single_solves(tp, oracle_mod, precond):
     assert len({p["iters"] for p in per[:-1]}) > 1
 
 
-def test_batch_explicit_tiling_and_loose_tolerance(tp, oracle_mod):
+@pytest.mark.parametrize("sweep", [0, 1], ids=["tma", "cpasync"])
+def test_batch_explicit_tiling_and_loose_tolerance(tp, oracle_mod, sweep):
     O = oracle_mod
     insts = _instances()[:4]
-    xs, per, total, zc = _batch_solve(tp, insts, 1e-6, zc=[1, 2, 3, 1])
+    xs, per, total, zc = _batch_solve(tp, insts, 1e-6, zc=[1, 2, 3, 1], sweep=sweep)
     assert zc == [1, 2, 3, 1]
     assert total["code"] == 0
     for i, w in enumerate(insts):
@@ -105,3 +110,23 @@ def test_batch_rejects_bad_grids(tp):
         tp.BatchContext([(4, 4, 4), (0, 3, 3)])
     with pytest.raises(tp.TpfaError):
         tp.BatchContext([(4, 4, 4)], zc=[-1])
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3])
+def test_batch_tma_tiles(tp, oracle_mod, tile):
+    """The other tiles of the TMA-staged batched sweep (plain CG)."""
+    O = oracle_mod
+    insts = _instances()
+    grids = [(w["nx"], w["ny"], w["nz"]) for w in insts]
+    with tp.BatchContext(grids) as bc:
+        bc.set_option("tma_tile", tile)
+        K, mask, pD = _cat(insts, "K"), _cat(insts, "mask"), _cat(insts, "pD")
+        coef, coef64 = bc.build_trans(K, mask, None, 0.0)
+        b = bc.build_rhs(K, mask, None, pD)
+        x, per, total = bc.cg_solve(coef, coef64, b, tol=1e-8)
+        torch.cuda.synchronize()
+        assert total["code"] == 0, (total, per)
+        for i, w in enumerate(insts):
+            xi = x[bc.offsets[i]:bc.offsets[i + 1]].cpu().numpy()
+            g = O.Grid(w["nx"], w["ny"], w["nz"])
+            assert O.rel_residual(g, w["K"], w["mask"], 0.0, None, w["pD"], xi) <= 1e-8 * 1.001

@@ -68,27 +68,54 @@ def _solve(tp, shape, c, tol, maxit, opts):
 
 
 def test_tiling_selection(tp):
-    for shape in ((64, 20, 9), (66, 20, 9)):
+    for shape in ((64, 20, 9), (66, 20, 9), (65, 20, 9)):
+        nx = shape[0]
         with tp.Context(*shape) as ctx:
-            assert tiling(tp, ctx)["kernel"] == 2          # FP32 records: TMA sweep
-            assert tiling(tp, ctx, 1)["kernel"] == 1       # BF16 records: cp.async sweep
-            assert tiling(tp, ctx, 2)["kernel"] == 1       # tpfa_apply
+            assert tiling(tp, ctx)["kernel"] == 2                                # FP32 records
+            assert tiling(tp, ctx, 1)["kernel"] == (2 if nx % 2 == 0 else 1)     # BF16 records
+            assert tiling(tp, ctx, 2)["kernel"] == 1                             # tpfa_apply
             ctx.set_option("precond", 1)
-            assert tiling(tp, ctx)["kernel"] == 1
+            assert tiling(tp, ctx)["kernel"] == 2
+            assert tiling(tp, ctx, 1)["kernel"] == (2 if nx % 4 == 0 else 1)     # BF16 Jacobi
             ctx.set_option("precond", 0)
             ctx.set_option("sweep", 1)
             assert tiling(tp, ctx)["kernel"] == 1
             ctx.set_option("sweep", 2)
             t = tiling(tp, ctx)
             assert t["kernel"] == 2 and t["warps"] == 4 and t["vy"] == 4 and t["stages"] == 4
-            nbx = (shape[0] + 31) // 32
+            nbx = (nx + 31) // 32
             for tile, (w, vy, st) in enumerate([(4, 4, 4), (4, 4, 3), (8, 4, 3), (4, 2, 6)]):
                 ctx.set_option("tma_tile", tile)
                 t = tiling(tp, ctx)
                 assert (t["warps"], t["vy"], t["stages"]) == (w, vy, st)
                 assert t["blocks"] == nbx * ((20 + w * vy - 1) // (w * vy)) * ((9 + t["zc"] - 1) // t["zc"])
+                if nx % 2 == 0:  # BF16 records always use tile 0
+                    t16 = tiling(tp, ctx, 1)
+                    assert (t16["warps"], t16["vy"], t16["stages"]) == (4, 4, 4)
             with pytest.raises(tp.TpfaError):
                 ctx.set_option("tma_tile", 4)
+            if nx % 2 != 0:
+                with pytest.raises(tp.TpfaError):
+                    tiling(tp, ctx, 1)  # TMA requested, BF16 records, odd nx
+
+
+def test_tma_sweep_refused_where_it_cannot_run(tp):
+    """BF16 records with an odd nx have row strides that are not multiples of
+    16 bytes: a requested TMA sweep is refused, the automatic choice falls
+    back to the cp.async sweep."""
+    shape = (65, 8, 8)
+    c = _case(shape, 1, "wells")
+    with tp.Context(*shape) as ctx:
+        K = _dev(c["K"])
+        coef, coef64 = ctx.build_trans(K, None, None, 1e-3)
+        c16 = ctx.build_trans_bf16(K, None, None, 1e-3)
+        b = ctx.build_rhs(K, None, _dev(c["q"]), None)
+        ctx.set_option("sweep", 2)
+        with pytest.raises(tp.TpfaError):
+            ctx.cg_solve(c16, coef64, b, tol=1e-8)
+        ctx.set_option("sweep", 0)
+        _, info = ctx.cg_solve(c16, coef64, b, tol=1e-8)
+        assert info["code"] == 0
 
 
 ITER_SHAPES = [((32, 32, 32), "dirx"), ((36, 17, 9), "wells"), ((4, 4, 4), "dirx"),
@@ -161,3 +188,46 @@ def test_tma_loop_modes_agree_bitwise(tp):
     xc, ic, _ = _solve(tp, shape, c, 1e-8, 400000, {"sweep": 2, "loop": 0})
     assert np.array_equal(xa, xb) and np.array_equal(xa, xc)
     assert ia["iters"] == ib["iters"] == ic["iters"]
+
+
+def _solve_var(tp, shape, c, tol, maxit, opts, b16):
+    with tp.Context(*shape) as ctx:
+        for k, v in opts.items():
+            ctx.set_option(k, v)
+        K, mask = _dev(c["K"]), _dev(c["mask"])
+        coef, coef64 = ctx.build_trans(K, mask, None, c["d"])
+        inner = ctx.build_trans_bf16(K, mask, None, c["d"]) if b16 else coef
+        b = ctx.build_rhs(K, mask, _dev(c["q"]), _dev(c["pD"]))
+        x, info = ctx.cg_solve(inner, coef64, b, tol=tol, maxit=maxit, check=False)
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), info, ctx.tiling(1 if b16 else 0)
+
+
+VARIANTS = [(False, 1), (True, 0), (True, 1)]  # (BF16 records, Jacobi)
+
+
+@pytest.mark.parametrize("b16,jac", VARIANTS, ids=["f32-jacobi", "bf16", "bf16-jacobi"])
+@pytest.mark.parametrize("shape,kind", [((32, 32, 32), "dirx"), ((36, 17, 9), "wells"),
+                                        ((100, 30, 41), "wells"), ((64, 1, 7), "wells"),
+                                        ((8, 50, 130), "dirx"), ((4, 1, 1), "wells")])
+def test_tma_variants_match_cpasync_and_oracle(tp, oracle_mod, b16, jac, shape, kind):
+    """The Jacobi and BF16-record TMA variants: the first iterates agree with
+    the cp.async sweep's (same per-cell arithmetic; dot products summed in
+    another order), and the refined solve meets the tolerance by the
+    oracle's FP64 residual."""
+    O = oracle_mod
+    c = _case(shape, 6, kind)
+    n = shape[0] * shape[1] * shape[2]
+    for k in [k for k in (1, 3, 8) if k < n]:  # CG ends exactly within n iterations
+        xs = {}
+        for sweep in (1, 2):
+            x, info, t = _solve_var(tp, shape, c, 1e-30, k,
+                                    {"sweep": sweep, "precond": jac, "max_outer": 1}, b16)
+            assert t["kernel"] == sweep and info["iters"] == k, (t, info)
+            xs[sweep] = x
+        assert np.linalg.norm(xs[1] - xs[2]) <= 1e-5 * np.linalg.norm(xs[1]), k
+    tol = 1e-10 if b16 else 1e-8
+    x, info, t = _solve_var(tp, shape, c, tol, 400000, {"sweep": 2, "precond": jac}, b16)
+    assert t["kernel"] == 2 and info["code"] == 0, info
+    g = O.Grid(*shape)
+    assert O.rel_residual(g, c["K"], c["mask"], c["d"], c["q"], c["pD"], x) <= tol * 1.01
