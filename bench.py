@@ -720,9 +720,23 @@ def run_learned(a, dev, rank, local, barrier):
                                     "fell_back": fi["fell_back"]},
                        "jacobi_pcg": {"iters": ji["iters"], "s": ji["total_ms"] / 1e3}})
         del pk
-    # the batched form: the uneven 96-instance ensemble with the same network
+    # the batched form: the uneven 96-instance ensemble, with the same network
+    # and with one trained on the ensemble's own distribution (sigma ~ U(0.5,
+    # 2.5), Dirichlet ends on a random axis, p_hi ~ U(0.5, 2))
     ensemble = learned.evaluate_ensemble(P, seed=a.seed, levels=LEARNED_LEVELS,
                                          fcg_m=LEARNED_FCG_M, tol=a.tol)
+    t1 = time.perf_counter()
+    ds_mix = learned.make_dataset(a.n_real, a.snaps, 64, mixed=True)
+    P_mix, hist_mix = learned.train(ds_mix, epochs=a.epochs, batch=16, lr=1e-3,
+                                    levels=LEARNED_LEVELS)
+    mix_s = time.perf_counter() - t1
+    del ds_mix
+    torch.cuda.empty_cache()
+    ens_mix = learned.evaluate_ensemble(P_mix, seed=a.seed, levels=LEARNED_LEVELS,
+                                        fcg_m=LEARNED_FCG_M, tol=a.tol)
+    ensemble["unet_fcg_batched_mixed_training"] = dict(
+        ens_mix["unet_fcg_batched"], training_s=mix_s,
+        final_val_loss=hist_mix["val_loss"][-1], jacobi_loss=hist_mix["jacobi_loss"])
     apply = learned.apply_bench(nn, 10)
     conv_ms = time_conv(tpfa, dev, nn, 16, 16)
     # the operator application: two per FCG iteration, the largest kernel time

@@ -51,18 +51,30 @@ def init_params(seed: int) -> torch.Tensor:
     return torch.from_numpy(p)
 
 
-def realization(seed: int, n: int, sigma: float):
+STREAM_TRAIN_MIX = 41
+
+
+def realization(seed: int, n: int, sigma: float, axis: str = "x", p_hi: float = 1.0):
     K = synth.lognormal_field(n, n, n, sigma, seed)
-    mask, pD = synth.dirichlet_faces(n, n, n, "x", 1.0, 0.0)
+    mask, pD = synth.dirichlet_faces(n, n, n, axis, p_hi, 0.0)
     return K, mask, pD
+
+
+def mixed_draw(seed: int, sigma_range=(0.5, 2.5)):
+    """sigma ~ U(sigma_range), Dirichlet axis from {x, y, z}, p_hi ~ U(0.5, 2):
+    the distribution the batched ensemble draws its instances from."""
+    u = synth.uniform(seed, STREAM_TRAIN_MIX, np.arange(3, dtype=np.uint64))
+    sigma = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * float(u[0])
+    return sigma, "xyz"[min(int(u[1] * 3), 2)], 0.5 + 1.5 * float(u[2])
 
 
 class Problem:
     """One realization on the GPU: coefficients, right-hand side, ln K."""
 
-    def __init__(self, ctx: tpfa.Context, seed: int, n: int, sigma: float):
+    def __init__(self, ctx: tpfa.Context, seed: int, n: int, sigma: float, axis: str = "x",
+                 p_hi: float = 1.0):
         dev = ctx.device
-        K, mask, pD = realization(seed, n, sigma)
+        K, mask, pD = realization(seed, n, sigma, axis, p_hi)
         Kd = torch.from_numpy(K).to(dev)
         md = torch.from_numpy(mask).to(dev)
         self.coef, self.coef64 = ctx.build_trans(Kd, md)
@@ -94,15 +106,21 @@ class Dataset:
         self.lnk = torch.stack([p.lnk for p in self.problems])
 
 
-def make_dataset(n_real=50, snaps=40, n=64, sigma=1.5, seed=1000, tol=1e-10, log=None):
-    """n_real realizations x snaps pairs (r_k, e_k) from plain CG."""
+def make_dataset(n_real=50, snaps=40, n=64, sigma=1.5, seed=1000, tol=1e-10, log=None,
+                 mixed=False):
+    """n_real realizations x snaps pairs (r_k, e_k) from plain CG.  mixed:
+    each realization draws sigma, the Dirichlet axis and p_hi as the batched
+    ensemble does (mixed_draw) instead of sigma with Dirichlet x ends."""
     ctx = tpfa.Context(n, n, n)
     ctx.set_option("precond", 0)
     ds = Dataset(n)
     ds.ctx = ctx
     t0 = time.perf_counter()
     for q in range(n_real):
-        pr = Problem(ctx, seed + q, n, sigma)
+        if mixed:
+            pr = Problem(ctx, seed + q, n, *mixed_draw(seed + q))
+        else:
+            pr = Problem(ctx, seed + q, n, sigma)
         ds.problems.append(pr)
         xs, info = ctx.cg_solve(pr.coef, pr.coef64, pr.b, tol=tol, maxit=100000)
         if info["code"] != tpfa.OK:
