@@ -220,16 +220,46 @@ def oracle_fcg_step(iters, params=None):
 
 
 def oracle_sample_iters(O, target_s=12.0, workload="paper"):
-    """Iterations that make one oracle step last about target_s: the per-iteration
-    cost is the slope between a 5- and a 15-iteration run (setup excluded)."""
+    """Iterations for one oracle step of about target_s: the solver's iterations
+    take about 60% of it, the sample's setup (generation, CSR assembly) the rest.
+    The per-iteration cost is timed on the solver alone (the setup varies by
+    more than a few iterations cost)."""
+    per = oracle_iteration_s(O, workload)
+    return max(5, min(int(0.6 * target_s / per), 100000))
+
+
+def oracle_iteration_s(O, workload="paper"):
+    """Seconds per iteration of the oracle's solver on the sample of `workload`
+    (the solver timed alone, 10 and 30 iterations)."""
+    if workload == "learned":
+        t = time.perf_counter()
+        oracle_fcg_step(3)
+        t3 = time.perf_counter() - t
+        t = time.perf_counter()
+        oracle_fcg_step(13)
+        return max((time.perf_counter() - t - t3) / 10, 1e-4)
+    if workload == "channelized":
+        nx, ny, nz = SAMPLE_CHANNELS
+        w = synth.channelized(seed=0, n=nx)
+        g = O.Grid(nx, ny, nz)
+        A = O.assemble(g, w["K"], w["mask"], 0.0)
+        b = O.rhs(g, w["K"], w["mask"], None, w["pD"])
+        solve = O.pcg_jacobi
+    else:
+        nx, ny, nz = SAMPLE
+        K = synth.lognormal_field(nx, ny, nz, 1.5, 0, layer=8)
+        idx, val = synth.well_pair(nx, ny, nz)
+        q = synth.dense_sources(nx * ny * nz, idx, val)
+        g = O.Grid(nx, ny, nz)
+        A = O.assemble(g, K, None, 1e-3)
+        b = O.rhs(g, K, None, q, None)
+        solve = O.cg
     t = time.perf_counter()
-    oracle_step(O, 5, workload)
-    t5 = time.perf_counter() - t
+    solve(A, b, tol=0.0, maxit=10)
+    t10 = time.perf_counter() - t
     t = time.perf_counter()
-    oracle_step(O, 15, workload)
-    t15 = time.perf_counter() - t
-    per = max((t15 - t5) / 10, 1e-6)
-    return max(5, int((target_s - t5) / per) + 5)
+    solve(A, b, tol=0.0, maxit=30)
+    return max((time.perf_counter() - t - t10) / 20, 1e-6)
 
 
 def sample_desc(workload):

@@ -522,12 +522,29 @@ TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, boo
   p.nby = (g.ny + ts.w * ts.vy - 1) / (ts.w * ts.vy);
   int zc = zc_opt;
   if (zc <= 0) {
-    // the longest run (at most 128 planes; each run re-reads two halo planes)
-    // that still gives about two blocks per SM
-    const int64_t target = (int64_t)num_sms * 2;
+    // Measured on GB300 (plain FP32 sweep, 128^3 ... 1024x1024x256): every run
+    // costs more than its two halo planes (pipeline fill at its start), so long
+    // runs win, and a partial second wave of blocks costs more than a partly
+    // idle first one.  Hence: 128-plane runs when they give at least one full
+    // wave of resident blocks; otherwise as many runs per column as still fit
+    // one wave (e.g. 256^3: 128-plane runs, 256 blocks, 0.133 ms per sweep
+    // against 0.145 ms with the 512 blocks of 64-plane runs; 128^3: 15-plane
+    // runs, 288 blocks, 0.029 ms against 0.039 ms with 8-plane runs).
     const int64_t cols = p.nbx * p.nby;
-    zc = 128;
-    while (zc > 1 && cols * ((g.nz + zc - 1) / zc) < target) zc /= 2;
+    int per_sm = tma_blocks_per_sm(p);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t slots = (int64_t)num_sms * per_sm;
+    const int64_t nz = g.nz;
+    if (cols * ((nz + 127) / 128) >= slots) {
+      zc = 128;
+    } else {
+      const int64_t k = slots / cols;  // runs per column (>= 1 here)
+      int64_t z = (nz + k - 1) / k;
+      const int64_t zmin = nz < 8 ? nz : 8;
+      if (z < zmin) z = zmin;
+      if (z > 128) z = 128;
+      zc = (int)z;
+    }
   }
   if (zc > g.nz) zc = (int)g.nz;
   p.zc = zc;
