@@ -365,8 +365,11 @@ int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, float* dw, int
  *     (dy, dx) offset to the three output planes an input plane feeds
  *     (accumulators in a TMEM ring), so every staged input row is read by the
  *     tensor core 9 instead of 27 times;
- * 3 = per layer shape, the faster of 1 and 2 on GB300 (default): 2 for
- *     16 -> 16, 1 for the others.
+ * 4 = kernel 2 with warp-specialised roles: a copy warp fills the ring of
+ *     triples, one thread issues the MMAs, four epilogue warps drain a ring
+ *     of TMEM accumulators, joined by mbarriers instead of block barriers;
+ * 3 = per layer shape, the fastest on GB300 (default): 1 for 32 -> 16, 4 for
+ *     the others.
  * (cin, cout) = (64, 32) always uses kernel 0.  Returns TPFA_EINVAL for
  * another value. */
 int tpfa_conv3d_select(int kernel);

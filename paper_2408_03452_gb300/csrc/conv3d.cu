@@ -663,6 +663,239 @@ conv_fwd_zf_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
   if (warp == 0) tc::tmem_dealloc(acc0, Cfg::kCols);
 }
 
+// ---- the folded z-marching kernel with warp-specialised roles -------------
+// Same work units, row-group triples, folded MMAs (N = 3 cout) and TMEM ring
+// of accumulators as conv_fwd_zf_kernel, but the three kinds of work no
+// longer wait for each other at a block barrier:
+//   warp 4 copies triples into a ring of ST slots (cp.async; each lane's
+//          copies arrive on the slot's "full" mbarrier when they land);
+//   warp 5 (one thread) issues the MMAs of a triple once it is full and the
+//          slot of the output it starts is free, and commits to the triple's
+//          "empty" barrier and to the "full" barrier of the output the triple
+//          completes;
+//   warps 0-3 (the four TMEM lane quarters) drain finished accumulators:
+//          load, release the slot ("empty"), then bias / ReLU / mask, BF16
+//          rounding and the stores.
+// Every wait is bounded; a wait that runs out raises a shared abort flag that
+// every role checks, and the kernel records the timeout like the others.
+template <int CIN, int COUT>
+struct WsCfg {
+  static constexpr int kST = zm_stages<CIN, COUT>();
+  static constexpr int kWTap = COUT * CIN * 2;
+  static constexpr int kWBytes = 27 * kWTap;
+  static constexpr int kRGBytes = kRG * CIN * 2;
+  static constexpr int kTriple = 3 * kRGBytes;
+  static constexpr int kSmem = kWBytes + kST * kTriple;
+  static constexpr int kR = 256 / COUT;
+  static constexpr uint32_t kCols = 256;
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+  static_assert(kR >= 4, "accumulator ring");
+};
+
+__device__ __forceinline__ void cp_mbar_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(192)
+conv_fwd_ws_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ w,
+                   const float* __restrict__ bias, const uint16_t* __restrict__ mask,
+                   uint16_t* __restrict__ y, Vol g, int flags, ZmGrid zg) {
+  using Cfg = WsCfg<CIN, COUT>;
+  constexpr int ST = Cfg::kST;
+  constexpr int R = Cfg::kR;
+  constexpr int kc = CIN / 8;
+  constexpr int kChunks = 3 * kRG * kc;  // 16-byte copies per triple
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t tfull[ST], tempty[ST], afull[R], aempty[R], done_bar;
+  __shared__ uint32_t tbase;
+  __shared__ float sbias[COUT];
+  __shared__ volatile int s_abort;
+  unsigned char* sW = sm;
+  unsigned char* sR = sm + Cfg::kWBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights in the folded order (see conv_fwd_zf_kernel)
+  for (int i = tid; i < 27 * COUT * kc; i += 192) {
+    const int c = i % kc, r = (i / kc) % COUT, t = i / (kc * COUT);
+    const int tt = (t % 9) * 3 + (2 - t / 9);
+    const uint4 v = *reinterpret_cast<const uint4*>(w + ((size_t)t * COUT + r) * CIN + c * 8);
+    *reinterpret_cast<uint4*>(sW + tt * Cfg::kWTap + tc::kmajor_off(r, c * 8, CIN)) = v;
+  }
+  if (tid < COUT) sbias[tid] = bias ? bias[tid] : 0.f;
+  if (tid == 0) {
+    for (int i = 0; i < ST; ++i) {
+      tc::mbar_init(&tfull[i], 32);
+      tc::mbar_init(&tempty[i], 1);
+    }
+    for (int i = 0; i < R; ++i) {
+      tc::mbar_init(&afull[i], 1);
+      tc::mbar_init(&aempty[i], 4);
+    }
+    tc::mbar_init(&done_bar, 1);
+    s_abort = 0;
+  }
+  if (warp == 5) tc::tmem_alloc(&tbase, Cfg::kCols);
+  tc::fence_proxy_async();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t acc0 = tbase;
+
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (s_abort) return false;
+    if (tc::mbar_wait(bar, parity, kWaitLimit)) return true;
+    s_abort = 1;
+    return false;
+  };
+
+  if (warp == 4) {
+    // ---- copy warp -----------------------------------------------------------
+    int tg = 0;
+    for (int u = blockIdx.x; u < zg.units && !s_abort; u += gridDim.x) {
+      const int bi = u % zg.nb, cz = u / zg.nb;
+      const int sidx = cz / zg.nzc;
+      const int z0 = (cz % zg.nzc) * zg.zc;
+      const int nout = min(zg.zc, g.nz - z0);
+      const int kp0 = sidx * g.dp + 1 + z0;
+      const int seg = bi * 128;
+      for (int j = 0; j < nout + 2; ++j, ++tg) {
+        const int s = tg % ST;
+        if (tg >= ST && !wait(&tempty[s], ((tg / ST) - 1) & 1)) break;
+        const int base = seg + (kp0 - 1 + j) * g.pp - g.wp - 1;
+        unsigned char* st = sR + s * Cfg::kTriple;
+        for (int i = lane; i < kChunks; i += 32) {
+          const int c = i % kc, v = (i / kc) % kRG, gi = i / (kc * kRG);
+          const int row = base + gi * g.wp + v;
+          const bool ok = row >= 0 && row < g.vp;
+          cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
+                x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
+        }
+        cp_mbar_arrive_noinc(&tfull[s]);
+      }
+    }
+    cp_wait_all();
+  } else if (warp == 5) {
+    // ---- MMA thread --------------------------------------------------------
+    if (lane == 0) {
+      const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sR), kRG * 16, 128);
+      const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sW), 128, kc * 128);
+      int tg = 0, obase = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < zg.units && !stop; u += gridDim.x) {
+        const int cz = u / zg.nb;
+        const int z0 = (cz % zg.nzc) * zg.zc;
+        const int nout = min(zg.zc, g.nz - z0);
+        for (int j = 0; j < nout + 2; ++j, ++tg) {
+          const int s = tg % ST;
+          if (!wait(&tfull[s], (tg / ST) & 1)) { stop = true; break; }
+          const int klo = max(0, j - 2), khi = min(nout - 1, j);
+          if (khi == j) {  // output j starts here: its accumulator slot must be free
+            const int oc = obase + j;
+            if (oc >= R && !wait(&aempty[oc % R], ((oc / R) - 1) & 1)) { stop = true; break; }
+          }
+          tc::fence_after();
+          const uint64_t slot = adesc0 + (uint64_t)(s * (Cfg::kTriple >> 4));
+          auto mma_range = [&](int ka, int kb, uint64_t ad, int tile0, int ks, bool accum) {
+            int k = ka;
+            while (k <= kb) {
+              const int sl = (obase + k) % R;
+              const int n = min(kb - k + 1, R - sl);
+              const uint64_t bd =
+                  bdesc0 + (uint64_t)(((tile0 + (k - ka)) * Cfg::kWTap + ks * 256) >> 4);
+              tc::mma_bf16(acc0 + (uint32_t)(sl * COUT), ad, bd,
+                           tc::idesc_bf16_f32(128, n * COUT), accum);
+              k += n;
+            }
+          };
+#pragma unroll 1
+          for (int gi = 0; gi < 3; ++gi)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+              for (int ks = 0; ks < CIN / 16; ++ks) {
+                const uint64_t ad =
+                    slot + (uint64_t)((gi * Cfg::kRGBytes + dx * 16 + ks * 2 * kRG * 16) >> 4);
+                const int grp = (gi * 3 + dx) * 3 + 2 - j;
+                if ((gi | dx | ks) == 0 && khi == j) {
+                  if (klo < j) mma_range(klo, j - 1, ad, grp + klo, ks, true);
+                  mma_range(j, j, ad, grp + j, ks, false);
+                } else {
+                  mma_range(klo, khi, ad, grp + klo, ks, true);
+                }
+              }
+          tc::mma_commit(&tempty[s]);
+          if (j >= 2) tc::mma_commit(&afull[(obase + j - 2) % R]);  // output j-2 is final
+        }
+        obase += nout;
+      }
+      // every MMA issued must be complete before the TMEM is released
+      tc::mma_commit(&done_bar);
+      if (!tc::mbar_wait(&done_bar, 0, kWaitLimit)) s_abort = 1;
+    }
+  } else {
+    // ---- epilogue warps 0-3: TMEM lanes 32 warp .. 32 warp + 31 -------------
+    int obase = 0;
+    for (int u = blockIdx.x; u < zg.units && !s_abort; u += gridDim.x) {
+      const int bi = u % zg.nb, cz = u / zg.nb;
+      const int sidx = cz / zg.nzc;
+      const int z0 = (cz % zg.nzc) * zg.zc;
+      const int nout = min(zg.zc, g.nz - z0);
+      const int kp0 = sidx * g.dp + 1 + z0;
+      const int poff = bi * 128 + warp * 32 + lane;
+      const int px = poff % g.wp, py = poff / g.wp;
+      const bool in_xy = poff < g.pp && px >= 1 && px <= g.nx && py >= 1 && py <= g.ny;
+      bool stop = false;
+      for (int k = 0; k < nout; ++k) {
+        const int oc = obase + k;
+        const int sl = oc % R;
+        if (!wait(&afull[sl], (oc / R) & 1)) { stop = true; break; }
+        tc::fence_after();
+        float va[COUT];
+        tc::tmem_ld_cols<COUT>(acc0 + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * COUT), va);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive1(&aempty[sl]);
+        if (in_xy) {
+          const size_t idx = (size_t)(kp0 + k) * g.pp + poff;
+#pragma unroll
+          for (int c0 = 0; c0 < COUT; c0 += 8) {
+            const float* v = va + c0;
+            uint4 mk = make_uint4(0, 0, 0, 0);
+            if (flags & kConvMask) mk = *reinterpret_cast<const uint4*>(mask + idx * COUT + c0);
+            const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
+            uint32_t ov[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              float a = v[2 * h] + sbias[c0 + 2 * h], b = v[2 * h + 1] + sbias[c0 + 2 * h + 1];
+              if (flags & kConvRelu) {
+                a = fmaxf(a, 0.f);
+                b = fmaxf(b, 0.f);
+              }
+              if (flags & kConvMask) {
+                if (!bf16_positive(mw[h] & 0xffffu)) a = 0.f;
+                if (!bf16_positive(mw[h] >> 16)) b = 0.f;
+              }
+              ov[h] = pack_bf16(a, b);
+            }
+            *reinterpret_cast<uint4*>(y + idx * COUT + c0) = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+          }
+        }
+      }
+      if (stop) break;
+      obase += nout;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (s_abort && tid == 0) atomicOr(&g_tc_timeout, 1);
+  if (warp == 5) tc::tmem_dealloc(acc0, Cfg::kCols);
+}
+
 template <int CIN, int COUT>
 struct WgCfg {
   static constexpr int kTaps = 128 / CIN;                    // taps per 128-row tile
@@ -873,6 +1106,28 @@ cudaError_t zf_launch(const uint16_t* x, const uint16_t* w, const float* bias,
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT>
+cudaError_t ws_launch(const uint16_t* x, const uint16_t* w, const float* bias,
+                      const uint16_t* mask, uint16_t* y, const Vol& g, int flags,
+                      cudaStream_t s) {
+  static int per_sm = -1, nsm = 0;
+  if (per_sm < 0)
+    per_sm = ctas_per_sm((const void*)conv_fwd_ws_kernel<CIN, COUT>, WsCfg<CIN, COUT>::kSmem,
+                         WsCfg<CIN, COUT>::kCols, &nsm);
+  const int ctas = per_sm * nsm;
+  ZmGrid zg;
+  zg.nb = (g.pp + 127) / 128;
+  zg.zc = g.nz;
+  while (zg.zc > 4 && (long long)zg.nb * g.ns * ((g.nz + zg.zc - 1) / zg.zc) < 2LL * ctas)
+    zg.zc = (zg.zc + 1) / 2;
+  zg.nzc = (g.nz + zg.zc - 1) / zg.zc;
+  zg.units = zg.nb * g.ns * zg.nzc;
+  const int grid = zg.units < ctas ? zg.units : ctas;
+  conv_fwd_ws_kernel<CIN, COUT><<<grid, 192, WsCfg<CIN, COUT>::kSmem, s>>>(x, w, bias, mask, y,
+                                                                           g, flags, zg);
+  return cudaGetLastError();
+}
+
 int wgrad_splits(int mtiles, int nchunks) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -918,14 +1173,21 @@ bool conv_shape_ok(int cin, int cout) {
 #define TPFA_CONV_SHAPES(X) X(16, 16) X(16, 32) X(32, 16) X(32, 64) X(64, 32)
 
 // 0: tile kernel, 1: z-marching kernel, 2: z-marching kernel with the z-taps
-// folded into N (both where their ring fits), 3: per layer shape the faster
-// of 1 and 2 as measured on GB300 (default: 2 for 16 -> 16, 1 otherwise)
+// folded into N, 4: the folded kernel with warp-specialised roles (1, 2 and 4
+// where their ring fits), 3: per layer shape the fastest as measured on GB300
+// (default: 1 for 32 -> 16, 4 otherwise)
 static int g_conv_kernel = 3;
 
 cudaError_t conv_fwd(const uint16_t* x, const uint16_t* w, const float* bias, const uint16_t* mask,
                      uint16_t* y, const Vol& g, int cin, int cout, int flags, cudaStream_t s) {
   const bool ring = !(cin == 64 && cout == 32);
-  const int kern = g_conv_kernel != 3 ? g_conv_kernel : (cin == 16 && cout == 16 ? 2 : 1);
+  const int kern = g_conv_kernel != 3 ? g_conv_kernel : (cin == 32 && cout == 16 ? 1 : 4);
+  if (ring && kern == 4) {
+#define X(CI, CO) \
+  if (cin == CI && cout == CO) return ws_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
+    X(16, 16) X(16, 32) X(32, 16) X(32, 64)
+#undef X
+  }
   if (ring && kern == 2) {
 #define X(CI, CO) \
   if (cin == CI && cout == CO) return zf_launch<CI, CO>(x, w, bias, mask, y, g, flags, s);
@@ -1017,9 +1279,10 @@ extern "C" int tpfa_conv3d_wgrad_bf16(const uint16_t* x, const uint16_t* dy, flo
 
 // Selects the forward convolution kernel: 0 = 128-voxel tiles with all nine
 // row groups per tile, 1 = z-marching ring where it fits, 2 = z-marching ring
-// with the z-taps folded into N, 3 = per layer shape (default).
+// with the z-taps folded into N, 3 = per layer shape (default), 4 = the folded
+// ring with warp-specialised roles.
 extern "C" int tpfa_conv3d_select(int kernel) {
-  if (kernel < 0 || kernel > 3) return TPFA_EINVAL;
+  if (kernel < 0 || kernel > 4) return TPFA_EINVAL;
   tpfa::net::g_conv_kernel = kernel;
   return TPFA_OK;
 }

@@ -27,11 +27,11 @@ def tp():
     return tpfa
 
 
-@pytest.fixture(params=[2, 1, 0], ids=["zfold", "zmarch", "tiles"])
+@pytest.fixture(params=[4, 2, 1, 0], ids=["zfold_ws", "zfold", "zmarch", "tiles"])
 def kernel(tp, request):
-    """Every forward kernel, forced for every layer shape: the z-marching ring
-    with the z-taps folded into N, the z-marching ring with one MMA per tap,
-    the tile kernel (the default picks 2 or 1 per shape)."""
+    """Every forward kernel, forced for every layer shape: the folded z-marching
+    ring with warp-specialised roles, the folded ring, the z-marching ring with
+    one MMA per tap, the tile kernel (the default picks one per shape)."""
     tp.conv3d_select(request.param)
     yield request.param
     tp.conv3d_select(3)
