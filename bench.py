@@ -108,6 +108,10 @@ def parse():
     ap.add_argument("--probe-iters", type=int, default=0,
                     help="profiling aid: build the workload, run one solve capped at this many "
                          "CG iterations (host-polled chunks of 4), print its info, no timing")
+    ap.add_argument("--probe-apply", type=int, default=0,
+                    help="profiling aid: build the workload's records, run this many operator "
+                         "applications (tpfa_apply, or tpfa_apply_bf16 with --inner bf16) with "
+                         "p'Ap, print the tiling, no timing")
     return ap.parse_args()
 
 
@@ -820,6 +824,8 @@ def run_learned(a, dev, rank, local, barrier):
                 "l2": "inputs larger than L2 (no flush needed)"},
             "roofline": {"kernel": "operator application A p (tpfa_apply, two per FCG "
                                    "iteration)", "bound": "hbm",
+                         "apply_kernel": ("TMA-staged" if ctx.tiling(2)["kernel"] == 2
+                                          else "cp.async-staged"),
                          "achieved": APPLY_BYTES_PER_CELL * cells / (apply_ms / 1e3) / 1e9,
                          "peak": hpeak, "unit": "GB/s",
                          "frac": APPLY_BYTES_PER_CELL * cells / (apply_ms / 1e3) / 1e9 / hpeak,
@@ -1086,6 +1092,20 @@ def main():
 
     builds_per_step = 3 + (1 if coef16 is not None else 0)
     K = inp["K"]
+
+    if a.probe_apply > 0:
+        inner = build(inp)
+        pv = torch.rand(ctx.n, dtype=torch.float32, device=dev)
+        av = torch.empty_like(pv)
+        pAp = torch.zeros(1, dtype=torch.float64, device=dev)
+        fn = ctx.apply_bf16 if coef16 is not None else ctx.apply
+        for _ in range(a.probe_apply):
+            fn(inner, pv, Ap=av, pAp=pAp)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe_apply": a.probe_apply, "pAp": pAp.item(),
+                          "tiling": ctx.tiling(3 if coef16 is not None else 2)}))
+        ctx.close()
+        return
 
     if a.probe_iters > 0:
         ctx.set_option("loop", 1)

@@ -109,7 +109,10 @@ enum tpfa_option {
                                 sweep (cg_solve returns TPFA_EINVAL where it cannot run: BF16
                                 records, Jacobi, or a driver without the tensor-map encoder).
                                 The TMA-staged sweep keeps r, q, p, x of a cell in one 16-byte
-                                record (32 B/cell of context memory, allocated on first use)   */
+                                record (32 B/cell of context memory, allocated on first use).
+                                tpfa_apply and tpfa_apply_bf16 follow it: TMA-staged unless 1,
+                                when nx % 4 == 0 and coef and p are 16-byte aligned, else
+                                cp.async-staged (same values either way)                         */
   TPFA_OPT_TMA_TILE = 16     /* tile of the TMA-staged sweep, 32 columns x rows per block:
                                 0 = 4 warps x 4 rows, 4 stages (default); 1 = 4 x 4, 3 stages;
                                 2 = 8 x 4, 3 stages; 3 = 4 x 2, 6 stages                         */
@@ -117,7 +120,8 @@ enum tpfa_option {
 
 /* The stencil-sweep tiling a context uses, for inspection and tests.
  * which: 0 = the CG loop of cg_solve with FP32 records, 1 = the CG loop of
- * cg_solve_bf16, 2 = tpfa_apply.  out: host array of 6 values:
+ * cg_solve_bf16, 2 = tpfa_apply, 3 = tpfa_apply_bf16 (for 16-byte aligned
+ * arguments).  out: host array of 6 values:
  * kernel (1 = cp.async-staged sweep, 2 = TMA-staged sweep), rows per warp,
  * shared-memory stages, compute warps per block, z-planes per run (zc),
  * blocks per launch.  Returns TPFA_EINVAL for a NULL argument, a bad `which`
@@ -198,6 +202,12 @@ int tpfa_build_rhs_transient(tpfa_ctx* ctx, const double* K, const uint8_t* diri
  * (must not alias p).  pAp: dev pointer to one double receiving p.Ap
  * (FP32 products, compensated FP32 partial sums, FP64 across warps and
  * blocks in a fixed order: bit-reproducible run to run), or NULL.
+ * Kernel: TMA-staged when nx % 4 == 0 and p is 16-byte aligned (unless
+ * TPFA_OPT_SWEEP = 1 or TPFA_OPT_TILE_VY != 4), else cp.async-staged; both
+ * give identical Ap (pAp may differ in the last bits: another grouping).  In
+ * the TMA-staged kernel every wait for a copy is bounded; a copy that never
+ * lands (not expected on working hardware) leaves NaN in the cells it held
+ * up and in pAp instead of hanging the GPU.
  */
 int tpfa_apply(tpfa_ctx* ctx, const float* coef, const float* p, float* Ap, double* pAp,
                void* stream);
@@ -542,9 +552,10 @@ int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_nets, const
  * synchronisation cudaFree implies) is not permitted.  tpfa_create
  * allocates, so these callers cannot hold a context; this call needs none.
  *
- * It computes exactly what tpfa_apply computes (same kernel, same per-cell
- * arithmetic; pAp may differ from tpfa_apply's in the last bits when the
- * tiling differs) and allocates nothing.  Its reduction workspace is a
+ * It computes exactly what tpfa_apply computes (the same per-cell
+ * arithmetic, always through the cp.async-staged kernel, where tpfa_apply
+ * may take the TMA-staged one; pAp may differ from tpfa_apply's in the last
+ * bits when the tiling differs) and allocates nothing.  Its reduction workspace is a
  * fixed array of 256 + 16384 * 8 = 131,328 bytes in the library's device
  * image, which every GPU that loads the library holds until the process
  * exits.

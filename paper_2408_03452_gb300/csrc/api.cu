@@ -135,6 +135,14 @@ bool use_tma(const tpfa_ctx* c, bool b16) {
   return c->sweep_sel != 1 && c->vy == 4 && tma_sweep_ok(c->g, b16, c->precond == 1);
 }
 
+// tpfa_apply: the TMA-staged operator unless the cp.async sweep is selected,
+// another VY is, or the grid does not suit the copy engine; the arguments
+// must then also be 16-byte aligned (cudaMalloc'd buffers are)
+bool use_tma_apply(const tpfa_ctx* c, bool b16) {
+  return c->sweep_sel != 1 && c->vy == 4 && tma_apply_ok(c->g, b16);
+}
+bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
 // The CG vectors of a solve: the separate arrays, or with the TMA-staged
 // sweep the interleaved records.
 CgVecs loop_vecs(const tpfa_ctx* c, bool b16) {
@@ -507,10 +515,22 @@ int tpfa_set_option(tpfa_ctx* c, int option, double value) {
 }
 
 int tpfa_sweep_tiling(const tpfa_ctx* c, int which, int64_t* out) {
-  if (c == nullptr || out == nullptr || which < 0 || which > 2) return TPFA_EINVAL;
+  if (c == nullptr || out == nullptr || which < 0 || which > 3) return TPFA_EINVAL;
   const Sweep sw = ctx_sweep(c);
-  const bool b16 = which == 1;
-  if (which != 2 && use_tma(c, b16)) {
+  const bool b16 = which == 1 || which == 3;
+  if (which >= 2) {
+    // the operator (TMA-staged for 16-byte aligned arguments)
+    if (use_tma_apply(c, b16)) {
+      const TmaPlan p = plan_tma(c->g, 0, c->zc, c->num_sms, b16, false, true);
+      out[0] = 2;
+      out[1] = p.vy;
+      out[2] = p.stages;
+      out[3] = p.w;
+      out[4] = p.zc;
+      out[5] = p.nblocks;
+      return TPFA_OK;
+    }
+  } else if (use_tma(c, b16)) {
     const TmaPlan p = plan_tma(c->g, c->tma_tile, c->zc, c->num_sms, b16, c->precond == 1);
     out[0] = 2;
     out[1] = p.vy;
@@ -520,7 +540,7 @@ int tpfa_sweep_tiling(const tpfa_ctx* c, int which, int64_t* out) {
     out[5] = p.nblocks;
     return TPFA_OK;
   }
-  if (which != 2 && c->sweep_sel == 2) return TPFA_EINVAL;
+  if (which < 2 && c->sweep_sel == 2) return TPFA_EINVAL;
   out[0] = 1;
   out[1] = sw.vy;
   out[2] = sw.stages;
@@ -577,6 +597,16 @@ static int apply_impl(tpfa_ctx* c, const void* coef, bool b16, const float* p, f
     return TPFA_EINVAL;
   if ((const void*)p == (const void*)Ap) return TPFA_EINVAL;
   if (b16 && c->vy != 4) return TPFA_EINVAL;
+  if (use_tma_apply(c, b16) && aligned16(coef) && aligned16(p)) {
+    const TmaPlan tp = plan_tma(c->g, 0, c->zc, c->num_sms, b16, false, true);
+    if (pAp != nullptr) {
+      rc = ensure_partials(c, (size_t)tp.nblocks);
+      if (rc) return rc;
+    }
+    CK(launch_apply_tma(c->g, tp, coef, p, Ap, pAp, c->partials, c->counter,
+                        (cudaStream_t)stream));
+    return TPFA_OK;
+  }
   const Sweep sw = ctx_sweep(c);
   if (pAp != nullptr) {
     rc = ensure_partials(c, (size_t)sw.nblocks);

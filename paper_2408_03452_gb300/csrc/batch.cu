@@ -207,6 +207,13 @@ int ensure_batch_loop(tpfa_batch* b, const float* coef) {
 
 }  // namespace
 
+std::vector<int> batch_tma_zc_request(const tpfa_batch* b) {
+  const int zauto = batch_tma_zauto(b);
+  std::vector<int> z(b->ninst);
+  for (int i = 0; i < b->ninst; ++i) z[i] = b->zc_req[i] > 0 ? b->zc_req[i] : zauto;
+  return z;
+}
+
 extern "C" {
 
 int tpfa_batch_create(const tpfa_grid* grids, int n_inst, const int* zc, tpfa_batch** out) {
@@ -360,6 +367,7 @@ int tpfa_batch_zc(const tpfa_batch* b, int* zc) {
   }
   return TPFA_OK;
 }
+
 
 int tpfa_batch_set_option(tpfa_batch* b, int option, double value) {
   if (b == nullptr || !isfinite(value)) return TPFA_EINVAL;

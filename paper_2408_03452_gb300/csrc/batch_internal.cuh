@@ -49,3 +49,7 @@ struct tpfa_batch {
   cudaEvent_t ev[4];
 };
 
+// Requested z-run of every instance in the batch's TMA-staged sweeps: the
+// instance's own request, else the batch-wide automatic length (the batched
+// CG sweep and the batched flexible-CG operator use the same runs).
+std::vector<int> batch_tma_zc_request(const tpfa_batch* b);

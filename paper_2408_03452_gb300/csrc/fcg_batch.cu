@@ -471,6 +471,13 @@ struct BWork {
   double *hist = nullptr, *hhist = nullptr;
   cudaEvent_t fork = nullptr;  // the networks' streams start after it
   int64_t launches = 0;
+  // TMA-staged operator (set up when every instance suits it): per-instance
+  // tilings and tensor maps {coefficients, z, P slot 0 .. m-1}, block partials
+  bool tma = false;
+  int64_t ablocks = 0;
+  CUtensorMap* amaps = nullptr;
+  tpfa::TmaInst* ainst = nullptr;
+  double* apart = nullptr;
 
   bool alloc() {
     const size_t v = (size_t)stride * 4;
@@ -531,10 +538,80 @@ struct BWork {
     cudaFreeHost(hnorms);
     cudaFree(hist);
     cudaFreeHost(hhist);
+    cudaFree(amaps);
+    cudaFree(ainst);
+    cudaFree(apart);
     if (fork) cudaEventDestroy(fork);
   }
   unsigned nchunks() const { return (unsigned)chunks.size(); }
 };
+
+// The batch's operator through the TMA-staged kernel when every instance
+// suits the copy engine (nx % 4 == 0, cell offsets on 16-byte boundaries) and
+// the cp.async sweep is not requested; the instances keep the z-runs of the
+// batch's CG sweep, so an instance's tiling does not depend on the batch it
+// is in once its run length is given.  Otherwise w.tma stays false.
+int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
+  using namespace tpfa;
+  if (batch->sweep_sel == 1 || !w.vec4 || reinterpret_cast<uintptr_t>(coef) % 16 != 0)
+    return TPFA_OK;
+  for (const Grid& g : batch->g)
+    if (!tma_apply_ok(g, false)) return TPFA_OK;
+  const int N = w.ninst, per = 2 + w.m;
+  const std::vector<int> zr = batch_tma_zc_request(batch);
+  std::vector<CUtensorMap> maps((size_t)per * N);
+  std::vector<TmaInst> inst(N);
+  std::vector<const float*> in(1 + w.m);
+  int64_t blocks = 0;
+  for (int i = 0; i < N; ++i) {
+    const TmaPlan p = plan_tma(batch->g[i], 0, zr[i], batch->num_sms, false, false, true);
+    const int64_t o = batch->off[i];
+    in[0] = w.z + o;
+    for (int k = 0; k < w.m; ++k) in[1 + k] = w.P + (size_t)k * w.stride + o;
+    if (!make_apply_maps(batch->g[i], p, reinterpret_cast<const float4*>(coef) + o, in.data(),
+                         1 + w.m, &maps[(size_t)per * i]))
+      return TPFA_ECUDA;
+    TmaInst& I = inst[i];
+    I.g = batch->g[i];
+    I.zc = p.zc;
+    I.nbx = (int)p.nbx;
+    I.nby = (int)p.nby;
+    I.off = o;
+    I.bstart = blocks;
+    I.nblocks = p.nblocks;
+    blocks += p.nblocks;
+  }
+  if (blocks > 0x7fffffff) return TPFA_OK;
+  if (cudaMalloc(&w.amaps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
+      cudaMalloc(&w.ainst, sizeof(TmaInst) * N) != cudaSuccess ||
+      cudaMalloc(&w.apart, sizeof(double) * blocks) != cudaSuccess) {
+    cudaGetLastError();
+    return TPFA_ENOMEM;
+  }
+  for (int i = 0; i < N; ++i) inst[i].maps = w.amaps + (size_t)per * i;
+  if (cudaMemcpyAsync(w.amaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                      cudaMemcpyHostToDevice, w.s) != cudaSuccess ||
+      cudaMemcpyAsync(w.ainst, inst.data(), sizeof(TmaInst) * N, cudaMemcpyHostToDevice, w.s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(w.s) != cudaSuccess)
+    return TPFA_ECUDA;
+  w.tma = true;
+  w.ablocks = blocks;
+  return TPFA_OK;
+}
+
+// Operator q = A (input) of the instances with (flags & need) == need, p'q per
+// instance into pap; input `which`: 0 = z, 1 + k = P slot k.
+bool batch_apply(const tpfa_batch* batch, BWork& w, const float4* cf4, int which, float* out,
+                 double* pap, int need) {
+  using namespace tpfa;
+  if (w.tma)
+    return launch_apply_tma_batch(w.ainst, w.ninst, w.ablocks, which, out, pap, w.flags, need,
+                                  w.apart, batch->counters, w.s) == cudaSuccess;
+  const float* in = which == 0 ? w.z : w.P + (size_t)(which - 1) * w.stride;
+  return launch_apply_batch(batch->inst_dev, w.ninst, batch->sweep_blocks, cf4, in, out, pap,
+                            w.flags, need, batch->partials, batch->counters, w.s) == cudaSuccess;
+}
 
 // The members of each network that iterate in blend mode (blend[i]): when
 // the set changes, their cell offsets and the offsets of their ln K samples
@@ -723,6 +800,10 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       dinv_kernel<<<w.nb, kT, 0, s>>>(reinterpret_cast<const float4*>(coef), w.dinv, w.cells);
       ok = cudaGetLastError() == cudaSuccess;
     }
+    if (ok) {
+      rc = setup_apply_tma(batch, coef, w);
+      if (rc) return rc;
+    }
     for (BNet& B : bn) {
       if (!ok) break;
       const int ns = (int)B.members.size();
@@ -840,9 +921,7 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
         if (any_blend) {
           rc = batch_network_term(bn, w);
           if (rc) break;
-          if (launch_apply_batch(batch->inst_dev, N, batch->sweep_blocks, cf4, w.z, w.au, w.uau,
-                                 w.flags, kAct | kNet, batch->partials, batch->counters,
-                                 s) != cudaSuccess) {
+          if (!batch_apply(batch, w, cf4, 0, w.au, w.uau, kAct | kNet)) {
             rc = TPFA_ECUDA;
             break;
           }
@@ -862,8 +941,7 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
                                              w.uau, w.sc, head, w.m);
         launch_bdir(gstored, w.nchunks(), s, w.chunks_dev, w.flags, w.sc, w.r, w.dinv, w.z, pd, p,
                     w.vec4, w.part);
-        if (launch_apply_batch(batch->inst_dev, N, batch->sweep_blocks, cf4, p, q, w.pq, w.flags,
-                               kAct, batch->partials, batch->counters, s) != cudaSuccess) {
+        if (!batch_apply(batch, w, cf4, 1 + head, q, w.pq, kAct)) {
           rc = TPFA_ECUDA;
           break;
         }

@@ -378,6 +378,245 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
     cg_finish(st, tot, a.cond, COND);
 }
 
+// ---------------------------------------------------------------------------
+// Operator application q = A p with p'q (Eq. 6 / Alg. 2 in the positive form),
+// TMA-staged: the CG sweep's tiling and pipeline with one FP32 field in place
+// of the vector records.  Per plane the producer copies
+//   p             [TY+2 rows][40 floats] from (X0-4, Y0-1) (a 16-byte aligned
+//                 start; columns X0-1 and X0+32 are the x-halo),
+//   coefficients  [TY+1 rows][33 records] from (X0-1, Y0-1)
+//                 (BF16 records: 36 from X0-2).
+// The per-cell arithmetic is that of the cp.async-staged operator of
+// kernels_cg.cu (same operands, same fused multiply-adds in the same order),
+// so both give bit-identical q; only the grouping of p'q differs.
+constexpr int kPX = 40;  // p box width: X0-4 .. X0+35
+
+template <int W, int VY, bool B16>
+struct ApplyLayout {
+  using RC = Rec<B16, false>;
+  static constexpr int TY = W * VY;
+  static constexpr int kPBytes = (TY + 2) * kPX * 4;
+  static constexpr int kRecBytes = (TY + 1) * RC::kX * RC::kBytes;
+  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int kP = 0;
+  static constexpr int kC = al(kPBytes);
+  static constexpr int kStage = kC + al(kRecBytes);
+  static constexpr uint32_t kTx = kPBytes + kRecBytes;  // bytes per stage
+};
+
+template <int W, int VY, int S, bool B16>
+constexpr int apply_smem_bytes() {
+  return S * ApplyLayout<W, VY, B16>::kStage + 2 * S * 8 + 128;
+}
+
+struct ApplyArgs {
+  CUtensorMap mp, mc;  // p, coefficient records
+  // batched operator: instance table; an instance's maps are {coefficients,
+  // input 0, input 1, ...} and `which` picks the input; only instances with
+  // (act[i] & need) == need are applied, the others' cells are left untouched
+  const TmaInst* inst;
+  int ninst, which;
+  const int* act;
+  int need;
+  Grid g;
+  int zc;
+  int nbx, nby;
+  float* Ap;
+  double* pAp;  // one double (per instance when batched), or null
+  double* partials;
+  unsigned int* counter;
+};
+
+template <int W, int VY, int S, bool B16, bool BATCH>
+__global__ void __launch_bounds__((W + 1) * 32)
+apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
+  static_assert(!BATCH || !B16, "batched operator: FP32 records");
+  using LY = ApplyLayout<W, VY, B16>;
+  using RC = Rec<B16, false>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * LY::kStage);
+  uint64_t* empty = full + S;
+
+  Grid g = a.g;
+  int nbx = a.nbx, nby = a.nby, zc = a.zc;
+  int64_t lb = blockIdx.x, pstart = 0, pcount = gridDim.x, off = 0;
+  int inst = 0;
+  unsigned int* counter = a.counter;
+  const CUtensorMap *mp = &a.mp, *mc = &a.mc;
+  if (BATCH) {
+    int lo = 0, hi = a.ninst - 1;  // last instance whose first block <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.inst[mid].bstart <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    if ((a.act[lo] & a.need) != a.need) return;  // every block of the instance returns
+    const TmaInst& I = a.inst[lo];
+    g = I.g; nbx = I.nbx; nby = I.nby; zc = I.zc; off = I.off;
+    lb = blockIdx.x - I.bstart; pstart = I.bstart; pcount = I.nblocks;
+    inst = lo;
+    counter = a.counter + lo;
+    mc = I.maps;
+    mp = I.maps + 1 + a.which;
+  }
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int bx = (int)(lb % nbx);
+  const int t = (int)(lb / nbx);
+  const int by = t % nby;
+  const int bz = t / nby;
+  const int X0 = 32 * bx, Y0 = LY::TY * by;
+  const int64_t z0 = (int64_t)bz * zc;
+  const int64_t z1 = min(z0 + (int64_t)zc, g.nz);
+  const int L = (int)(z1 - z0) + 2;  // planes z0-1 .. z1
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], W);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  Acc acc = {0.f, 0.f};
+  bool fault = false;
+
+  if (warp == W) {
+    // ---- producer ---------------------------------------------------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int j = 0; j < L; ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait(&empty[s], ((j / S) - 1) & 1, kWaitLimit)) {
+          fault = true;
+          break;
+        }
+        const int z = (int)(z0 - 1 + j);
+        unsigned char* sb = smem + s * LY::kStage;
+        mbar_expect_tx(&full[s], LY::kTx);
+        // x coordinates in 4-byte elements, multiples of 4 (16 bytes)
+        tma_3d(sb + LY::kP, mp, &full[s], X0 - 4, Y0 - 1, z);
+        tma_3d(sb + LY::kC, mc, &full[s], (RC::kBytes / 4) * (X0 - RC::kC0), Y0 - 1, z);
+        issued = j + 1;
+      }
+      // every issued copy lands before the block exits
+      for (int j = issued - 1; j >= 0 && j >= issued - S; --j)
+        if (!mbar_wait(&full[j % S], (j / S) & 1, kWaitLimit)) fault = true;
+    }
+  } else {
+    // ---- compute warps ----------------------------------------------------
+    const int jw = warp * VY;
+    const int gx = X0 + lane;
+    const bool inx = gx < g.nx;
+    unsigned rowok = 0u;
+#pragma unroll
+    for (int jj = 0; jj < VY; ++jj)
+      if (inx && Y0 + jw + jj < g.ny) rowok |= 1u << jj;
+    const int nxi = (int)g.nx;
+    const unsigned o0 = (unsigned)(Y0 + jw) * (unsigned)nxi + (unsigned)gx;
+    const int hc = lane == 0 ? 3 : 36;  // p box column of this lane's x-halo cell
+    float* out = a.Ap + off;
+
+    // p of plane j for rows -1..VY of this lane's column, and of the x-halo
+    // cell of the own rows
+    auto load = [&](int j, float (&P)[VY + 2], float (&H)[VY]) {
+      const float* sp = reinterpret_cast<const float*>(smem + (j % S) * LY::kStage + LY::kP);
+#pragma unroll
+      for (int jj = -1; jj <= VY; ++jj) {
+        const int r = jw + jj + 1;
+        P[jj + 1] = sp[r * kPX + lane + 4];
+        if (jj >= 0 && jj < VY) H[jj] = sp[r * kPX + hc];
+      }
+    };
+    auto wait_full = [&](int j) -> bool {
+      return mbar_wait(&full[j % S], (j / S) & 1, kWaitLimit);
+    };
+    auto release = [&](int j) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[j % S]);
+    };
+
+    float Pm[VY], P0[VY + 2], H0[VY], Tzm[VY];
+    int64_t zdone = z0;  // first plane of the run not yet written
+    if (!wait_full(0)) fault = true;
+    if (!fault) {  // plane z0 - 1: p below the first plane, and its Tz
+      float Pt[VY + 2], Ht[VY];
+      load(0, Pt, Ht);
+#pragma unroll
+      for (int jj = 0; jj < VY; ++jj) {
+        Pm[jj] = Pt[jj + 1];
+        Tzm[jj] = srec<B16>(smem + LY::kC, (jw + jj + 1) * RC::kX + lane + RC::kC0).z;
+      }
+      release(0);
+      if (!wait_full(1)) fault = true;
+    }
+    if (!fault) load(1, P0, H0);
+
+    for (int64_t z = z0; z < z1 && !fault; ++z) {
+      const int jc = (int)(z - z0) + 1;  // plane z
+      const int jf = jc + 1;             // plane z + 1
+      if (!wait_full(jf)) { fault = true; break; }
+      float Pp[VY + 2], Hp[VY];
+      load(jf, Pp, Hp);
+      const unsigned char* sb = smem + (jc % S) * LY::kStage;
+      float* oz = out + g.plane * z;
+      float s1 = 0.f;
+#pragma unroll
+      for (int jj = 0; jj < VY; ++jj) {
+        const int ri = (jw + jj + 1) * RC::kX + lane + RC::kC0;
+        float4 cf = srec<B16>(sb + LY::kC, ri);
+        const float txm = srec<B16>(sb + LY::kC, ri - 1).x;
+        const float tym = srec<B16>(sb + LY::kC, ri - RC::kX).y;
+        // BF16 records: D = T(-x) + T(+x) + T(-y) + T(+y) + T(-z) + T(+z) + E
+        if (B16) cf.w = (((((txm + cf.x) + tym) + cf.y) + Tzm[jj]) + cf.z) + cf.w;
+        const float pc = P0[jj + 1];
+        float pxm = __shfl_up_sync(kFull, pc, 1);
+        float pxp = __shfl_down_sync(kFull, pc, 1);
+        if (lane == 0) pxm = H0[jj];
+        if (lane == 31) pxp = H0[jj];
+        const float q = stencil7(cf, txm, tym, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
+                                 Pp[jj + 1], Pm[jj]);
+        if ((rowok >> jj) & 1u) {
+          oz[o0 + (unsigned)(jj * nxi)] = q;
+          s1 = fmaf(pc, q, s1);
+        }
+        Tzm[jj] = cf.z;
+        Pm[jj] = pc;
+      }
+      release(jc);
+      kadd(acc, s1);
+      zdone = z + 1;
+#pragma unroll
+      for (int jj = 0; jj < VY; ++jj) H0[jj] = Hp[jj];
+#pragma unroll
+      for (int jj = 0; jj < VY + 2; ++jj) P0[jj] = Pp[jj];
+    }
+    if (!fault) {
+      release(L - 1);  // the last plane (z1) was only read
+    } else {
+      // a copy that never landed: the cells this warp did not write become
+      // NaN, and so does p'q, so that the failure cannot pass unnoticed
+      const float qnan = __int_as_float(0x7fc00000);
+      for (int64_t z = zdone; z < z1; ++z)
+#pragma unroll
+        for (int jj = 0; jj < VY; ++jj)
+          if ((rowok >> jj) & 1u) out[g.plane * z + o0 + (unsigned)(jj * nxi)] = qnan;
+      kadd(acc, qnan);
+    }
+  }
+
+  if (a.pAp != nullptr) {
+    double v[1] = {kval(acc)};
+    block_partial<1>(v, a.partials);
+    double tot[1];
+    if (last_block_range<1>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0)
+      a.pAp[inst] = tot[0];
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -465,6 +704,28 @@ int tma_blocks_per_sm_t() {
   return nb;
 }
 
+template <bool B16>
+int apply_blocks_per_sm_t() {
+  constexpr int smem = apply_smem_bytes<4, 4, 4, B16>();
+  auto fn = apply_tma_kernel<4, 4, 4, B16, false>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 5 * 32, smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <bool B16, bool BATCH>
+cudaError_t launch_apply_t(const ApplyArgs& a, int64_t nblocks, cudaStream_t s) {
+  constexpr int smem = apply_smem_bytes<4, 4, 4, B16>();
+  auto fn = apply_tma_kernel<4, 4, 4, B16, BATCH>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)nblocks, 5 * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // (W, VY, S) of each tile choice; the Jacobi and BF16 variants use tile 0
 struct TileShape {
   int w, vy, s;
@@ -508,13 +769,16 @@ bool tma_sweep_ok(const Grid& g, bool b16, bool jac) {
 
 int tma_tile_count() { return kNumTmaTiles; }
 
-TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac) {
+TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac,
+                 bool apply) {
   TmaPlan p{};
-  if (tile < 0 || tile >= kNumTmaTiles || b16 || jac) tile = 0;
+  if (tile < 0 || tile >= kNumTmaTiles || b16 || jac || apply) tile = 0;
+  if (apply) jac = false;
   const TileShape ts = kTmaTiles[tile];
   p.tile = tile;
   p.b16 = b16;
   p.jac = jac;
+  p.apply = apply;
   p.w = ts.w;
   p.vy = ts.vy;
   p.stages = ts.s;
@@ -554,8 +818,22 @@ TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, boo
 }
 
 int tma_blocks_per_sm(const TmaPlan& p) {
+  // host-side occupancy queries cost microseconds; the answer is fixed per
+  // device and kernel, so it is kept (index: device, kernel variant)
+  constexpr int kDevs = 64, kVariants = 3 + kNumTmaTiles + 2;
+  static int memo[kDevs][kVariants] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  const int var = p.apply ? 3 + kNumTmaTiles + (p.b16 ? 1 : 0)
+                  : (p.b16 && p.jac) ? 0 : p.b16 ? 1 : p.jac ? 2 : 3 + p.tile;
+  if (dev >= 0 && dev < kDevs && var >= 0 && var < kVariants && memo[dev][var] > 0)
+    return memo[dev][var];
   int nb = 0;
-  if (p.b16 && p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, true, true>();
+  if (p.apply) nb = p.b16 ? apply_blocks_per_sm_t<true>() : apply_blocks_per_sm_t<false>();
+  else if (p.b16 && p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, true, true>();
   else if (p.b16) nb = tma_blocks_per_sm_t<4, 4, 4, true, false>();
   else if (p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, false, true>();
   else {
@@ -568,6 +846,7 @@ int tma_blocks_per_sm(const TmaPlan& p) {
     }
   }
   if (nb == 0) cudaGetLastError();
+  else if (dev >= 0 && dev < kDevs && var >= 0 && var < kVariants) memo[dev][var] = nb;
   return nb;
 }
 
@@ -615,6 +894,60 @@ cudaError_t launch_cg_sweep_tma(const Grid& g, const TmaPlan& p, const TmaMaps& 
   a.counter = counter;
   a.cond = cond;
   return use_cond != 0 ? launch_variant<true>(a, p, s) : launch_variant<false>(a, p, s);
+}
+
+bool tma_apply_ok(const Grid& g, bool b16) {
+  return tma_sweep_ok(g, b16, false) && g.nx % 4 == 0;  // FP32 rows of p: 16-byte strides
+}
+
+bool make_apply_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* const* in,
+                     int nin, CUtensorMap* out) {
+  const int ty = p.w * p.vy;
+  bool ok;
+  if (p.b16)
+    ok = encode_rec16(&out[0], static_cast<const uint2*>(coef), g, Rec<true, false>::kX, ty + 1);
+  else
+    ok = encode_rec(&out[0], static_cast<const float4*>(coef), g, Rec<false, false>::kX, ty + 1);
+  for (int i = 0; i < nin && ok; ++i) ok = encode_f32(&out[1 + i], in[i], g, kPX, ty + 2);
+  return ok;
+}
+
+cudaError_t launch_apply_tma(const Grid& g, const TmaPlan& p, const void* coef, const float* pin,
+                             float* Ap, double* pAp, double* partials, unsigned int* counter,
+                             cudaStream_t s) {
+  ApplyArgs a;
+  memset(&a, 0, sizeof(a));
+  CUtensorMap m[2];
+  if (!make_apply_maps(g, p, coef, &pin, 1, m)) return cudaErrorInvalidValue;
+  a.mc = m[0];
+  a.mp = m[1];
+  a.g = g;
+  a.zc = p.zc;
+  a.nbx = (int)p.nbx;
+  a.nby = (int)p.nby;
+  a.Ap = Ap;
+  a.pAp = pAp;
+  a.partials = partials;
+  a.counter = counter;
+  return p.b16 ? launch_apply_t<true, false>(a, p.nblocks, s)
+               : launch_apply_t<false, false>(a, p.nblocks, s);
+}
+
+cudaError_t launch_apply_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int which,
+                                   float* Ap, double* pAp, const int* act, int need,
+                                   double* partials, unsigned int* counters, cudaStream_t s) {
+  ApplyArgs a;
+  memset(&a, 0, sizeof(a));
+  a.inst = inst;
+  a.ninst = ninst;
+  a.which = which;
+  a.act = act;
+  a.need = need;
+  a.Ap = Ap;
+  a.pAp = pAp;
+  a.partials = partials;
+  a.counter = counters;
+  return launch_apply_t<false, true>(a, nblocks, s);
 }
 
 cudaError_t launch_cg_sweep_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int tile,

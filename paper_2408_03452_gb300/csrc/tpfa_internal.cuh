@@ -79,6 +79,7 @@ struct CgVecs {
 struct TmaPlan {
   int tile;    // index of the (w, vy, stages) choice
   bool b16, jac;
+  bool apply;  // the operator application q = A p (tile 0), not a CG sweep
   int w, vy, stages, zc;
   int64_t nbx, nby, nbz, nblocks;
 };
@@ -91,7 +92,8 @@ struct TmaMaps {
 // strides (BF16 records: nx even; BF16 Jacobi: nx % 4 == 0)
 bool tma_sweep_ok(const Grid& g, bool b16, bool jac);
 int tma_tile_count();
-TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac);
+TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac,
+                 bool apply = false);
 int tma_blocks_per_sm(const TmaPlan& p);
 bool make_tma_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* dinv,
                    const CgVecs& v, TmaMaps* m);
@@ -112,6 +114,25 @@ struct TmaInst {
 cudaError_t launch_cg_sweep_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int tile,
                                       bool jac, CgVecs v, CgState* st, double* partials,
                                       unsigned int* counters, cudaStream_t s);
+
+// Operator application q = A p (p'q into *pAp when given) through the
+// TMA-staged kernel (plan from plan_tma(..., apply = true)).  Needs
+// tma_apply_ok (the tensor-map encoder and nx % 4 == 0) and 16-byte aligned p
+// and coefficients.  A copy that never lands makes the unwritten cells and p'q
+// NaN.
+bool tma_apply_ok(const Grid& g, bool b16);
+cudaError_t launch_apply_tma(const Grid& g, const TmaPlan& p, const void* coef, const float* pin,
+                             float* Ap, double* pAp, double* partials, unsigned int* counter,
+                             cudaStream_t s);
+// Tensor maps of a batched operator instance: out[0] the coefficient records,
+// out[1 + i] the FP32 input in[i] (nin inputs).
+bool make_apply_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* const* in,
+                     int nin, CUtensorMap* out);
+// Batched operator through the TMA-staged kernel: inst[i].maps as from
+// make_apply_maps, input `which`; instances with (act[i] & need) == need only.
+cudaError_t launch_apply_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int which,
+                                   float* Ap, double* pAp, const int* act, int need,
+                                   double* partials, unsigned int* counters, cudaStream_t s);
 
 // ---- launchers (kernels_*.cu) ---------------------------------------------
 

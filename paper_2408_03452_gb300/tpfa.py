@@ -252,7 +252,8 @@ class Context:
 
     def tiling(self, which: int = 0) -> dict:
         """Sweep tiling: which = 0 (CG loop, FP32 records), 1 (CG loop, BF16
-        records), 2 (tpfa_apply).  kernel 1 = cp.async-staged, 2 = TMA-staged."""
+        records), 2 (tpfa_apply), 3 (tpfa_apply_bf16; both for 16-byte aligned
+        arguments).  kernel 1 = cp.async-staged, 2 = TMA-staged."""
         out = (C.c_int64 * 6)()
         _check(lib().tpfa_sweep_tiling(self._h, int(which), C.cast(out, C.c_void_p)),
                "tpfa_sweep_tiling")

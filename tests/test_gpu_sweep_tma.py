@@ -73,13 +73,15 @@ def test_tiling_selection(tp):
         with tp.Context(*shape) as ctx:
             assert tiling(tp, ctx)["kernel"] == 2                                # FP32 records
             assert tiling(tp, ctx, 1)["kernel"] == (2 if nx % 2 == 0 else 1)     # BF16 records
-            assert tiling(tp, ctx, 2)["kernel"] == 1                             # tpfa_apply
+            assert tiling(tp, ctx, 2)["kernel"] == (2 if nx % 4 == 0 else 1)     # tpfa_apply
+            assert tiling(tp, ctx, 3)["kernel"] == (2 if nx % 4 == 0 else 1)     # tpfa_apply_bf16
             ctx.set_option("precond", 1)
             assert tiling(tp, ctx)["kernel"] == 2
             assert tiling(tp, ctx, 1)["kernel"] == (2 if nx % 4 == 0 else 1)     # BF16 Jacobi
             ctx.set_option("precond", 0)
             ctx.set_option("sweep", 1)
             assert tiling(tp, ctx)["kernel"] == 1
+            assert tiling(tp, ctx, 2)["kernel"] == 1
             ctx.set_option("sweep", 2)
             t = tiling(tp, ctx)
             assert t["kernel"] == 2 and t["warps"] == 4 and t["vy"] == 4 and t["stages"] == 4

@@ -51,9 +51,13 @@ def test_noalloc_apply_matches_context_apply(tp, shape):
             assert rc == tp.OK, tp.strerror(rc)
             torch.cuda.synchronize()
             # same per-cell arithmetic: identical values; the dot product may
-            # differ in the last bits only through its summation order
+            # differ only through its summation order (tpfa_apply may take the
+            # TMA-staged kernel, whose warps own 32-column rows instead of 30):
+            # each side's compensated FP32 warp sums are within 2u of exact, so
+            # the two differ by at most 4u sum |p_i (Ap)_i|
             assert torch.equal(Ap, ref)
-            assert pAp.item() == pytest.approx(ref_pAp.item(), rel=1e-12)
+            absdot = float((p.double() * ref.double()).abs().sum())
+            assert abs(pAp.item() - ref_pAp.item()) <= 4 * 2.0 ** -24 * absdot
 
 
 def test_noalloc_rejects_bad_arguments(tp):
