@@ -111,6 +111,7 @@ int setup_batch_tma(tpfa_batch* b, const float* coef) {
     I.off = b->off[i];
     I.bstart = blocks;
     I.nblocks = p.nblocks;
+    I.id = i;
     I.maps = b->maps_dev + 4 * i;
     blocks += p.nblocks;
   }

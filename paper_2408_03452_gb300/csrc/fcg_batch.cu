@@ -48,7 +48,7 @@ struct BScal {
 
 struct BChunk {
   int inst;
-  int pad;
+  int id;            // index in the batch's full chunk list (its partial-sum slot)
   int64_t beg, end;  // cells [beg, end) of the concatenated arrays
 };
 
@@ -99,7 +99,7 @@ __global__ void bstart_kernel(const BChunk* __restrict__ chunks, const int* __re
     rr += (double)v * v;
   }
   double d[1] = {rr};
-  block_sum_m<1>(d, part);
+  block_sum_m<1>(d, part, ch.id);
 }
 
 // rr0 and the inner threshold of every active instance
@@ -186,7 +186,7 @@ __global__ void bdots_kernel(const BChunk* __restrict__ chunks, const int* __res
   double d[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) d[j] = s[j];
-  block_sum_m<K>(d, part);
+  block_sum_m<K>(d, part, ch.id);
 }
 
 // c and the beta_j of every active instance (beta_j = 0 beyond its own
@@ -286,7 +286,7 @@ __global__ void bdir_kernel(const BChunk* __restrict__ chunks, const int* __rest
         reinterpret_cast<float4*>(p)[k] = o;
       });
   double pr[1] = {prf};
-  block_sum_m<1>(pr, part);
+  block_sum_m<1>(pr, part, ch.id);
 }
 
 // alpha = p'r / p'q per active instance (0 and the bad flag when p'q is not
@@ -349,7 +349,7 @@ __global__ void bupdate_kernel(const BChunk* __restrict__ chunks, const int* __r
         rrf = fmaf(r4.w, r4.w, rrf);
       });
   double rr[1] = {rrf};
-  block_sum_m<1>(rr, part);
+  block_sum_m<1>(rr, part, ch.id);
 }
 
 // r'r of this iteration into the instance's history slot (-1 for an instance
@@ -474,15 +474,26 @@ struct BWork {
   // TMA-staged operator (set up when every instance suits it): per-instance
   // tilings and tensor maps {coefficients, z, P slot 0 .. m-1}, block partials
   bool tma = false;
-  int64_t ablocks = 0;
   CUtensorMap* amaps = nullptr;
-  tpfa::TmaInst* ainst = nullptr;
+  std::vector<tpfa::TmaInst> ainst_all;  // every instance (host)
+  tpfa::TmaInst* ainst = nullptr;         // the instances of aset (device)
+  int nainst = 0;
+  int64_t ablocks = 0;
   double* apart = nullptr;
+  // The per-iteration passes launch only over the instances that were
+  // iterating at the host's last look (aset): their chunks and operator
+  // blocks.  An instance that stops on the device in between keeps its
+  // blocks until the next look; they return at once.
+  std::vector<int> aset;
+  std::vector<BChunk> achunks;
+  BChunk* achunks_dev = nullptr;
+  unsigned nach = 0;
 
   bool alloc() {
     const size_t v = (size_t)stride * 4;
     const size_t nc = chunks.size();
     bool ok = cudaMalloc(&chunks_dev, sizeof(BChunk) * nc) == cudaSuccess &&
+              cudaMalloc(&achunks_dev, sizeof(BChunk) * nc) == cudaSuccess &&
               cudaMalloc(&cfirst_dev, sizeof(int) * ninst) == cudaSuccess &&
               cudaMalloc(&ccount_dev, sizeof(int) * ninst) == cudaSuccess &&
               cudaMalloc(&flags, sizeof(int) * ninst) == cudaSuccess &&
@@ -518,6 +529,7 @@ struct BWork {
   ~BWork() {
     if (s) cudaStreamSynchronize(s);
     cudaFree(chunks_dev);
+    cudaFree(achunks_dev);
     cudaFree(cfirst_dev);
     cudaFree(ccount_dev);
     cudaFree(flags);
@@ -576,6 +588,7 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
     I.zc = p.zc;
     I.nbx = (int)p.nbx;
     I.nby = (int)p.nby;
+    I.id = i;
     I.off = o;
     I.bstart = blocks;
     I.nblocks = p.nblocks;
@@ -595,8 +608,46 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
           cudaSuccess ||
       cudaStreamSynchronize(w.s) != cudaSuccess)
     return TPFA_ECUDA;
+  w.ainst_all = inst;
+  w.nainst = N;
   w.tma = true;
   w.ablocks = blocks;
+  return TPFA_OK;
+}
+
+// The launch lists of the per-iteration passes for the instances whose host
+// flags (w.hflags) hold kAct: their chunks, and their operator blocks
+// numbered consecutively.  The copies are ordered on the stream before the
+// passes that read the lists.
+int compact_active(BWork& w) {
+  using namespace tpfa;
+  std::vector<int> act;
+  for (int i = 0; i < w.ninst; ++i)
+    if (w.hflags[i] & kAct) act.push_back(i);
+  if (act == w.aset && w.nach > 0) return TPFA_OK;
+  w.aset = act;
+  w.achunks.clear();
+  for (int i : act)
+    for (int c = w.cfirst[i]; c < w.cfirst[i] + w.ccount[i]; ++c) w.achunks.push_back(w.chunks[c]);
+  w.nach = (unsigned)w.achunks.size();
+  if (w.nach > 0 && cudaMemcpyAsync(w.achunks_dev, w.achunks.data(), sizeof(BChunk) * w.nach,
+                                    cudaMemcpyHostToDevice, w.s) != cudaSuccess)
+    return TPFA_ECUDA;
+  if (w.tma) {
+    std::vector<TmaInst> t;
+    int64_t b = 0;
+    for (int i : act) {
+      TmaInst I = w.ainst_all[i];
+      I.bstart = b;
+      b += I.nblocks;
+      t.push_back(I);
+    }
+    w.nainst = (int)t.size();
+    w.ablocks = b;
+    if (!t.empty() && cudaMemcpyAsync(w.ainst, t.data(), sizeof(TmaInst) * t.size(),
+                                      cudaMemcpyHostToDevice, w.s) != cudaSuccess)
+      return TPFA_ECUDA;
+  }
   return TPFA_OK;
 }
 
@@ -605,9 +656,11 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
 bool batch_apply(const tpfa_batch* batch, BWork& w, const float4* cf4, int which, float* out,
                  double* pap, int need) {
   using namespace tpfa;
-  if (w.tma)
-    return launch_apply_tma_batch(w.ainst, w.ninst, w.ablocks, which, out, pap, w.flags, need,
+  if (w.tma) {
+    if (w.nainst == 0) return true;  // nothing iterates
+    return launch_apply_tma_batch(w.ainst, w.nainst, w.ablocks, which, out, pap, w.flags, need,
                                   w.apart, batch->counters, w.s) == cudaSuccess;
+  }
   const float* in = which == 0 ? w.z : w.P + (size_t)(which - 1) * w.stride;
   return launch_apply_batch(batch->inst_dev, w.ninst, batch->sweep_blocks, cf4, in, out, pap,
                             w.flags, need, batch->partials, batch->counters, w.s) == cudaSuccess;
@@ -787,7 +840,7 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       for (int64_t c0 = batch->off[i]; c0 < batch->off[i + 1]; c0 += kChunk) {
         BChunk ch;
         ch.inst = i;
-        ch.pad = 0;
+        ch.id = (int)w.chunks.size();
         ch.beg = c0;
         ch.end = std::min<int64_t>(c0 + kChunk, batch->off[i + 1]);
         w.chunks.push_back(ch);
@@ -914,6 +967,8 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       for (int i = 0; i < N; ++i) blend[i] = (w.hflags[i] & kNet) != 0;
       rc = update_active(bn, blend, batch->off, w);
       if (rc) break;
+      rc = compact_active(w);
+      if (rc) break;
       bool first = true;
       while (running && rc == TPFA_OK) {
         bool any_blend = false;
@@ -935,11 +990,11 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
         }
         float* p = w.P + (size_t)head * w.stride;
         float* q = w.Q + (size_t)head * w.stride;
-        launch_bdots(gstored, w.nchunks(), s, w.chunks_dev, w.flags, w.r, w.dinv, w.z, w.au, qd,
+        launch_bdots(gstored, w.nach, s, w.achunks_dev, w.flags, w.r, w.dinv, w.z, w.au, qd,
                      w.vec4, w.part);
         bfinish_dots_kernel<<<N, kT, 0, s>>>(w.cfirst_dev, w.ccount_dev, w.flags, w.part, gstored,
                                              w.uau, w.sc, head, w.m);
-        launch_bdir(gstored, w.nchunks(), s, w.chunks_dev, w.flags, w.sc, w.r, w.dinv, w.z, pd, p,
+        launch_bdir(gstored, w.nach, s, w.achunks_dev, w.flags, w.sc, w.r, w.dinv, w.z, pd, p,
                     w.vec4, w.part);
         if (!batch_apply(batch, w, cf4, 1 + head, q, w.pq, kAct)) {
           rc = TPFA_ECUDA;
@@ -947,8 +1002,8 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
         }
         bfinish_alpha_kernel<<<N, kT, 0, s>>>(w.cfirst_dev, w.ccount_dev, w.flags, w.part, w.pq,
                                               w.sc, head, w.m);
-        bupdate_kernel<<<w.nchunks(), kT, 0, s>>>(w.chunks_dev, w.flags, w.sc, w.e, w.r, p, q,
-                                                  w.vec4, w.part);
+        bupdate_kernel<<<w.nach, kT, 0, s>>>(w.achunks_dev, w.flags, w.sc, w.e, w.r, p, q,
+                                             w.vec4, w.part);
         bfinish_rr_kernel<<<N, kT, 0, s>>>(w.cfirst_dev, w.ccount_dev, w.flags, w.part, w.sc,
                                            w.hist, pending);
         w.launches += 7;
@@ -1028,8 +1083,11 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
           rc = TPFA_ECUDA;
           break;
         }
-        // the networks run on the members that still iterate with them
+        // the networks run on the members that still iterate with them, the
+        // passes on the instances that still iterate
         rc = update_active(bn, blend, batch->off, w);
+        if (rc) break;
+        rc = compact_active(w);
         if (rc) break;
         if (giters > maxit + kCheckEvery) break;  // every instance has its own limit below this
       }

@@ -22,9 +22,10 @@ namespace {
 constexpr int kT = 256;
 
 // Block sums of M per-thread FP64 values (warp shuffles, then the warps in
-// order): part[blockIdx.x * M + j].
+// order): part[slot * M + j].
 template <int M>
-__device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) {
+__device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part,
+                                            int64_t slot) {
   __shared__ double sh[M][kT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -38,8 +39,13 @@ __device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) 
   if (threadIdx.x < M) {
     double t = 0.0;
     for (int w = 0; w < kT / 32; ++w) t += sh[threadIdx.x][w];
-    part[(size_t)blockIdx.x * M + threadIdx.x] = t;
+    part[(size_t)slot * M + threadIdx.x] = t;
   }
+}
+// ... into the slot of this block
+template <int M>
+__device__ __forceinline__ void block_sum_m(const double (&v)[M], double* part) {
+  block_sum_m<M>(v, part, blockIdx.x);
 }
 
 constexpr int kMaxDirs = 16;

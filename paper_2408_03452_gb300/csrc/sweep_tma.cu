@@ -411,9 +411,11 @@ constexpr int apply_smem_bytes() {
 
 struct ApplyArgs {
   CUtensorMap mp, mc;  // p, coefficient records
-  // batched operator: instance table; an instance's maps are {coefficients,
-  // input 0, input 1, ...} and `which` picks the input; only instances with
-  // (act[i] & need) == need are applied, the others' cells are left untouched
+  // batched operator: instance table (all instances of the batch or a subset,
+  // blocks numbered consecutively through it); an instance's maps are
+  // {coefficients, input 0, input 1, ...} and `which` picks the input; only
+  // instances with (act[id] & need) == need are applied, the others' cells are
+  // left untouched
   const TmaInst* inst;
   int ninst, which;
   const int* act;
@@ -451,12 +453,13 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
       const int mid = (lo + hi + 1) >> 1;
       if (a.inst[mid].bstart <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    if ((a.act[lo] & a.need) != a.need) return;  // every block of the instance returns
     const TmaInst& I = a.inst[lo];
+    // the table may list a subset of the batch: I.id is the batch index
+    if ((a.act[I.id] & a.need) != a.need) return;  // every block of the instance returns
     g = I.g; nbx = I.nbx; nby = I.nby; zc = I.zc; off = I.off;
     lb = blockIdx.x - I.bstart; pstart = I.bstart; pcount = I.nblocks;
-    inst = lo;
-    counter = a.counter + lo;
+    inst = I.id;
+    counter = a.counter + I.id;
     mc = I.maps;
     mp = I.maps + 1 + a.which;
   }

@@ -104,6 +104,7 @@ bool make_tma_maps(const Grid& g, const TmaPlan& p, const void* coef, const floa
 struct TmaInst {
   Grid g;
   int zc, nbx, nby;
+  int id;  // the instance's index in the batch (its scalars, counter, flags)
   int64_t off;
   int64_t bstart;
   int64_t nblocks;
@@ -128,8 +129,10 @@ cudaError_t launch_apply_tma(const Grid& g, const TmaPlan& p, const void* coef, 
 // out[1 + i] the FP32 input in[i] (nin inputs).
 bool make_apply_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* const* in,
                      int nin, CUtensorMap* out);
-// Batched operator through the TMA-staged kernel: inst[i].maps as from
-// make_apply_maps, input `which`; instances with (act[i] & need) == need only.
+// Batched operator through the TMA-staged kernel: inst[k].maps as from
+// make_apply_maps, input `which`; the table may list any subset of the batch's
+// instances (inst[k].id, bstart consecutive through the table); only instances
+// with (act[id] & need) == need are applied; pAp and counters by id.
 cudaError_t launch_apply_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int which,
                                    float* Ap, double* pAp, const int* act, int need,
                                    double* partials, unsigned int* counters, cudaStream_t s);
