@@ -667,8 +667,10 @@ conv_fwd_zf_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
 // Same work units, row-group triples, folded MMAs (N = 3 cout) and TMEM ring
 // of accumulators as conv_fwd_zf_kernel, but the three kinds of work no
 // longer wait for each other at a block barrier:
-//   warp 4 copies triples into a ring of ST slots (cp.async; each lane's
-//          copies arrive on the slot's "full" mbarrier when they land);
+//   warp 4 copies triples into a ring of ST slots (cp.async); once the next
+//          triple's copies are issued, each lane waits for its copies of the
+//          previous one, fences them to the async proxy and arrives on that
+//          slot's "full" mbarrier;
 //   warp 5 (one thread) issues the MMAs of a triple once it is full and the
 //          slot of the output it starts is free, and commits to the triple's
 //          "empty" barrier and to the "full" barrier of the output the triple
@@ -692,10 +694,6 @@ struct WsCfg {
   static_assert(kR >= 4, "accumulator ring");
 };
 
-__device__ __forceinline__ void cp_mbar_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc::smem_addr(bar))
-               : "memory");
-}
 __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(bar)) : "memory");
 }
@@ -755,7 +753,19 @@ conv_fwd_ws_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
 
   if (warp == 4) {
     // ---- copy warp -----------------------------------------------------------
-    int tg = 0;
+    // A triple is handed to the tensor core once the copies of the next one
+    // are issued: each lane waits for its own copies of the triple, makes
+    // them visible to the async proxy (the MMAs read shared memory through
+    // it), then arrives on the triple's "full" barrier.
+    int tg = 0, pend = -1;  // pend: slot of the triple whose arrival is due
+    auto hand_over = [&](bool last) {
+      if (pend < 0) return;
+      if (last) cp_wait_all();
+      else cp_wait_groups<1>();
+      tc::fence_proxy_async();
+      mbar_arrive1(&tfull[pend]);
+      pend = -1;
+    };
     for (int u = blockIdx.x; u < zg.units && !s_abort; u += gridDim.x) {
       const int bi = u % zg.nb, cz = u / zg.nb;
       const int sidx = cz / zg.nzc;
@@ -775,9 +785,12 @@ conv_fwd_ws_kernel(const uint16_t* __restrict__ x, const uint16_t* __restrict__ 
           cp16z(st + gi * Cfg::kRGBytes + c * (kRG * 16) + v * 16,
                 x + (size_t)(ok ? row : 0) * CIN + c * 8, ok);
         }
-        cp_mbar_arrive_noinc(&tfull[s]);
+        cp_commit_group();
+        hand_over(false);  // the previous triple
+        pend = s;
       }
     }
+    hand_over(true);
     cp_wait_all();
   } else if (warp == 5) {
     // ---- MMA thread --------------------------------------------------------

@@ -180,7 +180,9 @@ def conv3d_wgrad_bf16(x, dy, dw, shape, cin, cout, accumulate=False):
 
 
 def conv3d_select(kernel: int):
-    """0: tile kernel; 1: z-marching kernel (default)."""
+    """Forward-convolution kernel (tpfa_conv3d_select): 0 tile, 1 z-marching,
+    2 z-taps folded, 3 automatic (default: 4 except 32 -> 16, which takes 1),
+    4 folded with warp-specialised roles; 64 -> 32 always takes 0."""
     _check(lib().tpfa_conv3d_select(int(kernel)), "tpfa_conv3d_select")
 
 
