@@ -441,21 +441,26 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def sweep_traffic(nx, ny, nz):
-    """DRAM bytes of one CG sweep launch (TMA-staged, FP32 records, plain CG)
-    from the committed ncu summary (bytes per cell of a smaller capture with
-    the same 128-plane runs, times the cells), if it was taken on the current
-    kernel source; else None."""
+def kernel_traffic(record, cells):
+    """DRAM bytes of one launch of a TMA-staged kernel over `cells` cells from
+    a committed ncu summary under profiles/ (bytes per cell of a smaller
+    capture with the same 128-plane runs, times the cells), if it was taken on
+    the current kernel source; else None."""
     src = os.path.join(ROOT, "paper_2408_03452_gb300", "csrc", "sweep_tma.cu")
-    prof = os.path.join(ROOT, "profiles", "cg_sweep_traffic.json")
+    prof = os.path.join(ROOT, "profiles", record)
     try:
         rec = json.load(open(prof))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if rec.get("source_sha256_16") != h:
             return None
-        return rec["dram_bytes_per_cell"] * nx * ny * nz
+        return rec["dram_bytes_per_cell"] * cells
     except Exception:
         return None
+
+
+def sweep_traffic(nx, ny, nz):
+    """The CG sweep (TMA-staged, FP32 records, plain CG)."""
+    return kernel_traffic("cg_sweep_traffic.json", nx * ny * nz)
 
 
 # Table III of the paper (Section V.C): grid, CG iterations, CS-2 and A100
@@ -830,7 +835,9 @@ def run_learned(a, dev, rank, local, barrier):
                          "peak": hpeak, "unit": "GB/s",
                          "frac": APPLY_BYTES_PER_CELL * cells / (apply_ms / 1e3) / 1e9 / hpeak,
                          "peak_source": hkind, "bytes_per_cell": APPLY_BYTES_PER_CELL,
-                         "launch_ms": apply_ms, "traffic": None},
+                         "launch_ms": apply_ms,
+                         "traffic": (kernel_traffic("apply_tma_traffic.json", cells)
+                                     if ctx.tiling(2)["kernel"] == 2 else None)},
             "roofline_network": {"kernel": f"tensor-core 3x3x3 convolution 16->16 on the "
                                            f"network's finest level ({nn}^3)",
                                  "bound": "tensor", "achieved": achieved, "peak": tpeak,
