@@ -492,7 +492,7 @@ int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* ln
     rc = tpfa_unet_forward(net, w.rl[L], w.lnkc, w.ul[L], w.s);
     if (rc) return rc;
     launch_prolong_levels(L, w.nb, w.s, w.ul[L], w.z, w.dims[0], w.dims[1], w.dims[2], 1, nullptr,
-                          0, 0, 0);
+                          0, 0, 0, true);
     w.launches += 17;
   } else {
     rc = tpfa_unet_forward(net, w.r, lnk, w.z, w.s);
@@ -851,6 +851,6 @@ extern "C" int tpfa_prolong_levels(const float* coarse, float* fine, int nx, int
     return TPFA_EINVAL;
   const int nb = (int)((n / 2 + kT - 1) / kT < 4096 ? (n / 2 + kT - 1) / kT : 4096);
   launch_prolong_levels(levels, nb, (cudaStream_t)stream, coarse, fine, nx, ny, nz, ns, nullptr, 0,
-                        0, 0);
+                        0, 0, true);
   return cudaGetLastError() == cudaSuccess ? TPFA_OK : TPFA_ECUDA;
 }

@@ -708,7 +708,7 @@ int network_class(BNet& N, BWork& w) {
     rc = tpfa_unet_forward_samples(N.net, ns, N.rl[L], N.lnkc, N.ul[L], w.s);
     if (rc) return rc;
     launch_prolong_levels(L, w.nb, w.s, N.ul[L], w.z, N.dims[0], N.dims[1], N.dims[2], ns, N.soff,
-                          N.pdims[0], N.pdims[1], N.pdims[2]);
+                          N.pdims[0], N.pdims[1], N.pdims[2], w.vec4 != 0);
     w.launches += 17;
   } else {
     const int64_t n = (int64_t)N.dims[0] * N.dims[1] * N.dims[2];

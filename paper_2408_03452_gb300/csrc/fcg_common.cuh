@@ -171,26 +171,35 @@ __global__ void restrict_levels_kernel(const float* __restrict__ fine, float* __
 }
 
 // fine[c] = coarse value of c's ancestor on the 2^L coarser grid (L nearest
-// prolongations in one pass); two x-neighbours per thread.  Sample offsets
-// and the padded coarse layout as in prolong2_kernel.
-template <int L>
+// prolongations in one pass).  Blocks walk (sample, z) planes along y and the
+// groups of V x-neighbours of one plane along x (no per-cell divisions); V = 4
+// (one 16-byte store per thread) needs nx % 4 == 0 and sample starts on 16-byte
+// boundaries, V = 2 an even nx and 8-byte boundaries.  Sample offsets and the
+// padded coarse layout as in prolong2_kernel.
+template <int L, int V>
 __global__ void prolong_levels_kernel(const float* __restrict__ coarse, float* __restrict__ fine,
                                       int nx, int ny, int nz, int ns,
                                       const int64_t* __restrict__ soff, int qx, int qy, int qz) {
-  const int hx = nx / 2;
   const int px = qx > 0 ? qx : nx >> L, py = qy > 0 ? qy : ny >> L, pz = qz > 0 ? qz : nz >> L;
-  const int per = hx * ny * nz;  // float2 pairs per sample
-  const int n2 = per * ns;
-  for (int c = blockIdx.x * kT + threadIdx.x; c < n2; c += gridDim.x * kT) {
-    const int i = c % hx;
-    int t = c / hx;
-    const int j = t % ny;
-    t /= ny;
-    const int k = t % nz;
-    const int s = t / nz;
-    const float v = coarse[((size_t)(s * pz + (k >> L)) * py + (j >> L)) * px + ((2 * i) >> L)];
-    float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * 2 * per);
-    *reinterpret_cast<float2*>(f + 2 * (size_t)(c - s * per)) = make_float2(v, v);
+  const int gx = nx / V;         // groups per row
+  const int per = gx * ny;       // groups per plane
+  const int planes = nz * ns;
+  for (int pl = blockIdx.y; pl < planes; pl += gridDim.y) {
+    const int s = pl / nz, k = pl - s * nz;
+    float* f = fine + (soff != nullptr ? (size_t)soff[s] : (size_t)s * nx * ny * nz) +
+               (size_t)k * nx * ny;
+    const float* c = coarse + (size_t)(s * pz + (k >> L)) * py * px;
+    for (int t = blockIdx.x * kT + threadIdx.x; t < per; t += gridDim.x * kT) {
+      const int j = t / gx, i = (t - j * gx) * V;
+      const float* cr = c + (size_t)(j >> L) * px;
+      const float v0 = cr[i >> L];
+      if constexpr (V == 4) {
+        const float v1 = L >= 2 ? v0 : cr[(i + 2) >> L];
+        *reinterpret_cast<float4*>(f + (size_t)j * nx + i) = make_float4(v0, v0, v1, v1);
+      } else {
+        *reinterpret_cast<float2*>(f + (size_t)j * nx + i) = make_float2(v0, v0);
+      }
+    }
   }
 }
 
@@ -207,13 +216,27 @@ inline void launch_restrict_levels(int L, int nb, cudaStream_t st, const float* 
 }
 inline void launch_prolong_levels(int L, int nb, cudaStream_t st, const float* coarse, float* fine,
                                   int nx, int ny, int nz, int ns, const int64_t* soff, int qx,
-                                  int qy, int qz) {
+                                  int qy, int qz, bool starts16 = false) {
+  // starts16: every sample starts on a 16-byte boundary (with soff: offsets
+  // that are multiples of 4 cells; without: a 16-byte aligned fine)
+  const bool v4 = nx % 4 == 0 && starts16 && reinterpret_cast<uintptr_t>(fine) % 16 == 0;
+  const int per = (nx / (v4 ? 4 : 2)) * ny;
+  const int planes = nz * ns;
+  int by = planes < 65535 ? planes : 65535;
+  int bx = (per + kT - 1) / kT;
+  const int cap = nb / by > 1 ? nb / by : 1;  // about nb blocks in all
+  if (bx > cap) bx = cap;
+  const dim3 grid((unsigned)bx, (unsigned)by);
+#define TPFA_PROLONG(LL)                                                                        \
+  if (v4) prolong_levels_kernel<LL, 4><<<grid, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); \
+  else prolong_levels_kernel<LL, 2><<<grid, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz);
   switch (L) {
-    case 1: prolong_levels_kernel<1><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
-    case 2: prolong_levels_kernel<2><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
-    case 3: prolong_levels_kernel<3><<<nb, kT, 0, st>>>(coarse, fine, nx, ny, nz, ns, soff, qx, qy, qz); break;
+    case 1: TPFA_PROLONG(1) break;
+    case 2: TPFA_PROLONG(2) break;
+    case 3: TPFA_PROLONG(3) break;
     default: break;
   }
+#undef TPFA_PROLONG
 }
 
 // iterations between the host's looks at the device scalars (convergence,

@@ -286,8 +286,8 @@ def test_restrict_prolong_match_oracle(tp):
                           .astype(np.float32))
 
 
-@pytest.mark.parametrize("levels,shape", [(1, (8, 6, 4, 2)), (2, (16, 8, 12, 2)),
-                                          (3, (16, 16, 8, 1))])
+@pytest.mark.parametrize("levels,shape", [(1, (8, 6, 4, 2)), (1, (6, 4, 2, 3)),
+                                          (2, (16, 8, 12, 2)), (3, (16, 16, 8, 1))])
 def test_restrict_prolong_levels_equal_repeated_single_level(tp, levels, shape):
     """The one-pass restriction to the 2^levels coarser grid (what the solvers
     use) is bit-identical to `levels` tpfa_restrict2 passes, the one-pass
@@ -317,6 +317,10 @@ def test_restrict_prolong_levels_equal_repeated_single_level(tp, levels, shape):
     for _ in range(levels):
         up = U.prolong2(up)
     assert np.array_equal(fused_p.cpu().double().numpy(), up.ravel())
+    # a fine vector on an 8- but not 16-byte boundary takes the two-cell stores: same values
+    buf2 = torch.zeros(nx * ny * nz * ns + 2, dtype=torch.float32, device="cuda")
+    assert buf2[2:].data_ptr() % 16 == 8
+    assert torch.equal(tp.prolong_levels(CC, shape, levels, fine=buf2[2:]), fused_p)
     # the prolongations write pairs of cells: a fine vector off an 8-byte boundary is refused
     buf = torch.zeros(nx * ny * nz * ns + 1, dtype=torch.float32, device="cuda")
     with pytest.raises(tp.TpfaError):
