@@ -131,10 +131,11 @@ template <int M>
 __global__ void bdots_kernel(const BChunk* __restrict__ chunks, const int* __restrict__ flags,
                              const float* __restrict__ r, const float* __restrict__ dinv,
                              const float* __restrict__ u, const float* __restrict__ au, Dirs qd,
-                             int vec4, double* part) {
+                             int vec4, double* part, int skip_net) {
   constexpr int K = 2 + 2 * M;
   const BChunk ch = chunks[blockIdx.x];
   const int f = flags[ch.inst];
+  if (skip_net && (f & kNet)) return;  // the fused operator took this instance's dots
   if (!(f & kAct)) return;
   const bool jac = (f & kJac) != 0, net = (f & kNet) != 0;
   float s[K];
@@ -194,13 +195,20 @@ __global__ void bdots_kernel(const BChunk* __restrict__ chunks, const int* __res
 __global__ void bfinish_dots_kernel(const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                     const int* __restrict__ flags, const double* __restrict__ part,
                                     int M, const double* __restrict__ uau, BScal* sc, int head,
-                                    int m) {
+                                    int m, const double* __restrict__ fdots) {
   const int i = blockIdx.x;
   const int f = flags[i];
   if (!(f & kAct)) return;
   __shared__ double tot[2 + 2 * kMaxDirs];
   const int K = 2 + 2 * M;
-  chunk_totals(part, cfirst[i], ccount[i], K, tot);
+  if (fdots != nullptr && (f & kNet)) {
+    // from the fused operator: u'q, then u'r, q'w, w'q_j, u'q_j
+    if (threadIdx.x < K)
+      tot[threadIdx.x] = fdots[(size_t)i * tpfa::kApplyDotsStride + 1 + threadIdx.x];
+    __syncthreads();
+  } else {
+    chunk_totals(part, cfirst[i], ccount[i], K, tot);
+  }
   if (threadIdx.x == 0) {
     BScal& S = sc[i];
     double c = 0.0;
@@ -389,11 +397,11 @@ __global__ void gather_kernel(const float* __restrict__ src, const int64_t* __re
 
 void launch_bdots(int M, unsigned nchunks, cudaStream_t s, const BChunk* ch, const int* flags,
                   const float* r, const float* dinv, const float* u, const float* au,
-                  const Dirs& qd, int vec4, double* part) {
+                  const Dirs& qd, int vec4, double* part, int skip_net) {
   switch (M) {
-#define X(MM)                                                                                 \
-  case MM:                                                                                    \
-    bdots_kernel<MM><<<nchunks, kT, 0, s>>>(ch, flags, r, dinv, u, au, qd, vec4, part); \
+#define X(MM)                                                                                  \
+  case MM:                                                                                     \
+    bdots_kernel<MM><<<nchunks, kT, 0, s>>>(ch, flags, r, dinv, u, au, qd, vec4, part, skip_net); \
     break;
     TPFA_FCG_M0(X)
 #undef X
@@ -477,6 +485,8 @@ struct BWork {
   CUtensorMap* amaps = nullptr;
   std::vector<tpfa::TmaInst> ainst_all;  // every instance (host)
   tpfa::TmaInst* ainst = nullptr;         // the instances of aset (device)
+  int own0 = 0;                           // first own-cell map of an instance
+  double* dots = nullptr;                 // fused operator: per-instance dot products
   int nainst = 0;
   int64_t ablocks = 0;
   double* apart = nullptr;
@@ -553,6 +563,7 @@ struct BWork {
     cudaFree(amaps);
     cudaFree(ainst);
     cudaFree(apart);
+    cudaFree(dots);
     if (fork) cudaEventDestroy(fork);
   }
   unsigned nchunks() const { return (unsigned)chunks.size(); }
@@ -569,7 +580,10 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
     return TPFA_OK;
   for (const Grid& g : batch->g)
     if (!tma_apply_ok(g, false)) return TPFA_OK;
-  const int N = w.ninst, per = 2 + w.m;
+  // maps per instance: coefficients, z, P slots (with halo); r, M^-1, Q slots
+  // (own cells, for the fused dot products)
+  const int N = w.ninst, per = 4 + 2 * w.m;
+  std::vector<const float*> own(2 + w.m);
   const std::vector<int> zr = batch_tma_zc_request(batch);
   std::vector<CUtensorMap> maps((size_t)per * N);
   std::vector<TmaInst> inst(N);
@@ -580,8 +594,12 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
     const int64_t o = batch->off[i];
     in[0] = w.z + o;
     for (int k = 0; k < w.m; ++k) in[1 + k] = w.P + (size_t)k * w.stride + o;
+    own[0] = w.r + o;
+    own[1] = w.dinv + o;
+    for (int k = 0; k < w.m; ++k) own[2 + k] = w.Q + (size_t)k * w.stride + o;
     if (!make_apply_maps(batch->g[i], p, reinterpret_cast<const float4*>(coef) + o, in.data(),
-                         1 + w.m, &maps[(size_t)per * i]))
+                         1 + w.m, &maps[(size_t)per * i]) ||
+        !make_own_maps(batch->g[i], p, own.data(), 2 + w.m, &maps[(size_t)per * i + 2 + w.m]))
       return TPFA_ECUDA;
     TmaInst& I = inst[i];
     I.g = batch->g[i];
@@ -597,7 +615,8 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
   if (blocks > 0x7fffffff) return TPFA_OK;
   if (cudaMalloc(&w.amaps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
       cudaMalloc(&w.ainst, sizeof(TmaInst) * N) != cudaSuccess ||
-      cudaMalloc(&w.apart, sizeof(double) * blocks) != cudaSuccess) {
+      cudaMalloc(&w.apart, sizeof(double) * blocks * (3 + 2 * kApplyMaxDirs)) != cudaSuccess ||
+      cudaMalloc(&w.dots, sizeof(double) * kApplyDotsStride * N) != cudaSuccess) {
     cudaGetLastError();
     return TPFA_ENOMEM;
   }
@@ -610,6 +629,7 @@ int setup_apply_tma(const tpfa_batch* batch, const float* coef, BWork& w) {
     return TPFA_ECUDA;
   w.ainst_all = inst;
   w.nainst = N;
+  w.own0 = 2 + w.m;
   w.tma = true;
   w.ablocks = blocks;
   return TPFA_OK;
@@ -971,29 +991,47 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
       if (rc) break;
       bool first = true;
       while (running && rc == TPFA_OK) {
-        bool any_blend = false;
-        for (int i = 0; i < N; ++i) any_blend = any_blend || blend[i];
+        bool any_blend = false, any_plain = false;  // instances with / without the network
+        for (int i = 0; i < N; ++i) {
+          any_blend = any_blend || blend[i];
+          any_plain = any_plain || ((w.hflags[i] & kAct) && !blend[i]);
+        }
+        Dirs qd, pd;
+        int qmap[kMaxDirs];
+        for (int j = 0; j < gstored; ++j) {
+          const size_t slot = (size_t)((head - 1 - j + w.m) % w.m);
+          qd.v[j] = w.Q + slot * w.stride;
+          pd.v[j] = w.P + slot * w.stride;
+          qmap[j] = (int)slot;
+        }
+        // the TMA-staged operator A u also forms the dot products of the blend
+        // instances (A u itself is not stored; r, M^-1 and the q_j come in
+        // through its producer); the dots pass then covers the others only
+        const bool fused = any_blend && w.tma && gstored <= kApplyMaxDirs;
         if (any_blend) {
           rc = batch_network_term(bn, w);
           if (rc) break;
-          if (!batch_apply(batch, w, cf4, 0, w.au, w.uau, kAct | kNet)) {
+          const bool ok =
+              fused ? launch_apply_dots_tma_batch(w.ainst, w.nainst, w.ablocks, 0, w.flags,
+                                                  kAct | kNet, w.own0, qmap, gstored, w.uau,
+                                                  w.dots, w.apart, batch->counters,
+                                                  s) == cudaSuccess
+                    : batch_apply(batch, w, cf4, 0, w.au, w.uau, kAct | kNet);
+          if (!ok) {
             rc = TPFA_ECUDA;
             break;
           }
           ++w.launches;
         }
-        Dirs qd, pd;
-        for (int j = 0; j < gstored; ++j) {
-          const size_t slot = (size_t)((head - 1 - j + w.m) % w.m);
-          qd.v[j] = w.Q + slot * w.stride;
-          pd.v[j] = w.P + slot * w.stride;
-        }
         float* p = w.P + (size_t)head * w.stride;
         float* q = w.Q + (size_t)head * w.stride;
-        launch_bdots(gstored, w.nach, s, w.achunks_dev, w.flags, w.r, w.dinv, w.z, w.au, qd,
-                     w.vec4, w.part);
+        if (!fused || any_plain) {
+          launch_bdots(gstored, w.nach, s, w.achunks_dev, w.flags, w.r, w.dinv, w.z, w.au, qd,
+                       w.vec4, w.part, fused ? 1 : 0);
+          ++w.launches;
+        }
         bfinish_dots_kernel<<<N, kT, 0, s>>>(w.cfirst_dev, w.ccount_dev, w.flags, w.part, gstored,
-                                             w.uau, w.sc, head, w.m);
+                                             w.uau, w.sc, head, w.m, fused ? w.dots : nullptr);
         launch_bdir(gstored, w.nach, s, w.achunks_dev, w.flags, w.sc, w.r, w.dinv, w.z, pd, p,
                     w.vec4, w.part);
         if (!batch_apply(batch, w, cf4, 1 + head, q, w.pq, kAct)) {
@@ -1006,7 +1044,7 @@ extern "C" int fcg_solve_batch(tpfa_batch* batch, tpfa_unet* const* nets, int n_
                                              w.vec4, w.part);
         bfinish_rr_kernel<<<N, kT, 0, s>>>(w.cfirst_dev, w.ccount_dev, w.flags, w.part, w.sc,
                                            w.hist, pending);
-        w.launches += 7;
+        w.launches += 6;
         ++pending;
         ++giters;
         head = (head + 1) % w.m;

@@ -391,22 +391,27 @@ cg_sweep_tma_kernel(const __grid_constant__ TmaArgs a) {
 // so both give bit-identical q; only the grouping of p'q differs.
 constexpr int kPX = 40;  // p box width: X0-4 .. X0+35
 
-template <int W, int VY, bool B16>
+// NE: further FP32 fields staged for the own cells only ([TY rows][32 floats]
+// from (X0, Y0) per own plane), for the fused dot products
+template <int W, int VY, bool B16, int NE = 0>
 struct ApplyLayout {
   using RC = Rec<B16, false>;
   static constexpr int TY = W * VY;
   static constexpr int kPBytes = (TY + 2) * kPX * 4;
   static constexpr int kRecBytes = (TY + 1) * RC::kX * RC::kBytes;
+  static constexpr int kOwnBytes = TY * 32 * 4;  // one own-cell field
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
   static constexpr int kP = 0;
   static constexpr int kC = al(kPBytes);
-  static constexpr int kStage = kC + al(kRecBytes);
-  static constexpr uint32_t kTx = kPBytes + kRecBytes;  // bytes per stage
+  static constexpr int kE = kC + al(kRecBytes);
+  static constexpr int kStage = kE + NE * kOwnBytes;
+  static constexpr uint32_t kTx = kPBytes + kRecBytes;  // bytes per stage (halo planes)
+  static constexpr uint32_t kTxOwn = kTx + NE * kOwnBytes;  // own planes
 };
 
-template <int W, int VY, int S, bool B16>
+template <int W, int VY, int S, bool B16, int NE = 0>
 constexpr int apply_smem_bytes() {
-  return S * ApplyLayout<W, VY, B16>::kStage + 2 * S * 8 + 128;
+  return S * ApplyLayout<W, VY, B16, NE>::kStage + 2 * S * 8 + 128;
 }
 
 struct ApplyArgs {
@@ -427,13 +432,25 @@ struct ApplyArgs {
   double* pAp;  // one double (per instance when batched), or null
   double* partials;
   unsigned int* counter;
+  // Flexible-CG dot products fused into the batched operator (DM >= 0 in the
+  // kernel): with u the input, q = A u (not stored) and w = M^-1 r, per
+  // instance u'q, u'r, q'w, w'q_j and u'q_j (j < DM) into
+  // dots[id * kApplyDotsStride + ...], u'q also into pAp[id].  r, M^-1 and
+  // the q_j are staged like p, own cells only, from the instance's maps
+  // own0 (r), own0 + 1 (M^-1) and own0 + 2 + qmap[j].
+  int own0;
+  int qmap[kApplyMaxDirs];
+  double* dots;
 };
 
-template <int W, int VY, int S, bool B16, bool BATCH>
+template <int W, int VY, int S, bool B16, bool BATCH, int DM = -1>
 __global__ void __launch_bounds__((W + 1) * 32)
 apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
   static_assert(!BATCH || !B16, "batched operator: FP32 records");
-  using LY = ApplyLayout<W, VY, B16>;
+  static_assert(DM < 0 || (BATCH && DM <= kApplyMaxDirs), "fused dots: batched, few directions");
+  constexpr int NE = DM < 0 ? 0 : 2 + DM;       // own-cell fields: r, M^-1, q_j
+  constexpr int NV = DM < 0 ? 1 : 3 + 2 * DM;   // reduced values
+  using LY = ApplyLayout<W, VY, B16, NE>;
   using RC = Rec<B16, false>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem =
@@ -446,7 +463,7 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
   int64_t lb = blockIdx.x, pstart = 0, pcount = gridDim.x, off = 0;
   int inst = 0;
   unsigned int* counter = a.counter;
-  const CUtensorMap *mp = &a.mp, *mc = &a.mc;
+  const CUtensorMap *mp = &a.mp, *mc = &a.mc, *mown = nullptr;
   if (BATCH) {
     int lo = 0, hi = a.ninst - 1;  // last instance whose first block <= blockIdx.x
     while (lo < hi) {
@@ -462,6 +479,7 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
     counter = a.counter + I.id;
     mc = I.maps;
     mp = I.maps + 1 + a.which;
+    mown = I.maps + a.own0;
   }
 
   const int warp = threadIdx.x >> 5;
@@ -484,7 +502,9 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
   }
   __syncthreads();
 
-  Acc acc = {0.f, 0.f};
+  Acc acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = {0.f, 0.f};
   bool fault = false;
 
   if (warp == W) {
@@ -498,11 +518,20 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
           break;
         }
         const int z = (int)(z0 - 1 + j);
+        const bool own = NE > 0 && j >= 1 && j <= L - 2;
         unsigned char* sb = smem + s * LY::kStage;
-        mbar_expect_tx(&full[s], LY::kTx);
+        mbar_expect_tx(&full[s], own ? LY::kTxOwn : LY::kTx);
         // x coordinates in 4-byte elements, multiples of 4 (16 bytes)
         tma_3d(sb + LY::kP, mp, &full[s], X0 - 4, Y0 - 1, z);
         tma_3d(sb + LY::kC, mc, &full[s], (RC::kBytes / 4) * (X0 - RC::kC0), Y0 - 1, z);
+        if (own) {
+          tma_3d(sb + LY::kE, mown, &full[s], X0, Y0, z);                        // r
+          tma_3d(sb + LY::kE + LY::kOwnBytes, mown + 1, &full[s], X0, Y0, z);    // M^-1
+#pragma unroll
+          for (int q = 0; q < (DM > 0 ? DM : 0); ++q)
+            tma_3d(sb + LY::kE + (2 + q) * LY::kOwnBytes, mown + 2 + a.qmap[q], &full[s], X0, Y0,
+                   z);
+        }
         issued = j + 1;
       }
       // every issued copy lands before the block exits
@@ -567,6 +596,9 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
       const unsigned char* sb = smem + (jc % S) * LY::kStage;
       float* oz = out + g.plane * z;
       float s1 = 0.f;
+      float sd[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sd[k] = 0.f;
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) {
         const int ri = (jw + jj + 1) * RC::kX + lane + RC::kC0;
@@ -583,14 +615,35 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
         const float q = stencil7(cf, txm, tym, Tzm[jj], pc, pxp, pxm, P0[jj + 2], P0[jj],
                                  Pp[jj + 1], Pm[jj]);
         if ((rowok >> jj) & 1u) {
-          oz[o0 + (unsigned)(jj * nxi)] = q;
-          s1 = fmaf(pc, q, s1);
+          if constexpr (DM < 0) {
+            oz[o0 + (unsigned)(jj * nxi)] = q;
+            s1 = fmaf(pc, q, s1);
+          } else {
+            // the dot products of the flexible-CG step at this cell (u = pc)
+            const float* se = reinterpret_cast<const float*>(sb + LY::kE) + (jw + jj) * 32 + lane;
+            const float rv = se[0];
+            const float wv = rv * se[LY::kOwnBytes / 4];
+            sd[0] = fmaf(pc, q, sd[0]);
+            sd[1] = fmaf(pc, rv, sd[1]);
+            sd[2] = fmaf(q, wv, sd[2]);
+#pragma unroll
+            for (int k = 0; k < (DM > 0 ? DM : 0); ++k) {
+              const float qv = se[(2 + k) * (LY::kOwnBytes / 4)];
+              sd[3 + k] = fmaf(wv, qv, sd[3 + k]);
+              sd[3 + DM + k] = fmaf(pc, qv, sd[3 + DM + k]);
+            }
+          }
         }
         Tzm[jj] = cf.z;
         Pm[jj] = pc;
       }
       release(jc);
-      kadd(acc, s1);
+      if constexpr (DM < 0) {
+        kadd(acc[0], s1);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) kadd(acc[k], sd[k]);
+      }
       zdone = z + 1;
 #pragma unroll
       for (int jj = 0; jj < VY; ++jj) H0[jj] = Hp[jj];
@@ -601,22 +654,32 @@ apply_tma_kernel(const __grid_constant__ ApplyArgs a) {
       release(L - 1);  // the last plane (z1) was only read
     } else {
       // a copy that never landed: the cells this warp did not write become
-      // NaN, and so does p'q, so that the failure cannot pass unnoticed
+      // NaN, and so do the dot products, so that the failure cannot pass
+      // unnoticed
       const float qnan = __int_as_float(0x7fc00000);
-      for (int64_t z = zdone; z < z1; ++z)
+      if (DM < 0)
+        for (int64_t z = zdone; z < z1; ++z)
 #pragma unroll
-        for (int jj = 0; jj < VY; ++jj)
-          if ((rowok >> jj) & 1u) out[g.plane * z + o0 + (unsigned)(jj * nxi)] = qnan;
-      kadd(acc, qnan);
+          for (int jj = 0; jj < VY; ++jj)
+            if ((rowok >> jj) & 1u) out[g.plane * z + o0 + (unsigned)(jj * nxi)] = qnan;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) kadd(acc[k], qnan);
     }
   }
 
   if (a.pAp != nullptr) {
-    double v[1] = {kval(acc)};
-    block_partial<1>(v, a.partials);
-    double tot[1];
-    if (last_block_range<1>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0)
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = kval(acc[k]);
+    block_partial<NV>(v, a.partials);
+    double tot[NV];
+    if (last_block_range<NV>(a.partials, counter, pstart, pcount, tot) && threadIdx.x == 0) {
       a.pAp[inst] = tot[0];
+      if constexpr (DM >= 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a.dots[(size_t)inst * kApplyDotsStride + k] = tot[k];
+      }
+    }
   }
 }
 
@@ -719,10 +782,10 @@ int apply_blocks_per_sm_t() {
   return nb;
 }
 
-template <bool B16, bool BATCH>
+template <bool B16, bool BATCH, int DM = -1>
 cudaError_t launch_apply_t(const ApplyArgs& a, int64_t nblocks, cudaStream_t s) {
-  constexpr int smem = apply_smem_bytes<4, 4, 4, B16>();
-  auto fn = apply_tma_kernel<4, 4, 4, B16, BATCH>;
+  constexpr int smem = apply_smem_bytes<4, 4, 4, B16, DM < 0 ? 0 : 2 + DM>();
+  auto fn = apply_tma_kernel<4, 4, 4, B16, BATCH, DM>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)nblocks, 5 * 32, smem, s>>>(a);
@@ -951,6 +1014,42 @@ cudaError_t launch_apply_tma_batch(const TmaInst* inst, int ninst, int64_t nbloc
   a.partials = partials;
   a.counter = counters;
   return launch_apply_t<false, true>(a, nblocks, s);
+}
+
+bool make_own_maps(const Grid& g, const TmaPlan& p, const float* const* in, int nin,
+                   CUtensorMap* out) {
+  bool ok = true;
+  for (int i = 0; i < nin && ok; ++i) ok = encode_f32(&out[i], in[i], g, 32, p.w * p.vy);
+  return ok;
+}
+
+cudaError_t launch_apply_dots_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks,
+                                        int which, const int* act, int need, int own0,
+                                        const int* qmap, int ndirs, double* uq, double* dots,
+                                        double* partials, unsigned int* counters,
+                                        cudaStream_t s) {
+  if (ndirs < 0 || ndirs > kApplyMaxDirs) return cudaErrorInvalidValue;
+  ApplyArgs a;
+  memset(&a, 0, sizeof(a));
+  a.inst = inst;
+  a.ninst = ninst;
+  a.which = which;
+  a.act = act;
+  a.need = need;
+  a.pAp = uq;
+  a.partials = partials;
+  a.counter = counters;
+  a.own0 = own0;
+  for (int j = 0; j < ndirs; ++j) a.qmap[j] = qmap[j];
+  a.dots = dots;
+  switch (ndirs) {
+    case 0: return launch_apply_t<false, true, 0>(a, nblocks, s);
+    case 1: return launch_apply_t<false, true, 1>(a, nblocks, s);
+    case 2: return launch_apply_t<false, true, 2>(a, nblocks, s);
+    case 3: return launch_apply_t<false, true, 3>(a, nblocks, s);
+    case 4: return launch_apply_t<false, true, 4>(a, nblocks, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_cg_sweep_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks, int tile,

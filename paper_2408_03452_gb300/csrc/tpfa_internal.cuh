@@ -129,6 +129,23 @@ cudaError_t launch_apply_tma(const Grid& g, const TmaPlan& p, const void* coef, 
 // out[1 + i] the FP32 input in[i] (nin inputs).
 bool make_apply_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* const* in,
                      int nin, CUtensorMap* out);
+// The batched operator fused with the flexible-CG dot products that read its
+// result (A u itself is not stored): for each instance with
+// (act[id] & need) == need, with u its input `which`, q = A u and w = M^-1 r:
+// u'q into uq[id] and, at dots + id * kApplyDotsStride, u'q, u'r, q'w, then
+// w'q_j and u'q_j (j < ndirs <= kApplyMaxDirs).  The instance's maps from
+// index own0 on are own-cell maps (make_own_maps) of r, M^-1 and the
+// direction slots; q_j is slot qmap[j].  partials: 3 + 2 ndirs doubles per
+// block.
+constexpr int kApplyMaxDirs = 4;
+constexpr int kApplyDotsStride = 3 + 2 * kApplyMaxDirs;
+bool make_own_maps(const Grid& g, const TmaPlan& p, const float* const* in, int nin,
+                   CUtensorMap* out);
+cudaError_t launch_apply_dots_tma_batch(const TmaInst* inst, int ninst, int64_t nblocks,
+                                        int which, const int* act, int need, int own0,
+                                        const int* qmap, int ndirs, double* uq, double* dots,
+                                        double* partials, unsigned int* counters,
+                                        cudaStream_t s);
 // Batched operator through the TMA-staged kernel: inst[k].maps as from
 // make_apply_maps, input `which`; the table may list any subset of the batch's
 // instances (inst[k].id, bstart consecutive through the table); only instances
