@@ -153,17 +153,24 @@ __global__ void dots_kernel(const float* __restrict__ r, const float* __restrict
 
 // c = (u'r - (Au)'w) / u'Au (0 without network, or when u'Au is not positive)
 // and beta_j = -(a_j + c b_j) / (p_j'q_j) for the M retained directions
+// fdots: the totals from the fused operator (u'Au, then s0, s1, a_j, b_j)
+// instead of the block partials
 __global__ void finish_dots_kernel(const double* __restrict__ part, int nb, int M, int net,
-                                   const double* __restrict__ uau, Scal* sc, int head, int m) {
+                                   const double* __restrict__ uau, Scal* sc, int head, int m,
+                                   const double* __restrict__ fdots) {
   __shared__ double tot[2 + 2 * kMaxDirs];
   const int K = 2 + 2 * M;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int k = warp; k < K; k += nw) {
-    double t = 0.0;
-    for (int b = lane; b < nb; b += 32) t += part[(size_t)b * K + k];
+  if (fdots != nullptr) {
+    if (threadIdx.x < K) tot[threadIdx.x] = fdots[1 + threadIdx.x];
+  } else {
+    for (int k = warp; k < K; k += nw) {
+      double t = 0.0;
+      for (int b = lane; b < nb; b += 32) t += part[(size_t)b * K + k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) tot[k] = t;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) tot[k] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -412,6 +419,17 @@ struct Work {
   float* ul[kMaxLevels + 1] = {};
   float* lnkc = nullptr;
   int64_t launches = 0;
+  // the TMA-staged operator fused with the blend's dot products (a batch of
+  // one): maps {coefficients, z, P slots, r, M^-1, Q slots}
+  bool fused = false;
+  CUtensorMap* fmaps = nullptr;
+  tpfa::TmaInst* finst = nullptr;
+  int* fact = nullptr;
+  unsigned int* fcnt = nullptr;
+  double* fpart = nullptr;
+  double* fdots = nullptr;
+  int64_t fblocks = 0;
+  int own0 = 0;
 
   // distance between retained directions: n rounded up to 4 floats, so that
   // every slot starts on a 16-byte boundary (the vector kernels read float4)
@@ -457,6 +475,12 @@ struct Work {
     cudaFree(sc);
     cudaFree(hist);
     cudaFreeHost(hhist);
+    cudaFree(fmaps);
+    cudaFree(finst);
+    cudaFree(fact);
+    cudaFree(fcnt);
+    cudaFree(fpart);
+    cudaFree(fdots);
   }
   // sums of the three per-block partials, in block order
   bool fetch(double* out3) {
@@ -482,8 +506,10 @@ struct Result {
 
 enum PrecMode { kIdentity = 0, kJacobi = 1, kBlend = 2 };
 
-// the network term u of the blend (into w.z) and A u (into w.au, u'Au into w.uau)
-int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w) {
+// the network term u of the blend (into w.z) and, unless the fused operator
+// takes it, A u (into w.au, u'Au into w.uau)
+int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, Work& w,
+                 bool with_apply) {
   int rc;
   if (w.levels > 0) {
     const int L = w.levels;
@@ -499,9 +525,64 @@ int network_term(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* ln
     if (rc) return rc;
     w.launches += 15;
   }
+  if (!with_apply) return TPFA_OK;
   rc = tpfa_apply(c, coef, w.z, w.au, w.uau, w.s);
   ++w.launches;
   return rc;
+}
+
+// Set up the fused operator when tpfa_apply would take the TMA-staged kernel.
+int setup_fused(const tpfa_ctx* c, const float* coef, Work& w) {
+  using namespace tpfa;
+  TmaPlan p;
+  Grid g;
+  if (!ctx_apply_tma_plan(c, &p, &g) || reinterpret_cast<uintptr_t>(coef) % 16 != 0 ||
+      w.m > kMaxDirs)
+    return TPFA_OK;
+  const int per = 4 + 2 * w.m;
+  std::vector<CUtensorMap> maps(per);
+  std::vector<const float*> in(1 + w.m), own(2 + w.m);
+  in[0] = w.z;
+  own[0] = w.r;
+  own[1] = w.dinv;
+  for (int k = 0; k < w.m; ++k) {
+    in[1 + k] = w.P + (size_t)k * w.slot_stride();
+    own[2 + k] = w.Q + (size_t)k * w.slot_stride();
+  }
+  if (!make_apply_maps(g, p, coef, in.data(), 1 + w.m, maps.data()) ||
+      !make_own_maps(g, p, own.data(), 2 + w.m, maps.data() + 2 + w.m))
+    return TPFA_OK;  // the unfused passes
+  TmaInst I{};
+  I.g = g;
+  I.zc = p.zc;
+  I.nbx = (int)p.nbx;
+  I.nby = (int)p.nby;
+  I.id = 0;
+  I.off = 0;
+  I.bstart = 0;
+  I.nblocks = p.nblocks;
+  const int one = 1;
+  if (cudaMalloc(&w.fmaps, sizeof(CUtensorMap) * per) != cudaSuccess ||
+      cudaMalloc(&w.finst, sizeof(TmaInst)) != cudaSuccess ||
+      cudaMalloc(&w.fact, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&w.fcnt, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&w.fpart, sizeof(double) * p.nblocks * (3 + 2 * kApplyMaxDirs)) != cudaSuccess ||
+      cudaMalloc(&w.fdots, sizeof(double) * kApplyDotsStride) != cudaSuccess) {
+    cudaGetLastError();
+    return TPFA_ENOMEM;
+  }
+  I.maps = w.fmaps;
+  if (cudaMemcpyAsync(w.fmaps, maps.data(), sizeof(CUtensorMap) * per, cudaMemcpyHostToDevice,
+                      w.s) != cudaSuccess ||
+      cudaMemcpyAsync(w.finst, &I, sizeof(TmaInst), cudaMemcpyHostToDevice, w.s) != cudaSuccess ||
+      cudaMemcpyAsync(w.fact, &one, sizeof(int), cudaMemcpyHostToDevice, w.s) != cudaSuccess ||
+      cudaMemsetAsync(w.fcnt, 0, sizeof(unsigned int), w.s) != cudaSuccess ||
+      cudaStreamSynchronize(w.s) != cudaSuccess)
+    return TPFA_ECUDA;
+  w.fused = true;
+  w.fblocks = p.nblocks;
+  w.own0 = 2 + w.m;
+  return TPFA_OK;
 }
 
 // Inner FCG on A e = r (r, e already set, r'r = rr0).  All scalars stay on the
@@ -518,21 +599,35 @@ int fcg_inner(tpfa_ctx* c, tpfa_unet* net, const float* coef, const float* lnk, 
   if (cudaMemsetAsync(w.sc, 0, sizeof(Scal), w.s) != cudaSuccess) return TPFA_ECUDA;
   while (res->iters < maxit && rr > target * target * rr0) {
     const int jac = mode != kIdentity, with_net = mode == kBlend;
-    if (with_net) {
-      const int rc = network_term(c, net, coef, lnk, w);
-      if (rc) return rc;
-    }
     Dirs qd, pd;
+    int qmap[kMaxDirs];
     for (int j = 0; j < stored; ++j) {
       const size_t slot = (size_t)((head - 1 - j + m) % m);
       qd.v[j] = w.Q + slot * w.slot_stride();
       pd.v[j] = w.P + slot * w.slot_stride();
+      qmap[j] = (int)slot;
     }
-    if (stored > 0 || with_net) {
+    // with the network, the TMA-staged operator A u also forms the dot
+    // products (A u itself is not stored)
+    const bool fused = with_net && w.fused && stored <= tpfa::kApplyMaxDirs;
+    if (with_net) {
+      int rc = network_term(c, net, coef, lnk, w, !fused);
+      if (rc) return rc;
+      if (fused) {
+        if (launch_apply_dots_tma_batch(w.finst, 1, w.fblocks, 0, w.fact, 1, w.own0, qmap, stored,
+                                        w.uau, w.fdots, w.fpart, w.fcnt, w.s) != cudaSuccess)
+          return TPFA_ECUDA;
+        ++w.launches;
+      }
+    }
+    if (fused) {
+      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, stored, 1, w.uau, w.sc, head, m, w.fdots);
+    } else if (stored > 0 || with_net) {
       launch_dots(stored, w.nb, w.s, w.r, w.dinv, w.z, w.au, qd, jac, with_net, w.n, w.part);
-      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, stored, with_net, w.uau, w.sc, head, m);
+      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, w.nb, stored, with_net, w.uau, w.sc, head, m,
+                                            nullptr);
     } else {
-      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, 0, 0, 0, w.uau, w.sc, head, m);
+      finish_dots_kernel<<<1, kT, 0, w.s>>>(w.part, 0, 0, 0, w.uau, w.sc, head, m, nullptr);
     }
     float* p = w.P + (size_t)head * w.slot_stride();
     float* q = w.Q + (size_t)head * w.slot_stride();
@@ -692,6 +787,7 @@ extern "C" int fcg_solve(tpfa_ctx* c, tpfa_unet* net, const float* coef, const d
         ok = cudaGetLastError() == cudaSuccess;
       }
     }
+    if (ok && net != nullptr) ok = setup_fused(c, coef, w) == TPFA_OK;
     if (!ok) {
       cudaGetLastError();
       rc = TPFA_ENOMEM;

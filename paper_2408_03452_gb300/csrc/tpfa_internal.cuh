@@ -222,6 +222,7 @@ cudaError_t launch_apply_batch(const BatchInst* inst, int ninst, int64_t nblocks
 int64_t ctx_cells(const tpfa_ctx* c);
 void ctx_dims(const tpfa_ctx* c, int64_t* d3);
 double ctx_option(const tpfa_ctx* c, int option);
+bool ctx_apply_tma_plan(const tpfa_ctx* c, TmaPlan* p, Grid* g);
 bool dev_ok(const void* p, size_t bytes, size_t align, int device);
 bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device);
 int elem_blocks(const Grid& g, int num_sms);
