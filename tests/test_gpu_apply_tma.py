@@ -174,3 +174,29 @@ def test_batched_fcg_with_tma_and_cp_async_operators(tp, oracle_mod):
         bc.close()
     for a, b_ in zip(res[0], res[1]):
         assert abs(a - b_) <= 0.05 * b_ + 3, res
+
+
+def test_batched_fcg_fused_dots_with_networks(tp, oracle_mod):
+    """With networks the TMA-staged operator A u also forms the step's dot
+    products (A u not stored); the cp.async sweep option takes the separate
+    operator and dots passes.  Both reach the oracle's FP64 tolerance, with
+    iteration counts within the spread that rounding gives a nonlinear
+    preconditioner."""
+    from test_gpu_fcg_batch import _mixed, _nets, _oracle_rel, _parts, _setup
+    O = oracle_mod
+    insts, net_of = _mixed()
+    res = {}
+    for sweep in (0, 1):
+        bc, coef, coef64, b, lnk = _setup(tp, insts)
+        bc.set_option("sweep", sweep)
+        bc.set_option("fcg_m", 2)
+        nets = _nets(tp, [((4, 4, 4), 2), ((16, 8, 8), 1)])
+        x, per, total = bc.fcg_solve(coef, coef64, b, nets=nets, net_of=net_of, lnk=lnk,
+                                     tol=1e-8, maxit=20000)
+        assert total["code"] == tp.OK, (sweep, total, per)
+        for i, xi in enumerate(_parts(bc, x)):
+            assert _oracle_rel(O, insts[i], xi) <= 1e-8 * 1.01, (sweep, i, per[i])
+        res[sweep] = [p["iters"] for p in per]
+        bc.close()
+    for a, b_ in zip(res[0], res[1]):
+        assert abs(a - b_) <= 0.3 * b_ + 5, res
