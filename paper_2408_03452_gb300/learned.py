@@ -324,7 +324,8 @@ def ensemble_problem(P, seed: int = 0, n_inst: int = 96, levels: int = 2):
 
 
 def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m: int = 2,
-                      tol: float = 1e-8, maxit: int = 200000, log=None) -> dict:
+                      tol: float = 1e-8, maxit: int = 200000, log=None,
+                      solvers=("unet_fcg_batched", "jacobi_pcg_batched", "plain_cg_batched")) -> dict:
     """The batched ensemble of synth.ensemble (uneven sizes, sigma ~ U(0.5, 2.5),
     Dirichlet ends on a random axis) solved to tol three ways on one batch
     object: flexible CG with the Jacobi-blended U-Net (one network per size
@@ -354,6 +355,8 @@ def evaluate_ensemble(P, seed: int = 0, n_inst: int = 96, levels: int = 2, fcg_m
            "levels_per_size": lv}
     for name, fn in (("unet_fcg_batched", fcg), ("jacobi_pcg_batched", cg(1)),
                      ("plain_cg_batched", cg(0))):
+        if name not in solvers:
+            continue
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
