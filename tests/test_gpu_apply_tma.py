@@ -200,3 +200,22 @@ def test_batched_fcg_fused_dots_with_networks(tp, oracle_mod):
         bc.close()
     for a, b_ in zip(res[0], res[1]):
         assert abs(a - b_) <= 0.3 * b_ + 5, res
+
+
+@pytest.mark.parametrize("m", [3, 4, 5])
+def test_batched_fcg_fused_dots_retained_directions(tp, oracle_mod, m):
+    """The fused operator carries up to four retained directions (one kernel
+    variant per count); with five the separate dots pass takes over.  Every
+    instance reaches the oracle's FP64 tolerance either way."""
+    from test_gpu_fcg_batch import _mixed, _nets, _oracle_rel, _parts, _setup
+    O = oracle_mod
+    insts, net_of = _mixed()
+    bc, coef, coef64, b, lnk = _setup(tp, insts)
+    bc.set_option("fcg_m", m)
+    nets = _nets(tp, [((4, 4, 4), 2), ((16, 8, 8), 1)])
+    x, per, total = bc.fcg_solve(coef, coef64, b, nets=nets, net_of=net_of, lnk=lnk, tol=1e-8,
+                                 maxit=20000)
+    assert total["code"] == tp.OK, (total, per)
+    for i, xi in enumerate(_parts(bc, x)):
+        assert _oracle_rel(O, insts[i], xi) <= 1e-8 * 1.01, (i, per[i])
+    bc.close()
