@@ -346,11 +346,12 @@ double ctx_option(const tpfa_ctx* c, int option) {
 }
 
 // The TMA-staged operator's plan for tpfa_apply's arguments (coef, p 16-byte
-// aligned), or false when tpfa_apply would take the cp.async kernel.
-bool ctx_apply_tma_plan(const tpfa_ctx* c, TmaPlan* p, Grid* g) {
+// aligned; dots: the variant fused with the flexible-CG dot products), or
+// false when tpfa_apply would take the cp.async kernel.
+bool ctx_apply_tma_plan(const tpfa_ctx* c, TmaPlan* p, Grid* g, bool dots) {
   if (!use_tma_apply(c, false)) return false;
   *g = c->g;
-  *p = plan_tma(c->g, 0, c->zc, c->num_sms, false, false, true);
+  *p = plan_tma(c->g, 0, c->zc, c->num_sms, false, false, true, dots);
   return true;
 }
 }  // namespace tpfa

@@ -536,7 +536,7 @@ int setup_fused(const tpfa_ctx* c, const float* coef, Work& w) {
   using namespace tpfa;
   TmaPlan p;
   Grid g;
-  if (!ctx_apply_tma_plan(c, &p, &g) || reinterpret_cast<uintptr_t>(coef) % 16 != 0 ||
+  if (!ctx_apply_tma_plan(c, &p, &g, true) || reinterpret_cast<uintptr_t>(coef) % 16 != 0 ||
       w.m > kMaxDirs)
     return TPFA_OK;
   const int per = 4 + 2 * w.m;

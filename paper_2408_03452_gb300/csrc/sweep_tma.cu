@@ -782,10 +782,29 @@ int apply_blocks_per_sm_t() {
   return nb;
 }
 
+// stages of the operator's ring: 4; 3 with the fused dot products, whose
+// stages also hold the own-cell boxes (three blocks per SM instead of two)
+template <int DM>
+constexpr int apply_stages() {
+  return DM < 0 ? 4 : 3;
+}
+
+int apply_dots_blocks_per_sm_t() {
+  constexpr int smem = apply_smem_bytes<4, 4, apply_stages<2>(), false, 4>();
+  auto fn = apply_tma_kernel<4, 4, apply_stages<2>(), false, true, 2>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 5 * 32, smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
 template <bool B16, bool BATCH, int DM = -1>
 cudaError_t launch_apply_t(const ApplyArgs& a, int64_t nblocks, cudaStream_t s) {
-  constexpr int smem = apply_smem_bytes<4, 4, 4, B16, DM < 0 ? 0 : 2 + DM>();
-  auto fn = apply_tma_kernel<4, 4, 4, B16, BATCH, DM>;
+  constexpr int S = apply_stages<DM>();
+  constexpr int smem = apply_smem_bytes<4, 4, S, B16, DM < 0 ? 0 : 2 + DM>();
+  auto fn = apply_tma_kernel<4, 4, S, B16, BATCH, DM>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)nblocks, 5 * 32, smem, s>>>(a);
@@ -836,10 +855,11 @@ bool tma_sweep_ok(const Grid& g, bool b16, bool jac) {
 int tma_tile_count() { return kNumTmaTiles; }
 
 TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac,
-                 bool apply) {
+                 bool apply, bool dots) {
   TmaPlan p{};
   if (tile < 0 || tile >= kNumTmaTiles || b16 || jac || apply) tile = 0;
   if (apply) jac = false;
+  p.dots = apply && dots && !b16;
   const TileShape ts = kTmaTiles[tile];
   p.tile = tile;
   p.b16 = b16;
@@ -886,19 +906,21 @@ TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, boo
 int tma_blocks_per_sm(const TmaPlan& p) {
   // host-side occupancy queries cost microseconds; the answer is fixed per
   // device and kernel, so it is kept (index: device, kernel variant)
-  constexpr int kDevs = 64, kVariants = 3 + kNumTmaTiles + 2;
+  constexpr int kDevs = 64, kVariants = 3 + kNumTmaTiles + 3;
   static int memo[kDevs][kVariants] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     dev = -1;
   }
-  const int var = p.apply ? 3 + kNumTmaTiles + (p.b16 ? 1 : 0)
+  const int var = p.dots ? 3 + kNumTmaTiles + 2
+                  : p.apply ? 3 + kNumTmaTiles + (p.b16 ? 1 : 0)
                   : (p.b16 && p.jac) ? 0 : p.b16 ? 1 : p.jac ? 2 : 3 + p.tile;
   if (dev >= 0 && dev < kDevs && var >= 0 && var < kVariants && memo[dev][var] > 0)
     return memo[dev][var];
   int nb = 0;
-  if (p.apply) nb = p.b16 ? apply_blocks_per_sm_t<true>() : apply_blocks_per_sm_t<false>();
+  if (p.dots) nb = apply_dots_blocks_per_sm_t();
+  else if (p.apply) nb = p.b16 ? apply_blocks_per_sm_t<true>() : apply_blocks_per_sm_t<false>();
   else if (p.b16 && p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, true, true>();
   else if (p.b16) nb = tma_blocks_per_sm_t<4, 4, 4, true, false>();
   else if (p.jac) nb = tma_blocks_per_sm_t<4, 4, 4, false, true>();

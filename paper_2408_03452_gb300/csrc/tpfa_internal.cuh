@@ -80,6 +80,7 @@ struct TmaPlan {
   int tile;    // index of the (w, vy, stages) choice
   bool b16, jac;
   bool apply;  // the operator application q = A p (tile 0), not a CG sweep
+  bool dots;   // ... fused with the flexible-CG dot products (its own ring depth)
   int w, vy, stages, zc;
   int64_t nbx, nby, nbz, nblocks;
 };
@@ -93,7 +94,7 @@ struct TmaMaps {
 bool tma_sweep_ok(const Grid& g, bool b16, bool jac);
 int tma_tile_count();
 TmaPlan plan_tma(const Grid& g, int tile, int zc_opt, int num_sms, bool b16, bool jac,
-                 bool apply = false);
+                 bool apply = false, bool dots = false);
 int tma_blocks_per_sm(const TmaPlan& p);
 bool make_tma_maps(const Grid& g, const TmaPlan& p, const void* coef, const float* dinv,
                    const CgVecs& v, TmaMaps* m);
@@ -222,7 +223,7 @@ cudaError_t launch_apply_batch(const BatchInst* inst, int ninst, int64_t nblocks
 int64_t ctx_cells(const tpfa_ctx* c);
 void ctx_dims(const tpfa_ctx* c, int64_t* d3);
 double ctx_option(const tpfa_ctx* c, int option);
-bool ctx_apply_tma_plan(const tpfa_ctx* c, TmaPlan* p, Grid* g);
+bool ctx_apply_tma_plan(const tpfa_ctx* c, TmaPlan* p, Grid* g, bool dots = false);
 bool dev_ok(const void* p, size_t bytes, size_t align, int device);
 bool opt_dev_ok(const void* p, size_t bytes, size_t align, int device);
 int elem_blocks(const Grid& g, int num_sms);
